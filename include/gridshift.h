@@ -1,0 +1,159 @@
+/*
+ * gridshift.h -- C ABI of the GB300 (sm_103a) GridShift mode-seeking library.
+ *
+ * GridShift (Kumar et al., "GridShift: A Faster Mode-seeking Algorithm for
+ * Image Segmentation and Object Tracking", arXiv 2206.02200) clusters n points
+ * of dimension d by (Sec. 2.1, Algorithm 1):
+ *   i)   binning every point into the grid cell floor(x / h) and keeping, per
+ *        active cell, its resident count and the sum of its residents;
+ *   ii)  moving every active cell to the count-weighted mean over its 3^d
+ *        neighbouring cells (Eq. 1-2, applied in the parallel form of Eq. 6);
+ *   iii) re-keying each moved cell by floor(centroid / h);
+ *   iv)  merging the cells that share a key, adding counts and count-weighted
+ *        centroids (Eq. 3-4);
+ *   v)   stopping when no active cell has another active cell among its 3^d
+ *        neighbours (Sec. 2.1 v, Theorem 2), or after max_iter updates;
+ * and returns, per point, the cluster (final cell) it belongs to, and per
+ * cluster its mode (final centroid).
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer named "device" must point to memory of the CUDA device
+ *     that is current on the calling thread; "host" pointers are plain host
+ *     memory.  The caller owns all input and output buffers; a gs_ctx owns its
+ *     device workspace and reuses or grows it between calls.
+ *   - Points are row-major n x d (point i, coordinate a at [i * d + a]) in
+ *     float64 (GS_IN_F64) or float32 (GS_IN_F32).  float32 inputs are widened
+ *     to float64 exactly.
+ *   - All work is issued on the stream set by gs_set_stream (default: the
+ *     legacy default stream); gs_fit and gs_fit_batched return after it has
+ *     finished (they read the cluster count back to the host).
+ *   - Labels are 0 .. k-1, numbered by ascending lexicographic order of the
+ *     final integer cell key (axis 0 most significant); modes are float64,
+ *     row-major k x d, in label order.
+ *   - No C++ exception crosses this boundary.  A ctx is not thread-safe: use
+ *     one per host thread.  On any status other than GS_OK the contents of
+ *     the output buffers are unspecified, except where stated.
+ *
+ * Arithmetic of the GS_FP64 precision: every sum the method forms (cell sums
+ * in i) and iv), neighbourhood sums in ii)) is computed exactly in integer
+ * fixed point and rounded once to the nearest float64 (ties to even); the
+ * centroid of ii) is the exact neighbourhood sum divided by the neighbourhood
+ * count, rounded once; floor(.) is taken of the exact quotient.  The result
+ * therefore does not depend on the order of the points or on thread
+ * scheduling.  The fixed-point window of coordinate a spans
+ * 2^(E_a - 126) .. 2^E_a with n * max_i |x_ia| < 2^E_a; a value with nonzero
+ * bits below that window is truncated and counted in gs_fit_info.inexact.
+ */
+#ifndef GRIDSHIFT_H
+#define GRIDSHIFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_E_INVALID = 1,  /* bad argument: null pointer, d out of 1..8, h not > 0, NaN/Inf input, ... */
+  GS_E_NOMEM = 2,    /* a device or pinned host allocation failed */
+  GS_E_KEYRANGE = 3, /* the integer cell keys do not fit the 63-bit packed key, or a
+                        coordinate's key range exceeds 2^22 cells */
+  GS_E_CAPACITY = 4, /* modes_cap < k: *k_out is set and labels are valid */
+  GS_E_CUDA = 5,     /* a CUDA runtime call failed; see gs_get_last_error */
+  GS_E_INTERNAL = 6  /* a device-side bound (hash probe limit, table overflow) was hit */
+} gs_status;
+
+typedef enum {
+  GS_FP64 = 0,       /* exact sums rounded once to float64 (see the header comment) */
+  GS_FP32_MIXED = 1  /* reserved: float32 compensated sums with float64 face re-checks */
+} gs_precision;
+
+typedef enum { GS_IN_F64 = 0, GS_IN_F32 = 1 } gs_dtype;
+
+typedef struct gs_ctx gs_ctx; /* opaque; owns the device workspace */
+
+typedef struct {
+  int32_t iterations;  /* update steps applied (ii-iv), 0 .. max_iter */
+  int32_t converged;   /* 1 if stopped by the criterion of Sec. 2.1 v (no cell has a neighbour) */
+  int64_t m0;          /* active cells after binning (i) */
+  int64_t k;           /* active cells at exit = number of clusters */
+  int64_t inexact;     /* values truncated by the fixed-point window (0 in normal use) */
+  int64_t cell_iters;  /* sum over applied updates of the active cells updated */
+  int64_t launches;    /* CUDA kernels the call launched */
+} gs_fit_info;
+
+/* Launch groups of one call, for gs_get_phase_times. */
+typedef enum {
+  GS_PHASE_RANGE = 0,   /* key range and finiteness of the input (step i, set-up) */
+  GS_PHASE_BIN = 1,     /* binning: cell key, count and exact sum per cell (step i) */
+  GS_PHASE_CELLS0 = 2,  /* list and lookup table of the initial cells (step i) */
+  GS_PHASE_GATHER = 3,  /* neighbourhood means and new keys, all iterations (steps ii, iii, v) */
+  GS_PHASE_MERGE = 4,   /* merging cells that share a key, all iterations (step iv) */
+  GS_PHASE_LABELS = 5,  /* final cell of every point, label numbering, modes */
+  GS_NPHASES = 6
+} gs_phase;
+
+typedef struct {
+  double ms[GS_NPHASES];    /* device time of each phase, summed over its launch groups */
+  int32_t count[GS_NPHASES]; /* launch groups timed in each phase */
+} gs_phase_times;
+
+/* Creates a context for d-dimensional points, cell side (bandwidth) h and at
+ * most max_iter update steps (Sec. 2.1; h is the cell side of step i).
+ * 1 <= d <= 8, h finite and > 0, max_iter >= 0.  Allocates no device memory
+ * yet.  *out receives the context (NULL on error).  Returns GS_OK,
+ * GS_E_INVALID or GS_E_NOMEM. */
+gs_status gs_create(int d, double h, int max_iter, gs_ctx** out);
+
+/* Selects the arithmetic (see gs_precision).  Only GS_FP64 is implemented;
+ * other values return GS_E_INVALID and leave the setting unchanged. */
+gs_status gs_set_precision(gs_ctx* ctx, gs_precision p);
+
+/* Sets the CUDA stream (a cudaStream_t passed as void*, e.g.
+ * torch.cuda.current_stream().cuda_stream) on which every later call issues
+ * its work.  NULL selects the legacy default stream. */
+gs_status gs_set_stream(gs_ctx* ctx, void* cuda_stream);
+
+/* Runs GridShift (Sec. 2.1 steps i-v, Algorithm 1, Eq. 1-4 with the parallel
+ * update of Eq. 6) on one point set.
+ *   points     device, n x d row-major, dtype as given
+ *   n          number of points, 0 <= n < 2^31
+ *   labels     device int32[n]: cluster of every point (output)
+ *   modes      device float64[modes_cap x d]: final centroid of every cluster
+ *              (output; may be NULL when modes_cap == 0)
+ *   modes_cap  rows available in modes
+ *   k_out      host: number of clusters k (output; required)
+ *   info       host: statistics (output; may be NULL)
+ * n == 0 returns GS_OK with k = 0.  If k > modes_cap, returns GS_E_CAPACITY
+ * with *k_out = k and labels filled; call again with a larger buffer. */
+gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int32_t* labels,
+                 double* modes, int64_t modes_cap, int64_t* k_out, gs_fit_info* info);
+
+/* Turns per-phase device timing of later gs_fit calls on (enable != 0) or
+ * off.  When on, each call records CUDA events on its stream around each
+ * launch group and reads their elapsed times after its final synchronisation;
+ * the result is available from gs_get_phase_times.  Off by default.  This is
+ * instrumentation, not a step of the paper's method.  Returns GS_OK or
+ * GS_E_INVALID (NULL ctx). */
+gs_status gs_set_timing(gs_ctx* ctx, int enable);
+
+/* Copies the per-phase times of the last gs_fit call of this context (all
+ * zero if timing was off) into *out (host).  Returns GS_OK or GS_E_INVALID. */
+gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
+
+/* Copies a description of the last error of this context (NUL-terminated,
+ * truncated to len bytes) into buf.  Returns GS_OK or GS_E_INVALID. */
+gs_status gs_get_last_error(gs_ctx* ctx, char* buf, size_t len);
+
+/* Static, human-readable name of a status code. */
+const char* gs_status_string(gs_status s);
+
+/* Releases the context and its device workspace.  NULL is ignored. */
+void gs_destroy(gs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIDSHIFT_H */

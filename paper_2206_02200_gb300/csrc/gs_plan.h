@@ -1,0 +1,48 @@
+// gs_plan.h -- per-call parameters shared by the host driver and the kernels
+// (plain C++ structs, passed to kernels by value).
+#pragma once
+
+#include <cstdint>
+
+namespace gs {
+
+constexpr int kMaxD = 8;
+
+// Error bits written to DevFlags::err.
+constexpr uint32_t kErrTableFull = 1u;  // a hash table ran out of free slots
+constexpr uint32_t kErrOverflow = 2u;   // more cells than the cell arrays hold
+constexpr uint32_t kErrWindow = 4u;     // a value above the fixed-point window
+
+// How integer cell keys (Sec. 2.1 i: floor(x / h) per coordinate) are packed
+// into one 64-bit word, and how sums are held in fixed point.
+struct Plan {
+  int d;
+  int nprobe;               // 3^d neighbour offsets v in {-1,0,1}^d (Eq. 1)
+  int center;               // index of v = 0 among them
+  int off[kMaxD];           // bit offset of the field of axis a (axis 0 most significant)
+  int span[kMaxD];          // kmax_a - kmin_a + 1 cells along axis a
+  int thr_off[kMaxD];       // start of axis a's face table in the threshold array
+  int L[kMaxD];             // fixed-point unit 2^L of axis a
+  int64_t kmin[kMaxD];      // smallest key of axis a
+};
+
+// Device-resident state of one update step t (Sec. 2.1 ii-iv).
+struct IterState {
+  uint32_t m;       // active cells at level t
+  uint32_t mask;    // capacity mask of the lookup table of level t
+  uint32_t has_nb;  // 1 if some cell of level t has an active neighbour (v != 0)
+  uint32_t base;    // first node of level t in the forest of merges
+};
+
+// Global device flags and counters of a call.
+struct DevFlags {
+  uint32_t err;                 // kErr* bits
+  uint32_t m0;                  // cells created by binning
+  unsigned long long inexact;   // values truncated by the fixed-point window
+  unsigned long long bad;       // non-finite input coordinates
+  long long min_ord[kMaxD];     // order code of min_i x_ia
+  long long max_ord[kMaxD];     // order code of max_i x_ia
+  unsigned long long maxabs[kMaxD];  // bits of max_i |x_ia|
+};
+
+}  // namespace gs

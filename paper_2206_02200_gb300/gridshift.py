@@ -1,0 +1,247 @@
+"""Python binding of libgridshift (the C ABI of include/gridshift.h).
+
+Argument marshalling only: every step of GridShift runs in the CUDA library.
+The low-level functions carry the C names (``gs_create``, ``gs_fit``, ...);
+``GridShift`` wraps a context for torch tensors on a CUDA device.
+
+There is no CPU fallback: if the library cannot be loaded, or no CUDA device is
+visible, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _native
+
+# Status codes (gs_status)
+GS_OK = 0
+GS_E_INVALID = 1
+GS_E_NOMEM = 2
+GS_E_KEYRANGE = 3
+GS_E_CAPACITY = 4
+GS_E_CUDA = 5
+GS_E_INTERNAL = 6
+
+# Precisions (gs_precision) and input types (gs_dtype)
+GS_FP64 = 0
+GS_FP32_MIXED = 1
+GS_IN_F64 = 0
+GS_IN_F32 = 1
+
+#: every symbol the header declares, in declaration order
+EXPORTS = ("gs_create", "gs_set_precision", "gs_set_stream", "gs_fit", "gs_set_timing",
+           "gs_get_phase_times", "gs_get_last_error", "gs_status_string", "gs_destroy")
+
+#: gs_phase names, in enum order
+PHASES = ("range", "bin", "cells0", "gather", "merge", "labels")
+
+
+class gs_fit_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("m0", ctypes.c_int64), ("k", ctypes.c_int64), ("inexact", ctypes.c_int64),
+                ("cell_iters", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class gs_phase_times(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("count", ctypes.c_int32 * len(PHASES))]
+
+    def as_dict(self) -> dict:
+        return {p: (float(self.ms[i]), int(self.count[i])) for i, p in enumerate(PHASES)}
+
+
+class GridShiftError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libgridshift.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _native.stale():
+        _native.build()
+    if not os.path.exists(_native.LIB):
+        raise RuntimeError(f"libgridshift is not built ({_native.LIB} missing)")
+    L = ctypes.CDLL(_native.LIB)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.gs_create.restype = i32
+    L.gs_create.argtypes = [i32, ctypes.c_double, i32, ctypes.POINTER(vp)]
+    L.gs_set_precision.restype = i32
+    L.gs_set_precision.argtypes = [vp, i32]
+    L.gs_set_stream.restype = i32
+    L.gs_set_stream.argtypes = [vp, vp]
+    L.gs_fit.restype = i32
+    L.gs_fit.argtypes = [vp, vp, i32, i64, vp, vp, i64, ctypes.POINTER(i64),
+                         ctypes.POINTER(gs_fit_info)]
+    L.gs_set_timing.restype = i32
+    L.gs_set_timing.argtypes = [vp, i32]
+    L.gs_get_phase_times.restype = i32
+    L.gs_get_phase_times.argtypes = [vp, ctypes.POINTER(gs_phase_times)]
+    L.gs_get_last_error.restype = i32
+    L.gs_get_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.gs_status_string.restype = ctypes.c_char_p
+    L.gs_status_string.argtypes = [i32]
+    L.gs_destroy.restype = None
+    L.gs_destroy.argtypes = [vp]
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# C names
+
+
+def gs_create(d: int, h: float, max_iter: int) -> int:
+    ctx = ctypes.c_void_p()
+    st = load().gs_create(int(d), float(h), int(max_iter), ctypes.byref(ctx))
+    if st != GS_OK:
+        raise GridShiftError(st, f"gs_create(d={d}, h={h}, max_iter={max_iter})")
+    return ctx.value
+
+
+def gs_set_precision(ctx: int, precision: int) -> int:
+    return load().gs_set_precision(ctx, int(precision))
+
+
+def gs_set_stream(ctx: int, stream: int | None) -> int:
+    return load().gs_set_stream(ctx, stream or None)
+
+
+def gs_fit(ctx: int, points_ptr: int, dtype: int, n: int, labels_ptr: int, modes_ptr: int,
+           modes_cap: int):
+    """Raw call; returns (status, k, gs_fit_info)."""
+    k = ctypes.c_int64(0)
+    info = gs_fit_info()
+    st = load().gs_fit(ctx, points_ptr or None, int(dtype), int(n), labels_ptr or None,
+                       modes_ptr or None, int(modes_cap), ctypes.byref(k), ctypes.byref(info))
+    return st, int(k.value), info
+
+
+def gs_set_timing(ctx: int, enable: bool) -> int:
+    return load().gs_set_timing(ctx, 1 if enable else 0)
+
+
+def gs_get_phase_times(ctx: int) -> dict:
+    """{phase: (device ms, launch groups)} of the context's last gs_fit."""
+    out = gs_phase_times()
+    st = load().gs_get_phase_times(ctx, ctypes.byref(out))
+    if st != GS_OK:
+        raise GridShiftError(st, "gs_get_phase_times")
+    return out.as_dict()
+
+
+def gs_get_last_error(ctx: int) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    load().gs_get_last_error(ctx, buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def gs_status_string(status: int) -> str:
+    return load().gs_status_string(int(status)).decode()
+
+
+def status_string(status: int) -> str:
+    try:
+        return gs_status_string(status)
+    except Exception:  # pragma: no cover
+        return f"status {status}"
+
+
+def gs_destroy(ctx: int) -> None:
+    if ctx:
+        load().gs_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Tensor front end
+
+
+class GridShift:
+    """A GridShift context (cell side h, at most max_iter updates) for d-dim points.
+
+    ``fit(points)`` takes an n x d float64 or float32 CUDA tensor and returns
+    (labels int32[n], modes float64[k x d], info dict), all on the points'
+    device, computed on the current torch stream.
+    """
+
+    def __init__(self, d: int, h: float, max_iter: int = 50, precision: int = GS_FP64):
+        import torch  # noqa: F401  (device memory and streams)
+        self.d, self.h, self.max_iter = int(d), float(h), int(max_iter)
+        self._ctx = gs_create(self.d, self.h, self.max_iter)
+        st = gs_set_precision(self._ctx, precision)
+        if st != GS_OK:
+            msg = gs_get_last_error(self._ctx)
+            gs_destroy(self._ctx)
+            self._ctx = None
+            raise GridShiftError(st, msg)
+        self._modes_cap = 1024
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            gs_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_timing(self, enable: bool) -> None:
+        gs_set_timing(self._ctx, enable)
+
+    def phase_times(self) -> dict:
+        return gs_get_phase_times(self._ctx)
+
+    def fit_into(self, points, labels, modes):
+        """Runs gs_fit with caller-provided output tensors; returns (status, k, info)."""
+        import torch
+        if points.dtype == torch.float64:
+            dt = GS_IN_F64
+        elif points.dtype == torch.float32:
+            dt = GS_IN_F32
+        else:
+            raise TypeError("points must be float64 or float32")
+        if not points.is_cuda or not points.is_contiguous() or points.dim() != 2:
+            raise ValueError("points must be a contiguous n x d CUDA tensor")
+        if points.shape[1] != self.d:
+            raise ValueError(f"points have d={points.shape[1]}, context has d={self.d}")
+        stream = torch.cuda.current_stream(points.device).cuda_stream
+        gs_set_stream(self._ctx, stream)
+        cap = 0 if modes is None else modes.shape[0]
+        return gs_fit(self._ctx, points.data_ptr(), dt, points.shape[0], labels.data_ptr(),
+                      0 if modes is None else modes.data_ptr(), cap)
+
+    def fit(self, points):
+        import torch
+        n = points.shape[0]
+        with torch.cuda.device(points.device):
+            labels = torch.empty(n, dtype=torch.int32, device=points.device)
+            while True:
+                modes = torch.empty((self._modes_cap, self.d), dtype=torch.float64,
+                                    device=points.device)
+                st, k, info = self.fit_into(points, labels, modes)
+                if st == GS_E_CAPACITY:
+                    self._modes_cap = max(2 * self._modes_cap, k)
+                    continue
+                if st != GS_OK:
+                    raise GridShiftError(st, gs_get_last_error(self._ctx))
+                return labels, modes[:k], info.as_dict()
+
+
+def fit(points, h: float, max_iter: int = 50):
+    """One-shot GridShift on an n x d CUDA tensor: (labels, modes, info)."""
+    with GridShift(points.shape[1], h, max_iter) as g:
+        return g.fit(points)

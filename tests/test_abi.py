@@ -1,0 +1,95 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/*.h declares; argument checks that need no GPU behave as declared.
+No compute call is made here (these run without a GPU)."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2206_02200_gb300 import _native, gridshift
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions() -> list:
+    names = []
+    for hdr in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(gs_\w+)\s*\(", text):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _native.build()
+    return gridshift.load(build_if_missing=False)
+
+
+def test_header_declares_the_boundary():
+    decl = _declared_functions()
+    assert set(gridshift.EXPORTS) <= set(decl), decl
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_status_strings(lib):
+    names = {gridshift.GS_OK: "GS_OK", gridshift.GS_E_INVALID: "GS_E_INVALID",
+             gridshift.GS_E_NOMEM: "GS_E_NOMEM", gridshift.GS_E_KEYRANGE: "GS_E_KEYRANGE",
+             gridshift.GS_E_CAPACITY: "GS_E_CAPACITY", gridshift.GS_E_CUDA: "GS_E_CUDA",
+             gridshift.GS_E_INTERNAL: "GS_E_INTERNAL"}
+    for code, name in names.items():
+        assert gridshift.gs_status_string(code) == name
+
+
+@pytest.mark.parametrize("d,h,max_iter", [(0, 1.0, 5), (9, 1.0, 5), (3, 0.0, 5), (3, -1.0, 5),
+                                          (3, float("nan"), 5), (3, float("inf"), 5),
+                                          (3, 1.0, -1)])
+def test_create_rejects_bad_arguments(lib, d, h, max_iter):
+    ctx = ctypes.c_void_p()
+    st = lib.gs_create(d, h, max_iter, ctypes.byref(ctx))
+    assert st == gridshift.GS_E_INVALID
+    assert not ctx.value
+
+
+def test_create_destroy_and_host_only_checks(lib):
+    ctx = gridshift.gs_create(3, 16.0, 50)
+    try:
+        assert gridshift.gs_set_precision(ctx, 7) == gridshift.GS_E_INVALID
+        assert "GS_FP64" in gridshift.gs_get_last_error(ctx) or gridshift.gs_get_last_error(ctx)
+        assert gridshift.gs_set_precision(ctx, gridshift.GS_FP64) == gridshift.GS_OK
+        # n == 0 returns before any device work
+        st, k, info = gridshift.gs_fit(ctx, 0, gridshift.GS_IN_F64, 0, 0, 0, 0)
+        assert st == gridshift.GS_OK and k == 0 and info.converged == 1
+        # bad arguments are rejected before any device work
+        st, _, _ = gridshift.gs_fit(ctx, 0, gridshift.GS_IN_F64, -1, 0, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        st, _, _ = gridshift.gs_fit(ctx, 0, 9, 10, 0, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        st, _, _ = gridshift.gs_fit(ctx, 0, gridshift.GS_IN_F64, 10, 0, 0, 0)
+        assert st == gridshift.GS_E_INVALID  # NULL points
+        st = lib.gs_fit(ctx, None, 0, 0, None, None, 0, None, None)
+        assert st == gridshift.GS_E_INVALID  # NULL k_out
+    finally:
+        gridshift.gs_destroy(ctx)
+    lib.gs_destroy(None)  # ignored
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2206_02200_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if not path.endswith((".py", ".cu", ".cuh", ".h")):
+            continue
+        text = open(path).read()
+        assert "import oracle" not in text and "from oracle" not in text, path
+        assert "gs_oracle" not in text and "gso_" not in text, path

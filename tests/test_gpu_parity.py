@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+The FP64 path forms every sum exactly and rounds once, as the oracle does, so
+the expected result is bit-identical: the same labels (canonical numbering by
+ascending final cell key), the same iteration count and the same float64
+modes.  The tolerance the FP64 path is held to is the partition up to renaming
+and modes within 1e-10 * h; both are asserted, and bit-identity is asserted on
+top of it.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2206_02200_gb300 import gridshift, synth
+from tests import golden_io
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _gpu_fit(X, h, max_iter=50, as_f32=False, stream=None):
+    dev = torch.device("cuda:0")
+    t = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    if as_f32:
+        t = t.float()
+    with torch.cuda.stream(stream) if stream is not None else _null():
+        labels, modes, info = gridshift.fit(t, h, max_iter)
+        torch.cuda.current_stream().synchronize()
+    return labels.cpu().numpy(), modes.cpu().numpy(), info
+
+
+class _null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def _same_partition(a, b) -> bool:
+    """True if label arrays a and b describe the same partition (up to renaming)."""
+    if a.shape != b.shape:
+        return False
+    if a.size == 0:
+        return True
+    pairs = np.unique(np.stack([a, b], 1), axis=0)
+    return (len(pairs) == len(np.unique(a)) == len(np.unique(b)))
+
+
+def check_parity(X, h, max_iter=50, as_f32=False, stream=None):
+    Xo = X.astype(np.float32).astype(np.float64) if as_f32 else X
+    ref = oracle.fit(Xo, h, max_iter)
+    lab, md, info = _gpu_fit(X, h, max_iter, as_f32=as_f32, stream=stream)
+    assert info["k"] == ref["k"]
+    assert info["m0"] == ref["m0"]
+    assert info["iterations"] == ref["iterations"]
+    assert bool(info["converged"]) == ref["converged"]
+    assert info["inexact"] == 0
+    # the stated tolerance: same partition, modes within 1e-10 h
+    assert _same_partition(lab, ref["labels"])
+    assert md.shape == ref["modes"].shape
+    if md.size:
+        assert np.max(np.abs(md - ref["modes"])) <= 1e-10 * h
+    # what exact arithmetic gives: bit-identical labels and modes
+    np.testing.assert_array_equal(lab, ref["labels"])
+    np.testing.assert_array_equal(md.view(np.int64), ref["modes"].view(np.int64))
+    return ref, info
+
+
+# ---------------------------------------------------------------------------
+# hand-worked examples
+
+
+@pytest.mark.parametrize("case", golden_io.all_cases(), ids=lambda c: c["name"])
+def test_golden_cases_on_gpu(case):
+    X = case["points"]
+    lab, md, info = _gpu_fit(X, case["h"], case.get("max_iter", 50))
+    assert list(lab) == case["labels"]
+    assert info["iterations"] == case["iterations"]
+    for r, row in enumerate(case["modes"]):
+        for a, v in enumerate(row):
+            assert abs(md[r, a] - float(v)) <= 4 * np.spacing(abs(float(v)))
+    check_parity(X, case["h"], case.get("max_iter", 50))
+
+
+# ---------------------------------------------------------------------------
+# random inputs: every dimension, ragged sizes, negative coordinates
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("n", [1, 7, 1000, 33_333])
+def test_random_blobs(d, n):
+    rng = np.random.default_rng(1000 * d + n)
+    centres = rng.uniform(-40, 40, size=(5, d))
+    X = centres[rng.integers(0, 5, n)] + rng.normal(0, 3.0, size=(n, d))
+    check_parity(X, 4.0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_uniform_noise_many_cells(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5000, 60000))
+    d = int(rng.integers(1, 5))
+    X = rng.uniform(-100, 100, size=(n, d))
+    check_parity(X, float(rng.uniform(2, 9)))
+
+
+def test_float32_input():
+    X = synth.gmm_points(200_000, 6, 40, seed=9)
+    ref, _ = check_parity(X.astype(np.float64), 4.0)
+    lab, md, info = _gpu_fit(X, 4.0, as_f32=True)
+    np.testing.assert_array_equal(lab, ref["labels"])
+    np.testing.assert_array_equal(md.view(np.int64), ref["modes"].view(np.int64))
+
+
+@pytest.mark.parametrize("max_iter", [0, 1, 2, 3])
+def test_max_iter_cap(max_iter):
+    X = synth.image_features(synth.voronoi_image(120, 160, 9, 8.0, seed=4))
+    ref, info = check_parity(X, 16.0, max_iter)
+    assert info["iterations"] <= max_iter
+
+
+def test_small_images_span_tiles_and_ragged_tails():
+    for (H, W, R, seed) in [(37, 53, 3, 1), (97, 131, 7, 2), (250, 333, 15, 3)]:
+        img = synth.voronoi_image(H, W, R, 10.0, seed=seed, gradient=0.02)
+        check_parity(synth.image_features(img, xy_scale=0.1), 10.0)
+        check_parity(synth.image_features(img), 16.0)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads
+
+
+def test_image_321x481_d3_full():
+    w = synth.WORKLOADS["image_321x481_d3"]()
+    check_parity(w["points"], w["h"], w["max_iter"])
+
+
+def test_image_1080p_d5_full():
+    w = synth.WORKLOADS["image_1080p_d5"]()
+    check_parity(w["points"], w["h"], w["max_iter"])
+
+
+def test_gmm_1M_d6():
+    X = synth.gmm_points(1_000_000, 6, 200, seed=5)
+    check_parity(X, 4.0, 50, as_f32=True)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+
+
+def test_empty_and_single_point():
+    lab, md, info = _gpu_fit(np.zeros((0, 3)), 1.0)
+    assert lab.shape == (0,) and md.shape == (0, 3) and info["k"] == 0
+    check_parity(np.array([[1.5, -2.25, 3.0]]), 1.0)
+
+
+def test_identical_points_and_exact_faces():
+    check_parity(np.full((5000, 2), 3.0), 1.0)          # all on one face corner
+    X = np.repeat(np.arange(0, 20, 1.0)[:, None], 3, axis=1)
+    check_parity(X, 1.0)                                 # every point on a face
+
+
+def test_nonfinite_input_is_rejected():
+    g = gridshift.GridShift(2, 1.0, 10)
+    for bad in (np.nan, np.inf, -np.inf):
+        X = np.zeros((100, 2))
+        X[37, 1] = bad
+        with pytest.raises(gridshift.GridShiftError) as e:
+            g.fit(torch.from_numpy(X).cuda())
+        assert e.value.status == gridshift.GS_E_INVALID
+    # the context stays usable
+    check_ctx_reuse(g)
+    g.close()
+
+
+def check_ctx_reuse(g):
+    X = np.random.default_rng(1).normal(0, 5, size=(3000, 2))
+    labels, modes, info = g.fit(torch.from_numpy(X).cuda())
+    ref = oracle.fit(X, 1.0, 10)
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+
+
+def test_key_range_error():
+    X = np.array([[0.0], [1e12]])
+    with pytest.raises(gridshift.GridShiftError) as e:
+        _gpu_fit(X, 1e-3)
+    assert e.value.status == gridshift.GS_E_KEYRANGE
+
+
+def test_capacity_error_leaves_labels_valid():
+    X = synth.image_features(synth.voronoi_image(64, 64, 8, 8.0, seed=3))
+    ref = oracle.fit(X, 16.0, 50)
+    assert ref["k"] > 1
+    g = gridshift.GridShift(3, 16.0, 50)
+    pts = torch.from_numpy(X).cuda()
+    labels = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+    modes = torch.empty((1, 3), dtype=torch.float64, device="cuda")
+    st, k, info = g.fit_into(pts, labels, modes)
+    torch.cuda.synchronize()
+    assert st == gridshift.GS_E_CAPACITY and k == ref["k"]
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    g.close()
+
+
+def test_context_reuse_across_sizes_and_streams():
+    g = gridshift.GridShift(5, 12.0, 50)
+    s = torch.cuda.Stream()
+    for (H, W, seed) in [(300, 400, 1), (40, 50, 2), (500, 600, 3), (40, 50, 2)]:
+        X = synth.image_features(synth.voronoi_image(H, W, 10, 10.0, seed=seed), xy_scale=0.1)
+        ref = oracle.fit(X, 12.0, 50)
+        with torch.cuda.stream(s):
+            pts = torch.from_numpy(X).cuda()
+            labels, modes, info = g.fit(pts)
+            s.synchronize()
+        np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+        np.testing.assert_array_equal(modes.cpu().numpy().view(np.int64),
+                                      ref["modes"].view(np.int64))
+    g.close()
