@@ -48,55 +48,58 @@ inline unsigned grid_for(int64_t work, int per_block = kBlock, unsigned cap = 15
 // ---------------------------------------------------------------------------
 // Key range and finiteness
 
+// The point array is read as one flat stream of n*D values: thread t reads the
+// values t, t + S, t + 2S, ... with S a multiple of D, so every thread sees a
+// single coordinate a = t mod D and consecutive threads read consecutive
+// values (coalesced).  Per-coordinate extremes are reduced in shared memory
+// and published with one global atomic per block and coordinate.
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int64_t n,
                                                   DevFlags* fl) {
-  int64_t mn[D], mx[D];
-  uint64_t ma[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    mn[a] = INT64_MAX;
-    mx[a] = INT64_MIN;
-    ma[a] = 0;
+  __shared__ long long s_mn[D], s_mx[D];
+  __shared__ unsigned long long s_ma[D], s_bad;
+  if (threadIdx.x < D) {
+    s_mn[threadIdx.x] = INT64_MAX;
+    s_mx[threadIdx.x] = INT64_MIN;
+    s_ma[threadIdx.x] = 0;
   }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  const int64_t total = n * D;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t S = nthreads - nthreads % D;  // stride, a multiple of D
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t mn = INT64_MAX, mx = INT64_MIN;
+  uint64_t ma = 0;
   unsigned long long bad = 0;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      uint64_t b = load_bits<T>(pts + i * D + a);
+  if (t < S) {
+    for (int64_t e = t; e < total; e += S) {
+      uint64_t b = load_bits<T>(pts + e);
       if (((b >> 52) & 0x7FF) == 0x7FF) {
         ++bad;
         continue;
       }
       int64_t o = ord_of_bits(b);
-      mn[a] = o < mn[a] ? o : mn[a];
-      mx[a] = o > mx[a] ? o : mx[a];
+      mn = o < mn ? o : mn;
+      mx = o > mx ? o : mx;
       uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
-      ma[a] = ab > ma[a] ? ab : ma[a];
+      ma = ab > ma ? ab : ma;
     }
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    for (int o = 16; o > 0; o >>= 1) {
-      int64_t x = __shfl_xor_sync(kFull, mn[a], o);
-      mn[a] = x < mn[a] ? x : mn[a];
-      x = __shfl_xor_sync(kFull, mx[a], o);
-      mx[a] = x > mx[a] ? x : mx[a];
-      uint64_t y = __shfl_xor_sync(kFull, ma[a], o);
-      ma[a] = y > ma[a] ? y : ma[a];
+    const int a = (int)(t % D);
+    if (mn != INT64_MAX) {
+      atomicMin(&s_mn[a], (long long)mn);
+      atomicMax(&s_mx[a], (long long)mx);
+      atomicMax(&s_ma[a], (unsigned long long)ma);
     }
+    if (bad) atomicAdd(&s_bad, bad);
   }
-  for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(kFull, bad, o);
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      atomicMin(&fl->min_ord[a], (long long)mn[a]);
-      atomicMax(&fl->max_ord[a], (long long)mx[a]);
-      atomicMax(&fl->maxabs[a], (unsigned long long)ma[a]);
-    }
-    if (bad) atomicAdd(&fl->bad, bad);
+  __syncthreads();
+  if (threadIdx.x < D && s_mn[threadIdx.x] != INT64_MAX) {
+    atomicMin(&fl->min_ord[threadIdx.x], s_mn[threadIdx.x]);
+    atomicMax(&fl->max_ord[threadIdx.x], s_mx[threadIdx.x]);
+    atomicMax(&fl->maxabs[threadIdx.x], s_ma[threadIdx.x]);
   }
+  if (threadIdx.x == 0 && s_bad) atomicAdd(&fl->bad, s_bad);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,7 +371,7 @@ __global__ void k_modes(Cells c, const uint32_t* __restrict__ rank, double* __re
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
                          cudaStream_t s) {
-  unsigned g = grid_for(n);
+  unsigned g = grid_for(n * d, kBlock * 8, 152u * 8u);
   if (f32) {
     GS_DISPATCH_D(d, k_range<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, fl));
   } else {
