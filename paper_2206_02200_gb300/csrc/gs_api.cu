@@ -482,11 +482,12 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
     GS_PH_END(GS_PHASE_BIN);
     GS_CU(cudaMemcpyAsync(hf, ctx->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
     GS_CU(cudaStreamSynchronize(s), "sync bin");
-    if (hf->err & ~kErrOverflow) {
+    const uint32_t regrow = kErrOverflow | kErrTableFull;
+    if (hf->err & ~regrow) {
       ctx->t0.clear(s);
-      return fail(ctx, GS_E_INTERNAL, "binning hit a device bound (table full or window)");
+      return fail(ctx, GS_E_INTERNAL, "binning hit a device bound (fixed-point window)");
     }
-    if (!(hf->err & kErrOverflow)) {
+    if (!(hf->err & regrow)) {
       m0 = hf->m0;
       break;
     }

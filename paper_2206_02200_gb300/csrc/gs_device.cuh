@@ -242,10 +242,18 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   return k;
 }
 
-// Slot holding key, or kNone.  Bounded by the capacity.
+// Longest probe sequence: an insert that finds no free slot within kMaxProbe
+// slots of the key's home slot fails (kErrTableFull), so every stored key lies
+// within kMaxProbe slots of its home and a lookup may stop there.  At the load
+// factors used (<= 1/2) sequences this long do not occur in practice; the
+// bound keeps an over-full table from turning into a near-endless scan.
+constexpr uint32_t kMaxProbe = 512;
+
+// Slot holding key, or kNone.
 __device__ __forceinline__ uint32_t table_find(const uint64_t* keys, uint32_t mask, uint64_t key) {
   uint32_t s = (uint32_t)mix64(key) & mask;
-  for (uint32_t i = 0; i <= mask; ++i) {
+  const uint32_t lim = mask < kMaxProbe ? mask + 1 : kMaxProbe;
+  for (uint32_t i = 0; i < lim; ++i) {
     uint64_t k = keys[s];
     if (k == key) return s;
     if (k == kEmpty) return kNone;
@@ -260,7 +268,8 @@ __device__ __forceinline__ uint32_t table_insert(uint64_t* keys, uint32_t mask, 
                                                  bool& won, uint32_t* err) {
   uint32_t s = (uint32_t)mix64(key) & mask;
   won = false;
-  for (uint32_t i = 0; i <= mask; ++i) {
+  const uint32_t lim = mask < kMaxProbe ? mask + 1 : kMaxProbe;
+  for (uint32_t i = 0; i < lim; ++i) {
     uint64_t k = *(volatile uint64_t*)&keys[s];
     if (k == key) return s;
     if (k == kEmpty) {
