@@ -62,7 +62,9 @@ typedef enum {
                         coordinate's key range exceeds 2^22 cells */
   GS_E_CAPACITY = 4, /* modes_cap < k: *k_out is set and labels are valid */
   GS_E_CUDA = 5,     /* a CUDA runtime call failed; see gs_get_last_error */
-  GS_E_INTERNAL = 6  /* a device-side bound (hash probe limit, table overflow) was hit */
+  GS_E_INTERNAL = 6, /* a device-side bound (hash probe limit, table overflow) was hit */
+  GS_E_SCRATCH = 7   /* gs_fit_noalloc only: the input needs more scratch than its static
+                        device array holds (too many points, cells or cells per axis) */
 } gs_status;
 
 typedef enum {
@@ -142,6 +144,46 @@ gs_status gs_set_timing(gs_ctx* ctx, int enable);
 /* Copies the per-phase times of the last gs_fit call of this context (all
  * zero if timing was off) into *out (host).  Returns GS_OK or GS_E_INVALID. */
 gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
+
+/* gs_fit without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they run,
+ * for instance a host program that fixes its whole GPU memory budget at
+ * start-up and forbids later cudaMalloc/cudaFree calls (which also synchronise
+ * the device), or a plug-in whose host application owns every allocation.
+ *
+ * It runs the same steps, with the same kernels and results, as gs_fit on a
+ * context created with gs_create(d, h, max_iter) and bound to cuda_stream
+ * (a cudaStream_t; NULL = legacy default stream).  The caller passes the
+ * inputs and outputs exactly as for gs_fit; every other device buffer the
+ * call needs is carved out of one static device array of 64 MiB that lives in
+ * this library: every GPU that loads the library holds those 64 MiB until the
+ * process exits.  The call allocates no device or pinned host memory and calls
+ * no allocating CUDA routine.
+ *
+ * Set-up: the first call on a device looks up the device address of the
+ * static array (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.
+ *
+ * Limits: the point-to-cell map takes 4 bytes per point and 1 MiB is kept
+ * for the rest, so n <= 16,515,072; the cell workspace (about 1.5 KB per
+ * initial active cell at d = 4 and max_iter = 50, growing with d and
+ * max_iter) must fit what the points leave; the cell-face table holds at most
+ * 8192 entries (over all axes, the number of cells the data spans plus 3).
+ * Beyond these the call returns GS_E_SCRATCH; use gs_fit.
+ *
+ * Sharing: every call uses the same array, which keeps the previous call's
+ * contents; the call clears what must start at zero itself.  Calls are
+ * serialised on the host by a lock and each returns only after its work on
+ * cuda_stream has finished, so they do not overlap; GPU work that overlapped
+ * a call's use of the array (another thread launching on the array through a
+ * second copy of this library, say) would race.
+ *
+ * Returns GS_OK, GS_E_INVALID, GS_E_KEYRANGE, GS_E_CAPACITY (k > modes_cap:
+ * *k_out and labels set, as for gs_fit), GS_E_SCRATCH, GS_E_CUDA or
+ * GS_E_INTERNAL.  No error text is kept (there is no context). */
+gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_stream, const void* points,
+                         gs_dtype dtype, int64_t n, int32_t* labels, double* modes,
+                         int64_t modes_cap, int64_t* k_out, gs_fit_info* info);
 
 /* Copies a description of the last error of this context (NUL-terminated,
  * truncated to len bytes) into buf.  Returns GS_OK or GS_E_INVALID. */

@@ -324,6 +324,7 @@ const char* gs_status_string(gs_status s) {
     case GS_E_CAPACITY: return "GS_E_CAPACITY";
     case GS_E_CUDA: return "GS_E_CUDA";
     case GS_E_INTERNAL: return "GS_E_INTERNAL";
+    case GS_E_SCRATCH: return "GS_E_SCRATCH";
   }
   return "GS_E_UNKNOWN";
 }

@@ -22,6 +22,7 @@ GS_E_KEYRANGE = 3
 GS_E_CAPACITY = 4
 GS_E_CUDA = 5
 GS_E_INTERNAL = 6
+GS_E_SCRATCH = 7
 
 # Precisions (gs_precision) and input types (gs_dtype)
 GS_FP64 = 0
@@ -31,7 +32,8 @@ GS_IN_F32 = 1
 
 #: every symbol the header declares, in declaration order
 EXPORTS = ("gs_create", "gs_set_precision", "gs_set_stream", "gs_fit", "gs_set_timing",
-           "gs_get_phase_times", "gs_get_last_error", "gs_status_string", "gs_destroy")
+           "gs_get_phase_times", "gs_fit_noalloc", "gs_get_last_error", "gs_status_string",
+           "gs_destroy")
 
 #: gs_phase names, in enum order
 PHASES = ("range", "bin", "cells0", "gather", "merge", "labels")
@@ -86,6 +88,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.gs_set_timing.argtypes = [vp, i32]
     L.gs_get_phase_times.restype = i32
     L.gs_get_phase_times.argtypes = [vp, ctypes.POINTER(gs_phase_times)]
+    L.gs_fit_noalloc.restype = i32
+    L.gs_fit_noalloc.argtypes = [i32, ctypes.c_double, i32, vp, vp, i32, i64, vp, vp, i64,
+                                 ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
     L.gs_get_last_error.restype = i32
     L.gs_get_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     L.gs_status_string.restype = ctypes.c_char_p
@@ -137,6 +142,19 @@ def gs_get_phase_times(ctx: int) -> dict:
     if st != GS_OK:
         raise GridShiftError(st, "gs_get_phase_times")
     return out.as_dict()
+
+
+def gs_fit_noalloc(d: int, h: float, max_iter: int, stream: int | None, points_ptr: int,
+                   dtype: int, n: int, labels_ptr: int, modes_ptr: int, modes_cap: int):
+    """gs_fit with all scratch in the library's static device array; returns
+    (status, k, gs_fit_info).  For callers that cannot allocate device memory."""
+    k = ctypes.c_int64(0)
+    info = gs_fit_info()
+    st = load().gs_fit_noalloc(int(d), float(h), int(max_iter), stream or None,
+                               points_ptr or None, int(dtype), int(n), labels_ptr or None,
+                               modes_ptr or None, int(modes_cap), ctypes.byref(k),
+                               ctypes.byref(info))
+    return st, int(k.value), info
 
 
 def gs_get_last_error(ctx: int) -> str:
