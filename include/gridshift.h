@@ -86,20 +86,27 @@ typedef struct {
   int64_t launches;    /* CUDA kernels the call launched */
 } gs_fit_info;
 
-/* Launch groups of one call, for gs_get_phase_times. */
+/* Timed parts of one call, for gs_get_phase_times.  The first four are CUDA
+ * event pairs on the call's stream around launch groups; the last five split
+ * the loop kernel's time by the device clock, read by one block at the grid
+ * barriers between its phases. */
 typedef enum {
-  GS_PHASE_RANGE = 0,   /* key range and finiteness of the input (step i, set-up) */
-  GS_PHASE_BIN = 1,     /* binning: cell key, count and exact sum per cell (step i) */
-  GS_PHASE_CELLS0 = 2,  /* list and lookup table of the initial cells (step i) */
-  GS_PHASE_GATHER = 3,  /* neighbourhood means and new keys, all iterations (steps ii, iii, v) */
-  GS_PHASE_MERGE = 4,   /* merging cells that share a key, all iterations (step iv) */
-  GS_PHASE_LABELS = 5,  /* final cell of every point, label numbering, modes */
-  GS_NPHASES = 6
+  GS_PHASE_RANGE = 0,    /* key range and finiteness of the input (step i, set-up) */
+  GS_PHASE_BIN = 1,      /* binning: cell key, count and exact sum per cell (step i) */
+  GS_PHASE_LOOP = 2,     /* the loop kernel: steps ii-v, labels and modes */
+  GS_PHASE_SORT = 3,     /* numbering by a radix sort, when there are too many clusters
+                            to number inside the loop kernel */
+  GS_PHASE_K_LEVEL0 = 4, /* in the loop kernel: the initial cells and their lookup table */
+  GS_PHASE_K_GATHER = 5, /* in the loop kernel: neighbourhood means, new keys (ii, iii, v) */
+  GS_PHASE_K_MERGE = 6,  /* in the loop kernel: adding cells that share a key (iv) */
+  GS_PHASE_K_COMPACT = 7,/* in the loop kernel: the next level's cells and lookup table */
+  GS_PHASE_K_LABELS = 8, /* in the loop kernel: final cell of every point, labels, modes */
+  GS_NPHASES = 9
 } gs_phase;
 
 typedef struct {
-  double ms[GS_NPHASES];    /* device time of each phase, summed over its launch groups */
-  int32_t count[GS_NPHASES]; /* launch groups timed in each phase */
+  double ms[GS_NPHASES];    /* device time of each phase, summed over its occurrences */
+  int32_t count[GS_NPHASES]; /* occurrences timed in each phase */
 } gs_phase_times;
 
 /* Creates a context for d-dimensional points, cell side (bandwidth) h and at

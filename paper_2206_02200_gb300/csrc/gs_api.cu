@@ -1,6 +1,6 @@
 // gs_api.cu -- host side of the C ABI declared in include/gridshift.h: argument
-// checks, the per-call plan (packed keys, face tables, fixed-point windows),
-// the device workspace and the order of kernel launches of one GridShift run.
+// checks, the context and its growable device workspace.  The order of the
+// steps of one run is in gs_driver.cu.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "../../include/gridshift.h"
-#include "gs_kernels.h"
+#include "gs_driver.h"
 
 using namespace gs;
 
@@ -81,66 +81,19 @@ struct TableBuf {
 struct CellBuf {
   DBuf<uint64_t> key;
   DBuf<uint32_t> cnt;
-  DBuf<double> cs;
+  DBuf<ulonglong2> fix;
   cudaError_t ensure(uint32_t m, int d) {
     cudaError_t e;
     if ((e = key.ensure(m)) != cudaSuccess) return e;
     if ((e = cnt.ensure(m)) != cudaSuccess) return e;
-    return cs.ensure((size_t)m * d);
+    return fix.ensure((size_t)m * d);
   }
-  Cells view() const { return Cells{key.p, cnt.p, cs.p}; }
-  void release() { key.release(); cnt.release(); cs.release(); }
+  Cells view() const { return Cells{key.p, cnt.p, fix.p}; }
+  void release() { key.release(); cnt.release(); fix.release(); }
 };
 
-uint32_t pow2_at_least(uint64_t v, uint32_t lo) {
-  uint64_t c = lo;
-  while (c < v && c < (1ull << 31)) c <<= 1;
-  return (uint32_t)c;
-}
-
-int64_t ord_of(double x) {
-  if (x == 0.0) x = 0.0;
-  int64_t s;
-  std::memcpy(&s, &x, 8);
-  return s ^ ((s >> 63) & 0x7FFFFFFFFFFFFFFFll);
-}
-
-double from_ord(int64_t o) {
-  int64_t s = o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll);
-  double x;
-  std::memcpy(&x, &s, 8);
-  return x;
-}
-
-// The least double t with t >= q * h (exactly); the error of the rounded
-// product q * h is itself a double, obtained exactly by one fused multiply-add.
-double face(int64_t q, double h) {
-  double qd = (double)q;
-  double p = qd * h;
-  double r = std::fma(qd, h, -p);
-  if (r > 0) p = std::nextafter(p, INFINITY);
-  return p;
-}
-
-// floor(x / h) of the exact quotient: the q with face(q) <= x < face(q + 1).
-int64_t floor_div(double x, double h) {
-  int64_t q = (int64_t)std::floor(x / h);
-  for (int i = 0; i < 4 && face(q, h) > x; ++i) --q;
-  for (int i = 0; i < 4 && face(q + 1, h) <= x; ++i) ++q;
-  return q;
-}
-
-int bitlen(uint64_t v) {
-  int b = 0;
-  while (v) {
-    ++b;
-    v >>= 1;
-  }
-  return b;
-}
-
 // CUDA events around the launch groups of one call (opt-in, gs_set_timing).
-struct PhaseTimer {
+struct PhaseTimer : public EventTimer {
   std::vector<cudaEvent_t> pool;
   std::vector<int> phase;  // phase of the event pair (2i, 2i+1)
   size_t used = 0;
@@ -153,11 +106,196 @@ struct PhaseTimer {
     }
     return cudaEventRecord(pool[used++], s);
   }
+  cudaError_t begin(int ph, cudaStream_t s) override {
+    phase.push_back(ph);
+    return record(s);
+  }
+  cudaError_t end(cudaStream_t s) override { return record(s); }
+  void reset() {
+    used = 0;
+    phase.clear();
+  }
   void release() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     pool.clear();
     phase.clear();
     used = 0;
+  }
+};
+
+// The growable workspace of a context: buffers are allocated on first need,
+// grown when a call needs more, and kept for later calls.
+struct CtxWorkspace : public Workspace {
+  DBuf<DevFlags> flags;
+  DBuf<IterState> st;
+  DBuf<LoopResult> res;
+  DBuf<GridBar> bar;
+  DBuf<int64_t> thr;
+  DBuf<uint64_t> dtab;
+  DBuf<uint32_t> slot0;
+  TableBuf t0, tab[2];
+  CellBuf cells[2];
+  DBuf<double> sp;
+  DBuf<uint64_t> nkey;
+  DBuf<uint32_t> pslot, forest, forest2, labslot, rank;
+  DBuf<uint64_t> skey, skey2;
+  DBuf<uint32_t> sval, sval2, shist;
+
+  DevFlags* h_flags = nullptr;    // pinned
+  LoopResult* h_res = nullptr;    // pinned
+  int64_t* h_words = nullptr;     // pinned staging of the face and offset tables
+  size_t h_words_cap = 0;
+  bool dirty = false;             // a call stopped with tables not returned to clean
+
+  std::string alloc_err(cudaError_t e, const char* what) {
+    return std::string(what) + ": " + cudaGetErrorName(e);
+  }
+
+  DevFlags* host_flags() override { return h_flags; }
+  LoopResult* host_result() override { return h_res; }
+
+  gs_status host_words(size_t words, int64_t** out, std::string* err) override {
+    if (words > h_words_cap) {
+      if (h_words) cudaFreeHost(h_words);
+      h_words = nullptr;
+      h_words_cap = 0;
+      cudaError_t e = cudaMallocHost((void**)&h_words, sizeof(int64_t) * words);
+      if (e != cudaSuccess) {
+        h_words = nullptr;
+        *err = alloc_err(e, "cudaMallocHost");
+        return GS_E_NOMEM;
+      }
+      h_words_cap = words;
+    }
+    *out = h_words;
+    return GS_OK;
+  }
+
+  gs_status begin(Bufs& b, std::string* err) override {
+    cudaError_t e = cudaSuccess;
+    if (!h_flags) e = cudaMallocHost((void**)&h_flags, sizeof(DevFlags));
+    if (e == cudaSuccess && !h_res) e = cudaMallocHost((void**)&h_res, sizeof(LoopResult));
+    if (e == cudaSuccess) e = flags.ensure(1);
+    if (e != cudaSuccess) {
+      *err = alloc_err(e, "workspace");
+      return e == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA;
+    }
+    b.flags = flags.p;
+    return GS_OK;
+  }
+
+  gs_status prepare(int64_t n, int d, int max_iter, size_t thr_words, int nprobe,
+                    uint64_t m_bound, cudaStream_t s, Bufs& b, std::string* err) override {
+    cudaError_t e;
+#define WS_CU(call, what)                                              \
+  do {                                                                 \
+    e = (call);                                                        \
+    if (e != cudaSuccess) {                                            \
+      *err = alloc_err(e, what);                                       \
+      return e == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA;  \
+    }                                                                  \
+  } while (0)
+    WS_CU(st.ensure(max_iter + 2), "alloc state");
+    WS_CU(res.ensure(1), "alloc result");
+    WS_CU(bar.ensure(1), "alloc barrier");
+    WS_CU(thr.ensure(thr_words), "alloc face table");
+    WS_CU(dtab.ensure(nprobe), "alloc offsets");
+    WS_CU(slot0.ensure(n), "alloc slot0");
+    uint32_t cap0 = pow2_at_least(2 * m_bound, 1024);
+    if (t0.cap > cap0 && t0.d == d) cap0 = t0.cap;
+    if (dirty) {
+      if (t0.cap) WS_CU(t0.clear(s), "clear T0");
+      if (tab[0].cap) WS_CU(tab[0].clear(s), "clear table A");
+      if (tab[1].cap) WS_CU(tab[1].clear(s), "clear table B");
+    }
+    WS_CU(t0.ensure(cap0, d, cap0 / 2, s), "alloc T0");
+    b.st = st.p;
+    b.res = res.p;
+    b.bar = bar.p;
+    b.thr = thr.p;
+    b.dtab = dtab.p;
+    b.slot0 = slot0.p;
+    b.t0 = t0.view();
+    b.t0_maxcells = t0.cap / 2;
+    return GS_OK;
+  }
+
+  gs_status regrow_bin(int d, cudaStream_t s, Bufs& b, std::string* err) override {
+    if (t0.cap >= (1u << 29)) {
+      *err = "binning table overflow";
+      return GS_E_INTERNAL;
+    }
+    cudaError_t e;
+    WS_CU(t0.clear(s), "clear T0");
+    WS_CU(t0.ensure(t0.cap << 2, d, t0.cap << 1, s), "alloc T0");
+    b.t0 = t0.view();
+    b.t0_maxcells = t0.cap / 2;
+    return GS_OK;
+  }
+
+  gs_status levels(uint32_t m0, int d, int max_iter, cudaStream_t s, Bufs& b,
+                   std::string* err) override {
+    cudaError_t e;
+    const uint32_t capAB = pow2_at_least(2ull * m0, 64);
+    const uint32_t m = m0 > 0 ? m0 : 1;
+    WS_CU(tab[0].ensure(capAB, d, m, s), "alloc table A");
+    WS_CU(tab[1].ensure(capAB, d, m, s), "alloc table B");
+    WS_CU(cells[0].ensure(m, d), "alloc cells");
+    WS_CU(cells[1].ensure(m, d), "alloc cells");
+    WS_CU(sp.ensure((size_t)m * d), "alloc sp");
+    WS_CU(nkey.ensure(m), "alloc nkey");
+    WS_CU(pslot.ensure(m), "alloc pslot");
+    WS_CU(forest.ensure((size_t)m * (max_iter + 1)), "alloc forest");
+    WS_CU(forest2.ensure((size_t)m * (max_iter + 1)), "alloc forest");
+    WS_CU(labslot.ensure(t0.cap), "alloc labslot");
+    WS_CU(rank.ensure(m), "alloc rank");
+    for (int i = 0; i < 2; ++i) {
+      b.tab[i] = tab[i].view();
+      b.cells[i] = cells[i].view();
+    }
+    b.capAB = tab[0].cap < tab[1].cap ? tab[0].cap : tab[1].cap;
+    b.sp = sp.p;
+    b.nkey = nkey.p;
+    b.pslot = pslot.p;
+    b.forest = forest.p;
+    b.forest2 = forest2.p;
+    b.labslot = labslot.p;
+    b.rank = rank.p;
+    return GS_OK;
+  }
+
+  gs_status sort_space(uint32_t k, Bufs& b, std::string* err) override {
+    cudaError_t e;
+    WS_CU(skey.ensure(k), "alloc sort");
+    WS_CU(skey2.ensure(k), "alloc sort");
+    WS_CU(sval.ensure(k), "alloc sort");
+    WS_CU(sval2.ensure(k), "alloc sort");
+    WS_CU(shist.ensure(radix_hist_words(k)), "alloc sort");
+#undef WS_CU
+    b.skey = skey.p;
+    b.skey2 = skey2.p;
+    b.sval = sval.p;
+    b.sval2 = sval2.p;
+    b.shist = shist.p;
+    return GS_OK;
+  }
+
+  void mark_dirty(bool d) override { dirty = d; }
+
+  void release() {
+    flags.release(); st.release(); res.release(); bar.release(); thr.release(); dtab.release();
+    slot0.release(); t0.release(); tab[0].release(); tab[1].release(); cells[0].release();
+    cells[1].release(); sp.release(); nkey.release(); pslot.release(); forest.release();
+    forest2.release(); labslot.release(); rank.release(); skey.release(); skey2.release();
+    sval.release(); sval2.release(); shist.release();
+    if (h_flags) cudaFreeHost(h_flags);
+    if (h_res) cudaFreeHost(h_res);
+    if (h_words) cudaFreeHost(h_words);
+    h_flags = nullptr;
+    h_res = nullptr;
+    h_words = nullptr;
+    h_words_cap = 0;
+    dirty = false;
   }
 };
 
@@ -172,43 +310,13 @@ struct gs_ctx {
   int device = -1;
   std::string err;
   bool timing = false;
-  bool dirty = false;  // a call stopped between binning and its end: tables need clearing
   PhaseTimer tm;
   gs_phase_times last_times{};
-  int64_t launches = 0;  // kernels launched by the current call
-
-  DBuf<DevFlags> flags;
-  DBuf<IterState> st;
-  DBuf<int64_t> thr;
-  DBuf<uint64_t> dtab;
-  DBuf<uint32_t> slot0;
-  TableBuf t0, tab[2];
-  CellBuf cells[2];
-  DBuf<double> sp;
-  DBuf<uint64_t> nkey;
-  DBuf<uint32_t> pslot, forest, forest2, labslot, rank;
-  DBuf<uint64_t> skey, skey2;
-  DBuf<uint32_t> sval, sval2, shist;
-
-  DevFlags* h_flags = nullptr;  // pinned
-  IterState* h_st = nullptr;    // pinned, max_iter + 2 entries
-  int64_t* h_thr = nullptr;     // pinned staging of thr + dtab
-  size_t h_thr_cap = 0;
+  CtxWorkspace ws;
 
   void release_device() {
-    flags.release(); st.release(); thr.release(); dtab.release(); slot0.release();
-    t0.release(); tab[0].release(); tab[1].release(); cells[0].release(); cells[1].release();
-    sp.release(); nkey.release(); pslot.release(); forest.release(); forest2.release();
-    labslot.release(); rank.release(); skey.release(); skey2.release(); sval.release();
-    sval2.release(); shist.release();
+    ws.release();
     tm.release();
-    if (h_flags) cudaFreeHost(h_flags);
-    if (h_st) cudaFreeHost(h_st);
-    if (h_thr) cudaFreeHost(h_thr);
-    h_flags = nullptr;
-    h_st = nullptr;
-    h_thr = nullptr;
-    h_thr_cap = 0;
   }
 };
 
@@ -217,98 +325,6 @@ namespace {
 gs_status fail(gs_ctx* c, gs_status s, const std::string& msg) {
   c->err = msg;
   return s;
-}
-
-gs_status cuda_fail(gs_ctx* c, cudaError_t e, const char* where) {
-  c->err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-  return e == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA;
-}
-
-#define GS_CU(call, where)                                  \
-  do {                                                      \
-    cudaError_t e_ = (call);                                \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
-  } while (0)
-
-// A kernel launch: counted, and checked like any runtime call.
-#define GS_LAUNCH(call, where, nk) \
-  do {                             \
-    GS_CU(call, where);            \
-    ctx->launches += (nk);         \
-  } while (0)
-
-// Start and end of a timed phase (events on the call's stream, if timing is on).
-#define GS_PH_BEGIN(ph)                                   \
-  do {                                                    \
-    if (ctx->timing) {                                    \
-      GS_CU(ctx->tm.record(s), "cudaEventRecord");        \
-      ctx->tm.phase.push_back(ph);                        \
-    }                                                     \
-  } while (0)
-#define GS_PH_END(ph) \
-  do {                \
-    if (ctx->timing) GS_CU(ctx->tm.record(s), "cudaEventRecord"); \
-  } while (0)
-
-// Host plan of one call: packed-key layout, face tables and fixed-point windows.
-gs_status make_plan(gs_ctx* ctx, const DevFlags& fl, int64_t n, Plan& P,
-                    std::vector<int64_t>& thr, std::vector<uint64_t>& dtab, uint64_t& span_prod,
-                    int& total_bits) {
-  const int d = ctx->d;
-  const double h = ctx->h;
-  std::memset(&P, 0, sizeof(P));
-  P.d = d;
-  int bits[kMaxD];
-  int clog2n = 0;
-  while ((1ll << clog2n) < n) ++clog2n;
-  span_prod = 1;
-  thr.clear();
-  for (int a = 0; a < d; ++a) {
-    double lo = from_ord(fl.min_ord[a]), hi = from_ord(fl.max_ord[a]);
-    if (!(std::fabs(lo / h) < 4.0e15) || !(std::fabs(hi / h) < 4.0e15))
-      return fail(ctx, GS_E_KEYRANGE, "a coordinate divided by h exceeds 2^52");
-    // The key box of the data, widened by one cell on each side: centroids are
-    // convex combinations of the points (Eq. 1, Eq. 3) and leave the data's box
-    // by at most a few roundings, never by a whole cell.
-    int64_t kmin = floor_div(lo, h) - 1, kmax = floor_div(hi, h) + 1;
-    int64_t span = kmax - kmin + 1;
-    if (span > (1ll << 22))
-      return fail(ctx, GS_E_KEYRANGE, "more than 2^22 cells along one axis");
-    P.kmin[a] = kmin;
-    P.span[a] = (int)span;
-    bits[a] = bitlen((uint64_t)span + 1);
-    P.thr_off[a] = (int)thr.size();
-    for (int64_t j = 0; j <= span; ++j) thr.push_back(ord_of(face(kmin + j, h)));
-    span_prod = span_prod > (1ull << 40) ? span_prod : span_prod * (uint64_t)span;
-    double ma;
-    uint64_t mb = fl.maxabs[a];
-    std::memcpy(&ma, &mb, 8);
-    int e = 0;
-    if (ma > 0) std::frexp(ma, &e);  // ma < 2^e
-    P.L[a] = e + clog2n - 126;
-  }
-  total_bits = 0;
-  for (int a = d - 1; a >= 0; --a) {
-    P.off[a] = total_bits;
-    total_bits += bits[a];
-  }
-  if (total_bits > 63) return fail(ctx, GS_E_KEYRANGE, "packed cell key needs more than 63 bits");
-  int np = 1;
-  for (int a = 0; a < d; ++a) np *= 3;
-  P.nprobe = np;
-  P.center = (np - 1) / 2;
-  dtab.resize(np);
-  for (int p = 0; p < np; ++p) {
-    int64_t delta = 0;
-    int rest = p;
-    for (int a = d - 1; a >= 0; --a) {  // axis 0 is the slowest digit
-      int v = rest % 3 - 1;
-      rest /= 3;
-      delta += (int64_t)v * (int64_t)(1ull << P.off[a]);
-    }
-    dtab[p] = (uint64_t)delta;
-  }
-  return GS_OK;
 }
 
 }  // namespace
@@ -393,228 +409,51 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   gs_fit_info inf;
   std::memset(&inf, 0, sizeof(inf));
   *k_out = 0;
-  ctx->launches = 0;
-  ctx->tm.used = 0;
-  ctx->tm.phase.clear();
+  ctx->tm.reset();
   std::memset(&ctx->last_times, 0, sizeof(ctx->last_times));
   if (n == 0) {
     inf.converged = 1;
     if (info) *info = inf;
     return GS_OK;
   }
-  const int d = ctx->d;
-  const bool f32 = dtype == GS_IN_F32;
-  cudaStream_t s = ctx->stream;
   int dev = 0;
-  GS_CU(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(ctx, GS_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorName(ce));
   if (ctx->device != dev) {
     ctx->release_device();
     ctx->device = dev;
   }
-  const int max_iter = ctx->max_iter;
-
-  // pinned host mirrors
-  if (!ctx->h_flags) GS_CU(cudaMallocHost((void**)&ctx->h_flags, sizeof(DevFlags)), "cudaMallocHost");
-  if (!ctx->h_st)
-    GS_CU(cudaMallocHost((void**)&ctx->h_st, sizeof(IterState) * (max_iter + 2)), "cudaMallocHost");
-  GS_CU(ctx->flags.ensure(1), "alloc flags");
-  GS_CU(ctx->st.ensure(max_iter + 2), "alloc state");
-
-  // a0: key range, fixed-point window, finiteness
-  DevFlags* hf = ctx->h_flags;
-  std::memset(hf, 0, sizeof(DevFlags));
-  for (int a = 0; a < kMaxD; ++a) {
-    hf->min_ord[a] = INT64_MAX;
-    hf->max_ord[a] = INT64_MIN;
-  }
-  GS_CU(cudaMemcpyAsync(ctx->flags.p, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
-  GS_PH_BEGIN(GS_PHASE_RANGE);
-  GS_LAUNCH(launch_range(points, f32, n, d, ctx->flags.p, s), "k_range", 1);
-  GS_PH_END(GS_PHASE_RANGE);
-  GS_CU(cudaMemcpyAsync(hf, ctx->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
-  GS_CU(cudaStreamSynchronize(s), "sync range");
-  if (hf->bad) return fail(ctx, GS_E_INVALID, "non-finite input coordinate");
-
-  Plan P;
-  std::vector<int64_t> thr;
-  std::vector<uint64_t> dtab;
-  uint64_t span_prod = 0;
-  int total_bits = 0;
-  gs_status ps = make_plan(ctx, *hf, n, P, thr, dtab, span_prod, total_bits);
-  if (ps != GS_OK) return ps;
-
-  // upload face table and neighbour offsets through pinned staging
-  size_t words = thr.size() + dtab.size();
-  if (words > ctx->h_thr_cap) {
-    if (ctx->h_thr) cudaFreeHost(ctx->h_thr);
-    ctx->h_thr = nullptr;
-    ctx->h_thr_cap = 0;
-    GS_CU(cudaMallocHost((void**)&ctx->h_thr, sizeof(int64_t) * words), "cudaMallocHost");
-    ctx->h_thr_cap = words;
-  }
-  std::memcpy(ctx->h_thr, thr.data(), sizeof(int64_t) * thr.size());
-  std::memcpy(ctx->h_thr + thr.size(), dtab.data(), sizeof(uint64_t) * dtab.size());
-  GS_CU(ctx->thr.ensure(thr.size()), "alloc thr");
-  GS_CU(ctx->dtab.ensure(dtab.size()), "alloc dtab");
-  GS_CU(cudaMemcpyAsync(ctx->thr.p, ctx->h_thr, sizeof(int64_t) * thr.size(),
-                        cudaMemcpyHostToDevice, s), "H2D thr");
-  GS_CU(cudaMemcpyAsync(ctx->dtab.p, ctx->h_thr + thr.size(), sizeof(uint64_t) * dtab.size(),
-                        cudaMemcpyHostToDevice, s), "H2D dtab");
-
-  // i: binning into T0 (retried with a larger table if the cells overflow it)
-  GS_CU(ctx->slot0.ensure(n), "alloc slot0");
-  GS_CU(cudaMemsetAsync(ctx->st.p, 0, sizeof(IterState) * (max_iter + 2), s), "memset state");
-  uint64_t m_bound = (uint64_t)n < span_prod ? (uint64_t)n : span_prod;
-  uint32_t cap0 = pow2_at_least(2 * m_bound, 1024);
-  if (ctx->t0.cap > cap0 && ctx->t0.d == d) cap0 = ctx->t0.cap;
-  if (ctx->dirty) {
-    if (ctx->t0.cap) GS_CU(ctx->t0.clear(s), "clear T0");
-    if (ctx->tab[0].cap) GS_CU(ctx->tab[0].clear(s), "clear table A");
-    if (ctx->tab[1].cap) GS_CU(ctx->tab[1].clear(s), "clear table B");
-  }
-  ctx->dirty = true;
-  uint32_t m0 = 0;
-  for (int attempt = 0;; ++attempt) {
-    uint32_t maxcells = cap0 / 2;
-    GS_CU(ctx->t0.ensure(cap0, d, maxcells, s), "alloc T0");
-    GS_PH_BEGIN(GS_PHASE_BIN);
-    GS_LAUNCH(launch_bin(points, f32, n, P, ctx->thr.p, ctx->t0.view(), cap0 - 1, maxcells,
-                         ctx->slot0.p, ctx->flags.p, s), "k_bin", 1);
-    GS_PH_END(GS_PHASE_BIN);
-    GS_CU(cudaMemcpyAsync(hf, ctx->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
-    GS_CU(cudaStreamSynchronize(s), "sync bin");
-    const uint32_t regrow = kErrOverflow | kErrTableFull;
-    if (hf->err & ~regrow) {
-      ctx->t0.clear(s);
-      return fail(ctx, GS_E_INTERNAL, "binning hit a device bound (fixed-point window)");
-    }
-    if (!(hf->err & regrow)) {
-      m0 = hf->m0;
-      break;
-    }
-    if (attempt >= 4 || cap0 >= (1u << 31)) {
-      ctx->t0.clear(s);
-      return fail(ctx, GS_E_INTERNAL, "binning table overflow");
-    }
-    GS_CU(ctx->t0.clear(s), "clear T0");
-    cap0 <<= 2;
-    hf->err = 0;
-    hf->m0 = 0;
-    GS_CU(cudaMemcpyAsync(ctx->flags.p, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
-  }
-  inf.m0 = m0;
-
-  // workspace of the cell levels
-  uint32_t capAB = pow2_at_least(2ull * m0, 64);
-  GS_CU(ctx->tab[0].ensure(capAB, d, m0, s), "alloc table A");
-  GS_CU(ctx->tab[1].ensure(capAB, d, m0, s), "alloc table B");
-  GS_CU(ctx->cells[0].ensure(m0, d), "alloc cells");
-  GS_CU(ctx->cells[1].ensure(m0, d), "alloc cells");
-  GS_CU(ctx->sp.ensure((size_t)m0 * d), "alloc sp");
-  GS_CU(ctx->nkey.ensure(m0), "alloc nkey");
-  GS_CU(ctx->pslot.ensure(m0), "alloc pslot");
-  GS_CU(ctx->forest.ensure((size_t)m0 * (max_iter + 1)), "alloc forest");
-  GS_CU(ctx->forest2.ensure((size_t)m0 * (max_iter + 1)), "alloc forest");
-  GS_CU(ctx->labslot.ensure(cap0), "alloc labslot");
-  GS_CU(ctx->rank.ensure(m0), "alloc rank");
-
-  GS_PH_BEGIN(GS_PHASE_CELLS0);
-  GS_LAUNCH(launch_compact0(P, ctx->t0.view(), ctx->cells[0].view(), ctx->tab[0].view(), capAB,
-                            m0, ctx->st.p, ctx->flags.p, s), "k_compact0", 1);
-  GS_PH_END(GS_PHASE_CELLS0);
-
-  // ii-v: update steps
-  int t = 0;
-  uint32_t m_t = m0;
-  bool converged = false;
-  int64_t cell_iters = 0;
-  for (;;) {
-    Table G = ctx->tab[t & 1].view(), M = ctx->tab[(t + 1) & 1].view();
-    Cells c = ctx->cells[t & 1].view(), nx = ctx->cells[(t + 1) & 1].view();
-    GS_PH_BEGIN(GS_PHASE_GATHER);
-    GS_LAUNCH(launch_gather(P, ctx->thr.p, ctx->dtab.p, G, c, ctx->sp.p, ctx->nkey.p, ctx->st.p,
-                            t, m_t, ctx->flags.p, s), "k_gather", 1);
-    GS_PH_END(GS_PHASE_GATHER);
-    GS_CU(cudaMemcpyAsync(ctx->h_st + t, ctx->st.p + t, sizeof(IterState), cudaMemcpyDeviceToHost, s),
-          "D2H state");
-    GS_CU(cudaStreamSynchronize(s), "sync gather");
-    m_t = ctx->h_st[t].m;
-    if (!ctx->h_st[t].has_nb) {
-      converged = true;
-      break;
-    }
-    if (t == max_iter) break;
-    GS_PH_BEGIN(GS_PHASE_MERGE);
-    GS_LAUNCH(launch_merge(P, c, ctx->sp.p, ctx->nkey.p, M, ctx->pslot.p, ctx->st.p, t, m_t,
-                           ctx->flags.p, s), "k_merge", 1);
-    GS_LAUNCH(launch_compact(P, M, nx, ctx->st.p, t, m_t, ctx->flags.p, s), "k_compact", 1);
-    GS_LAUNCH(launch_finish(G, M, ctx->pslot.p, ctx->forest.p, ctx->st.p, t, m_t, s), "k_finish",
-              1);
-    GS_PH_END(GS_PHASE_MERGE);
-    cell_iters += m_t;
-    ++t;
-  }
-  const int T = t;
-  GS_PH_BEGIN(GS_PHASE_LABELS);
-  GS_LAUNCH(launch_final_level(ctx->tab[T & 1].view(), ctx->forest.p, ctx->st.p, T, m_t, s),
-            "k_final_level", 1);
-  GS_CU(cudaMemcpyAsync(ctx->h_st + T, ctx->st.p + T, sizeof(IterState), cudaMemcpyDeviceToHost, s),
-        "D2H state");
-  GS_CU(cudaStreamSynchronize(s), "sync final");
-  const uint32_t k = ctx->h_st[T].m;
-  const uint32_t baseT = ctx->h_st[T].base;
-  const uint32_t nodes = baseT + k;
-
-  // pointer jumping: every node reaches its final cell
-  uint32_t* root = ctx->forest.p;
-  uint32_t* other = ctx->forest2.p;
-  for (int hop = 1; hop < T; hop <<= 1) {
-    GS_LAUNCH(launch_jump(root, other, nodes, s), "k_jump", 1);
-    uint32_t* tmp = root;
-    root = other;
-    other = tmp;
-  }
-  // number the final cells by ascending key
-  Cells fin = ctx->cells[T & 1].view();
-  GS_CU(ctx->skey.ensure(k), "alloc sort");
-  GS_CU(ctx->skey2.ensure(k), "alloc sort");
-  GS_CU(ctx->sval.ensure(k), "alloc sort");
-  GS_CU(ctx->sval2.ensure(k), "alloc sort");
-  GS_CU(ctx->shist.ensure(radix_hist_words(k)), "alloc sort");
-  GS_LAUNCH(launch_iota_keys(fin, ctx->skey.p, ctx->sval.p, k, s), "k_iota_keys", 1);
-  GS_LAUNCH(radix_sort(ctx->skey.p, ctx->sval.p, ctx->skey2.p, ctx->sval2.p, ctx->shist.p, k,
-                       total_bits, s), "radix_sort", radix_sort_launches(k, total_bits));
-  GS_LAUNCH(launch_rank(ctx->sval.p, ctx->rank.p, k, s), "k_rank", 1);
-  GS_LAUNCH(launch_label_slots(ctx->t0.list.p, root, ctx->rank.p, baseT, ctx->labslot.p, m0, s),
-            "k_label_slots", 1);
-  GS_LAUNCH(launch_labels(ctx->slot0.p, ctx->labslot.p, labels, n, s), "k_labels", 1);
-  if ((int64_t)k <= modes_cap)
-    GS_LAUNCH(launch_modes(fin, ctx->rank.p, modes, k, d, s), "k_modes", 1);
-  GS_PH_END(GS_PHASE_LABELS);
-  GS_CU(cudaMemcpyAsync(hf, ctx->flags.p, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
-  GS_CU(cudaStreamSynchronize(s), "sync end");
-  if (hf->err) return fail(ctx, GS_E_INTERNAL, "an update step hit a device bound");
-  ctx->dirty = false;
-
+  FitArgs a;
+  a.d = ctx->d;
+  a.h = ctx->h;
+  a.max_iter = ctx->max_iter;
+  a.stream = ctx->stream;
+  a.points = points;
+  a.f32 = dtype == GS_IN_F32;
+  a.n = n;
+  a.labels = labels;
+  a.modes = modes;
+  a.modes_cap = modes_cap;
+  double kms[kLoopPhases] = {};
+  gs_status st = fit_pipeline(a, ctx->ws, ctx->timing ? &ctx->tm : nullptr, k_out, &inf, kms,
+                              &ctx->err);
+  if (info) *info = inf;
+  if (st != GS_OK && st != GS_E_CAPACITY) return st;
   if (ctx->timing) {
     for (size_t i = 0; i < ctx->tm.phase.size(); ++i) {
       float ms = 0.f;
-      GS_CU(cudaEventElapsedTime(&ms, ctx->tm.pool[2 * i], ctx->tm.pool[2 * i + 1]),
-            "cudaEventElapsedTime");
+      ce = cudaEventElapsedTime(&ms, ctx->tm.pool[2 * i], ctx->tm.pool[2 * i + 1]);
+      if (ce != cudaSuccess)
+        return fail(ctx, GS_E_CUDA, std::string("cudaEventElapsedTime: ") + cudaGetErrorName(ce));
       ctx->last_times.ms[ctx->tm.phase[i]] += ms;
       ctx->last_times.count[ctx->tm.phase[i]] += 1;
     }
+    for (int i = 0; i < kLoopPhases; ++i) {
+      ctx->last_times.ms[GS_PHASE_K_LEVEL0 + i] = kms[i];
+      ctx->last_times.count[GS_PHASE_K_LEVEL0 + i] = 1;
+    }
   }
-  inf.iterations = T;
-  inf.converged = converged ? 1 : 0;
-  inf.launches = ctx->launches;
-  inf.k = k;
-  inf.inexact = (int64_t)hf->inexact;
-  inf.cell_iters = cell_iters;
-  *k_out = k;
-  if (info) *info = inf;
-  if ((int64_t)k > modes_cap) return fail(ctx, GS_E_CAPACITY, "modes_cap < number of clusters");
-  return GS_OK;
+  return st;
 }
 
 }  // extern "C"

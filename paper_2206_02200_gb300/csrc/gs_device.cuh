@@ -185,23 +185,38 @@ __device__ __forceinline__ double round_fixed(u128 V, int L, unsigned& inexact) 
   return round_limbs<4>(w, L, neg, false, inexact);
 }
 
-// Round the exact quotient (N * 2^L) / D to float64 (D >= 1).
+// Round the exact quotient (N * 2^L) / D to float64 (D >= 1).  Long division
+// of N * 2^64 by D in 32-bit digits, from the top; once three digits below
+// the leading nonzero one are known (at least 65 quotient bits), the rest only
+// matters as a sticky bit: nonzero iff the partial remainder is.  Each digit
+// is estimated with a 64-bit reciprocal of D and corrected exactly.
 __device__ __forceinline__ double div_round(u128 N, uint32_t D, int L, unsigned& inexact) {
   bool neg = is_neg(N);
   u128 mag = neg ? (u128)0 - N : N;
-  // dividend = mag * 2^64, as six 32-bit limbs; long division by D
   uint32_t w[6] = {0u, 0u, (uint32_t)mag, (uint32_t)(mag >> 32), (uint32_t)(mag >> 64),
                    (uint32_t)(mag >> 96)};
-  uint32_t q[6];
+  uint32_t q[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  const uint64_t r = ~0ull / D;  // floor((2^64 - 1) / D) <= 2^64 / D
   uint64_t rem = 0;
+  int lead = -1;  // index of the leading nonzero quotient digit
+  bool sticky = false;
 #pragma unroll
   for (int k = 5; k >= 0; --k) {
-    uint64_t cur = (rem << 32) | w[k];
-    uint64_t qq = cur / D;
+    if (lead >= 0 && lead - k >= 3) {
+      sticky = sticky || w[k] != 0u;
+      continue;
+    }
+    uint64_t cur = (rem << 32) | w[k];  // cur < D * 2^32
+    uint64_t qq = __umul64hi(cur, r);  // qq <= cur / D < qq + 3
+    uint64_t rr = cur - qq * D;
+    if (rr >= D) { rr -= D; ++qq; }
+    if (rr >= D) { rr -= D; ++qq; }
     q[k] = (uint32_t)qq;
-    rem = cur - qq * D;
+    rem = rr;
+    if (lead < 0 && qq != 0) lead = k;
   }
-  return round_limbs<6>(q, L - 64, neg, rem != 0, inexact);
+  sticky = sticky || rem != 0;
+  return round_limbs<6>(q, L - 64, neg, sticky, inexact);
 }
 
 // Sum of four 64-bit limb accumulators (limb k holds a sum of 32-bit pieces of
@@ -230,16 +245,16 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
 
 // ---------------------------------------------------------------------------
 // Hash table over packed keys: open addressing, linear probing, capacity a
-// power of two.  The slot hash is the 64-bit finaliser of MurmurHash3
-// (Appleby, public domain).
+// power of two.  The home slot is Fibonacci (multiplicative) hashing: the top
+// log2(capacity) bits of key * 2^64/phi, which depend on every bit of the key.
 
-__device__ __forceinline__ uint64_t mix64(uint64_t k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
+__device__ __host__ __forceinline__ uint32_t home_slot(uint64_t key, uint32_t mask) {
+#ifdef __CUDA_ARCH__
+  const int b = __popc(mask);
+#else
+  const int b = __builtin_popcount(mask);
+#endif
+  return b == 0 ? 0u : (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - b));
 }
 
 // Longest probe sequence: an insert that finds no free slot within kMaxProbe
@@ -251,7 +266,7 @@ constexpr uint32_t kMaxProbe = 512;
 
 // Slot holding key, or kNone.
 __device__ __forceinline__ uint32_t table_find(const uint64_t* keys, uint32_t mask, uint64_t key) {
-  uint32_t s = (uint32_t)mix64(key) & mask;
+  uint32_t s = home_slot(key, mask);
   const uint32_t lim = mask < kMaxProbe ? mask + 1 : kMaxProbe;
   for (uint32_t i = 0; i < lim; ++i) {
     uint64_t k = keys[s];
@@ -266,7 +281,7 @@ __device__ __forceinline__ uint32_t table_find(const uint64_t* keys, uint32_t ma
 // Returns kNone (and sets kErrTableFull) when no free slot is found.
 __device__ __forceinline__ uint32_t table_insert(uint64_t* keys, uint32_t mask, uint64_t key,
                                                  bool& won, uint32_t* err) {
-  uint32_t s = (uint32_t)mix64(key) & mask;
+  uint32_t s = home_slot(key, mask);
   won = false;
   const uint32_t lim = mask < kMaxProbe ? mask + 1 : kMaxProbe;
   for (uint32_t i = 0; i < lim; ++i) {
@@ -295,16 +310,53 @@ __device__ __host__ __forceinline__ uint32_t mask_for(uint32_t m, uint32_t cap_m
 }
 
 // ---------------------------------------------------------------------------
-// Cell key of one coordinate: index j in [0, span) with thr[j] <= v < thr[j+1],
-// where thr[j] is the order code of the least double >= (kmin + j) * h.  This is
-// floor(v / h) - kmin of the exact quotient, decided with integer compares.
-__device__ __forceinline__ int key_index(const int64_t* __restrict__ thr, int span, int64_t v) {
+// Cell key of one coordinate: the index j in [0, span) with
+// thr[j] <= v < thr[j+1], where thr[j] is the order code of the least double
+// >= (kmin + j) * h.  That is floor(x / h) - kmin of the exact quotient,
+// decided by integer compares.  A float estimate of x / h gives the first
+// guess (at most a cell off while |x / h| < 2^20), a few steps correct it, and
+// a binary search settles anything further away.
+
+// float with the sign, exponent and leading 23 significand bits of a double
+// (0 for magnitudes below the float normal range, +-2^127 above it).
+__device__ __forceinline__ float approx_float(uint64_t b) {
+  uint32_t sign = (uint32_t)(b >> 63) << 31;
+  int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | (254u << 23));
+  return __uint_as_float(sign | ((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7FFFFF));
+}
+
+__device__ __forceinline__ int key_index_search(const int64_t* __restrict__ thr, int span,
+                                                int64_t v) {
   int lo = 0, hi = span - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (__ldg(&thr[mid]) <= v) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+__device__ __forceinline__ int key_index(const int64_t* __restrict__ thr, int span, int64_t kmin,
+                                         float inv_h, uint64_t bits) {
+  const int64_t v = ord_of_bits(bits);
+  const float g = approx_float(bits) * inv_h;
+  int idx = 0;
+  if (fabsf(g) < 4.0e15f) {
+    const long long q = __float2ll_rd(g) - kmin;
+    idx = q < 0 ? 0 : (q >= span ? span - 1 : (int)q);
+  }
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    if (idx > 0 && v < __ldg(&thr[idx])) {
+      --idx;
+    } else if (idx < span - 1 && v >= __ldg(&thr[idx + 1])) {
+      ++idx;
+    } else {
+      return idx;
+    }
+  }
+  return key_index_search(thr, span, v);
 }
 
 }  // namespace gs

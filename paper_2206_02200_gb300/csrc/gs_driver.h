@@ -1,0 +1,109 @@
+// gs_driver.h -- the host-side order of one GridShift run, shared by gs_fit
+// (growable workspace owned by a context) and gs_fit_noalloc (workspace carved
+// from a static device array).  Where the device buffers come from is the only
+// difference between the two, so it sits behind the Workspace interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gridshift.h"
+#include "gs_kernels.h"
+
+namespace gs {
+
+// Device views of every buffer one run uses.
+struct Bufs {
+  DevFlags* flags = nullptr;
+  IterState* st = nullptr;     // max_iter + 2 entries
+  LoopResult* res = nullptr;
+  GridBar* bar = nullptr;
+  int64_t* thr = nullptr;      // cell-face table
+  uint64_t* dtab = nullptr;    // neighbour offsets
+  uint32_t* slot0 = nullptr;   // n
+  Table t0{};                  // binning table
+  uint32_t t0_maxcells = 0;    // length of t0.list
+  Table tab[2]{};              // level tables, capacity capAB each, lists of m0
+  uint32_t capAB = 0;
+  Cells cells[2]{};            // m0 cells each
+  double* sp = nullptr;        // m0 x d
+  uint64_t* nkey = nullptr;    // m0
+  uint32_t* pslot = nullptr;   // m0
+  uint32_t* forest = nullptr;  // m0 * (max_iter + 1)
+  uint32_t* forest2 = nullptr; // m0 * (max_iter + 1)
+  uint32_t* labslot = nullptr; // t0.cap
+  uint32_t* rank = nullptr;    // m0
+  uint64_t* skey = nullptr;    // sort of k final keys (only when k > rank_max)
+  uint64_t* skey2 = nullptr;
+  uint32_t* sval = nullptr;
+  uint32_t* sval2 = nullptr;
+  uint32_t* shist = nullptr;   // radix_hist_words(k)
+};
+
+// Source of the device buffers and host staging of one run.  Each method
+// returns GS_OK or an error status (setting *err where it has text).
+class Workspace {
+ public:
+  virtual ~Workspace() = default;
+  // Host mirrors of DevFlags and LoopResult (pinned where the workspace can).
+  virtual DevFlags* host_flags() = 0;
+  virtual LoopResult* host_result() = 0;
+  // Host staging of `words` 64-bit words for the face and offset tables.
+  virtual gs_status host_words(size_t words, int64_t** out, std::string* err) = 0;
+  // b.flags (needed before the plan).
+  virtual gs_status begin(Bufs& b, std::string* err) = 0;
+  // Everything up to and including binning, for n points, a face table of
+  // thr_words entries, 3^d offsets, and a binning table for at most m_bound
+  // cells (load factor <= 1/2).  Tables handed out are clean (keys empty,
+  // counts and sums zero).
+  virtual gs_status prepare(int64_t n, int d, int max_iter, size_t thr_words, int nprobe,
+                            uint64_t m_bound, cudaStream_t s, Bufs& b, std::string* err) = 0;
+  // Binning found more cells than b.t0 holds: a larger clean table in b.t0
+  // (and b.t0_maxcells), or an error.
+  virtual gs_status regrow_bin(int d, cudaStream_t s, Bufs& b, std::string* err) = 0;
+  // Workspace of the cell levels for m0 initial cells.
+  virtual gs_status levels(uint32_t m0, int d, int max_iter, cudaStream_t s, Bufs& b,
+                           std::string* err) = 0;
+  // Sort buffers for k final cells.
+  virtual gs_status sort_space(uint32_t k, Bufs& b, std::string* err) = 0;
+  // The run stopped before the kernels returned every table to clean.
+  virtual void mark_dirty(bool dirty) = 0;
+};
+
+// Optional per-phase CUDA-event timing of a run.
+class EventTimer {
+ public:
+  virtual ~EventTimer() = default;
+  virtual cudaError_t begin(int phase, cudaStream_t s) = 0;
+  virtual cudaError_t end(cudaStream_t s) = 0;
+};
+
+struct FitArgs {
+  int d;
+  double h;
+  int max_iter;
+  cudaStream_t stream;
+  const void* points;
+  bool f32;
+  int64_t n;  // >= 1
+  int32_t* labels;
+  double* modes;
+  int64_t modes_cap;
+};
+
+// Runs GridShift end to end on the workspace.  Fills *k_out and *info
+// (statistics and in-kernel phase times) and returns a status; err receives a
+// description of any error (may be null).
+gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64_t* k_out,
+                       gs_fit_info* info, double* inkernel_ms, std::string* err);
+
+// Largest number of final cells numbered inside the loop kernel; more are
+// numbered by a radix sort of their keys.
+constexpr uint32_t kRankMax = 16384;
+
+// Host helpers shared by the entry points.
+uint32_t pow2_at_least(uint64_t v, uint32_t lo);
+
+}  // namespace gs

@@ -10,7 +10,8 @@ namespace gs {
 
 // A hash table of packed cell keys with per-slot payload.  key[] is kEmpty
 // where free; cnt[] and acc[] (d x 4 limb accumulators per slot) are zero
-// where free.  list[i] is the slot of the i-th key inserted (in arrival order).
+// where free.  list[i] is the slot of the i-th key inserted (in arrival
+// order); id[] maps a slot to the cell that owns it.
 struct Table {
   uint64_t* key;
   uint32_t* id;
@@ -21,11 +22,42 @@ struct Table {
 };
 
 // The active cells of one level: packed key, resident count and coordinate
-// sum (row-major m x d, float64).
+// sum.  The sum is the float64 value of Sec. 2.1 (exact sum rounded once),
+// held as the two's-complement 128-bit integer it equals in units of 2^L_a
+// (fix[j * d + a] = {low word, high word}).
 struct Cells {
   uint64_t* key;
   uint32_t* cnt;
-  double* cs;
+  ulonglong2* fix;
+};
+
+// Everything the persistent update loop reads and writes.
+struct LoopArgs {
+  Plan P;
+  const int64_t* thr;    // cell-face table (order codes)
+  const uint64_t* dtab;  // packed-key offsets of the 3^d neighbours
+  Table T0;              // binning table (its slots are the points' cell slots)
+  Table tab[2];          // lookup/merge tables of alternate levels
+  uint32_t capAB;        // capacity of tab[0], tab[1]
+  Cells cells[2];        // cells of alternate levels
+  double* sp;            // new centroids of the current level (m x d)
+  uint64_t* nkey;        // new packed keys of the current level
+  uint32_t* pslot;       // merge-table slot of every cell of the current level
+  uint32_t* forest;      // parent of every cell of every level, then its final cell
+  uint32_t* forest2;     // pointer-jumping buffer
+  uint32_t* labslot;     // label of every binning slot
+  uint32_t* rank;        // label of every final cell
+  const uint32_t* slot0;  // binning slot of every point
+  int32_t* labels;        // output: label of every point
+  int64_t n;
+  double* modes;          // output: k x d modes (written if k <= modes_cap)
+  int64_t modes_cap;
+  IterState* st;          // max_iter + 2 levels, zeroed by the host
+  DevFlags* fl;
+  GridBar* bar;           // zeroed by the host
+  LoopResult* res;
+  int max_iter;
+  uint32_t rank_max;      // largest k numbered inside the loop kernel
 };
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
@@ -33,30 +65,22 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
                        Table T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, cudaStream_t s);
-cudaError_t launch_compact0(const Plan& P, Table T0, Cells c0, Table A, uint32_t capA,
-                            uint32_t m0_bound, IterState* st, DevFlags* fl, cudaStream_t s);
-cudaError_t launch_gather(const Plan& P, const int64_t* thr, const uint64_t* dtab, Table G,
-                          Cells c, double* sp, uint64_t* nkey, IterState* st, int t,
-                          uint32_t m_bound, DevFlags* fl, cudaStream_t s);
-cudaError_t launch_merge(const Plan& P, Cells c, const double* sp, const uint64_t* nkey,
-                         Table M, uint32_t* pslot, IterState* st, int t, uint32_t m_bound,
-                         DevFlags* fl, cudaStream_t s);
-cudaError_t launch_compact(const Plan& P, Table M, Cells next, IterState* st, int t,
-                           uint32_t m_bound, DevFlags* fl, cudaStream_t s);
-cudaError_t launch_finish(Table G, Table M, const uint32_t* pslot, uint32_t* forest,
-                          IterState* st, int t, uint32_t m_bound, cudaStream_t s);
-cudaError_t launch_final_level(Table G, uint32_t* forest, IterState* st, int T,
-                               uint32_t m_bound, cudaStream_t s);
-cudaError_t launch_jump(const uint32_t* in, uint32_t* out, uint32_t nodes, cudaStream_t s);
+
+// Blocks of the cooperative loop kernel for dimension d on the current device
+// (all co-resident), or a negative value on error.
+int loop_grid(int d);
+// Steps ii-v for every level, then labels and modes (Sec. 2.1, Algorithm 1),
+// in one cooperative launch of `grid` blocks.
+cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s);
+
+// Numbering of the final cells when k > rank_max: labels of the final cells
+// from the sorted order (sorted_vals[p] = cell of rank p), then labels and
+// modes.  forest holds the final cell of every initial cell.
 cudaError_t launch_iota_keys(Cells c, uint64_t* keys, uint32_t* vals, uint32_t k,
                              cudaStream_t s);
 cudaError_t launch_rank(const uint32_t* sorted_vals, uint32_t* rank, uint32_t k, cudaStream_t s);
-cudaError_t launch_label_slots(const uint32_t* list0, const uint32_t* root, const uint32_t* rank,
-                               uint32_t baseT, uint32_t* labslot, uint32_t m0, cudaStream_t s);
-cudaError_t launch_labels(const uint32_t* slot0, const uint32_t* labslot, int32_t* labels,
-                          int64_t n, cudaStream_t s);
-cudaError_t launch_modes(Cells c, const uint32_t* rank, double* modes, uint32_t k, int d,
-                         cudaStream_t s);
+cudaError_t launch_label_tail(const LoopArgs& a, uint32_t m0, uint32_t k, uint32_t baseT, int T,
+                              cudaStream_t s);
 
 // Stable LSD radix sort of (key, val) pairs by key bits [0, nbits).  keys/vals
 // hold the input and receive the output; tkeys/tvals are scratch of the same

@@ -1,13 +1,14 @@
-// gs_noalloc.cu -- gs_fit_noalloc: the GridShift pipeline of gs_fit with every
+// gs_noalloc.cu -- gs_fit_noalloc: the GridShift run of gs_fit with every
 // piece of device scratch carved out of one file-scope static device array, for
 // callers that must not allocate device or pinned memory (see the declaration
-// in include/gridshift.h).  The kernels are the ones gs_fit launches.
+// in include/gridshift.h).  The steps and kernels are the ones gs_fit runs
+// (gs_driver.cu); only the source of the buffers differs.
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
 #include "../../include/gridshift.h"
-#include "gs_kernels.h"
+#include "gs_driver.h"
 
 using namespace gs;
 
@@ -20,48 +21,14 @@ constexpr size_t kScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-constexpr int kThrMax = 8192;  // face-table entries (sum over axes of span + 1)
-constexpr int kProbeMax = 6561;  // 3^8 neighbour offsets
+constexpr size_t kThrMax = 8192;   // face-table entries (sum over axes of span + 1)
+constexpr size_t kProbeMax = 6561; // 3^8 neighbour offsets
 
 std::mutex g_mu;  // serialises calls: they share g_scratch and the host buffers below
 unsigned char* g_dev_ptr[kMaxDevices] = {};
-int64_t g_thr[kThrMax];
-uint64_t g_dtab[kProbeMax];
-
-int64_t ord_of(double x) {
-  if (x == 0.0) x = 0.0;
-  int64_t s;
-  std::memcpy(&s, &x, 8);
-  return s ^ ((s >> 63) & 0x7FFFFFFFFFFFFFFFll);
-}
-
-double from_ord(int64_t o) {
-  int64_t s = o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll);
-  double x;
-  std::memcpy(&x, &s, 8);
-  return x;
-}
-
-// Least double >= q * h: the rounding error of q * h is exact under one fma.
-double face(int64_t q, double h) {
-  double qd = (double)q;
-  double p = qd * h;
-  if (std::fma(qd, h, -p) > 0) p = std::nextafter(p, INFINITY);
-  return p;
-}
-
-int64_t floor_div(double x, double h) {
-  int64_t q = (int64_t)std::floor(x / h);
-  for (int i = 0; i < 4 && face(q, h) > x; ++i) --q;
-  for (int i = 0; i < 4 && face(q + 1, h) <= x; ++i) ++q;
-  return q;
-}
-
-int bitlen(uint64_t v) {
-  int b = 0;
-  for (; v; v >>= 1) ++b;
-  return b;
-}
+int64_t g_words[kThrMax + kProbeMax];
+DevFlags g_hflags;
+LoopResult g_hres;
 
 // Bump allocator over the static scratch (256-byte aligned pieces).
 struct Carve {
@@ -69,27 +36,10 @@ struct Carve {
   size_t used = 0;
   template <typename T>
   T* take(size_t count) {
-    size_t off = (used + 255) & ~size_t(255);
+    const size_t off = (used + 255) & ~size_t(255);
     used = off + count * sizeof(T);
     return reinterpret_cast<T*>(base + off);
   }
-};
-
-// Views of every workspace array of one call, for at most M cells (lookup
-// tables of 2M slots) and n points.
-struct Work {
-  DevFlags* flags;
-  IterState* st;
-  int64_t* thr;
-  uint64_t* dtab;
-  uint32_t* slot0;
-  Table t0, tab[2];
-  Cells cells[2];
-  double* sp;
-  uint64_t* nkey;
-  uint32_t *pslot, *forest, *forest2, *labslot, *rank;
-  uint64_t *skey, *skey2;
-  uint32_t *sval, *sval2, *shist;
 };
 
 Table carve_table(Carve& c, uint32_t cap, uint32_t lmax, int d) {
@@ -103,37 +53,43 @@ Table carve_table(Carve& c, uint32_t cap, uint32_t lmax, int d) {
   return t;
 }
 
-size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, int thr_words,
-              int nprobe, Work* w) {
+// Lays out every buffer of one run for at most M cells (tables of 2M slots)
+// and n points from `base` (null: sizes only); returns the bytes used.
+size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, size_t thr_words,
+              int nprobe, Bufs* out) {
   Carve c{base};
-  Work tmp;
-  Work& W = w ? *w : tmp;
+  Bufs tmp;
+  Bufs& B = out ? *out : tmp;
   const uint32_t cap = 2 * M;
-  W.flags = c.take<DevFlags>(1);
-  W.st = c.take<IterState>(max_iter + 2);
-  W.thr = c.take<int64_t>(thr_words);
-  W.dtab = c.take<uint64_t>(nprobe);
-  W.slot0 = c.take<uint32_t>(n);
-  W.t0 = carve_table(c, cap, M, d);
-  W.tab[0] = carve_table(c, cap, M, d);
-  W.tab[1] = carve_table(c, cap, M, d);
-  for (int b = 0; b < 2; ++b) {
-    W.cells[b].key = c.take<uint64_t>(M);
-    W.cells[b].cnt = c.take<uint32_t>(M);
-    W.cells[b].cs = c.take<double>((size_t)M * d);
+  B.flags = c.take<DevFlags>(1);
+  B.st = c.take<IterState>(max_iter + 2);
+  B.res = c.take<LoopResult>(1);
+  B.bar = c.take<GridBar>(1);
+  B.thr = c.take<int64_t>(thr_words);
+  B.dtab = c.take<uint64_t>(nprobe);
+  B.slot0 = c.take<uint32_t>(n);
+  B.t0 = carve_table(c, cap, M, d);
+  B.t0_maxcells = M;
+  B.tab[0] = carve_table(c, cap, M, d);
+  B.tab[1] = carve_table(c, cap, M, d);
+  B.capAB = cap;
+  for (int i = 0; i < 2; ++i) {
+    B.cells[i].key = c.take<uint64_t>(M);
+    B.cells[i].cnt = c.take<uint32_t>(M);
+    B.cells[i].fix = c.take<ulonglong2>((size_t)M * d);
   }
-  W.sp = c.take<double>((size_t)M * d);
-  W.nkey = c.take<uint64_t>(M);
-  W.pslot = c.take<uint32_t>(M);
-  W.forest = c.take<uint32_t>((size_t)M * (max_iter + 1));
-  W.forest2 = c.take<uint32_t>((size_t)M * (max_iter + 1));
-  W.labslot = c.take<uint32_t>(cap);
-  W.rank = c.take<uint32_t>(M);
-  W.skey = c.take<uint64_t>(M);
-  W.skey2 = c.take<uint64_t>(M);
-  W.sval = c.take<uint32_t>(M);
-  W.sval2 = c.take<uint32_t>(M);
-  W.shist = c.take<uint32_t>(radix_hist_words(M));
+  B.sp = c.take<double>((size_t)M * d);
+  B.nkey = c.take<uint64_t>(M);
+  B.pslot = c.take<uint32_t>(M);
+  B.forest = c.take<uint32_t>((size_t)M * (max_iter + 1));
+  B.forest2 = c.take<uint32_t>((size_t)M * (max_iter + 1));
+  B.labslot = c.take<uint32_t>(cap);
+  B.rank = c.take<uint32_t>(M);
+  B.skey = c.take<uint64_t>(M);
+  B.skey2 = c.take<uint64_t>(M);
+  B.sval = c.take<uint32_t>(M);
+  B.sval2 = c.take<uint32_t>(M);
+  B.shist = c.take<uint32_t>(radix_hist_words(M));
   return c.used;
 }
 
@@ -144,177 +100,56 @@ cudaError_t clear_table(const Table& t, int d, cudaStream_t s) {
   return e;
 }
 
-gs_status run(int d, double h, int max_iter, cudaStream_t s, const void* points, bool f32,
-              int64_t n, int32_t* labels, double* modes, int64_t modes_cap, int64_t* k_out,
-              gs_fit_info* inf, unsigned char* base) {
-#define NA_CU(call)                                                           \
-  do {                                                                        \
-    cudaError_t e_ = (call);                                                  \
-    if (e_ != cudaSuccess)                                                    \
-      return e_ == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA;        \
-  } while (0)
-#define NA_LAUNCH(call, nk) \
-  do {                      \
-    NA_CU(call);            \
-    inf->launches += (nk);  \
-  } while (0)
+// The workspace of one call: everything is laid out at once in prepare(), for
+// the largest cell bound that fits; nothing is allocated.
+struct StaticWorkspace : public Workspace {
+  unsigned char* base;
+  Bufs laid;
+  explicit StaticWorkspace(unsigned char* b) : base(b) {}
 
-  // a0: key range, fixed-point window, finiteness (the flags live at the
-  // start of the scratch; their host copy is plain stack memory)
-  DevFlags hf;
-  std::memset(&hf, 0, sizeof(hf));
-  for (int a = 0; a < kMaxD; ++a) {
-    hf.min_ord[a] = INT64_MAX;
-    hf.max_ord[a] = INT64_MIN;
+  DevFlags* host_flags() override { return &g_hflags; }
+  LoopResult* host_result() override { return &g_hres; }
+  gs_status host_words(size_t words, int64_t** out, std::string*) override {
+    if (words > kThrMax + kProbeMax) return GS_E_SCRATCH;
+    *out = g_words;
+    return GS_OK;
   }
-  DevFlags* dflags = reinterpret_cast<DevFlags*>(base);
-  NA_CU(cudaMemcpyAsync(dflags, &hf, sizeof(hf), cudaMemcpyHostToDevice, s));
-  NA_LAUNCH(launch_range(points, f32, n, d, dflags, s), 1);
-  NA_CU(cudaMemcpyAsync(&hf, dflags, sizeof(hf), cudaMemcpyDeviceToHost, s));
-  NA_CU(cudaStreamSynchronize(s));
-  if (hf.bad) return GS_E_INVALID;
-
-  // plan: packed keys, face table, fixed-point windows
-  Plan P;
-  std::memset(&P, 0, sizeof(P));
-  P.d = d;
-  int bits[kMaxD];
-  int clog2n = 0;
-  while ((1ll << clog2n) < n) ++clog2n;
-  uint64_t span_prod = 1;
-  int thr_words = 0;
-  for (int a = 0; a < d; ++a) {
-    double lo = from_ord(hf.min_ord[a]), hi = from_ord(hf.max_ord[a]);
-    if (!(std::fabs(lo / h) < 4.0e15) || !(std::fabs(hi / h) < 4.0e15)) return GS_E_KEYRANGE;
-    int64_t kmin = floor_div(lo, h) - 1, kmax = floor_div(hi, h) + 1;
-    int64_t span = kmax - kmin + 1;
-    if (span > (1ll << 22)) return GS_E_KEYRANGE;
-    if (thr_words + span + 1 > kThrMax) return GS_E_SCRATCH;
-    P.kmin[a] = kmin;
-    P.span[a] = (int)span;
-    bits[a] = bitlen((uint64_t)span + 1);
-    P.thr_off[a] = thr_words;
-    for (int64_t j = 0; j <= span; ++j) g_thr[thr_words++] = ord_of(face(kmin + j, h));
-    span_prod = span_prod > (1ull << 40) ? span_prod : span_prod * (uint64_t)span;
-    double ma;
-    uint64_t mb = hf.maxabs[a];
-    std::memcpy(&ma, &mb, 8);
-    int e = 0;
-    if (ma > 0) std::frexp(ma, &e);
-    P.L[a] = e + clog2n - 126;
+  gs_status begin(Bufs& b, std::string*) override {
+    b.flags = reinterpret_cast<DevFlags*>(base);  // where layout() puts them
+    return GS_OK;
   }
-  int total_bits = 0;
-  for (int a = d - 1; a >= 0; --a) {
-    P.off[a] = total_bits;
-    total_bits += bits[a];
+  gs_status prepare(int64_t n, int d, int max_iter, size_t thr_words, int nprobe,
+                    uint64_t m_bound, cudaStream_t s, Bufs& b, std::string*) override {
+    if (thr_words > kThrMax || (size_t)nprobe > kProbeMax) return GS_E_SCRATCH;
+    // the largest cell bound M (a power of two, at most what the data can
+    // need) whose workspace fits the scratch
+    uint32_t M = 64;
+    while (M < m_bound && M < (1u << 30)) M <<= 1;
+    while (M > 64 && layout(nullptr, n, d, max_iter, M, thr_words, nprobe, nullptr) > kScratchBytes)
+      M >>= 1;
+    if (layout(nullptr, n, d, max_iter, M, thr_words, nprobe, nullptr) > kScratchBytes)
+      return GS_E_SCRATCH;
+    layout(base, n, d, max_iter, M, thr_words, nprobe, &laid);
+    // the scratch keeps the previous call's contents: clear what must start
+    // empty or zero
+    if (clear_table(laid.t0, d, s) != cudaSuccess || clear_table(laid.tab[0], d, s) != cudaSuccess ||
+        clear_table(laid.tab[1], d, s) != cudaSuccess)
+      return GS_E_CUDA;
+    b = laid;
+    return GS_OK;
   }
-  if (total_bits > 63) return GS_E_KEYRANGE;
-  int np = 1;
-  for (int a = 0; a < d; ++a) np *= 3;
-  P.nprobe = np;
-  P.center = (np - 1) / 2;
-  for (int p = 0; p < np; ++p) {
-    int64_t delta = 0;
-    int rest = p;
-    for (int a = d - 1; a >= 0; --a) {
-      int v = rest % 3 - 1;
-      rest /= 3;
-      delta += (int64_t)v * (int64_t)(1ull << P.off[a]);
-    }
-    g_dtab[p] = (uint64_t)delta;
+  gs_status regrow_bin(int, cudaStream_t, Bufs&, std::string*) override { return GS_E_SCRATCH; }
+  gs_status levels(uint32_t m0, int, int, cudaStream_t, Bufs& b, std::string*) override {
+    if (m0 > laid.t0_maxcells) return GS_E_SCRATCH;
+    b = laid;
+    return GS_OK;
   }
-
-  // the largest cell bound M (a power of two) whose workspace fits the scratch
-  uint64_t want = (uint64_t)n < span_prod ? (uint64_t)n : span_prod;
-  uint32_t M = 64;
-  while (M < want && M < (1u << 30)) M <<= 1;
-  while (M > 64 && layout(nullptr, n, d, max_iter, M, thr_words, np, nullptr) > kScratchBytes)
-    M >>= 1;
-  if (layout(nullptr, n, d, max_iter, M, thr_words, np, nullptr) > kScratchBytes)
-    return GS_E_SCRATCH;
-  Work W;
-  layout(base, n, d, max_iter, M, thr_words, np, &W);
-
-  // clear what must start at zero: the scratch keeps the previous call's contents
-  NA_CU(cudaMemcpyAsync(W.thr, g_thr, sizeof(int64_t) * thr_words, cudaMemcpyHostToDevice, s));
-  NA_CU(cudaMemcpyAsync(W.dtab, g_dtab, sizeof(uint64_t) * np, cudaMemcpyHostToDevice, s));
-  NA_CU(cudaMemsetAsync(W.st, 0, sizeof(IterState) * (max_iter + 2), s));
-  NA_CU(clear_table(W.t0, d, s));
-  NA_CU(clear_table(W.tab[0], d, s));
-  NA_CU(clear_table(W.tab[1], d, s));
-  hf.err = 0;
-  hf.m0 = 0;
-  NA_CU(cudaMemcpyAsync(W.flags, &hf, sizeof(hf), cudaMemcpyHostToDevice, s));
-
-  // i: binning (at most M cells fit)
-  NA_LAUNCH(launch_bin(points, f32, n, P, W.thr, W.t0, 2 * M - 1, M, W.slot0, W.flags, s), 1);
-  NA_CU(cudaMemcpyAsync(&hf, W.flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
-  NA_CU(cudaStreamSynchronize(s));
-  if (hf.err & (kErrOverflow | kErrTableFull)) return GS_E_SCRATCH;
-  if (hf.err) return GS_E_INTERNAL;
-  const uint32_t m0 = hf.m0;
-  inf->m0 = m0;
-  NA_LAUNCH(launch_compact0(P, W.t0, W.cells[0], W.tab[0], 2 * M, m0, W.st, W.flags, s), 1);
-
-  // ii-v: update steps
-  IterState hs;
-  int t = 0;
-  uint32_t m_t = m0;
-  bool converged = false;
-  for (;;) {
-    Table G = W.tab[t & 1], Mt = W.tab[(t + 1) & 1];
-    Cells c = W.cells[t & 1], nx = W.cells[(t + 1) & 1];
-    NA_LAUNCH(launch_gather(P, W.thr, W.dtab, G, c, W.sp, W.nkey, W.st, t, m_t, W.flags, s), 1);
-    NA_CU(cudaMemcpyAsync(&hs, W.st + t, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    NA_CU(cudaStreamSynchronize(s));
-    m_t = hs.m;
-    if (!hs.has_nb) {
-      converged = true;
-      break;
-    }
-    if (t == max_iter) break;
-    NA_LAUNCH(launch_merge(P, c, W.sp, W.nkey, Mt, W.pslot, W.st, t, m_t, W.flags, s), 1);
-    NA_LAUNCH(launch_compact(P, Mt, nx, W.st, t, m_t, W.flags, s), 1);
-    NA_LAUNCH(launch_finish(G, Mt, W.pslot, W.forest, W.st, t, m_t, s), 1);
-    inf->cell_iters += m_t;
-    ++t;
+  gs_status sort_space(uint32_t, Bufs& b, std::string*) override {
+    b = laid;
+    return GS_OK;
   }
-  const int T = t;
-  NA_LAUNCH(launch_final_level(W.tab[T & 1], W.forest, W.st, T, m_t, s), 1);
-  NA_CU(cudaMemcpyAsync(&hs, W.st + T, sizeof(hs), cudaMemcpyDeviceToHost, s));
-  NA_CU(cudaStreamSynchronize(s));
-  const uint32_t k = hs.m, baseT = hs.base, nodes = baseT + k;
-
-  // labels and modes
-  uint32_t* root = W.forest;
-  uint32_t* other = W.forest2;
-  for (int hop = 1; hop < T; hop <<= 1) {
-    NA_LAUNCH(launch_jump(root, other, nodes, s), 1);
-    uint32_t* tmp = root;
-    root = other;
-    other = tmp;
-  }
-  Cells fin = W.cells[T & 1];
-  NA_LAUNCH(launch_iota_keys(fin, W.skey, W.sval, k, s), 1);
-  NA_LAUNCH(radix_sort(W.skey, W.sval, W.skey2, W.sval2, W.shist, k, total_bits, s),
-            radix_sort_launches(k, total_bits));
-  NA_LAUNCH(launch_rank(W.sval, W.rank, k, s), 1);
-  NA_LAUNCH(launch_label_slots(W.t0.list, root, W.rank, baseT, W.labslot, m0, s), 1);
-  NA_LAUNCH(launch_labels(W.slot0, W.labslot, labels, n, s), 1);
-  if ((int64_t)k <= modes_cap) NA_LAUNCH(launch_modes(fin, W.rank, modes, k, d, s), 1);
-  NA_CU(cudaMemcpyAsync(&hf, W.flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
-  NA_CU(cudaStreamSynchronize(s));
-  if (hf.err) return GS_E_INTERNAL;
-  inf->iterations = T;
-  inf->converged = converged ? 1 : 0;
-  inf->k = k;
-  inf->inexact = (int64_t)hf.inexact;
-  *k_out = k;
-  if ((int64_t)k > modes_cap) return GS_E_CAPACITY;
-  return GS_OK;
-#undef NA_CU
-#undef NA_LAUNCH
-}
+  void mark_dirty(bool) override {}
+};
 
 }  // namespace
 
@@ -351,8 +186,19 @@ extern "C" gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_st
     g_dev_ptr[dev] = static_cast<unsigned char*>(p);
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  gs_status st = run(d, h, max_iter, s, points, dtype == GS_IN_F32, n, labels, modes, modes_cap,
-                     k_out, &inf, g_dev_ptr[dev]);
+  FitArgs a;
+  a.d = d;
+  a.h = h;
+  a.max_iter = max_iter;
+  a.stream = s;
+  a.points = points;
+  a.f32 = dtype == GS_IN_F32;
+  a.n = n;
+  a.labels = labels;
+  a.modes = modes;
+  a.modes_cap = modes_cap;
+  StaticWorkspace ws(g_dev_ptr[dev]);
+  gs_status st = fit_pipeline(a, ws, nullptr, k_out, &inf, nullptr, nullptr);
   // no work of this call may still run when the next one reuses the scratch
   if (st != GS_OK) cudaStreamSynchronize(s);
   if (info) *info = inf;

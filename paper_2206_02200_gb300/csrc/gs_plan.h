@@ -1,5 +1,5 @@
-// gs_plan.h -- per-call parameters shared by the host driver and the kernels
-// (plain C++ structs, passed to kernels by value).
+// gs_plan.h -- per-call parameters and device-resident state shared by the host
+// driver and the kernels (plain structs, passed to kernels by value).
 #pragma once
 
 #include <cstdint>
@@ -12,6 +12,7 @@ constexpr int kMaxD = 8;
 constexpr uint32_t kErrTableFull = 1u;  // a hash table ran out of free slots
 constexpr uint32_t kErrOverflow = 2u;   // more cells than the cell arrays hold
 constexpr uint32_t kErrWindow = 4u;     // a value above the fixed-point window
+constexpr uint32_t kErrBarrier = 8u;    // a grid barrier wait gave up (time limit)
 
 // How integer cell keys (Sec. 2.1 i: floor(x / h) per coordinate) are packed
 // into one 64-bit word, and how sums are held in fixed point.
@@ -24,9 +25,10 @@ struct Plan {
   int thr_off[kMaxD];       // start of axis a's face table in the threshold array
   int L[kMaxD];             // fixed-point unit 2^L of axis a
   int64_t kmin[kMaxD];      // smallest key of axis a
+  float inv_h;              // 1/h rounded to float: first guess of a cell index only
 };
 
-// Device-resident state of one update step t (Sec. 2.1 ii-iv).
+// Device-resident state of one level t (the cells before update step t).
 struct IterState {
   uint32_t m;       // active cells at level t
   uint32_t mask;    // capacity mask of the lookup table of level t
@@ -43,6 +45,31 @@ struct DevFlags {
   long long min_ord[kMaxD];     // order code of min_i x_ia
   long long max_ord[kMaxD];     // order code of max_i x_ia
   unsigned long long maxabs[kMaxD];  // bits of max_i |x_ia|
+};
+
+// Segments of the loop kernel timed on the device clock by block 0 (between
+// grid barriers): level 0, gather (+ parent links), merge, compact, labels.
+constexpr int kLoopPhases = 5;
+
+// What the update loop reports back (written by one thread at its end).
+struct LoopResult {
+  int32_t iterations;   // update steps applied
+  int32_t converged;    // 1: stopped by the criterion of Sec. 2.1 v
+  uint32_t k;           // final cells
+  uint32_t base;        // first forest node of the final level
+  uint32_t need_sort;   // 1: k too large for the in-loop numbering; labels not written
+  uint32_t pad;
+  unsigned long long cell_iters;  // sum of m_t over applied updates
+  unsigned long long ns[kLoopPhases];  // nanoseconds spent in each segment
+};
+
+// Arrival counter and generation of a software grid barrier, and the stop
+// decision its last arrival takes for every block (any error bit set).
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  unsigned int stop;
+  unsigned int pad;
 };
 
 }  // namespace gs

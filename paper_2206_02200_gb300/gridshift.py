@@ -35,8 +35,10 @@ EXPORTS = ("gs_create", "gs_set_precision", "gs_set_stream", "gs_fit", "gs_set_t
            "gs_get_phase_times", "gs_fit_noalloc", "gs_get_last_error", "gs_status_string",
            "gs_destroy")
 
-#: gs_phase names, in enum order
-PHASES = ("range", "bin", "cells0", "gather", "merge", "labels")
+#: gs_phase names, in enum order: CUDA-event phases, then the loop kernel's
+#: own device-clock split
+PHASES = ("range", "bin", "loop", "sort", "k_level0", "k_gather", "k_merge", "k_compact",
+          "k_labels")
 
 
 class gs_fit_info(ctypes.Structure):

@@ -150,6 +150,36 @@ def test_gmm_1M_d6():
 
 
 # ---------------------------------------------------------------------------
+# more clusters than the loop kernel numbers itself (16384): the final cells
+# are numbered by a radix sort of their keys instead
+
+
+def _lattice_pairs(side: int, with_partner: bool):
+    """side x side sites 4 cells apart; with_partner adds a point in the next
+    cell along axis 0, so each pair merges in one update."""
+    i, j = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
+    base = np.stack([4.0 * i.ravel() + 0.5, 4.0 * j.ravel() + 0.5], 1)
+    if not with_partner:
+        return base
+    return np.concatenate([base, base + np.array([1.0, 0.0])], 0)
+
+
+def test_many_clusters_numbered_by_sort():
+    X = _lattice_pairs(150, with_partner=False)          # 22500 isolated cells, 0 updates
+    ref, info = check_parity(X, 1.0)
+    assert ref["k"] == 22500 and ref["iterations"] == 0
+    X = _lattice_pairs(150, with_partner=True)           # 45000 cells merge into 22500
+    ref, info = check_parity(X, 1.0)
+    assert ref["k"] == 22500 and ref["iterations"] == 1
+
+
+def test_cluster_count_at_the_numbering_threshold():
+    for side in (127, 128, 129):                         # k = 16129, 16384, 16641
+        ref, info = check_parity(_lattice_pairs(side, with_partner=True), 1.0)
+        assert ref["k"] == side * side
+
+
+# ---------------------------------------------------------------------------
 # edge cases and errors
 
 
