@@ -87,21 +87,26 @@ typedef struct {
 } gs_fit_info;
 
 /* Timed parts of one call, for gs_get_phase_times.  The first four are CUDA
- * event pairs on the call's stream around launch groups; the last five split
- * the loop kernel's time by the device clock, read by one block at the grid
+ * event pairs on the call's stream around launch groups; the others split the
+ * loop kernel's time by the device clock, read by one block at the grid
  * barriers between its phases. */
 typedef enum {
   GS_PHASE_RANGE = 0,    /* key range and finiteness of the input (step i, set-up) */
-  GS_PHASE_BIN = 1,      /* binning: cell key, count and exact sum per cell (step i) */
-  GS_PHASE_LOOP = 2,     /* the loop kernel: steps ii-v, labels and modes */
+  GS_PHASE_BIN = 1,      /* binning, first pass: cell key and count per point (step i) */
+  GS_PHASE_LOOP = 2,     /* the loop kernel: exact cell sums, steps ii-v, labels and modes */
   GS_PHASE_SORT = 3,     /* numbering by a radix sort, when there are too many clusters
                             to number inside the loop kernel */
-  GS_PHASE_K_LEVEL0 = 4, /* in the loop kernel: the initial cells and their lookup table */
-  GS_PHASE_K_GATHER = 5, /* in the loop kernel: neighbourhood means, new keys (ii, iii, v) */
-  GS_PHASE_K_MERGE = 6,  /* in the loop kernel: adding cells that share a key (iv) */
-  GS_PHASE_K_COMPACT = 7,/* in the loop kernel: the next level's cells and lookup table */
-  GS_PHASE_K_LABELS = 8, /* in the loop kernel: final cell of every point, labels, modes */
-  GS_NPHASES = 9
+  GS_PHASE_K_OFFSETS = 4, /* in the loop kernel: binning, second pass: offsets of the
+                             cells in a counting sort of the points by cell (step i) */
+  GS_PHASE_K_SCATTER = 5, /* in the loop kernel: the points sorted by cell */
+  GS_PHASE_K_SUMS = 6,    /* in the loop kernel: exact cell sums from the sorted points */
+  GS_PHASE_K_LEVEL0 = 7,  /* in the loop kernel: the initial cells and their table */
+  GS_PHASE_K_UPDATE_FIRST = 8, /* in the loop kernel: the first update step (ii-v, merge
+                                  into the next level's table), over the initial cells */
+  GS_PHASE_K_UPDATE_REST = 9,  /* in the loop kernel: all later update steps */
+  GS_PHASE_K_COMPACT = 10, /* in the loop kernel: each next level's cell list and sums */
+  GS_PHASE_K_LABELS = 11,  /* in the loop kernel: final cell of every point, labels, modes */
+  GS_NPHASES = 12
 } gs_phase;
 
 typedef struct {

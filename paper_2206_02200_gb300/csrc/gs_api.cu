@@ -42,10 +42,10 @@ struct DBuf {
   }
 };
 
-// Device storage of a hash table (see gs::Table).
-struct TableBuf {
+// Device storage of the binning table (see gs::BinTable).
+struct BinTableBuf {
   DBuf<uint64_t> key;
-  DBuf<uint32_t> id, cnt, list;
+  DBuf<uint32_t> cnt, off, list;
   DBuf<uint64_t> acc;
   uint32_t cap = 0;
   int d = 0;
@@ -54,10 +54,11 @@ struct TableBuf {
   cudaError_t ensure(uint32_t c, int dd, uint32_t lmax, cudaStream_t s) {
     cudaError_t e;
     if (c > cap || dd != d) {
-      key.release(); id.release(); cnt.release(); acc.release();
+      key.release(); cnt.release(); off.release(); acc.release();
+      cap = 0;
       if ((e = key.ensure(c)) != cudaSuccess) return e;
-      if ((e = id.ensure(c)) != cudaSuccess) return e;
       if ((e = cnt.ensure(c)) != cudaSuccess) return e;
+      if ((e = off.ensure(c)) != cudaSuccess) return e;
       if ((e = acc.ensure((size_t)c * dd * 4)) != cudaSuccess) return e;
       cap = c;
       d = dd;
@@ -71,9 +72,45 @@ struct TableBuf {
     if ((e = cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * cnt.cap, s)) != cudaSuccess) return e;
     return cudaMemsetAsync(acc.p, 0, sizeof(uint64_t) * acc.cap, s);
   }
-  Table view() const { return Table{key.p, id.p, cnt.p, acc.p, list.p, cap}; }
+  BinTable view() const { return BinTable{key.p, cnt.p, off.p, acc.p, list.p, cap}; }
   void release() {
-    key.release(); id.release(); cnt.release(); acc.release(); list.release();
+    key.release(); cnt.release(); off.release(); acc.release(); list.release();
+    cap = 0;
+  }
+};
+
+// Device storage of a level table (see gs::LevelTable).
+struct LevelTableBuf {
+  DBuf<uint64_t> key;
+  DBuf<uint32_t> id, list;
+  DBuf<ulonglong2> row;
+  DBuf<uint64_t> acc;
+  uint32_t cap = 0;
+  int d = 0;
+  cudaError_t ensure(uint32_t c, int dd, uint32_t lmax, cudaStream_t s) {
+    cudaError_t e;
+    if (c > cap || dd != d) {
+      key.release(); id.release(); row.release(); acc.release();
+      cap = 0;
+      if ((e = key.ensure(c)) != cudaSuccess) return e;
+      if ((e = id.ensure(c)) != cudaSuccess) return e;
+      if ((e = row.ensure((size_t)c * (dd + 1))) != cudaSuccess) return e;
+      if ((e = acc.ensure((size_t)c * dd * 4)) != cudaSuccess) return e;
+      cap = c;
+      d = dd;
+      if ((e = clear(s)) != cudaSuccess) return e;
+    }
+    return list.ensure(lmax);
+  }
+  cudaError_t clear(cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(key.p, 0xFF, sizeof(uint64_t) * key.cap, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(row.p, 0, sizeof(ulonglong2) * row.cap, s)) != cudaSuccess) return e;
+    return cudaMemsetAsync(acc.p, 0, sizeof(uint64_t) * acc.cap, s);
+  }
+  LevelTable view() const { return LevelTable{key.p, id.p, row.p, acc.p, list.p, cap}; }
+  void release() {
+    key.release(); id.release(); row.release(); acc.release(); list.release();
     cap = 0;
   }
 };
@@ -81,15 +118,13 @@ struct TableBuf {
 struct CellBuf {
   DBuf<uint64_t> key;
   DBuf<uint32_t> cnt;
-  DBuf<ulonglong2> fix;
-  cudaError_t ensure(uint32_t m, int d) {
+  cudaError_t ensure(uint32_t m) {
     cudaError_t e;
     if ((e = key.ensure(m)) != cudaSuccess) return e;
-    if ((e = cnt.ensure(m)) != cudaSuccess) return e;
-    return fix.ensure((size_t)m * d);
+    return cnt.ensure(m);
   }
-  Cells view() const { return Cells{key.p, cnt.p, fix.p}; }
-  void release() { key.release(); cnt.release(); fix.release(); }
+  Cells view() const { return Cells{key.p, cnt.p}; }
+  void release() { key.release(); cnt.release(); }
 };
 
 // CUDA events around the launch groups of one call (opt-in, gs_set_timing).
@@ -132,12 +167,11 @@ struct CtxWorkspace : public Workspace {
   DBuf<GridBar> bar;
   DBuf<int64_t> thr;
   DBuf<uint64_t> dtab;
-  DBuf<uint32_t> slot0;
-  TableBuf t0, tab[2];
+  DBuf<uint32_t> slot0, perm, blocksum;
+  BinTableBuf t0;
+  LevelTableBuf tab[3];
   CellBuf cells[2];
-  DBuf<double> sp;
-  DBuf<uint64_t> nkey;
-  DBuf<uint32_t> pslot, forest, forest2, labslot, rank;
+  DBuf<uint32_t> pslot[2], forest, forest2, labslot, rank;
   DBuf<uint64_t> skey, skey2;
   DBuf<uint32_t> sval, sval2, shist;
 
@@ -201,12 +235,14 @@ struct CtxWorkspace : public Workspace {
     WS_CU(thr.ensure(thr_words), "alloc face table");
     WS_CU(dtab.ensure(nprobe), "alloc offsets");
     WS_CU(slot0.ensure(n), "alloc slot0");
+    WS_CU(perm.ensure(n), "alloc perm");
+    WS_CU(blocksum.ensure(kMaxLoopGrid), "alloc block sums");
     uint32_t cap0 = pow2_at_least(2 * m_bound, 1024);
     if (t0.cap > cap0 && t0.d == d) cap0 = t0.cap;
     if (dirty) {
       if (t0.cap) WS_CU(t0.clear(s), "clear T0");
-      if (tab[0].cap) WS_CU(tab[0].clear(s), "clear table A");
-      if (tab[1].cap) WS_CU(tab[1].clear(s), "clear table B");
+      for (int i = 0; i < 3; ++i)
+        if (tab[i].cap) WS_CU(tab[i].clear(s), "clear level table");
     }
     WS_CU(t0.ensure(cap0, d, cap0 / 2, s), "alloc T0");
     b.st = st.p;
@@ -215,6 +251,8 @@ struct CtxWorkspace : public Workspace {
     b.thr = thr.p;
     b.dtab = dtab.p;
     b.slot0 = slot0.p;
+    b.perm = perm.p;
+    b.blocksum = blocksum.p;
     b.t0 = t0.view();
     b.t0_maxcells = t0.cap / 2;
     return GS_OK;
@@ -236,27 +274,26 @@ struct CtxWorkspace : public Workspace {
   gs_status levels(uint32_t m0, int d, int max_iter, cudaStream_t s, Bufs& b,
                    std::string* err) override {
     cudaError_t e;
-    const uint32_t capAB = pow2_at_least(2ull * m0, 64);
+    const uint32_t capAB = pow2_at_least(4ull * m0, 64);
     const uint32_t m = m0 > 0 ? m0 : 1;
-    WS_CU(tab[0].ensure(capAB, d, m, s), "alloc table A");
-    WS_CU(tab[1].ensure(capAB, d, m, s), "alloc table B");
-    WS_CU(cells[0].ensure(m, d), "alloc cells");
-    WS_CU(cells[1].ensure(m, d), "alloc cells");
-    WS_CU(sp.ensure((size_t)m * d), "alloc sp");
-    WS_CU(nkey.ensure(m), "alloc nkey");
-    WS_CU(pslot.ensure(m), "alloc pslot");
+    for (int i = 0; i < 3; ++i) WS_CU(tab[i].ensure(capAB, d, m, s), "alloc level table");
+    for (int i = 0; i < 2; ++i) {
+      WS_CU(cells[i].ensure(m), "alloc cells");
+      WS_CU(pslot[i].ensure(m), "alloc pslot");
+    }
     WS_CU(forest.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(forest2.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(labslot.ensure(t0.cap), "alloc labslot");
     WS_CU(rank.ensure(m), "alloc rank");
-    for (int i = 0; i < 2; ++i) {
+    b.capAB = tab[0].cap;
+    for (int i = 0; i < 3; ++i) {
       b.tab[i] = tab[i].view();
-      b.cells[i] = cells[i].view();
+      if (tab[i].cap < b.capAB) b.capAB = tab[i].cap;
     }
-    b.capAB = tab[0].cap < tab[1].cap ? tab[0].cap : tab[1].cap;
-    b.sp = sp.p;
-    b.nkey = nkey.p;
-    b.pslot = pslot.p;
+    for (int i = 0; i < 2; ++i) {
+      b.cells[i] = cells[i].view();
+      b.pslot[i] = pslot[i].p;
+    }
     b.forest = forest.p;
     b.forest2 = forest2.p;
     b.labslot = labslot.p;
@@ -284,10 +321,14 @@ struct CtxWorkspace : public Workspace {
 
   void release() {
     flags.release(); st.release(); res.release(); bar.release(); thr.release(); dtab.release();
-    slot0.release(); t0.release(); tab[0].release(); tab[1].release(); cells[0].release();
-    cells[1].release(); sp.release(); nkey.release(); pslot.release(); forest.release();
-    forest2.release(); labslot.release(); rank.release(); skey.release(); skey2.release();
-    sval.release(); sval2.release(); shist.release();
+    slot0.release(); perm.release(); blocksum.release(); t0.release();
+    for (int i = 0; i < 3; ++i) tab[i].release();
+    for (int i = 0; i < 2; ++i) {
+      cells[i].release();
+      pslot[i].release();
+    }
+    forest.release(); forest2.release(); labslot.release(); rank.release();
+    skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
     if (h_flags) cudaFreeHost(h_flags);
     if (h_res) cudaFreeHost(h_res);
     if (h_words) cudaFreeHost(h_words);
@@ -449,8 +490,8 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
       ctx->last_times.count[ctx->tm.phase[i]] += 1;
     }
     for (int i = 0; i < kLoopPhases; ++i) {
-      ctx->last_times.ms[GS_PHASE_K_LEVEL0 + i] = kms[i];
-      ctx->last_times.count[GS_PHASE_K_LEVEL0 + i] = 1;
+      ctx->last_times.ms[GS_PHASE_K_OFFSETS + i] = kms[i];
+      ctx->last_times.count[GS_PHASE_K_OFFSETS + i] = 1;
     }
   }
   return st;

@@ -244,68 +244,143 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
 }
 
 // ---------------------------------------------------------------------------
-// Hash table over packed keys: open addressing, linear probing, capacity a
-// power of two.  The home slot is Fibonacci (multiplicative) hashing: the top
-// log2(capacity) bits of key * 2^64/phi, which depend on every bit of the key.
+// Hash table over packed keys: open addressing over buckets of kBucket = 4
+// slots (32 bytes of keys, one DRAM/L2 sector), linear probing from bucket to
+// bucket, capacity a power of two >= 4.  The home bucket is Fibonacci
+// (multiplicative) hashing: the top log2(buckets) bits of key * 2^64/phi,
+// which depend on every bit of the key.  Within a bucket, inserts fill slots
+// in order, so once the inserts of a phase are done the occupied slots of a
+// bucket are a prefix and a lookup can stop at the first bucket holding an
+// empty slot.  The key array must be 32-byte aligned.
 
-__device__ __host__ __forceinline__ uint32_t home_slot(uint64_t key, uint32_t mask) {
+constexpr uint32_t kBucket = 4;
+
+__device__ __host__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t bmask) {
 #ifdef __CUDA_ARCH__
-  const int b = __popc(mask);
+  const int b = __popc(bmask);
 #else
-  const int b = __builtin_popcount(mask);
+  const int b = __builtin_popcount(bmask);
 #endif
   return b == 0 ? 0u : (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - b));
 }
 
-// Longest probe sequence: an insert that finds no free slot within kMaxProbe
-// slots of the key's home slot fails (kErrTableFull), so every stored key lies
-// within kMaxProbe slots of its home and a lookup may stop there.  At the load
-// factors used (<= 1/2) sequences this long do not occur in practice; the
-// bound keeps an over-full table from turning into a near-endless scan.
-constexpr uint32_t kMaxProbe = 512;
+// Longest probe sequence: an insert that finds no free slot within
+// kMaxProbeBuckets buckets of the key's home fails (kErrTableFull), so every
+// stored key lies within that many buckets of its home and a lookup may stop
+// there.  At the load factors used (<= 1/2) sequences this long do not occur
+// in practice; the bound keeps an over-full table from turning into a
+// near-endless scan.
+constexpr uint32_t kMaxProbeBuckets = 128;
 
-// Slot holding key, or kNone.
-__device__ __forceinline__ uint32_t table_find(const uint64_t* keys, uint32_t mask, uint64_t key) {
-  uint32_t s = home_slot(key, mask);
-  const uint32_t lim = mask < kMaxProbe ? mask + 1 : kMaxProbe;
-  for (uint32_t i = 0; i < lim; ++i) {
-    uint64_t k = keys[s];
-    if (k == key) return s;
-    if (k == kEmpty) return kNone;
-    s = (s + 1) & mask;
+__device__ __forceinline__ uint32_t probe_limit(uint32_t bmask) {
+  return bmask < kMaxProbeBuckets ? bmask + 1 : kMaxProbeBuckets;
+}
+
+// Index of key in the four keys of a bucket, 4 if absent; *open is set when
+// the bucket holds an empty slot (so the key is in no later bucket).
+__device__ __forceinline__ uint32_t bucket_match(ulonglong2 lo, ulonglong2 hi, uint64_t key,
+                                                 bool* open) {
+  *open = lo.x == kEmpty || lo.y == kEmpty || hi.x == kEmpty || hi.y == kEmpty;
+  return lo.x == key ? 0u : lo.y == key ? 1u : hi.x == key ? 2u : hi.y == key ? 3u : 4u;
+}
+
+// Slot holding key, or kNone, scanning from bucket b (the i0-th bucket of the
+// key's sequence).  mask = capacity - 1.
+__device__ __forceinline__ uint32_t table_find_from(const uint64_t* keys, uint32_t mask,
+                                                    uint64_t key, uint32_t b, uint32_t i0) {
+  const uint32_t bmask = mask >> 2;
+  const uint32_t lim = probe_limit(bmask);
+  for (uint32_t i = i0; i < lim; ++i) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + (size_t)b * kBucket);
+    const ulonglong2 lo = p[0], hi = p[1];
+    bool open;
+    const uint32_t j = bucket_match(lo, hi, key, &open);
+    if (j < kBucket) return b * kBucket + j;
+    if (open) return kNone;
+    b = (b + 1) & bmask;
   }
   return kNone;
 }
 
+__device__ __forceinline__ uint32_t table_find(const uint64_t* keys, uint32_t mask, uint64_t key) {
+  return table_find_from(keys, mask, key, home_bucket(key, mask >> 2), 0);
+}
+
+// Lookups of U keys at once: the home buckets of all of them are loaded
+// before any is examined, so the U loads are in flight together.  valid[u]
+// false leaves slot[u] = kNone.
+template <int U>
+__device__ __forceinline__ void table_find_many(const uint64_t* keys, uint32_t mask,
+                                                const uint64_t (&key)[U], const bool (&valid)[U],
+                                                uint32_t (&slot)[U]) {
+  const uint32_t bmask = mask >> 2;
+  uint32_t b[U];
+  ulonglong2 lo[U], hi[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    b[u] = home_bucket(key[u], bmask);
+    if (valid[u]) {
+      const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + (size_t)b[u] * kBucket);
+      lo[u] = p[0];
+      hi[u] = p[1];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    slot[u] = kNone;
+    if (!valid[u]) continue;
+    bool open;
+    const uint32_t j = bucket_match(lo[u], hi[u], key[u], &open);
+    if (j < kBucket) {
+      slot[u] = b[u] * kBucket + j;
+    } else if (!open) {
+      slot[u] = table_find_from(keys, mask, key[u], (b[u] + 1) & bmask, 1);
+    }
+  }
+}
+
 // Slot of key, inserting it if absent; won is set for the inserting thread.
-// Returns kNone (and sets kErrTableFull) when no free slot is found.
+// Returns kNone (and sets kErrTableFull) when no free slot is found.  The
+// bucket is read at L2 (the point of coherence), then empty slots are claimed
+// in order with compare-and-swap.
 __device__ __forceinline__ uint32_t table_insert(uint64_t* keys, uint32_t mask, uint64_t key,
                                                  bool& won, uint32_t* err) {
-  uint32_t s = home_slot(key, mask);
+  const uint32_t bmask = mask >> 2;
+  uint32_t b = home_bucket(key, bmask);
   won = false;
-  const uint32_t lim = mask < kMaxProbe ? mask + 1 : kMaxProbe;
+  const uint32_t lim = probe_limit(bmask);
   for (uint32_t i = 0; i < lim; ++i) {
-    uint64_t k = *(volatile uint64_t*)&keys[s];
-    if (k == key) return s;
-    if (k == kEmpty) {
-      uint64_t prev = atomicCAS((unsigned long long*)&keys[s], (unsigned long long)kEmpty,
-                                (unsigned long long)key);
-      if (prev == kEmpty) {
-        won = true;
-        return s;
+    uint64_t* p = keys + (size_t)b * kBucket;
+    const ulonglong2 lo = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+    const ulonglong2 hi = __ldcg(reinterpret_cast<const ulonglong2*>(p) + 1);
+    bool open;
+    const uint32_t j = bucket_match(lo, hi, key, &open);
+    if (j < kBucket) return b * kBucket + j;
+    if (open) {
+      const uint64_t seen[kBucket] = {lo.x, lo.y, hi.x, hi.y};
+#pragma unroll
+      for (uint32_t q = 0; q < kBucket; ++q) {
+        if (seen[q] != kEmpty) continue;
+        const uint64_t prev = atomicCAS((unsigned long long*)&p[q], (unsigned long long)kEmpty,
+                                        (unsigned long long)key);
+        if (prev == kEmpty) {
+          won = true;
+          return b * kBucket + q;
+        }
+        if (prev == key) return b * kBucket + q;
       }
-      if (prev == key) return s;
     }
-    s = (s + 1) & mask;
+    b = (b + 1) & bmask;
   }
   atomicOr(err, kErrTableFull);
   return kNone;
 }
 
-// Capacity mask of a table that receives at most m distinct keys (load <= 1/2).
+// Capacity mask of a table that receives at most m distinct keys: load <= 1/4
+// where cap_max allows (lookups then rarely leave the home bucket).
 __device__ __host__ __forceinline__ uint32_t mask_for(uint32_t m, uint32_t cap_max) {
   uint32_t c = 64;
-  while (c < 2u * m && c < cap_max) c <<= 1;
+  while (c < 4u * m && c < cap_max) c <<= 1;
   return c - 1;
 }
 

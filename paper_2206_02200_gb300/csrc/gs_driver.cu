@@ -225,17 +225,19 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   LoopArgs L;
   std::memset(&L, 0, sizeof(L));
   L.P = P;
+  L.pts = a.points;
+  L.f32 = a.f32;
+  L.perm = b.perm;
+  L.blocksum = b.blocksum;
   L.thr = b.thr;
   L.dtab = b.dtab;
   L.T0 = b.t0;
-  L.tab[0] = b.tab[0];
-  L.tab[1] = b.tab[1];
+  for (int i = 0; i < 3; ++i) L.tab[i] = b.tab[i];
   L.capAB = b.capAB;
   L.cells[0] = b.cells[0];
   L.cells[1] = b.cells[1];
-  L.sp = b.sp;
-  L.nkey = b.nkey;
-  L.pslot = b.pslot;
+  L.pslot[0] = b.pslot[0];
+  L.pslot[1] = b.pslot[1];
   L.forest = b.forest;
   L.forest2 = b.forest2;
   L.labslot = b.labslot;
@@ -272,8 +274,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_LAUNCH(radix_sort(b.skey, b.sval, b.skey2, b.sval2, b.shist, k, total_bits, s),
               "radix_sort", radix_sort_launches(k, total_bits));
     GS_LAUNCH(launch_rank(b.sval, b.rank, k, s), "k_rank", 1);
-    GS_LAUNCH(launch_label_tail(L, m0, k, hr->base, T, s), "label tail",
-              (int64_t)k <= a.modes_cap ? 3 : 2);
+    GS_LAUNCH(launch_label_tail(L, m0, k, hr->base, T, s), "label tail", 3);
     GS_T_END();
     GS_CU(cudaStreamSynchronize(s), "sync labels");
   }

@@ -23,14 +23,14 @@ struct Bufs {
   int64_t* thr = nullptr;      // cell-face table
   uint64_t* dtab = nullptr;    // neighbour offsets
   uint32_t* slot0 = nullptr;   // n
-  Table t0{};                  // binning table
+  uint32_t* perm = nullptr;    // n
+  uint32_t* blocksum = nullptr;  // kMaxLoopGrid
+  BinTable t0{};               // binning table
   uint32_t t0_maxcells = 0;    // length of t0.list
-  Table tab[2]{};              // level tables, capacity capAB each, lists of m0
+  LevelTable tab[3]{};         // level tables, capacity capAB each, lists of m0
   uint32_t capAB = 0;
   Cells cells[2]{};            // m0 cells each
-  double* sp = nullptr;        // m0 x d
-  uint64_t* nkey = nullptr;    // m0
-  uint32_t* pslot = nullptr;   // m0
+  uint32_t* pslot[2] = {nullptr, nullptr};  // m0 each
   uint32_t* forest = nullptr;  // m0 * (max_iter + 1)
   uint32_t* forest2 = nullptr; // m0 * (max_iter + 1)
   uint32_t* labslot = nullptr; // t0.cap

@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
+constexpr int kLoopBlock = 512;  // threads per block of the loop kernel
 
 inline unsigned grid_for(int64_t work, int per_block = kBlock, unsigned cap = 152u * 32u) {
   int64_t g = (work + per_block - 1) / per_block;
@@ -52,14 +53,67 @@ inline unsigned grid_for(int64_t work, int per_block = kBlock, unsigned cap = 15
 // ---------------------------------------------------------------------------
 // Key range and finiteness
 
-// The point array is read as one flat stream of n*D values: thread t reads the
-// values t, t + S, t + 2S, ... with S a multiple of D, so every thread sees a
-// single coordinate a = t mod D and consecutive threads read consecutive
-// values (coalesced).  Per-coordinate extremes are reduced in shared memory
-// and published with one global atomic per block and coordinate.
-template <int D, typename T>
+// The point array is read as one flat stream of n*D values in words of W
+// values (W = 16 bytes / sizeof(T) when the array is 16-byte aligned, else 1):
+// thread t reads the words t, t + S, t + 2S, ... with S a multiple of D, so
+// the j-th value of every word a thread reads has the same coordinate
+// (t*W + j) mod D, and consecutive threads read consecutive words
+// (coalesced).  Four words per thread are in flight at once.  Per-coordinate
+// extremes are reduced in shared memory and published with one global atomic
+// per block and coordinate.
+template <int W, typename T>
+struct Word;
+template <>
+struct Word<1, double> {
+  static __device__ __forceinline__ void load(const double* p, uint64_t (&b)[1]) {
+    b[0] = (uint64_t)__double_as_longlong(__ldg(p));
+  }
+};
+template <>
+struct Word<1, float> {
+  static __device__ __forceinline__ void load(const float* p, uint64_t (&b)[1]) {
+    b[0] = f32_bits_to_f64_bits(__float_as_uint(__ldg(p)));
+  }
+};
+template <>
+struct Word<2, double> {
+  static __device__ __forceinline__ void load(const double* p, uint64_t (&b)[2]) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    b[0] = v.x;
+    b[1] = v.y;
+  }
+};
+template <>
+struct Word<4, float> {
+  static __device__ __forceinline__ void load(const float* p, uint64_t (&b)[4]) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    b[0] = f32_bits_to_f64_bits(v.x);
+    b[1] = f32_bits_to_f64_bits(v.y);
+    b[2] = f32_bits_to_f64_bits(v.z);
+    b[3] = f32_bits_to_f64_bits(v.w);
+  }
+};
+
+struct RangeAcc {
+  int64_t mn = INT64_MAX, mx = INT64_MIN;
+  uint64_t ma = 0;
+  __device__ __forceinline__ void add(uint64_t b, unsigned long long& bad) {
+    if (((b >> 52) & 0x7FF) == 0x7FF) {
+      ++bad;
+      return;
+    }
+    const int64_t o = ord_of_bits(b);
+    mn = o < mn ? o : mn;
+    mx = o > mx ? o : mx;
+    const uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
+    ma = ab > ma ? ab : ma;
+  }
+};
+
+template <int D, typename T, int W>
 __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int64_t n,
                                                   DevFlags* fl) {
+  constexpr int U = 4;  // words in flight per thread
   __shared__ long long s_mn[D], s_mx[D];
   __shared__ unsigned long long s_ma[D], s_bad;
   if (threadIdx.x < D) {
@@ -70,33 +124,55 @@ __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   const int64_t total = n * D;
+  const int64_t words = total / W;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t S = nthreads - nthreads % D;  // stride, a multiple of D
+  const int64_t S = nthreads - nthreads % D;  // stride in words, a multiple of D
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t mn = INT64_MAX, mx = INT64_MIN;
-  uint64_t ma = 0;
+  RangeAcc acc[W];
   unsigned long long bad = 0;
   if (t < S) {
-    for (int64_t e = t; e < total; e += S) {
-      uint64_t b = load_bits<T>(pts + e);
-      if (((b >> 52) & 0x7FF) == 0x7FF) {
-        ++bad;
-        continue;
+    int64_t q = t;
+    for (; q + (U - 1) * S < words; q += U * S) {
+      uint64_t b[U][W];
+#pragma unroll
+      for (int u = 0; u < U; ++u) Word<W, T>::load(pts + (q + u * S) * W, b[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc[j].add(b[u][j], bad);
+    }
+    for (; q < words; q += S) {
+      uint64_t b[W];
+      Word<W, T>::load(pts + q * W, b);
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc[j].add(b[j], bad);
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int a = (int)((t * W + j) % D);
+      if (acc[j].mn != INT64_MAX) {
+        atomicMin(&s_mn[a], (long long)acc[j].mn);
+        atomicMax(&s_mx[a], (long long)acc[j].mx);
+        atomicMax(&s_ma[a], (unsigned long long)acc[j].ma);
       }
-      int64_t o = ord_of_bits(b);
-      mn = o < mn ? o : mn;
-      mx = o > mx ? o : mx;
-      uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
-      ma = ab > ma ? ab : ma;
     }
-    const int a = (int)(t % D);
-    if (mn != INT64_MAX) {
-      atomicMin(&s_mn[a], (long long)mn);
-      atomicMax(&s_mx[a], (long long)mx);
-      atomicMax(&s_ma[a], (unsigned long long)ma);
-    }
-    if (bad) atomicAdd(&s_bad, bad);
   }
+  if (t == 0) {
+    // values after the last whole word
+    for (int64_t e = words * W; e < total; ++e) {
+      uint64_t b[1];
+      Word<1, T>::load(pts + e, b);
+      RangeAcc r;
+      r.add(b[0], bad);
+      const int a = (int)(e % D);
+      if (r.mn != INT64_MAX) {
+        atomicMin(&s_mn[a], (long long)r.mn);
+        atomicMax(&s_mx[a], (long long)r.mx);
+        atomicMax(&s_ma[a], (unsigned long long)r.ma);
+      }
+    }
+  }
+  if (bad) atomicAdd(&s_bad, bad);
   __syncthreads();
   if (threadIdx.x < D && s_mn[threadIdx.x] != INT64_MAX) {
     atomicMin(&fl->min_ord[threadIdx.x], s_mn[threadIdx.x]);
@@ -107,14 +183,15 @@ __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int
 }
 
 // ---------------------------------------------------------------------------
-// Step i: binning
+// Step i: binning, first pass (cell keys and counts)
 //
 // A warp takes 32 consecutive points at a time.  It copies their d
 // coordinates (one contiguous run of 32*d values) into shared memory with
 // 16-byte loads, so the global reads are coalesced.  Lanes holding the same
-// cell key (__match_any_sync) add their exact fixed-point values in shared
-// memory, and only the lowest such lane touches the global table: one insert,
-// one count add and one exact-sum add per distinct key per warp.
+// cell key (__match_any_sync) are counted together: only the lowest such lane
+// touches the global table, with one insert and one count add per distinct
+// key per warp.  The exact cell sums are formed later (k_loop, after a
+// counting sort of the points by cell), without per-point atomics.
 
 template <typename T>
 __device__ __forceinline__ void stage_points(const T* __restrict__ src, int count,
@@ -139,12 +216,10 @@ __device__ __forceinline__ uint64_t bits_of(float v) {
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock)
     k_bin(const T* __restrict__ pts, int64_t n, Plan P, const int64_t* __restrict__ thr,
-          Table T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
+          BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
           DevFlags* fl, bool vec_ok) {
   __shared__ __align__(16) T s_pts[kWarps][32 * D];
-  __shared__ ulonglong2 s_val[kWarps][32 * D];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned inexact = 0, werr = 0;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = gwarp * 32; base < n; base += nwarps * 32) {
@@ -157,11 +232,9 @@ __global__ void __launch_bounds__(kBlock)
       key = 0;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        uint64_t b = bits_of(s_pts[w][lane * D + a]);
-        int idx = key_index(thr + P.thr_off[a], P.span[a], P.kmin[a], P.inv_h, b);
+        const uint64_t b = bits_of(s_pts[w][lane * D + a]);
+        const int idx = key_index(thr + P.thr_off[a], P.span[a], P.kmin[a], P.inv_h, b);
         key |= (uint64_t)(idx + 1) << P.off[a];
-        u128 V = to_fixed(b, P.L[a], inexact, werr);
-        s_val[w][lane * D + a] = make_ulonglong2((uint64_t)V, (uint64_t)(V >> 64));
       }
     }
     __syncwarp();
@@ -173,27 +246,16 @@ __global__ void __launch_bounds__(kBlock)
       s = table_insert(T0.key, mask0, key, won, &fl->err);
       if (s != kNone) {
         if (won) {
-          uint32_t id = atomicAdd(&fl->m0, 1u);
+          const uint32_t id = atomicAdd(&fl->m0, 1u);
           if (id < maxcells) T0.list[id] = s; else atomicOr(&fl->err, kErrOverflow);
         }
         atomicAdd(&T0.cnt[s], (uint32_t)__popc(peers));
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          u128 S = 0;
-          for (unsigned pm = peers; pm; pm &= pm - 1) {
-            const ulonglong2 v = s_val[w][(__ffs(pm) - 1) * D + a];
-            S += (u128)v.x | ((u128)v.y << 64);
-          }
-          atomic_add_fixed(T0.acc + ((size_t)s * D + a) * 4, S);
-        }
       }
     }
     s = __shfl_sync(kFull, s, leader);
     if (valid) slot0[base + lane] = s;
     __syncwarp();
   }
-  if (inexact) atomicAdd(&fl->inexact, 1ull);
-  if (werr) atomicOr(&fl->err, kErrWindow);
 }
 
 // ---------------------------------------------------------------------------
@@ -262,84 +324,319 @@ struct SegClock {
   }
 };
 
-enum { kSegLevel0 = 0, kSegGather = 1, kSegMerge = 2, kSegCompact = 3, kSegLabels = 4 };
+enum {
+  kSegOffsets = 0,
+  kSegScatter = 1,
+  kSegSums = 2,
+  kSegLevel0 = 3,
+  kSegUpdateFirst = 4,
+  kSegUpdateRest = 5,
+  kSegCompact = 6,
+  kSegLabels = 7
+};
 
-template <int D>
-__device__ __forceinline__ u128 fix_at(const ulonglong2* __restrict__ fix, uint32_t i, int a) {
-  const ulonglong2 v = fix[(size_t)i * D + a];
-  return (u128)v.x | ((u128)v.y << 64);
-}
+__device__ __forceinline__ u128 as_u128(ulonglong2 v) { return (u128)v.x | ((u128)v.y << 64); }
 
 __device__ __forceinline__ ulonglong2 pack(u128 v) {
   return make_ulonglong2((uint64_t)v, (uint64_t)(v >> 64));
 }
 
-// Lanes given to one cell in the gather: enough for the 3^d probes of small d.
+// The cell sum of one axis as the float64 value of Sec. 2.1 (the exact sum in
+// the limb accumulators rounded once), held as the fixed-point integer it
+// equals; clears the accumulators.
+__device__ __forceinline__ ulonglong2 settle_sum(uint64_t* acc, int L, unsigned& inexact,
+                                                 unsigned& werr) {
+  const double v = round_fixed(limbs_value(acc), L, inexact);
+  acc[0] = acc[1] = acc[2] = acc[3] = 0;
+  return pack(to_fixed(bits_of(v), L, inexact, werr));
+}
+
+// Lanes given to one cell in the update: enough for the 3^d probes of small d.
 template <int D>
 struct GatherLanes {
   static constexpr int value = D == 1 ? 4 : (D == 2 ? 16 : 32);
 };
 
+constexpr int pow3(int d) { return d == 0 ? 1 : 3 * pow3(d - 1); }
+
+// Probes each lane has in flight at once: min(4, its probes per cell).
+template <int D>
+struct ProbeBatch {
+  static constexpr int probes = pow3(D);
+  static constexpr int per_lane = (probes + GatherLanes<D>::value - 1) / GatherLanes<D>::value;
+  static constexpr int value = per_lane < 4 ? per_lane : 4;
+};
+
+// ---------------------------------------------------------------------------
+// Step i, second pass: the exact sum of every cell, by a counting sort of the
+// points by cell.  Offsets follow the cells' list order; a cell's points then
+// occupy one contiguous run of perm[], and a warp reading 32 consecutive
+// entries adds each run of equal cells with a segmented shuffle reduction, so
+// the sum accumulators receive a few atomic adds per run instead of d per
+// point.  Exact integer sums make the order irrelevant.
+
+// Per-block totals of the counts of cells [b * chunk, (b + 1) * chunk).
+__device__ void phase_count_totals(const LoopArgs& A, uint32_t m0) {
+  __shared__ uint32_t s_part[kLoopBlock / 32];
+  const uint32_t chunk = (m0 + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = lo + chunk < m0 ? lo + chunk : m0;
+  uint32_t sum = 0;
+  for (uint32_t id = lo + threadIdx.x; id < hi; id += blockDim.x) sum += A.T0.cnt[A.T0.list[id]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+    A.blocksum[blockIdx.x] = t;
+  }
+}
+
+// Start offset of every cell's run: T0.off[slot] = points of all earlier cells.
+__device__ void phase_offsets(const LoopArgs& A, uint32_t m0) {
+  __shared__ uint32_t s_warp[kLoopBlock / 32];
+  __shared__ uint32_t s_base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (w == 0) {
+    uint32_t t = 0;
+    for (uint32_t b = lane; b < blockIdx.x; b += 32) t += A.blocksum[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if (lane == 0) s_base = t;
+  }
+  __syncthreads();
+  const uint32_t chunk = (m0 + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = lo + chunk < m0 ? lo + chunk : m0;
+  uint32_t run = s_base;
+  for (uint32_t c0 = lo; c0 < hi; c0 += blockDim.x) {
+    const uint32_t id = c0 + threadIdx.x;
+    const uint32_t slot = id < hi ? A.T0.list[id] : 0u;
+    const uint32_t v = id < hi ? A.T0.cnt[slot] : 0u;
+    uint32_t x = v;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int q = 0; q < nw; ++q) {
+      const uint32_t t = s_warp[q];
+      before += q < w ? t : 0u;
+      total += t;
+    }
+    if (id < hi) A.T0.off[slot] = run + before + x - v;
+    run += total;
+    __syncthreads();
+  }
+}
+
+// perm[off[cell] + rank] = point: each point claims a position in its cell's
+// run (equal cells within a warp claim theirs with one atomic add).  A warp
+// handles kScatterBatch chunks of 32 points at once, so their loads and
+// atomics are in flight together.
+constexpr int kScatterBatch = 4;
+
+__device__ void phase_scatter(const LoopArgs& A) {
+  constexpr int B = kScatterBatch;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gwarp * 32 * B; base < A.n; base += nwarps * 32 * B) {
+    uint32_t s[B], pos[B];
+    unsigned peers[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int64_t i = base + b * 32 + lane;
+      s[b] = i < A.n ? A.slot0[i] : kNone;
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      peers[b] = __match_any_sync(kFull, s[b]);
+      pos[b] = 0;
+      if (lane == __ffs(peers[b]) - 1 && s[b] != kNone)
+        pos[b] = atomicAdd(&A.T0.off[s[b]], (uint32_t)__popc(peers[b]));
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const uint32_t p = __shfl_sync(kFull, pos[b], __ffs(peers[b]) - 1);
+      if (s[b] != kNone) A.perm[p + __popc(peers[b] & below)] = (uint32_t)(base + b * 32 + lane);
+    }
+  }
+}
+
+// Exact sums of the cells: sums of the fixed-point values of their points.
+// Lane l of a warp takes kSumRun consecutive entries of perm[] (one 16-byte
+// load) and adds the runs of equal cells among them in registers; every run
+// but its last is added into the cell's limb accumulators at once.  The
+// lanes' last runs are contiguous in cell order across the warp, so a
+// segmented shuffle reduction combines them and the first lane of each
+// segment adds the segment's sum.
+constexpr int kSumRun = 4;
+
+template <int D>
+__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t s, const u128 (&V)[D]) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)s * D + a) * 4, V[a]);
+}
+
+template <int D, typename T>
+__device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& werr) {
+  constexpr int E = kSumRun;
+  const T* __restrict__ pts = static_cast<const T*>(A.pts);
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gwarp * 32 * E; base < A.n; base += nwarps * 32 * E) {
+    const int64_t p0 = base + (int64_t)lane * E;
+    uint32_t idx[E], s[E];
+    if (p0 + E <= A.n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(A.perm + p0);
+      idx[0] = q.x;
+      idx[1] = q.y;
+      idx[2] = q.z;
+      idx[3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) idx[e] = p0 + e < A.n ? A.perm[p0 + e] : kNone;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) s[e] = idx[e] != kNone ? A.slot0[idx[e]] : kNone;
+    uint64_t raw[E][D];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)idx[e] * D + a) : 0ull;
+    // runs within the lane
+    uint32_t cur = s[0];
+    u128 V[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], A.P.L[a], inexact, werr);
+#pragma unroll
+    for (int e = 1; e < E; ++e) {
+      if (s[e] != cur) {
+        if (cur != kNone) add_cell_sum<D>(A, cur, V);
+        cur = s[e];
+#pragma unroll
+        for (int a = 0; a < D; ++a) V[a] = 0;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) V[a] += to_fixed(raw[e][a], A.P.L[a], inexact, werr);
+    }
+    // the lanes' last runs: lane l ends with the sum of [l, end of its segment)
+    const uint32_t prev = __shfl_up_sync(kFull, cur, 1);
+    const bool head = lane == 0 || prev != cur;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned after = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
+    const int end = after ? __ffs(after) - 1 : 32;
+    if (__any_sync(kFull, end - lane > 1)) {
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const uint64_t lo = __shfl_down_sync(kFull, (uint64_t)V[a], o);
+          const uint64_t hi = __shfl_down_sync(kFull, (uint64_t)(V[a] >> 64), o);
+          if (lane + o < end) V[a] += (u128)lo | ((u128)hi << 64);
+        }
+      }
+    }
+    if (head && cur != kNone) add_cell_sum<D>(A, cur, V);
+  }
+}
+
 // Level 0: the cells binning created (in arrival order), their sums rounded
-// once, and their lookup table.  Resets the binning table's slots.
+// once, in the level table tab[0].  Resets the binning table's slots.
 template <int D>
 __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, unsigned& inexact,
                              unsigned& werr) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nth = gridDim.x * blockDim.x;
-  const Table T0 = A.T0;
-  const Table G = A.tab[0];
+  const BinTable T0 = A.T0;
+  const LevelTable G = A.tab[0];
   const Cells c = A.cells[0];
   for (uint32_t id = tid; id < m0; id += nth) {
     const uint32_t s = T0.list[id];
     const uint64_t key = T0.key[s];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      uint64_t* acc = T0.acc + ((size_t)s * D + a) * 4;
-      const double v = round_fixed(limbs_value(acc), A.P.L[a], inexact);
-      c.fix[(size_t)id * D + a] = pack(to_fixed(bits_of(v), A.P.L[a], inexact, werr));
-      acc[0] = acc[1] = acc[2] = acc[3] = 0;
-    }
-    c.key[id] = key;
-    c.cnt[id] = T0.cnt[s];
-    T0.cnt[s] = 0;
-    T0.key[s] = kEmpty;
+    const uint32_t cnt = T0.cnt[s];
     bool won;
     const uint32_t sa = table_insert(G.key, maskA, key, won, &A.fl->err);
     if (sa != kNone) {
+      ulonglong2* r = G.row + (size_t)sa * (D + 1);
+      r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        r[1 + a] = settle_sum(T0.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
       G.id[sa] = id;
       G.list[id] = sa;
     }
+    c.key[id] = key;
+    c.cnt[id] = cnt;
+    T0.cnt[s] = 0;
+    T0.key[s] = kEmpty;
   }
 }
 
-// Steps ii-iii for every cell of level t, and the neighbour test of step v.
+// One update step t for every cell of level t (table tab[t % 3]):
+//   ii)  D = sum of the counts and N = sum of the coordinate sums over the
+//        3^d neighbours present (Eq. 1-2, all cells reading level t: Eq. 6),
+//        centroid N / D rounded once, and whether a neighbour v != 0 is
+//        present (step v);
+//   iii) new key floor(centroid / h);
+//   iv)  the cell's count and count-weighted centroid (Eq. 3-4) added exactly
+//        into the slot of its new key in tab[(t + 1) % 3].
+// The merge is applied before the stop test is known; when the test stops
+// the run, the merge table is cleared instead of used.
+// For t > 0 the same phase links every cell of level t-1 to its cell of level
+// t (the union of resident sets of Eq. 4) and clears level t-1's table.
 template <int D>
-__device__ void phase_gather(const LoopArgs& A, int t, uint32_t m, uint32_t mask, bool& any_nb,
-                             unsigned& inexact) {
+__device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
+                             uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
+                             unsigned& inexact, unsigned& werr) {
   constexpr int GS = GatherLanes<D>::value;
+  constexpr int U = ProbeBatch<D>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
   const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / GS;
   const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
-  const Table G = (t & 1) ? A.tab[1] : A.tab[0];
-  const Cells c = (t & 1) ? A.cells[1] : A.cells[0];
+  const LevelTable G = A.tab[t % 3];
+  const LevelTable M = A.tab[(t + 1) % 3];
+  const Cells c = A.cells[t & 1];
+  uint32_t* pslot = A.pslot[t & 1];
   const int nprobe = A.P.nprobe, center = A.P.center;
   for (uint32_t j = group; j < m; j += ngroups) {
     const uint64_t key = c.key[j];
+    const uint32_t cj = c.cnt[j];
     uint32_t Dc = 0;
     u128 N[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) N[a] = 0;
-    for (int p = glane; p < nprobe; p += GS) {
-      const uint32_t s = table_find(G.key, mask, key + __ldg(&A.dtab[p]));
-      if (s == kNone) continue;
-      const uint32_t id = G.id[s];
-      Dc += c.cnt[id];
+    for (int p0 = glane; p0 < nprobe; p0 += GS * U) {
+      uint64_t q[U];
+      bool v[U];
+      uint32_t sl[U];
 #pragma unroll
-      for (int a = 0; a < D; ++a) N[a] += fix_at<D>(c.fix, id, a);
-      if (p != center) any_nb = true;
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * GS;
+        v[u] = p < nprobe;
+        q[u] = key + (v[u] ? __ldg(&A.dtab[p]) : 0ull);
+      }
+      table_find_many<U>(G.key, mask, q, v, sl);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (sl[u] == kNone) continue;
+        const ulonglong2* r = G.row + (size_t)sl[u] * (D + 1);
+        Dc += (uint32_t)r[0].x;
+#pragma unroll
+        for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
+        if (p0 + u * GS != center) any_nb = true;
+      }
     }
 #pragma unroll
     for (int o = GS / 2; o > 0; o >>= 1) {
@@ -352,10 +649,13 @@ __device__ void phase_gather(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         N[a] += (u128)lo | ((u128)hi << 64);
       }
     }
+    // lane a < d: coordinate a of the centroid, its key field, its fixed value
     uint64_t field = 0;
+    u128 V = 0;
+    int La = 0;
     if (glane < D) {
       u128 Na = 0;
-      int La = 0, off = 0, span = 1, toff = 0;
+      int off = 0, span = 1, toff = 0;
       int64_t kmin = 0;
 #pragma unroll
       for (int a = 0; a < D; ++a)
@@ -368,55 +668,42 @@ __device__ void phase_gather(const LoopArgs& A, int t, uint32_t m, uint32_t mask
           kmin = A.P.kmin[a];
         }
       const double sv = div_round(Na, Dc, La, inexact);
-      A.sp[(size_t)j * D + glane] = sv;
       const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
       field = (uint64_t)(idx + 1) << off;
+      V = to_fixed(bits_of(sv), La, inexact, werr);
     }
 #pragma unroll
     for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
-    if (glane == 0) A.nkey[j] = field;
-  }
-}
-
-// Parent links of level t-1 (its merge slots now carry the ids of level t),
-// and release of level t-1's lookup table, which the merge of step t reuses.
-__device__ void phase_finish(const LoopArgs& A, int t, uint32_t m_prev, uint32_t base_prev,
-                             uint32_t base) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nth = gridDim.x * blockDim.x;
-  const Table cur = (t & 1) ? A.tab[1] : A.tab[0];
-  const Table old = (t & 1) ? A.tab[0] : A.tab[1];
-  for (uint32_t j = tid; j < m_prev; j += nth) {
-    A.forest[base_prev + j] = base + cur.id[A.pslot[j]];
-    old.key[old.list[j]] = kEmpty;
-  }
-}
-
-// Step iv: every cell of level t adds its count and count-weighted centroid
-// (Eq. 3-4) into the slot of its new key.
-template <int D>
-__device__ void phase_merge(const LoopArgs& A, int t, uint32_t m, uint32_t maskM,
-                            unsigned& inexact, unsigned& werr) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nth = gridDim.x * blockDim.x;
-  const Table M = (t & 1) ? A.tab[0] : A.tab[1];
-  const Cells c = (t & 1) ? A.cells[1] : A.cells[0];
-  for (uint32_t j = tid; j < m; j += nth) {
-    bool won;
-    const uint32_t s = table_insert(M.key, maskM, A.nkey[j], won, &A.fl->err);
-    if (s == kNone) continue;
-    if (won) {
-      const uint32_t id = atomicAdd(&A.st[t + 1].m, 1u);
-      M.list[id] = s;
+    // iv: merge into the slot of the new key
+    uint32_t ms = kNone;
+    if (glane == 0) {
+      bool won;
+      ms = table_insert(M.key, maskM, field, won, &A.fl->err);
+      if (ms != kNone) {
+        if (won) {
+          const uint32_t id = atomicAdd(&A.st[t + 1].m, 1u);
+          M.list[id] = ms;
+        }
+        atomicAdd((unsigned long long*)&M.row[(size_t)ms * (D + 1)].x, (unsigned long long)cj);
+      }
+      pslot[j] = ms;
     }
-    const uint32_t cnt = c.cnt[j];
-    atomicAdd(&M.cnt[s], cnt);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const u128 V = to_fixed(bits_of(A.sp[(size_t)j * D + a]), A.P.L[a], inexact, werr);
-      atomic_add_fixed(M.acc + ((size_t)s * D + a) * 4, V * (u128)cnt);
+    ms = __shfl_sync(gmask, ms, 0, GS);
+    if (glane < D && ms != kNone)
+      atomic_add_fixed(M.acc + ((size_t)ms * D + glane) * 4, V * (u128)cj);
+  }
+  if (t > 0) {
+    // level t-1: parent links, then its table is released
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nth = gridDim.x * blockDim.x;
+    const LevelTable Lp = A.tab[(t + 2) % 3];
+    const uint32_t* pp = A.pslot[(t - 1) & 1];
+    for (uint32_t i = tid; i < m_prev; i += nth) {
+      A.forest[base_prev + i] = base + G.id[pp[i]];
+      const uint32_t s = Lp.list[i];
+      Lp.key[s] = kEmpty;
+      Lp.row[(size_t)s * (D + 1)].x = 0;
     }
-    A.pslot[j] = s;
   }
 }
 
@@ -426,26 +713,40 @@ __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& i
                               unsigned& werr) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nth = gridDim.x * blockDim.x;
-  const Table M = (t & 1) ? A.tab[0] : A.tab[1];
-  const Cells nx = (t & 1) ? A.cells[0] : A.cells[1];
+  const LevelTable M = A.tab[(t + 1) % 3];
+  const Cells nx = A.cells[(t + 1) & 1];
   for (uint32_t id = tid; id < m1; id += nth) {
     const uint32_t s = M.list[id];
+    ulonglong2* r = M.row + (size_t)s * (D + 1);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      uint64_t* acc = M.acc + ((size_t)s * D + a) * 4;
-      const double v = round_fixed(limbs_value(acc), A.P.L[a], inexact);
-      nx.fix[(size_t)id * D + a] = pack(to_fixed(bits_of(v), A.P.L[a], inexact, werr));
-      acc[0] = acc[1] = acc[2] = acc[3] = 0;
-    }
+    for (int a = 0; a < D; ++a)
+      r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
     nx.key[id] = M.key[s];
-    nx.cnt[id] = M.cnt[s];
-    M.cnt[s] = 0;
+    nx.cnt[id] = (uint32_t)r[0].x;
     M.id[s] = id;
   }
 }
 
+// Mode of final cell r (row of its table slot) written to its label's row,
+// then the slot is released.
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_loop(LoopArgs A) {
+__device__ __forceinline__ void mode_and_release(const LevelTable& G, const Plan& P, uint32_t r,
+                                                 uint32_t label, double* modes, bool write,
+                                                 unsigned& inexact) {
+  const uint32_t s = G.list[r];
+  ulonglong2* row = G.row + (size_t)s * (D + 1);
+  if (write) {
+    const double cnt = (double)row[0].x;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      modes[(size_t)label * D + a] = round_fixed(as_u128(row[1 + a]), P.L[a], inexact) / cnt;
+  }
+  row[0].x = 0;
+  G.key[s] = kEmpty;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   unsigned inexact = 0, werr = 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nth = gridDim.x * blockDim.x;
@@ -453,8 +754,24 @@ __global__ void __launch_bounds__(kBlock) k_loop(LoopArgs A) {
   SegClock clk;
   clk.start();
 
-  // level 0
+  // step i, second pass: exact cell sums
   const uint32_t m0 = *(volatile uint32_t*)&A.fl->m0;
+  phase_count_totals(A, m0);
+  if (!grid_sync(A.bar, A.fl)) return;
+  phase_offsets(A, m0);
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegOffsets);
+  phase_scatter(A);
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegScatter);
+  if (A.f32)
+    phase_cell_sums<D, float>(A, inexact, werr);
+  else
+    phase_cell_sums<D, double>(A, inexact, werr);
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegSums);
+
+  // level 0
   const uint32_t maskA = mask_for(m0, A.capAB);
   if (tid == 0) {
     A.st[0].m = m0;
@@ -471,20 +788,16 @@ __global__ void __launch_bounds__(kBlock) k_loop(LoopArgs A) {
   bool converged = false;
   for (;;) {
     bool any_nb = false;
-    phase_gather<D>(A, t, m, mask, any_nb, inexact);
-    if (t > 0) phase_finish(A, t, m_prev, base_prev, base);
+    const uint32_t maskM = mask_for(m, A.capAB);
+    phase_update<D>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact, werr);
     if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
     if (!grid_sync(A.bar, A.fl)) return;
-    clk.lap(kSegGather);
+    clk.lap(t == 0 ? kSegUpdateFirst : kSegUpdateRest);
     if (!vst[t].has_nb) {
       converged = true;
       break;
     }
     if (t == A.max_iter) break;
-    const uint32_t maskM = mask_for(m, A.capAB);
-    phase_merge<D>(A, t, m, maskM, inexact, werr);
-    if (!grid_sync(A.bar, A.fl)) return;
-    clk.lap(kSegMerge);
     const uint32_t m1 = vst[t + 1].m;
     phase_compact<D>(A, t, m1, inexact, werr);
     if (tid == 0) {
@@ -504,13 +817,22 @@ __global__ void __launch_bounds__(kBlock) k_loop(LoopArgs A) {
   const int T = t;
   const uint32_t k = m;
 
-  // the final level: every cell is its own root; release its lookup table
+  // the update of step T is not applied: clear its merge table; every final
+  // cell is its own root
   {
-    const Table G = (T & 1) ? A.tab[1] : A.tab[0];
-    for (uint32_t j = tid; j < k; j += nth) {
-      A.forest[base + j] = base + j;
-      G.key[G.list[j]] = kEmpty;
+    const LevelTable Ms = A.tab[(T + 1) % 3];
+    const uint32_t ms = vst[T + 1].m;
+    for (uint32_t id = tid; id < ms; id += nth) {
+      const uint32_t s = Ms.list[id];
+      Ms.key[s] = kEmpty;
+      Ms.row[(size_t)s * (D + 1)].x = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        uint64_t* acc = Ms.acc + ((size_t)s * D + a) * 4;
+        acc[0] = acc[1] = acc[2] = acc[3] = 0;
+      }
     }
+    for (uint32_t j = tid; j < k; j += nth) A.forest[base + j] = base + j;
   }
   if (!grid_sync(A.bar, A.fl)) return;
 
@@ -535,7 +857,7 @@ __global__ void __launch_bounds__(kBlock) k_loop(LoopArgs A) {
   if (numbered) {
     // label of a final cell = number of final keys below its key (keys are
     // unique), i.e. ascending lexicographic order of the integer keys
-    const Cells c = (T & 1) ? A.cells[1] : A.cells[0];
+    const Cells c = A.cells[T & 1];
     const uint32_t warp = tid >> 5, nwarps = nth >> 5;
     const int lane = threadIdx.x & 31;
     for (uint32_t r = warp; r < k; r += nwarps) {
@@ -551,16 +873,10 @@ __global__ void __launch_bounds__(kBlock) k_loop(LoopArgs A) {
       A.labslot[A.T0.list[cc]] = A.rank[A.forest[cc] - base];
     if (!grid_sync(A.bar, A.fl)) return;
     for (int64_t i = tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
-    if ((int64_t)k <= A.modes_cap) {
-      for (uint32_t r = tid; r < k; r += nth) {
-        const uint32_t rr = A.rank[r];
-        const double cnt = (double)c.cnt[r];
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-          A.modes[(size_t)rr * D + a] =
-              round_fixed(fix_at<D>(c.fix, r, a), A.P.L[a], inexact) / cnt;
-      }
-    }
+    const LevelTable G = A.tab[T % 3];
+    const bool write = (int64_t)k <= A.modes_cap;
+    for (uint32_t r = tid; r < k; r += nth)
+      mode_and_release<D>(G, A.P, r, A.rank[r], A.modes, write, inexact);
   }
   clk.lap(kSegLabels);
   if (tid == 0) {
@@ -596,16 +912,11 @@ __global__ void k_labels_tail(const uint32_t* __restrict__ slot0,
 }
 
 template <int D>
-__global__ void k_modes_tail(Cells c, Plan P, const uint32_t* __restrict__ rank,
-                             double* __restrict__ modes, uint32_t k) {
+__global__ void k_modes_tail(LevelTable G, Plan P, const uint32_t* __restrict__ rank,
+                             double* __restrict__ modes, uint32_t k, bool write) {
   unsigned inexact = 0;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x) {
-    const uint32_t rr = rank[r];
-    const double cnt = (double)c.cnt[r];
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      modes[(size_t)rr * D + a] = round_fixed(fix_at<D>(c.fix, r, a), P.L[a], inexact) / cnt;
-  }
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x)
+    mode_and_release<D>(G, P, r, rank[r], modes, write, inexact);
 }
 
 __global__ void k_iota_keys(Cells c, uint64_t* keys, uint32_t* vals, uint32_t k) {
@@ -628,17 +939,27 @@ __global__ void k_rank(const uint32_t* __restrict__ sorted_vals, uint32_t* __res
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
                          cudaStream_t s) {
-  unsigned g = grid_for(n * d, kBlock * 8, 152u * 8u);
+  const bool vec = ((uintptr_t)pts & 15u) == 0;
+  const int W = vec ? (f32 ? 4 : 2) : 1;
+  const unsigned g = grid_for(n * d / W, kBlock * 4, 152u * 8u);
   if (f32) {
-    GS_DISPATCH_D(d, k_range<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, fl));
+    if (vec) {
+      GS_DISPATCH_D(d, k_range<D, float, 4><<<g, kBlock, 0, s>>>((const float*)pts, n, fl));
+    } else {
+      GS_DISPATCH_D(d, k_range<D, float, 1><<<g, kBlock, 0, s>>>((const float*)pts, n, fl));
+    }
   } else {
-    GS_DISPATCH_D(d, k_range<D, double><<<g, kBlock, 0, s>>>((const double*)pts, n, fl));
+    if (vec) {
+      GS_DISPATCH_D(d, k_range<D, double, 2><<<g, kBlock, 0, s>>>((const double*)pts, n, fl));
+    } else {
+      GS_DISPATCH_D(d, k_range<D, double, 1><<<g, kBlock, 0, s>>>((const double*)pts, n, fl));
+    }
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
-                       Table T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
+                       BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, cudaStream_t s) {
   const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * 6u);
   const bool vec_ok = ((uintptr_t)pts & 15u) == 0;
@@ -658,11 +979,13 @@ int loop_grid_d() {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D>, kBlock, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D>, kLoopBlock, 0) !=
+      cudaSuccess)
     return -1;
   if (per_sm < 1) return -1;
   if (per_sm > 2) per_sm = 2;  // fewer blocks make the grid barriers cheaper
-  return sms * per_sm;
+  const int g = sms * per_sm;
+  return g < kMaxLoopGrid ? g : kMaxLoopGrid;
 }
 }  // namespace
 
@@ -684,7 +1007,7 @@ cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s) {
   LoopArgs args = a;
   void* params[] = {&args};
   GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D>, dim3(grid),
-                                                          dim3(kBlock), params, 0, s));
+                                                          dim3(kLoopBlock), params, 0, s));
   return cudaSuccess;
 }
 
@@ -709,11 +1032,10 @@ cudaError_t launch_label_tail(const LoopArgs& a, uint32_t m0, uint32_t k, uint32
   k_labels_tail<<<grid_for(a.n), kBlock, 0, s>>>(a.slot0, a.labslot, a.labels, a.n);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((int64_t)k <= a.modes_cap) {
-    const Cells c = (T & 1) ? a.cells[1] : a.cells[0];
-    GS_DISPATCH_D(a.P.d, k_modes_tail<D><<<grid_for(k), kBlock, 0, s>>>(c, a.P, a.rank, a.modes,
-                                                                         k));
-  }
+  // modes (if they fit) and release of the final level's table
+  const bool write = (int64_t)k <= a.modes_cap;
+  GS_DISPATCH_D(a.P.d, k_modes_tail<D><<<grid_for(k), kBlock, 0, s>>>(a.tab[T % 3], a.P, a.rank,
+                                                                       a.modes, k, write));
   return cudaGetLastError();
 }
 

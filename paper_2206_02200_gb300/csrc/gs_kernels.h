@@ -8,41 +8,61 @@
 
 namespace gs {
 
-// A hash table of packed cell keys with per-slot payload.  key[] is kEmpty
-// where free; cnt[] and acc[] (d x 4 limb accumulators per slot) are zero
-// where free.  list[i] is the slot of the i-th key inserted (in arrival
-// order); id[] maps a slot to the cell that owns it.
-struct Table {
+// The binning table of step i: packed cell keys with, per slot, the resident
+// count, the offset of the cell's run in the counting sort of the points, and
+// the exact coordinate sums (d x 4 limb accumulators).  key[] is kEmpty where
+// free; cnt[] and acc[] are zero where free (off[] needs no clearing).
+// list[i] is the slot of the i-th key inserted (arrival order).
+struct BinTable {
   uint64_t* key;
-  uint32_t* id;
   uint32_t* cnt;
+  uint32_t* off;
   uint64_t* acc;
   uint32_t* list;
   uint32_t cap;  // power of two
 };
 
-// The active cells of one level: packed key, resident count and coordinate
-// sum.  The sum is the float64 value of Sec. 2.1 (exact sum rounded once),
-// held as the two's-complement 128-bit integer it equals in units of 2^L_a
-// (fix[j * d + a] = {low word, high word}).
+// A table of the cells of one level, also the merge target of the update
+// that creates the next level.  Per slot:
+//   key  packed cell key (kEmpty where free)
+//   id   the cell's index in the level's cell list
+//   row  d + 1 pairs of 64-bit words: row[0].x = resident count, row[1 + a] =
+//        the cell's coordinate sum of axis a (the float64 value of Sec. 2.1,
+//        an exact sum rounded once) as the two's-complement 128-bit integer it
+//        equals in units of 2^L_a, {low word, high word}
+//   acc  d x 4 limb accumulators of exact sums while the table is a merge
+//        target (zero otherwise)
+// A clean table has every key empty, every row[0] and every acc zero.
+// list[i] is the slot of the level's i-th cell.
+struct LevelTable {
+  uint64_t* key;
+  uint32_t* id;
+  ulonglong2* row;
+  uint64_t* acc;
+  uint32_t* list;
+  uint32_t cap;  // power of two
+};
+
+// The active cells of one level, in list order: packed key and resident count.
 struct Cells {
   uint64_t* key;
   uint32_t* cnt;
-  ulonglong2* fix;
 };
 
 // Everything the persistent update loop reads and writes.
 struct LoopArgs {
   Plan P;
+  const void* pts;       // the points (n x d, float64 or float32)
+  bool f32;              // points are float32
+  uint32_t* perm;        // n: the points sorted by cell (counting sort)
+  uint32_t* blocksum;    // one word per block of the loop kernel
   const int64_t* thr;    // cell-face table (order codes)
   const uint64_t* dtab;  // packed-key offsets of the 3^d neighbours
-  Table T0;              // binning table (its slots are the points' cell slots)
-  Table tab[2];          // lookup/merge tables of alternate levels
-  uint32_t capAB;        // capacity of tab[0], tab[1]
+  BinTable T0;           // binning table (its slots are the points' cell slots)
+  LevelTable tab[3];     // level t uses tab[t % 3]; its update merges into tab[(t + 1) % 3]
+  uint32_t capAB;        // capacity of each of tab[0..2]
   Cells cells[2];        // cells of alternate levels
-  double* sp;            // new centroids of the current level (m x d)
-  uint64_t* nkey;        // new packed keys of the current level
-  uint32_t* pslot;       // merge-table slot of every cell of the current level
+  uint32_t* pslot[2];    // merge slot of every cell of alternate levels
   uint32_t* forest;      // parent of every cell of every level, then its final cell
   uint32_t* forest2;     // pointer-jumping buffer
   uint32_t* labslot;     // label of every binning slot
@@ -63,11 +83,12 @@ struct LoopArgs {
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
                          cudaStream_t s);
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
-                       Table T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
+                       BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, cudaStream_t s);
 
 // Blocks of the cooperative loop kernel for dimension d on the current device
-// (all co-resident), or a negative value on error.
+// (all co-resident, at most kMaxLoopGrid), or a negative value on error.
+constexpr int kMaxLoopGrid = 4096;
 int loop_grid(int d);
 // Steps ii-v for every level, then labels and modes (Sec. 2.1, Algorithm 1),
 // in one cooperative launch of `grid` blocks.

@@ -42,11 +42,22 @@ struct Carve {
   }
 };
 
-Table carve_table(Carve& c, uint32_t cap, uint32_t lmax, int d) {
-  Table t;
+BinTable carve_bin_table(Carve& c, uint32_t cap, uint32_t lmax, int d) {
+  BinTable t;
+  t.key = c.take<uint64_t>(cap);
+  t.cnt = c.take<uint32_t>(cap);
+  t.off = c.take<uint32_t>(cap);
+  t.acc = c.take<uint64_t>((size_t)cap * d * 4);
+  t.list = c.take<uint32_t>(lmax);
+  t.cap = cap;
+  return t;
+}
+
+LevelTable carve_level_table(Carve& c, uint32_t cap, uint32_t lmax, int d) {
+  LevelTable t;
   t.key = c.take<uint64_t>(cap);
   t.id = c.take<uint32_t>(cap);
-  t.cnt = c.take<uint32_t>(cap);
+  t.row = c.take<ulonglong2>((size_t)cap * (d + 1));
   t.acc = c.take<uint64_t>((size_t)cap * d * 4);
   t.list = c.take<uint32_t>(lmax);
   t.cap = cap;
@@ -68,19 +79,17 @@ size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, s
   B.thr = c.take<int64_t>(thr_words);
   B.dtab = c.take<uint64_t>(nprobe);
   B.slot0 = c.take<uint32_t>(n);
-  B.t0 = carve_table(c, cap, M, d);
+  B.perm = c.take<uint32_t>(n);
+  B.blocksum = c.take<uint32_t>(kMaxLoopGrid);
+  B.t0 = carve_bin_table(c, cap, M, d);
   B.t0_maxcells = M;
-  B.tab[0] = carve_table(c, cap, M, d);
-  B.tab[1] = carve_table(c, cap, M, d);
+  for (int i = 0; i < 3; ++i) B.tab[i] = carve_level_table(c, cap, M, d);
   B.capAB = cap;
   for (int i = 0; i < 2; ++i) {
     B.cells[i].key = c.take<uint64_t>(M);
     B.cells[i].cnt = c.take<uint32_t>(M);
-    B.cells[i].fix = c.take<ulonglong2>((size_t)M * d);
+    B.pslot[i] = c.take<uint32_t>(M);
   }
-  B.sp = c.take<double>((size_t)M * d);
-  B.nkey = c.take<uint64_t>(M);
-  B.pslot = c.take<uint32_t>(M);
   B.forest = c.take<uint32_t>((size_t)M * (max_iter + 1));
   B.forest2 = c.take<uint32_t>((size_t)M * (max_iter + 1));
   B.labslot = c.take<uint32_t>(cap);
@@ -93,9 +102,16 @@ size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, s
   return c.used;
 }
 
-cudaError_t clear_table(const Table& t, int d, cudaStream_t s) {
+cudaError_t clear_bin_table(const BinTable& t, int d, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(t.key, 0xFF, sizeof(uint64_t) * t.cap, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.cnt, 0, sizeof(uint32_t) * t.cap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t.acc, 0, sizeof(uint64_t) * t.cap * d * 4, s);
+  return e;
+}
+
+cudaError_t clear_level_table(const LevelTable& t, int d, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(t.key, 0xFF, sizeof(uint64_t) * t.cap, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t.row, 0, sizeof(ulonglong2) * t.cap * (d + 1), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.acc, 0, sizeof(uint64_t) * t.cap * d * 4, s);
   return e;
 }
@@ -132,9 +148,9 @@ struct StaticWorkspace : public Workspace {
     layout(base, n, d, max_iter, M, thr_words, nprobe, &laid);
     // the scratch keeps the previous call's contents: clear what must start
     // empty or zero
-    if (clear_table(laid.t0, d, s) != cudaSuccess || clear_table(laid.tab[0], d, s) != cudaSuccess ||
-        clear_table(laid.tab[1], d, s) != cudaSuccess)
-      return GS_E_CUDA;
+    if (clear_bin_table(laid.t0, d, s) != cudaSuccess) return GS_E_CUDA;
+    for (int i = 0; i < 3; ++i)
+      if (clear_level_table(laid.tab[i], d, s) != cudaSuccess) return GS_E_CUDA;
     b = laid;
     return GS_OK;
   }
@@ -172,8 +188,8 @@ extern "C" gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_st
     if (info) *info = inf;
     return GS_OK;
   }
-  // the per-point slot array alone must fit
-  if ((size_t)n * sizeof(uint32_t) + (size_t(1) << 20) > kScratchBytes) return GS_E_SCRATCH;
+  // the per-point arrays (cell slot and counting-sort position) alone must fit
+  if ((size_t)n * 2 * sizeof(uint32_t) + (size_t(1) << 20) > kScratchBytes) return GS_E_SCRATCH;
 
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;

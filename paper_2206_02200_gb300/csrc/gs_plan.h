@@ -48,8 +48,10 @@ struct DevFlags {
 };
 
 // Segments of the loop kernel timed on the device clock by block 0 (between
-// grid barriers): level 0, gather (+ parent links), merge, compact, labels.
-constexpr int kLoopPhases = 5;
+// grid barriers): counting-sort offsets, scatter, exact cell sums (the second
+// pass of binning), level 0, the first update step, the later update steps,
+// compaction, labels.
+constexpr int kLoopPhases = 8;
 
 // What the update loop reports back (written by one thread at its end).
 struct LoopResult {
@@ -65,11 +67,12 @@ struct LoopResult {
 
 // Arrival counter and generation of a software grid barrier, and the stop
 // decision its last arrival takes for every block (any error bit set).
+// count and gen sit on separate 128-byte lines, so the polling of gen does
+// not contend with the arrivals.
 struct GridBar {
-  unsigned int count;
-  unsigned int gen;
+  alignas(128) unsigned int count;
+  alignas(128) unsigned int gen;
   unsigned int stop;
-  unsigned int pad;
 };
 
 }  // namespace gs

@@ -37,8 +37,8 @@ EXPORTS = ("gs_create", "gs_set_precision", "gs_set_stream", "gs_fit", "gs_set_t
 
 #: gs_phase names, in enum order: CUDA-event phases, then the loop kernel's
 #: own device-clock split
-PHASES = ("range", "bin", "loop", "sort", "k_level0", "k_gather", "k_merge", "k_compact",
-          "k_labels")
+PHASES = ("range", "bin", "loop", "sort", "k_offsets", "k_scatter", "k_sums", "k_level0",
+          "k_update_first", "k_update_rest", "k_compact", "k_labels")
 
 
 class gs_fit_info(ctypes.Structure):

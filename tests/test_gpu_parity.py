@@ -108,6 +108,25 @@ def test_uniform_noise_many_cells(seed):
     check_parity(X, float(rng.uniform(2, 9)))
 
 
+def test_unaligned_input():
+    # points starting 8 bytes (float64) or 4 bytes (float32) past a 16-byte
+    # boundary take the scalar load paths
+    rng = np.random.default_rng(77)
+    X = rng.normal(0, 6, size=(20001, 3))
+    ref = oracle.fit(X, 2.0, 50)
+    for dt, Xd in ((torch.float64, X), (torch.float32, X.astype(np.float32))):
+        buf = torch.empty(X.size + 1, dtype=dt, device="cuda")
+        pts = buf[1:].view(X.shape)
+        pts.copy_(torch.from_numpy(np.ascontiguousarray(Xd)))
+        assert pts.data_ptr() % 16 != 0
+        labels, modes, info = gridshift.fit(pts, 2.0, 50)
+        torch.cuda.synchronize()
+        exp = ref if dt == torch.float64 else oracle.fit(Xd.astype(np.float64), 2.0, 50)
+        np.testing.assert_array_equal(labels.cpu().numpy(), exp["labels"])
+        np.testing.assert_array_equal(modes.cpu().numpy().view(np.int64),
+                                      exp["modes"].view(np.int64))
+
+
 def test_float32_input():
     X = synth.gmm_points(200_000, 6, 40, seed=9)
     ref, _ = check_parity(X.astype(np.float64), 4.0)
