@@ -171,7 +171,7 @@ struct CtxWorkspace : public Workspace {
   BinTableBuf t0;
   LevelTableBuf tab[3];
   CellBuf cells[2];
-  DBuf<uint32_t> pslot[2], forest, forest2, labslot, rank;
+  DBuf<uint32_t> pslot[2], forest, forest2, labslot, rank, filter;
   DBuf<uint64_t> skey, skey2;
   DBuf<uint32_t> sval, sval2, shist;
 
@@ -285,6 +285,8 @@ struct CtxWorkspace : public Workspace {
     WS_CU(forest2.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(labslot.ensure(t0.cap), "alloc labslot");
     WS_CU(rank.ensure(m), "alloc rank");
+    WS_CU(filter.ensure(2 * kFilterWords), "alloc filters");
+    b.filter = filter.p;
     b.capAB = tab[0].cap;
     for (int i = 0; i < 3; ++i) {
       b.tab[i] = tab[i].view();
@@ -327,7 +329,7 @@ struct CtxWorkspace : public Workspace {
       cells[i].release();
       pslot[i].release();
     }
-    forest.release(); forest2.release(); labslot.release(); rank.release();
+    forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
     if (h_flags) cudaFreeHost(h_flags);
     if (h_res) cudaFreeHost(h_res);

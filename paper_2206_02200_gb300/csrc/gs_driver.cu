@@ -238,6 +238,8 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   L.cells[1] = b.cells[1];
   L.pslot[0] = b.pslot[0];
   L.pslot[1] = b.pslot[1];
+  L.filter[0] = b.filter;
+  L.filter[1] = b.filter + kFilterWords;
   L.forest = b.forest;
   L.forest2 = b.forest2;
   L.labslot = b.labslot;
@@ -253,6 +255,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   L.res = b.res;
   L.max_iter = a.max_iter;
   L.rank_max = kRankMax;
+  GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
   GS_T_BEGIN(GS_PHASE_LOOP);
   GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
   GS_T_END();

@@ -31,6 +31,7 @@ struct Bufs {
   uint32_t capAB = 0;
   Cells cells[2]{};            // m0 cells each
   uint32_t* pslot[2] = {nullptr, nullptr};  // m0 each
+  uint32_t* filter = nullptr;  // 2 * kFilterWords
   uint32_t* forest = nullptr;  // m0 * (max_iter + 1)
   uint32_t* forest2 = nullptr; // m0 * (max_iter + 1)
   uint32_t* labslot = nullptr; // t0.cap

@@ -351,19 +351,45 @@ __device__ __forceinline__ ulonglong2 settle_sum(uint64_t* acc, int L, unsigned&
   return pack(to_fixed(bits_of(v), L, inexact, werr));
 }
 
-// Lanes given to one cell in the update: enough for the 3^d probes of small d.
+// ---------------------------------------------------------------------------
+// Occupancy filter of a level: one bit per hashed key (a Bloom filter with
+// one hash function), 2^B bits with 2^B >= 32 m (at most kFilterBits).  A
+// neighbour probe whose bit is clear cannot hit and never leaves the SM: the
+// update phase copies the level's filter into shared memory first.
+constexpr uint32_t kFilterBits = 1u << kFilterLog2Max;
+
+__device__ __forceinline__ int filter_log2(uint32_t m) {
+  int b = 10;
+  while (b < kFilterLog2Max && (1u << b) < 32u * m) ++b;
+  return b;
+}
+
+__device__ __forceinline__ uint32_t filter_bit(uint64_t key, int lg) {
+  return (uint32_t)((key * 0xD6E8FEB86659FD93ull) >> (64 - lg));
+}
+
+__device__ __forceinline__ void filter_set(uint32_t* f, uint64_t key, int lg) {
+  const uint32_t b = filter_bit(key, lg);
+  atomicOr(&f[b >> 5], 1u << (b & 31));
+}
+
+// Lanes given to one cell in the update: a power of two, at least d and at
+// least GatherLanes<D>::min.  Few lanes per cell put several cells in flight
+// per warp, which hides the latency of their dependent table loads when a
+// level has many cells; a level with few cells gets 32 lanes per cell, which
+// shortens each cell's chain of probes.
 template <int D>
 struct GatherLanes {
-  static constexpr int value = D == 1 ? 4 : (D == 2 ? 16 : 32);
+  static constexpr int min = D <= 3 ? 4 : D <= 5 ? 8 : D == 6 ? 16 : 32;
 };
 
 constexpr int pow3(int d) { return d == 0 ? 1 : 3 * pow3(d - 1); }
 
 // Probes each lane has in flight at once: min(4, its probes per cell).
-template <int D>
+template <int D, int GS>
 struct ProbeBatch {
   static constexpr int probes = pow3(D);
-  static constexpr int per_lane = (probes + GatherLanes<D>::value - 1) / GatherLanes<D>::value;
+  static constexpr int per_lane = (probes + GS - 1) / GS;
   static constexpr int value = per_lane < 4 ? per_lane : 4;
 };
 
@@ -560,6 +586,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
   const BinTable T0 = A.T0;
   const LevelTable G = A.tab[0];
   const Cells c = A.cells[0];
+  const int lg0 = filter_log2(m0);
   for (uint32_t id = tid; id < m0; id += nth) {
     const uint32_t s = T0.list[id];
     const uint64_t key = T0.key[s];
@@ -575,6 +602,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
       G.id[sa] = id;
       G.list[id] = sa;
     }
+    filter_set(A.filter[0], key, lg0);
     c.key[id] = key;
     c.cnt[id] = cnt;
     T0.cnt[s] = 0;
@@ -594,12 +622,11 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
 // the run, the merge table is cleared instead of used.
 // For t > 0 the same phase links every cell of level t-1 to its cell of level
 // t (the union of resident sets of Eq. 4) and clears level t-1's table.
-template <int D>
+template <int D, int GS>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
                              unsigned& inexact, unsigned& werr) {
-  constexpr int GS = GatherLanes<D>::value;
-  constexpr int U = ProbeBatch<D>::value;
+  constexpr int U = ProbeBatch<D, GS>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
@@ -610,6 +637,24 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
   const int nprobe = A.P.nprobe, center = A.P.center;
+  // the level's occupancy filter, into shared memory; the filter of level
+  // t-1 is cleared for level t+1
+  extern __shared__ uint4 s_dyn[];
+  uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
+  const int lg = filter_log2(m);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.filter[t & 1]);
+    uint4* dst = reinterpret_cast<uint4*>(s_filter);
+    const uint32_t n4 = (1u << lg) / 128;
+    for (uint32_t w = threadIdx.x; w < n4; w += blockDim.x) dst[w] = __ldcg(src + w);
+    if (t > 0) {
+      uint4* old = reinterpret_cast<uint4*>(A.filter[(t + 1) & 1]);
+      const uint32_t o4 = (1u << filter_log2(m_prev)) / 128;
+      const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (uint32_t w = tid; w < o4; w += gridDim.x * blockDim.x) old[w] = make_uint4(0, 0, 0, 0);
+    }
+    __syncthreads();
+  }
   for (uint32_t j = group; j < m; j += ngroups) {
     const uint64_t key = c.key[j];
     const uint32_t cj = c.cnt[j];
@@ -624,8 +669,9 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int p = p0 + u * GS;
-        v[u] = p < nprobe;
-        q[u] = key + (v[u] ? __ldg(&A.dtab[p]) : 0ull);
+        q[u] = key + (p < nprobe ? __ldg(&A.dtab[p]) : 0ull);
+        const uint32_t fb = filter_bit(q[u], lg);
+        v[u] = p < nprobe && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
       }
       table_find_many<U>(G.key, mask, q, v, sl);
 #pragma unroll
@@ -715,15 +761,19 @@ __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& i
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable M = A.tab[(t + 1) % 3];
   const Cells nx = A.cells[(t + 1) & 1];
+  uint32_t* f = A.filter[(t + 1) & 1];
+  const int lg = filter_log2(m1);
   for (uint32_t id = tid; id < m1; id += nth) {
     const uint32_t s = M.list[id];
     ulonglong2* r = M.row + (size_t)s * (D + 1);
 #pragma unroll
     for (int a = 0; a < D; ++a)
       r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
-    nx.key[id] = M.key[s];
+    const uint64_t key = M.key[s];
+    nx.key[id] = key;
     nx.cnt[id] = (uint32_t)r[0].x;
     M.id[s] = id;
+    filter_set(f, key, lg);
   }
 }
 
@@ -789,7 +839,13 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   for (;;) {
     bool any_nb = false;
     const uint32_t maskM = mask_for(m, A.capAB);
-    phase_update<D>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact, werr);
+    // lanes per cell: the fewest (most cells in flight) while the level has
+    // more cells than warps, else 32
+    constexpr int GSmin = GatherLanes<D>::min;
+    if (GSmin < 32 && m > (nth >> 5))
+      phase_update<D, GSmin>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact, werr);
+    else
+      phase_update<D, 32>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact, werr);
     if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
     if (!grid_sync(A.bar, A.fl)) return;
     clk.lap(t == 0 ? kSegUpdateFirst : kSegUpdateRest);
@@ -979,7 +1035,11 @@ int loop_grid_d() {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D>, kLoopBlock, 0) !=
+  const int smem = (int)(kFilterWords * sizeof(uint32_t));
+  if (cudaFuncSetAttribute(k_loop<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D>, kLoopBlock, smem) !=
       cudaSuccess)
     return -1;
   if (per_sm < 1) return -1;
@@ -1006,8 +1066,9 @@ int loop_grid(int d) {
 cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s) {
   LoopArgs args = a;
   void* params[] = {&args};
+  const size_t smem = kFilterWords * sizeof(uint32_t);
   GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D>, dim3(grid),
-                                                          dim3(kLoopBlock), params, 0, s));
+                                                          dim3(kLoopBlock), params, smem, s));
   return cudaSuccess;
 }
 

@@ -43,6 +43,10 @@ struct LevelTable {
   uint32_t cap;  // power of two
 };
 
+// Occupancy filter of a level (see the loop kernel): at most 2^20 bits.
+constexpr int kFilterLog2Max = 20;
+constexpr uint32_t kFilterWords = (1u << kFilterLog2Max) / 32;
+
 // The active cells of one level, in list order: packed key and resident count.
 struct Cells {
   uint64_t* key;
@@ -63,6 +67,8 @@ struct LoopArgs {
   uint32_t capAB;        // capacity of each of tab[0..2]
   Cells cells[2];        // cells of alternate levels
   uint32_t* pslot[2];    // merge slot of every cell of alternate levels
+  uint32_t* filter[2];   // occupancy filters of alternate levels, kFilterWords each,
+                         // zeroed by the host
   uint32_t* forest;      // parent of every cell of every level, then its final cell
   uint32_t* forest2;     // pointer-jumping buffer
   uint32_t* labslot;     // label of every binning slot

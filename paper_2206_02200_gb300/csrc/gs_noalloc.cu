@@ -94,6 +94,7 @@ size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, s
   B.forest2 = c.take<uint32_t>((size_t)M * (max_iter + 1));
   B.labslot = c.take<uint32_t>(cap);
   B.rank = c.take<uint32_t>(M);
+  B.filter = c.take<uint32_t>(2 * kFilterWords);
   B.skey = c.take<uint64_t>(M);
   B.skey2 = c.take<uint64_t>(M);
   B.sval = c.take<uint32_t>(M);
