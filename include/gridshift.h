@@ -145,6 +145,36 @@ gs_status gs_set_stream(gs_ctx* ctx, void* cuda_stream);
 gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int32_t* labels,
                  double* modes, int64_t modes_cap, int64_t* k_out, gs_fit_info* info);
 
+/* Runs GridShift on B independent point sets (instances) in one call, with
+ * the same d, h and max_iter: the result for every instance is the result
+ * gs_fit gives for that instance alone (Sec. 2.1; the paper has no batched
+ * form, instances simply never interact).
+ *   points        device, all instances' points concatenated, n x d row-major
+ *   offsets       host int64[B + 1]: instance b owns points
+ *                 offsets[b] .. offsets[b + 1] - 1; offsets[0] = 0,
+ *                 non-decreasing, n = offsets[B] < 2^31 (empty instances allowed)
+ *   B             1 <= B <= 2^20
+ *   labels        device int32[n]: cluster of every point, numbered 0 .. k_b - 1
+ *                 within its instance b (output)
+ *   modes         device float64[modes_cap x d]: the modes of instance 0, then
+ *                 of instance 1, ... (output)
+ *   modes_cap     rows available in modes
+ *   mode_offsets  host int64[B + 1]: instance b's modes are rows
+ *                 mode_offsets[b] .. mode_offsets[b + 1] - 1 (output)
+ *   infos         host gs_fit_info[B]: per-instance iterations, converged, m0,
+ *                 k and cell_iters; inexact and launches are those of the whole
+ *                 call (output)
+ * All instances run in one pass of the pipeline: every cell key carries its
+ * instance, an instance that meets the stop criterion is frozen while the
+ * others continue.  If the total number of clusters exceeds modes_cap,
+ * returns GS_E_CAPACITY with labels, mode_offsets and infos filled.  Returns
+ * GS_OK, GS_E_INVALID, GS_E_NOMEM, GS_E_KEYRANGE (also when the instance
+ * index does not fit the packed key beside the axes), GS_E_CAPACITY,
+ * GS_E_CUDA or GS_E_INTERNAL. */
+gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const int64_t* offsets,
+                         int B, int32_t* labels, double* modes, int64_t modes_cap,
+                         int64_t* mode_offsets, gs_fit_info* infos);
+
 /* Turns per-phase device timing of later gs_fit calls on (enable != 0) or
  * off.  When on, each call records CUDA events on its stream around each
  * launch group and reads their elapsed times after its final synchronisation;

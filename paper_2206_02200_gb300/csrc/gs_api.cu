@@ -174,6 +174,9 @@ struct CtxWorkspace : public Workspace {
   DBuf<uint32_t> pslot[2], forest, forest2, labslot, rank, filter;
   DBuf<uint64_t> skey, skey2;
   DBuf<uint32_t> sval, sval2, shist;
+  DBuf<int64_t> offsets;
+  DBuf<uint32_t> inst;
+  std::vector<uint64_t> h_inst;   // host copy of the per-instance state (8-byte aligned)
 
   DevFlags* h_flags = nullptr;    // pinned
   LoopResult* h_res = nullptr;    // pinned
@@ -310,7 +313,6 @@ struct CtxWorkspace : public Workspace {
     WS_CU(sval.ensure(k), "alloc sort");
     WS_CU(sval2.ensure(k), "alloc sort");
     WS_CU(shist.ensure(radix_hist_words(k)), "alloc sort");
-#undef WS_CU
     b.skey = skey.p;
     b.skey2 = skey2.p;
     b.sval = sval.p;
@@ -318,6 +320,18 @@ struct CtxWorkspace : public Workspace {
     b.shist = shist.p;
     return GS_OK;
   }
+
+  gs_status batch_space(int B, Bufs& b, uint32_t** host, std::string* err) override {
+    cudaError_t e;
+    WS_CU(offsets.ensure((size_t)B + 1), "alloc offsets");
+    WS_CU(inst.ensure(inst_words(B) + 2), "alloc instance state");
+    h_inst.resize(inst_words(B) / 2 + 2);
+    b.offsets = offsets.p;
+    b.inst = inst.p;
+    *host = reinterpret_cast<uint32_t*>(h_inst.data());
+    return GS_OK;
+  }
+#undef WS_CU
 
   void mark_dirty(bool d) override { dirty = d; }
 
@@ -331,6 +345,7 @@ struct CtxWorkspace : public Workspace {
     }
     forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
+    offsets.release(); inst.release();
     if (h_flags) cudaFreeHost(h_flags);
     if (h_res) cudaFreeHost(h_res);
     if (h_words) cudaFreeHost(h_words);
@@ -497,6 +512,64 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
     }
   }
   return st;
+}
+
+gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const int64_t* offsets,
+                         int B, int32_t* labels, double* modes, int64_t modes_cap,
+                         int64_t* mode_offsets, gs_fit_info* infos) {
+  if (!ctx) return GS_E_INVALID;
+  ctx->err.clear();
+  if (!offsets || !mode_offsets || !infos) return fail(ctx, GS_E_INVALID, "NULL offsets, mode_offsets or infos");
+  if (B < 1 || B > kMaxBatch) return fail(ctx, GS_E_INVALID, "B out of range");
+  if (offsets[0] != 0) return fail(ctx, GS_E_INVALID, "offsets[0] must be 0");
+  for (int i = 0; i < B; ++i)
+    if (offsets[i + 1] < offsets[i]) return fail(ctx, GS_E_INVALID, "offsets must not decrease");
+  const int64_t n = offsets[B];
+  if (n >= (1ll << 31)) return fail(ctx, GS_E_INVALID, "n out of range");
+  if (dtype != GS_IN_F64 && dtype != GS_IN_F32) return fail(ctx, GS_E_INVALID, "bad dtype");
+  if (modes_cap < 0 || (modes_cap > 0 && !modes))
+    return fail(ctx, GS_E_INVALID, "modes is NULL with modes_cap > 0");
+  if (n > 0 && (!points || !labels)) return fail(ctx, GS_E_INVALID, "NULL points or labels");
+  std::memset(infos, 0, sizeof(gs_fit_info) * (size_t)B);
+  for (int i = 0; i <= B; ++i) mode_offsets[i] = 0;
+  ctx->tm.reset();
+  std::memset(&ctx->last_times, 0, sizeof(ctx->last_times));
+  if (n == 0) {
+    for (int i = 0; i < B; ++i) infos[i].converged = 1;
+    return GS_OK;
+  }
+  if (B == 1) {
+    int64_t k = 0;
+    gs_status st = gs_fit(ctx, points, dtype, n, labels, modes, modes_cap, &k, &infos[0]);
+    mode_offsets[1] = k;
+    return st;
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(ctx, GS_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorName(ce));
+  if (ctx->device != dev) {
+    ctx->release_device();
+    ctx->device = dev;
+  }
+  FitArgs a;
+  a.d = ctx->d;
+  a.h = ctx->h;
+  a.max_iter = ctx->max_iter;
+  a.stream = ctx->stream;
+  a.points = points;
+  a.f32 = dtype == GS_IN_F32;
+  a.n = n;
+  a.labels = labels;
+  a.modes = modes;
+  a.modes_cap = modes_cap;
+  a.B = B;
+  a.offsets = offsets;
+  a.infos = infos;
+  a.mode_offsets = mode_offsets;
+  gs_fit_info total;
+  std::memset(&total, 0, sizeof(total));
+  int64_t k = 0;
+  return fit_pipeline(a, ctx->ws, nullptr, &k, &total, nullptr, &ctx->err);
 }
 
 }  // extern "C"

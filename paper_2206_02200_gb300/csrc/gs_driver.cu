@@ -9,6 +9,25 @@
 
 namespace gs {
 
+InstState inst_views(uint32_t* base, int B) {
+  InstState I;
+  const size_t b = (size_t)B;
+  I.cell_iters = reinterpret_cast<unsigned long long*>(base);  // first: 8-byte aligned
+  uint32_t* p = base + 2 * b;
+  I.done[0] = p; p += b;
+  I.done[1] = p; p += b;
+  I.nbf[0] = p; p += b;
+  I.nbf[1] = p; p += b;
+  I.mt[0] = p; p += b;
+  I.mt[1] = p; p += b;
+  I.iters = reinterpret_cast<int32_t*>(p); p += b;
+  I.conv = reinterpret_cast<int32_t*>(p); p += b;
+  I.m0 = p; p += b;
+  I.k = p; p += b;
+  I.koff = p;
+  return I;
+}
+
 uint32_t pow2_at_least(uint64_t v, uint32_t lo) {
   uint64_t c = lo;
   while (c < v && c < (1ull << 31)) c <<= 1;
@@ -69,8 +88,8 @@ gs_status cuda_fail(std::string* err, cudaError_t e, const char* where) {
 // per axis the data's key box widened by one cell each side (centroids are
 // convex combinations of the points, Eq. 1 and Eq. 3, and leave that box by a
 // few roundings at most), packed axis 0 most significant.
-gs_status make_plan(int d, double h, int64_t n, const DevFlags& fl, Plan& P, size_t& thr_words,
-                    uint64_t& span_prod, int& total_bits, std::string* err) {
+gs_status make_plan(int d, double h, int64_t n, int B, const DevFlags& fl, Plan& P,
+                    size_t& thr_words, uint64_t& span_prod, int& total_bits, std::string* err) {
   std::memset(&P, 0, sizeof(P));
   P.d = d;
   P.inv_h = (float)(1.0 / h);
@@ -104,6 +123,10 @@ gs_status make_plan(int d, double h, int64_t n, const DevFlags& fl, Plan& P, siz
     P.off[a] = total_bits;
     total_bits += bits[a];
   }
+  // batched runs: the instance index in the field above all axes (it is
+  // never probed, so cells of different instances never meet)
+  P.inst_off = total_bits;
+  if (B > 1) total_bits += bitlen((uint64_t)(B - 1));
   if (total_bits > 63) return fail(err, GS_E_KEYRANGE, "packed cell key needs more than 63 bits");
   int np = 1;
   for (int a = 0; a < d; ++a) np *= 3;
@@ -178,7 +201,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   size_t thr_words = 0;
   uint64_t span_prod = 0;
   int total_bits = 0;
-  GS_ST(make_plan(d, a.h, n, *hf, P, thr_words, span_prod, total_bits, err));
+  GS_ST(make_plan(d, a.h, n, a.B, *hf, P, thr_words, span_prod, total_bits, err));
   const uint64_t m_bound = (uint64_t)n < span_prod ? (uint64_t)n : span_prod;
   GS_ST(ws.prepare(n, d, a.max_iter, thr_words, P.nprobe, m_bound, s, b, err));
 
@@ -192,6 +215,14 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
                         cudaMemcpyHostToDevice, s), "H2D dtab");
   GS_CU(cudaMemsetAsync(b.st, 0, sizeof(IterState) * (a.max_iter + 2), s), "memset state");
   GS_CU(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), s), "memset barrier");
+  uint32_t* hinst = nullptr;
+  if (a.B > 1) {
+    // batched: instance offsets, cleared per-instance state
+    GS_ST(ws.batch_space(a.B, b, &hinst, err));
+    GS_CU(cudaMemcpyAsync(b.offsets, a.offsets, sizeof(int64_t) * (a.B + 1),
+                          cudaMemcpyHostToDevice, s), "H2D offsets");
+    GS_CU(cudaMemsetAsync(b.inst, 0, sizeof(uint32_t) * inst_words(a.B), s), "memset instances");
+  }
 
   // i: binning (retried with a larger table if the cells overflow it)
   ws.mark_dirty(true);
@@ -199,7 +230,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   for (int attempt = 0;; ++attempt) {
     GS_T_BEGIN(GS_PHASE_BIN);
     GS_LAUNCH(launch_bin(a.points, a.f32, n, P, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells, b.slot0,
-                         b.flags, s), "k_bin", 1);
+                         b.flags, b.offsets, a.B, s), "k_bin", 1);
     GS_T_END();
     GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
     GS_CU(cudaStreamSynchronize(s), "sync bin");
@@ -255,6 +286,8 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   L.res = b.res;
   L.max_iter = a.max_iter;
   L.rank_max = kRankMax;
+  L.B = a.B;
+  if (a.B > 1) L.I = inst_views(b.inst, a.B);
   GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
   GS_T_BEGIN(GS_PHASE_LOOP);
   GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
@@ -277,10 +310,13 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_LAUNCH(radix_sort(b.skey, b.sval, b.skey2, b.sval2, b.shist, k, total_bits, s),
               "radix_sort", radix_sort_launches(k, total_bits));
     GS_LAUNCH(launch_rank(b.sval, b.rank, k, s), "k_rank", 1);
-    GS_LAUNCH(launch_label_tail(L, m0, k, hr->base, T, s), "label tail", 3);
+    GS_LAUNCH(launch_label_tail(L, m0, k, hr->base, T, s), "label tail", kLabelTailLaunches);
     GS_T_END();
-    GS_CU(cudaStreamSynchronize(s), "sync labels");
   }
+  if (a.B > 1)
+    GS_CU(cudaMemcpyAsync(hinst, b.inst, sizeof(uint32_t) * inst_words(a.B),
+                          cudaMemcpyDeviceToHost, s), "D2H instances");
+  if (hr->need_sort || a.B > 1) GS_CU(cudaStreamSynchronize(s), "sync labels");
   ws.mark_dirty(false);
 
   info->iterations = T;
@@ -291,6 +327,25 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   if (inkernel_ms)
     for (int i = 0; i < kLoopPhases; ++i) inkernel_ms[i] = (double)hr->ns[i] * 1e-6;
   *k_out = k;
+  if (a.B > 1) {
+    // per-instance results (the host copy of InstState, same layout)
+    const InstState H = inst_views(hinst, a.B);
+    int64_t run = 0;
+    for (int i = 0; i < a.B; ++i) {
+      gs_fit_info& fi = a.infos[i];
+      std::memset(&fi, 0, sizeof(fi));
+      fi.iterations = H.iters[i];
+      fi.converged = H.conv[i];
+      fi.m0 = H.m0[i];
+      fi.k = H.k[i];
+      fi.inexact = info->inexact;
+      fi.cell_iters = (int64_t)H.cell_iters[i];
+      fi.launches = info->launches;
+      a.mode_offsets[i] = run;
+      run += H.k[i];
+    }
+    a.mode_offsets[a.B] = run;
+  }
   if ((int64_t)k > a.modes_cap) return fail(err, GS_E_CAPACITY, "modes_cap < number of clusters");
   return GS_OK;
 }

@@ -32,6 +32,8 @@ struct Bufs {
   Cells cells[2]{};            // m0 cells each
   uint32_t* pslot[2] = {nullptr, nullptr};  // m0 each
   uint32_t* filter = nullptr;  // 2 * kFilterWords
+  int64_t* offsets = nullptr;  // batched runs: B + 1 point offsets
+  uint32_t* inst = nullptr;    // batched runs: per-instance state (inst_words(B) words)
   uint32_t* forest = nullptr;  // m0 * (max_iter + 1)
   uint32_t* forest2 = nullptr; // m0 * (max_iter + 1)
   uint32_t* labslot = nullptr; // t0.cap
@@ -69,6 +71,9 @@ class Workspace {
                            std::string* err) = 0;
   // Sort buffers for k final cells.
   virtual gs_status sort_space(uint32_t k, Bufs& b, std::string* err) = 0;
+  // Batched runs: b.offsets (B + 1) and b.inst (inst_words(B)), and host
+  // staging of per-instance results (inst_words(B) words).
+  virtual gs_status batch_space(int B, Bufs& b, uint32_t** host, std::string* err) = 0;
   // The run stopped before the kernels returned every table to clean.
   virtual void mark_dirty(bool dirty) = 0;
 };
@@ -92,7 +97,20 @@ struct FitArgs {
   int32_t* labels;
   double* modes;
   int64_t modes_cap;
+  // batched runs (B > 1): host offsets (B + 1), per-instance results (host)
+  int B = 1;
+  const int64_t* offsets = nullptr;
+  gs_fit_info* infos = nullptr;
+  int64_t* mode_offsets = nullptr;
 };
+
+// 32-bit words of per-instance state of a batched run of B instances: one
+// array of B 64-bit counters and eleven of B 32-bit words (see InstState).
+inline size_t inst_words(int B) { return (size_t)B * 13; }
+
+// Device views of the per-instance state laid out in `base` (inst_words(B)
+// 32-bit words, 8-byte aligned).
+InstState inst_views(uint32_t* base, int B);
 
 // Runs GridShift end to end on the workspace.  Fills *k_out and *info
 // (statistics and in-kernel phase times) and returns a status; err receives a
@@ -103,6 +121,9 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
 // Largest number of final cells numbered inside the loop kernel; more are
 // numbered by a radix sort of their keys.
 constexpr uint32_t kRankMax = 16384;
+
+// Largest number of instances of one batched call.
+constexpr int kMaxBatch = 1 << 20;
 
 // Host helpers shared by the entry points.
 uint32_t pow2_at_least(uint64_t v, uint32_t lo);

@@ -213,11 +213,22 @@ __device__ __forceinline__ uint64_t bits_of(float v) {
   return f32_bits_to_f64_bits((uint32_t)__float_as_uint(v));
 }
 
+// Instance of point i in a batched run: the b with offsets[b] <= i < offsets[b + 1].
+__device__ __forceinline__ uint32_t instance_of(const int64_t* __restrict__ offsets, int B,
+                                                int64_t i) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&offsets[mid]) <= i) lo = mid; else hi = mid - 1;
+  }
+  return (uint32_t)lo;
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock)
     k_bin(const T* __restrict__ pts, int64_t n, Plan P, const int64_t* __restrict__ thr,
           BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
-          DevFlags* fl, bool vec_ok) {
+          DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B) {
   __shared__ __align__(16) T s_pts[kWarps][32 * D];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(kBlock)
     const bool valid = lane < cnt;
     uint64_t key = kEmpty;
     if (valid) {
-      key = 0;
+      key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << P.inst_off : 0ull;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const uint64_t b = bits_of(s_pts[w][lane * D + a]);
@@ -622,7 +633,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
 // the run, the merge table is cleared instead of used.
 // For t > 0 the same phase links every cell of level t-1 to its cell of level
 // t (the union of resident sets of Eq. 4) and clears level t-1's table.
-template <int D, int GS>
+template <int D, int GS, bool BT>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
                              unsigned& inexact, unsigned& werr) {
@@ -653,16 +664,33 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
       const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
       for (uint32_t w = tid; w < o4; w += gridDim.x * blockDim.x) old[w] = make_uint4(0, 0, 0, 0);
     }
+    if (BT) {
+      // per-instance flags of the next step start clear
+      const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (uint32_t b = tid; b < (uint32_t)A.B; b += gridDim.x * blockDim.x) {
+        A.I.nbf[(t + 1) & 1][b] = 0;
+        A.I.mt[(t + 1) & 1][b] = 0;
+      }
+    }
     __syncthreads();
   }
   for (uint32_t j = group; j < m; j += ngroups) {
     const uint64_t key = c.key[j];
     const uint32_t cj = c.cnt[j];
+    // batched runs: a cell of an instance that has stopped is carried to the
+    // next level unchanged (same key, its own exact sum)
+    uint32_t inst = 0;
+    bool live = true;
+    if (BT) {
+      inst = (uint32_t)(key >> A.P.inst_off);
+      live = A.I.done[t & 1][inst] == 0;
+    }
     uint32_t Dc = 0;
+    bool nbc = false;
     u128 N[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) N[a] = 0;
-    for (int p0 = glane; p0 < nprobe; p0 += GS * U) {
+    for (int p0 = glane; live && p0 < nprobe; p0 += GS * U) {
       uint64_t q[U];
       bool v[U];
       uint32_t sl[U];
@@ -681,9 +709,10 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         Dc += (uint32_t)r[0].x;
 #pragma unroll
         for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
-        if (p0 + u * GS != center) any_nb = true;
+        if (p0 + u * GS != center) nbc = true;
       }
     }
+    any_nb = any_nb || nbc;
 #pragma unroll
     for (int o = GS / 2; o > 0; o >>= 1) {
       Dc += __shfl_xor_sync(gmask, Dc, o);
@@ -699,7 +728,12 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
     uint64_t field = 0;
     u128 V = 0;
     int La = 0;
-    if (glane < D) {
+    uint32_t mult = cj;
+    if (BT && !live) {
+      field = key;
+      mult = 1;
+      if (glane < D) V = as_u128(G.row[(size_t)G.list[j] * (D + 1) + 1 + glane]);
+    } else if (glane < D) {
       u128 Na = 0;
       int off = 0, span = 1, toff = 0;
       int64_t kmin = 0;
@@ -718,8 +752,12 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
       field = (uint64_t)(idx + 1) << off;
       V = to_fixed(bits_of(sv), La, inexact, werr);
     }
+    if (!BT || live) {
 #pragma unroll
-    for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
+      for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
+      if (BT) field |= (key >> A.P.inst_off) << A.P.inst_off;  // the instance field
+    }
+    const bool nbg = BT && (__ballot_sync(gmask, nbc) & gmask) != 0u;
     // iv: merge into the slot of the new key
     uint32_t ms = kNone;
     if (glane == 0) {
@@ -729,14 +767,19 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         if (won) {
           const uint32_t id = atomicAdd(&A.st[t + 1].m, 1u);
           M.list[id] = ms;
+          if (BT) M.id[ms] = j;  // a member, to restore an instance that stops here
         }
         atomicAdd((unsigned long long*)&M.row[(size_t)ms * (D + 1)].x, (unsigned long long)cj);
       }
       pslot[j] = ms;
+      if (BT && live) {
+        if (nbg && !A.I.nbf[t & 1][inst]) atomicOr(&A.I.nbf[t & 1][inst], 1u);
+        atomicAdd(&A.I.mt[t & 1][inst], 1u);
+      }
     }
     ms = __shfl_sync(gmask, ms, 0, GS);
     if (glane < D && ms != kNone)
-      atomic_add_fixed(M.acc + ((size_t)ms * D + glane) * 4, V * (u128)cj);
+      atomic_add_fixed(M.acc + ((size_t)ms * D + glane) * 4, V * (u128)mult);
   }
   if (t > 0) {
     // level t-1: parent links, then its table is released
@@ -754,26 +797,60 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
 }
 
 // The cells of level t+1 from the merge table: sums rounded once.
-template <int D>
+// Batched runs: a cell of an instance that stops at step t (it had no
+// neighbour) is restored from its single member (no merges happen in such an
+// instance), since the update of step t is not applied to it.
+template <int D, bool BT>
 __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& inexact,
                               unsigned& werr) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nth = gridDim.x * blockDim.x;
+  const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
+  const Cells cur = A.cells[t & 1];
   const Cells nx = A.cells[(t + 1) & 1];
   uint32_t* f = A.filter[(t + 1) & 1];
   const int lg = filter_log2(m1);
   for (uint32_t id = tid; id < m1; id += nth) {
     const uint32_t s = M.list[id];
     ulonglong2* r = M.row + (size_t)s * (D + 1);
+    uint64_t key = M.key[s];
+    bool restored = false;
+    if (BT) {
+      const uint32_t inst = (uint32_t)(key >> A.P.inst_off);
+      if (!A.I.done[t & 1][inst] && !A.I.nbf[t & 1][inst]) {
+        const uint32_t j = M.id[s];
+        const ulonglong2* o = G.row + (size_t)G.list[j] * (D + 1);
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-      r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
-    const uint64_t key = M.key[s];
+        for (int a = 0; a < D; ++a) {
+          r[1 + a] = o[1 + a];
+          uint64_t* acc = M.acc + ((size_t)s * D + a) * 4;
+          acc[0] = acc[1] = acc[2] = acc[3] = 0;
+        }
+        key = cur.key[j];
+        restored = true;
+      }
+    }
+    if (!restored) {
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
+    }
     nx.key[id] = key;
     nx.cnt[id] = (uint32_t)r[0].x;
     M.id[s] = id;
     filter_set(f, key, lg);
+  }
+  if (BT) {
+    for (uint32_t b = tid; b < (uint32_t)A.B; b += nth) {
+      const bool act = A.I.done[t & 1][b] == 0, nb = A.I.nbf[t & 1][b] != 0;
+      A.I.done[(t + 1) & 1][b] = act && nb ? 0u : 1u;
+      if (act && nb) A.I.cell_iters[b] += A.I.mt[t & 1][b];
+      if (act && !nb) {
+        A.I.iters[b] = t;
+        A.I.conv[b] = 1;
+      }
+    }
   }
 }
 
@@ -795,7 +872,7 @@ __device__ __forceinline__ void mode_and_release(const LevelTable& G, const Plan
   G.key[s] = kEmpty;
 }
 
-template <int D>
+template <int D, bool BT>
 __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   unsigned inexact = 0, werr = 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -829,6 +906,10 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     A.st[0].base = 0;
   }
   phase_level0<D>(A, m0, maskA, inexact, werr);
+  if (BT) {
+    for (uint32_t id = tid; id < m0; id += nth)
+      atomicAdd(&A.I.m0[(uint32_t)(A.cells[0].key[id] >> A.P.inst_off)], 1u);
+  }
   if (!grid_sync(A.bar, A.fl)) return;
   clk.lap(kSegLevel0);
 
@@ -843,9 +924,11 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     // more cells than warps, else 32
     constexpr int GSmin = GatherLanes<D>::min;
     if (GSmin < 32 && m > (nth >> 5))
-      phase_update<D, GSmin>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact, werr);
+      phase_update<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact,
+                                 werr);
     else
-      phase_update<D, 32>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact, werr);
+      phase_update<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact,
+                              werr);
     if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
     if (!grid_sync(A.bar, A.fl)) return;
     clk.lap(t == 0 ? kSegUpdateFirst : kSegUpdateRest);
@@ -855,7 +938,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     }
     if (t == A.max_iter) break;
     const uint32_t m1 = vst[t + 1].m;
-    phase_compact<D>(A, t, m1, inexact, werr);
+    phase_compact<D, BT>(A, t, m1, inexact, werr);
     if (tid == 0) {
       A.st[t + 1].mask = maskM;
       A.st[t + 1].base = base + m;
@@ -889,8 +972,29 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       }
     }
     for (uint32_t j = tid; j < k; j += nth) A.forest[base + j] = base + j;
+    if (BT) {
+      // instances still updating stop at step T (converged unless the step
+      // limit stopped them with a neighbour present); final cells per instance
+      for (uint32_t b = tid; b < (uint32_t)A.B; b += nth) {
+        if (!A.I.done[T & 1][b]) {
+          A.I.iters[b] = T;
+          A.I.conv[b] = A.I.nbf[T & 1][b] ? 0 : 1;
+        }
+      }
+      const Cells c = A.cells[T & 1];
+      for (uint32_t j = tid; j < k; j += nth)
+        atomicAdd(&A.I.k[(uint32_t)(c.key[j] >> A.P.inst_off)], 1u);
+    }
   }
   if (!grid_sync(A.bar, A.fl)) return;
+  if (BT && tid == 0) {
+    // labels of instance b start at 0: subtract the final cells of earlier ones
+    uint32_t run = 0;
+    for (int b = 0; b < A.B; ++b) {
+      A.I.koff[b] = run;
+      run += A.I.k[b];
+    }
+  }
 
   // pointer jumping over the forest of merges: after r rounds every node
   // points 2^r levels up (or to its root)
@@ -925,8 +1029,12 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       if (lane == 0) A.rank[r] = below;
     }
     if (!grid_sync(A.bar, A.fl)) return;
-    for (uint32_t cc = tid; cc < m0; cc += nth)
-      A.labslot[A.T0.list[cc]] = A.rank[A.forest[cc] - base];
+    for (uint32_t cc = tid; cc < m0; cc += nth) {
+      const uint32_t r = A.forest[cc] - base;
+      uint32_t label = A.rank[r];
+      if (BT) label -= A.I.koff[(uint32_t)(c.key[r] >> A.P.inst_off)];
+      A.labslot[A.T0.list[cc]] = label;
+    }
     if (!grid_sync(A.bar, A.fl)) return;
     for (int64_t i = tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
     const LevelTable G = A.tab[T % 3];
@@ -951,12 +1059,19 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
 
 // Labels and modes when the final cells were too many to number inside
 // k_loop (after a radix sort of their keys has filled rank[]).
+// Batched runs (koff != null) number each instance's clusters from 0.
 __global__ void k_labslot_tail(const uint32_t* __restrict__ list0,
                                const uint32_t* __restrict__ root,
                                const uint32_t* __restrict__ rank, uint32_t baseT,
-                               uint32_t* __restrict__ labslot, uint32_t m0) {
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m0; c += gridDim.x * blockDim.x)
-    labslot[list0[c]] = rank[root[c] - baseT];
+                               uint32_t* __restrict__ labslot, uint32_t m0,
+                               const uint64_t* __restrict__ fkey,
+                               const uint32_t* __restrict__ koff, int inst_off) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < m0; c += gridDim.x * blockDim.x) {
+    const uint32_t r = root[c] - baseT;
+    uint32_t label = rank[r];
+    if (koff) label -= koff[(uint32_t)(fkey[r] >> inst_off)];
+    labslot[list0[c]] = label;
+  }
 }
 
 __global__ void k_labels_tail(const uint32_t* __restrict__ slot0,
@@ -1016,15 +1131,17 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
 
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
-                       DevFlags* fl, cudaStream_t s) {
+                       DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s) {
   const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * 6u);
   const bool vec_ok = ((uintptr_t)pts & 15u) == 0;
   if (f32) {
     GS_DISPATCH_D(P.d, k_bin<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, P, thr, T0,
-                                                            mask0, maxcells, slot0, fl, vec_ok));
+                                                            mask0, maxcells, slot0, fl, vec_ok,
+                                                            offsets, B));
   } else {
     GS_DISPATCH_D(P.d, k_bin<D, double><<<g, kBlock, 0, s>>>((const double*)pts, n, P, thr, T0,
-                                                             mask0, maxcells, slot0, fl, vec_ok));
+                                                             mask0, maxcells, slot0, fl, vec_ok,
+                                                             offsets, B));
   }
   return cudaGetLastError();
 }
@@ -1036,12 +1153,19 @@ int loop_grid_d() {
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
   const int smem = (int)(kFilterWords * sizeof(uint32_t));
-  if (cudaFuncSetAttribute(k_loop<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+  if (cudaFuncSetAttribute(k_loop<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_loop<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess)
+    return -1;
+  int per_sm_b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_loop<D, true>, kLoopBlock, smem) !=
       cudaSuccess)
     return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D>, kLoopBlock, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D, false>, kLoopBlock, smem) !=
       cudaSuccess)
     return -1;
+  if (per_sm_b < per_sm) per_sm = per_sm_b;  // one grid size serves both variants
   if (per_sm < 1) return -1;
   if (per_sm > 2) per_sm = 2;  // fewer blocks make the grid barriers cheaper
   const int g = sms * per_sm;
@@ -1067,7 +1191,12 @@ cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s) {
   LoopArgs args = a;
   void* params[] = {&args};
   const size_t smem = kFilterWords * sizeof(uint32_t);
-  GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D>, dim3(grid),
+  if (a.B > 1) {
+    GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D, true>,
+                                                            dim3(grid), dim3(kLoopBlock), params,
+                                                            smem, s));
+  }
+  GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D, false>, dim3(grid),
                                                           dim3(kLoopBlock), params, smem, s));
   return cudaSuccess;
 }
@@ -1086,8 +1215,10 @@ cudaError_t launch_rank(const uint32_t* sorted_vals, uint32_t* rank, uint32_t k,
 
 cudaError_t launch_label_tail(const LoopArgs& a, uint32_t m0, uint32_t k, uint32_t baseT, int T,
                               cudaStream_t s) {
+  const bool bt = a.B > 1;
   k_labslot_tail<<<grid_for(m0), kBlock, 0, s>>>(a.T0.list, a.forest, a.rank, baseT, a.labslot,
-                                                 m0);
+                                                 m0, a.cells[T & 1].key,
+                                                 bt ? a.I.koff : nullptr, a.P.inst_off);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_labels_tail<<<grid_for(a.n), kBlock, 0, s>>>(a.slot0, a.labslot, a.labels, a.n);

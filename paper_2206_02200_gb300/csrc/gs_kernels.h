@@ -84,13 +84,17 @@ struct LoopArgs {
   LoopResult* res;
   int max_iter;
   uint32_t rank_max;      // largest k numbered inside the loop kernel
+  int B;                  // instances (1: a plain run)
+  InstState I;            // per-instance state when B > 1
 };
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
                          cudaStream_t s);
+// Binning, first pass.  offsets (device, B + 1 entries) give the points of
+// each instance of a batched run (B > 1); ignored when B == 1.
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
-                       DevFlags* fl, cudaStream_t s);
+                       DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s);
 
 // Blocks of the cooperative loop kernel for dimension d on the current device
 // (all co-resident, at most kMaxLoopGrid), or a negative value on error.
@@ -108,6 +112,8 @@ cudaError_t launch_iota_keys(Cells c, uint64_t* keys, uint32_t* vals, uint32_t k
 cudaError_t launch_rank(const uint32_t* sorted_vals, uint32_t* rank, uint32_t k, cudaStream_t s);
 cudaError_t launch_label_tail(const LoopArgs& a, uint32_t m0, uint32_t k, uint32_t baseT, int T,
                               cudaStream_t s);
+// Launches launch_label_tail makes.
+constexpr int kLabelTailLaunches = 3;
 
 // Stable LSD radix sort of (key, val) pairs by key bits [0, nbits).  keys/vals
 // hold the input and receive the output; tkeys/tvals are scratch of the same

@@ -165,6 +165,7 @@ struct StaticWorkspace : public Workspace {
     b = laid;
     return GS_OK;
   }
+  gs_status batch_space(int, Bufs&, uint32_t**, std::string*) override { return GS_E_INVALID; }
   void mark_dirty(bool) override {}
 };
 

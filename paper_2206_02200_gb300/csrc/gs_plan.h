@@ -26,6 +26,7 @@ struct Plan {
   int L[kMaxD];             // fixed-point unit 2^L of axis a
   int64_t kmin[kMaxD];      // smallest key of axis a
   float inv_h;              // 1/h rounded to float: first guess of a cell index only
+  int inst_off;             // batched runs: bit offset of the instance field (above all axes)
 };
 
 // Device-resident state of one level t (the cells before update step t).
@@ -63,6 +64,21 @@ struct LoopResult {
   uint32_t pad;
   unsigned long long cell_iters;  // sum of m_t over applied updates
   unsigned long long ns[kLoopPhases];  // nanoseconds spent in each segment
+};
+
+// Per-instance state of a batched run (B point sets in one run, each cell
+// key carrying its instance in the field above the axes).  Arrays of B
+// entries; [2] arrays alternate between update steps.
+struct InstState {
+  uint32_t* done[2];       // 1 once the instance has stopped updating (step t uses done[t & 1])
+  uint32_t* nbf[2];        // 1 if a cell of the instance had a neighbour at step t
+  uint32_t* mt[2];         // cells of the instance at level t
+  int32_t* iters;          // update steps applied to the instance
+  int32_t* conv;           // 1 if the instance stopped by the criterion of Sec. 2.1 v
+  uint32_t* m0;            // initial cells of the instance
+  uint32_t* k;             // final cells of the instance
+  uint32_t* koff;          // final cells of all earlier instances
+  unsigned long long* cell_iters;  // sum over its applied steps of the instance's cells
 };
 
 // Arrival counter and generation of a software grid barrier, and the stop

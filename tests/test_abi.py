@@ -80,6 +80,13 @@ def test_create_destroy_and_host_only_checks(lib):
         assert st == gridshift.GS_E_INVALID  # NULL points
         st = lib.gs_fit(ctx, None, 0, 0, None, None, 0, None, None)
         assert st == gridshift.GS_E_INVALID  # NULL k_out
+        # batched: host-side checks, and an all-empty batch returns at once
+        st, mo, infos = gridshift.gs_fit_batched(ctx, 0, gridshift.GS_IN_F64, [0, 0, 0], 0, 0, 0)
+        assert st == gridshift.GS_OK and mo == [0, 0, 0]
+        assert [i.converged for i in infos] == [1, 1]
+        for bad in ([1, 2], [0, 5, 3], [0]):
+            st, _, _ = gridshift.gs_fit_batched(ctx, 0, gridshift.GS_IN_F64, bad, 0, 0, 0)
+            assert st == gridshift.GS_E_INVALID, bad
     finally:
         gridshift.gs_destroy(ctx)
     lib.gs_destroy(None)  # ignored
