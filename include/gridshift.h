@@ -69,7 +69,11 @@ typedef enum {
 
 typedef enum {
   GS_FP64 = 0,       /* exact sums rounded once to float64 (see the header comment) */
-  GS_FP32_MIXED = 1  /* reserved: float32 compensated sums with float64 face re-checks */
+  GS_FP32_MIXED = 1  /* float32 cell state: per-axis mean offsets from the cell's lower face,
+                        neighbour sums in compensated (float-float) float32, merges and
+                        binning partial sums added with float32 atomics (the result may vary
+                        in its last bits from run to run); a centroid within 1e-5 h of a cell
+                        face has its key decided again in float64 (gs_fit_info.face_rechecks) */
 } gs_precision;
 
 typedef enum { GS_IN_F64 = 0, GS_IN_F32 = 1 } gs_dtype;
@@ -84,6 +88,7 @@ typedef struct {
   int64_t inexact;     /* values truncated by the fixed-point window (0 in normal use) */
   int64_t cell_iters;  /* sum over applied updates of the active cells updated */
   int64_t launches;    /* CUDA kernels the call launched */
+  int64_t face_rechecks; /* GS_FP32_MIXED: key decisions redone in float64 near a face */
 } gs_fit_info;
 
 /* Timed parts of one call, for gs_get_phase_times.  The first four are CUDA
@@ -121,8 +126,8 @@ typedef struct {
  * GS_E_INVALID or GS_E_NOMEM. */
 gs_status gs_create(int d, double h, int max_iter, gs_ctx** out);
 
-/* Selects the arithmetic (see gs_precision).  Only GS_FP64 is implemented;
- * other values return GS_E_INVALID and leave the setting unchanged. */
+/* Selects the arithmetic of later calls (see gs_precision; default GS_FP64).
+ * Unknown values return GS_E_INVALID and leave the setting unchanged. */
 gs_status gs_set_precision(gs_ctx* ctx, gs_precision p);
 
 /* Sets the CUDA stream (a cudaStream_t passed as void*, e.g.

@@ -419,7 +419,9 @@ gs_status gs_create(int d, double h, int max_iter, gs_ctx** out) {
 
 gs_status gs_set_precision(gs_ctx* ctx, gs_precision p) {
   if (!ctx) return GS_E_INVALID;
-  if (p != GS_FP64) return fail(ctx, GS_E_INVALID, "only GS_FP64 is implemented");
+  if (p != GS_FP64 && p != GS_FP32_MIXED) return fail(ctx, GS_E_INVALID, "unknown precision");
+  // the two precisions keep different state in the same tables: clear them
+  if (p != ctx->prec) ctx->ws.mark_dirty(true);
   ctx->prec = p;
   return GS_OK;
 }
@@ -492,6 +494,7 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   a.labels = labels;
   a.modes = modes;
   a.modes_cap = modes_cap;
+  a.mixed = ctx->prec == GS_FP32_MIXED;
   double kms[kLoopPhases] = {};
   gs_status st = fit_pipeline(a, ctx->ws, ctx->timing ? &ctx->tm : nullptr, k_out, &inf, kms,
                               &ctx->err);
@@ -562,6 +565,7 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   a.labels = labels;
   a.modes = modes;
   a.modes_cap = modes_cap;
+  a.mixed = ctx->prec == GS_FP32_MIXED;
   a.B = B;
   a.offsets = offsets;
   a.infos = infos;

@@ -93,6 +93,7 @@ gs_status make_plan(int d, double h, int64_t n, int B, const DevFlags& fl, Plan&
   std::memset(&P, 0, sizeof(P));
   P.d = d;
   P.inv_h = (float)(1.0 / h);
+  P.h32 = (float)h;
   int bits[kMaxD];
   int clog2n = 0;
   while ((1ll << clog2n) < n) ++clog2n;
@@ -251,7 +252,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
 
   // ii-v, labels and modes: one cooperative launch
   GS_ST(ws.levels(m0, d, a.max_iter, s, b, err));
-  const int grid = loop_grid(d);
+  const int grid = loop_grid(d, a.mixed);
   if (grid <= 0) return fail(err, GS_E_CUDA, "no co-resident grid for the loop kernel");
   LoopArgs L;
   std::memset(&L, 0, sizeof(L));
@@ -287,6 +288,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   L.max_iter = a.max_iter;
   L.rank_max = kRankMax;
   L.B = a.B;
+  L.mixed = a.mixed;
   if (a.B > 1) L.I = inst_views(b.inst, a.B);
   GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
   GS_T_BEGIN(GS_PHASE_LOOP);
@@ -323,6 +325,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   info->converged = hr->converged;
   info->k = k;
   info->inexact = (int64_t)hf->inexact;
+  info->face_rechecks = (int64_t)hf->rechecks;
   info->cell_iters = (int64_t)hr->cell_iters;
   if (inkernel_ms)
     for (int i = 0; i < kLoopPhases; ++i) inkernel_ms[i] = (double)hr->ns[i] * 1e-6;
@@ -341,6 +344,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
       fi.inexact = info->inexact;
       fi.cell_iters = (int64_t)H.cell_iters[i];
       fi.launches = info->launches;
+      fi.face_rechecks = info->face_rechecks;
       a.mode_offsets[i] = run;
       run += H.k[i];
     }

@@ -97,6 +97,7 @@ struct FitArgs {
   int32_t* labels;
   double* modes;
   int64_t modes_cap;
+  bool mixed = false;  // the float32 mixed-precision variant (GS_FP32_MIXED)
   // batched runs (B > 1): host offsets (B + 1), per-instance results (host)
   int B = 1;
   const int64_t* offsets = nullptr;

@@ -86,6 +86,7 @@ struct LoopArgs {
   uint32_t rank_max;      // largest k numbered inside the loop kernel
   int B;                  // instances (1: a plain run)
   InstState I;            // per-instance state when B > 1
+  bool mixed;             // the float32 mixed-precision variant (GS_FP32_MIXED)
 };
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
@@ -97,12 +98,25 @@ cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, cons
                        DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s);
 
 // Blocks of the cooperative loop kernel for dimension d on the current device
-// (all co-resident, at most kMaxLoopGrid), or a negative value on error.
+// (all co-resident, at most kMaxLoopGrid), or a negative value on error;
+// mixed selects the float32 variant.
 constexpr int kMaxLoopGrid = 4096;
-int loop_grid(int d);
-// Steps ii-v for every level, then labels and modes (Sec. 2.1, Algorithm 1),
-// in one cooperative launch of `grid` blocks.
+int loop_grid(int d, bool mixed);
+// The rest of step i, steps ii-v for every level, then labels and modes
+// (Sec. 2.1, Algorithm 1), in one cooperative launch of `grid` blocks
+// (a.mixed selects the float32 variant).
 cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s);
+// Modes of the final cells and release of their table, after numbering by
+// a radix sort (a.mixed selects the float32 variant).
+cudaError_t launch_modes_tail(const LoopArgs& a, uint32_t k, int T, cudaStream_t s);
+
+// Per-precision implementations (gs_loop64.cu, gs_loop32.cu).
+int loop_grid_fp64(int d);
+int loop_grid_fp32(int d);
+cudaError_t launch_loop_fp64(const LoopArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_loop_fp32(const LoopArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_modes_tail_fp64(const LoopArgs& a, uint32_t k, int T, cudaStream_t s);
+cudaError_t launch_modes_tail_fp32(const LoopArgs& a, uint32_t k, int T, cudaStream_t s);
 
 // Numbering of the final cells when k > rank_max: labels of the final cells
 // from the sorted order (sorted_vals[p] = cell of rank p), then labels and

@@ -1,0 +1,1404 @@
+// gs_loop.cuh -- the loop kernel of the GridShift hot path (Kumar et al.,
+// arXiv 2206.02200, Sec. 2.1 and Algorithm 1): one cooperative launch for
+// everything between the first binning pass and the labels:
+//   binning, second pass: exact cell sums through a counting sort of the
+//            points by cell (step i)
+//   level 0: the initial cells and their table
+//   per update step t:
+//     update   steps ii-iv: Eq. 1-2 over the 3^d neighbours in the parallel
+//              form (Eq. 6), centroid, new key, and the neighbour test of
+//              step v; the count-weighted centroid merged (Eq. 3-4) into the
+//              slot of the new key
+//     compact  the next level's cells and sums
+//   then the forest of merges (the union of resident sets of Eq. 4) is
+//   resolved by pointer jumping, the final cells are numbered by ascending
+//   key, and every point gets its label.
+// Phases are separated by a software grid barrier whose waits are bounded in
+// time.  Included by gs_loop64.cu (exact sums rounded once to float64) and
+// gs_loop32.cu (the float32 mixed-precision variant), which instantiate it.
+#pragma once
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Software grid barrier for the cooperative loop kernel.  All blocks are
+// co-resident (cooperative launch).  Block leaders arrive on a counter; the
+// last one, after every block's writes of the phase, reads the error flags,
+// records whether the kernel must stop, resets the counter and advances the
+// generation the others wait on.  Every block therefore takes the same stop
+// decision at the same barrier.  A wait gives up after kBarrierNs of global
+// time, sets kErrBarrier and makes the kernel return.
+
+constexpr unsigned long long kBarrierNs = 10ull * 1000ull * 1000ull * 1000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_sync(GridBar* bar, DevFlags* fl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = &bar->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      *(volatile unsigned int*)&bar->stop = *(volatile uint32_t*)&fl->err != 0u ? 1u : 0u;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        __nanosleep(64);
+        if (global_ns() - t0 > kBarrierNs) {
+          atomicOr(&fl->err, kErrBarrier);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && *(volatile unsigned int*)&bar->stop == 0u;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Device-clock split of the loop kernel, kept by thread 0 of block 0.
+struct SegClock {
+  unsigned long long last = 0;
+  unsigned long long ns[kLoopPhases] = {};
+  bool on = false;
+  __device__ void start() {
+    on = blockIdx.x == 0 && threadIdx.x == 0;
+    if (on) last = global_ns();
+  }
+  __device__ void lap(int seg) {
+    if (!on) return;
+    const unsigned long long now = global_ns();
+    ns[seg] += now - last;
+    last = now;
+  }
+};
+
+enum {
+  kSegOffsets = 0,
+  kSegScatter = 1,
+  kSegSums = 2,
+  kSegLevel0 = 3,
+  kSegUpdateFirst = 4,
+  kSegUpdateRest = 5,
+  kSegCompact = 6,
+  kSegLabels = 7
+};
+
+__device__ __forceinline__ u128 as_u128(ulonglong2 v) { return (u128)v.x | ((u128)v.y << 64); }
+
+__device__ __forceinline__ ulonglong2 pack(u128 v) {
+  return make_ulonglong2((uint64_t)v, (uint64_t)(v >> 64));
+}
+
+// The cell sum of one axis as the float64 value of Sec. 2.1 (the exact sum in
+// the limb accumulators rounded once), held as the fixed-point integer it
+// equals; clears the accumulators.
+__device__ __forceinline__ ulonglong2 settle_sum(uint64_t* acc, int L, unsigned& inexact,
+                                                 unsigned& werr) {
+  const double v = round_fixed(limbs_value(acc), L, inexact);
+  acc[0] = acc[1] = acc[2] = acc[3] = 0;
+  return pack(to_fixed(bits_of(v), L, inexact, werr));
+}
+
+// ---------------------------------------------------------------------------
+// Occupancy filter of a level: one bit per hashed key (a Bloom filter with
+// one hash function), 2^B bits with 2^B >= 32 m (at most 2^kFilterLog2Max).  A
+// neighbour probe whose bit is clear cannot hit and never leaves the SM: the
+// update phase copies the level's filter into shared memory first.
+
+__device__ __forceinline__ int filter_log2(uint32_t m) {
+  int b = 10;
+  while (b < kFilterLog2Max && (1u << b) < 32u * m) ++b;
+  return b;
+}
+
+__device__ __forceinline__ uint32_t filter_bit(uint64_t key, int lg) {
+  return (uint32_t)((key * 0xD6E8FEB86659FD93ull) >> (64 - lg));
+}
+
+__device__ __forceinline__ void filter_set(uint32_t* f, uint64_t key, int lg) {
+  const uint32_t b = filter_bit(key, lg);
+  atomicOr(&f[b >> 5], 1u << (b & 31));
+}
+
+// Lanes given to one cell in the update: a power of two, at least d and at
+// least GatherLanes<D>::min.  Few lanes per cell put several cells in flight
+// per warp, which hides the latency of their dependent table loads when a
+// level has many cells; a level with few cells gets 32 lanes per cell, which
+// shortens each cell's chain of probes.
+template <int D>
+struct GatherLanes {
+  static constexpr int min = D <= 3 ? 4 : D <= 5 ? 8 : D == 6 ? 16 : 32;
+};
+
+constexpr int pow3(int d) { return d == 0 ? 1 : 3 * pow3(d - 1); }
+
+// Probes each lane has in flight at once: min(4, its probes per cell).
+template <int D, int GS>
+struct ProbeBatch {
+  static constexpr int probes = pow3(D);
+  static constexpr int per_lane = (probes + GS - 1) / GS;
+  static constexpr int value = per_lane < 4 ? per_lane : 4;
+};
+
+// ---------------------------------------------------------------------------
+// Step i, second pass: the exact sum of every cell, by a counting sort of the
+// points by cell.  Offsets follow the cells' list order; a cell's points then
+// occupy one contiguous run of perm[], and a warp reading 32 consecutive
+// entries adds each run of equal cells with a segmented shuffle reduction, so
+// the sum accumulators receive a few atomic adds per run instead of d per
+// point.  Exact integer sums make the order irrelevant.
+
+// Per-block totals of the counts of cells [b * chunk, (b + 1) * chunk).
+__device__ void phase_count_totals(const LoopArgs& A, uint32_t m0) {
+  __shared__ uint32_t s_part[kLoopBlock / 32];
+  const uint32_t chunk = (m0 + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = lo + chunk < m0 ? lo + chunk : m0;
+  uint32_t sum = 0;
+  for (uint32_t id = lo + threadIdx.x; id < hi; id += blockDim.x) sum += A.T0.cnt[A.T0.list[id]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+    A.blocksum[blockIdx.x] = t;
+  }
+}
+
+// Start offset of every cell's run: T0.off[slot] = points of all earlier cells.
+__device__ void phase_offsets(const LoopArgs& A, uint32_t m0) {
+  __shared__ uint32_t s_warp[kLoopBlock / 32];
+  __shared__ uint32_t s_base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (w == 0) {
+    uint32_t t = 0;
+    for (uint32_t b = lane; b < blockIdx.x; b += 32) t += A.blocksum[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if (lane == 0) s_base = t;
+  }
+  __syncthreads();
+  const uint32_t chunk = (m0 + gridDim.x - 1) / gridDim.x;
+  const uint32_t lo = blockIdx.x * chunk;
+  const uint32_t hi = lo + chunk < m0 ? lo + chunk : m0;
+  uint32_t run = s_base;
+  for (uint32_t c0 = lo; c0 < hi; c0 += blockDim.x) {
+    const uint32_t id = c0 + threadIdx.x;
+    const uint32_t slot = id < hi ? A.T0.list[id] : 0u;
+    const uint32_t v = id < hi ? A.T0.cnt[slot] : 0u;
+    uint32_t x = v;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int q = 0; q < nw; ++q) {
+      const uint32_t t = s_warp[q];
+      before += q < w ? t : 0u;
+      total += t;
+    }
+    if (id < hi) A.T0.off[slot] = run + before + x - v;
+    run += total;
+    __syncthreads();
+  }
+}
+
+// perm[off[cell] + rank] = point: each point claims a position in its cell's
+// run (equal cells within a warp claim theirs with one atomic add).  A warp
+// handles kScatterBatch chunks of 32 points at once, so their loads and
+// atomics are in flight together.
+constexpr int kScatterBatch = 4;
+
+__device__ void phase_scatter(const LoopArgs& A) {
+  constexpr int B = kScatterBatch;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gwarp * 32 * B; base < A.n; base += nwarps * 32 * B) {
+    uint32_t s[B], pos[B];
+    unsigned peers[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int64_t i = base + b * 32 + lane;
+      s[b] = i < A.n ? A.slot0[i] : kNone;
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      peers[b] = __match_any_sync(kFull, s[b]);
+      pos[b] = 0;
+      if (lane == __ffs(peers[b]) - 1 && s[b] != kNone)
+        pos[b] = atomicAdd(&A.T0.off[s[b]], (uint32_t)__popc(peers[b]));
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const uint32_t p = __shfl_sync(kFull, pos[b], __ffs(peers[b]) - 1);
+      if (s[b] != kNone) A.perm[p + __popc(peers[b] & below)] = (uint32_t)(base + b * 32 + lane);
+    }
+  }
+}
+
+// Exact sums of the cells: sums of the fixed-point values of their points.
+// Lane l of a warp takes kSumRun consecutive entries of perm[] (one 16-byte
+// load) and adds the runs of equal cells among them in registers; every run
+// but its last is added into the cell's limb accumulators at once.  The
+// lanes' last runs are contiguous in cell order across the warp, so a
+// segmented shuffle reduction combines them and the first lane of each
+// segment adds the segment's sum.
+constexpr int kSumRun = 4;
+
+template <int D>
+__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t s, const u128 (&V)[D]) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)s * D + a) * 4, V[a]);
+}
+
+template <int D, typename T>
+__device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& werr) {
+  constexpr int E = kSumRun;
+  const T* __restrict__ pts = static_cast<const T*>(A.pts);
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gwarp * 32 * E; base < A.n; base += nwarps * 32 * E) {
+    const int64_t p0 = base + (int64_t)lane * E;
+    uint32_t idx[E], s[E];
+    if (p0 + E <= A.n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(A.perm + p0);
+      idx[0] = q.x;
+      idx[1] = q.y;
+      idx[2] = q.z;
+      idx[3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) idx[e] = p0 + e < A.n ? A.perm[p0 + e] : kNone;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) s[e] = idx[e] != kNone ? A.slot0[idx[e]] : kNone;
+    uint64_t raw[E][D];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)idx[e] * D + a) : 0ull;
+    // runs within the lane
+    uint32_t cur = s[0];
+    u128 V[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], A.P.L[a], inexact, werr);
+#pragma unroll
+    for (int e = 1; e < E; ++e) {
+      if (s[e] != cur) {
+        if (cur != kNone) add_cell_sum<D>(A, cur, V);
+        cur = s[e];
+#pragma unroll
+        for (int a = 0; a < D; ++a) V[a] = 0;
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) V[a] += to_fixed(raw[e][a], A.P.L[a], inexact, werr);
+    }
+    // the lanes' last runs: lane l ends with the sum of [l, end of its segment)
+    const uint32_t prev = __shfl_up_sync(kFull, cur, 1);
+    const bool head = lane == 0 || prev != cur;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned after = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
+    const int end = after ? __ffs(after) - 1 : 32;
+    if (__any_sync(kFull, end - lane > 1)) {
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const uint64_t lo = __shfl_down_sync(kFull, (uint64_t)V[a], o);
+          const uint64_t hi = __shfl_down_sync(kFull, (uint64_t)(V[a] >> 64), o);
+          if (lane + o < end) V[a] += (u128)lo | ((u128)hi << 64);
+        }
+      }
+    }
+    if (head && cur != kNone) add_cell_sum<D>(A, cur, V);
+  }
+}
+
+// Level 0: the cells binning created (in arrival order), their sums rounded
+// once, in the level table tab[0].  Resets the binning table's slots.
+template <int D>
+__device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, unsigned& inexact,
+                             unsigned& werr) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const BinTable T0 = A.T0;
+  const LevelTable G = A.tab[0];
+  const Cells c = A.cells[0];
+  const int lg0 = filter_log2(m0);
+  for (uint32_t id = tid; id < m0; id += nth) {
+    const uint32_t s = T0.list[id];
+    const uint64_t key = T0.key[s];
+    const uint32_t cnt = T0.cnt[s];
+    bool won;
+    const uint32_t sa = table_insert(G.key, maskA, key, won, &A.fl->err);
+    if (sa != kNone) {
+      ulonglong2* r = G.row + (size_t)sa * (D + 1);
+      r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        r[1 + a] = settle_sum(T0.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
+      G.id[sa] = id;
+      G.list[id] = sa;
+    }
+    filter_set(A.filter[0], key, lg0);
+    c.key[id] = key;
+    c.cnt[id] = cnt;
+    T0.cnt[s] = 0;
+    T0.key[s] = kEmpty;
+  }
+}
+
+// One update step t for every cell of level t (table tab[t % 3]):
+//   ii)  D = sum of the counts and N = sum of the coordinate sums over the
+//        3^d neighbours present (Eq. 1-2, all cells reading level t: Eq. 6),
+//        centroid N / D rounded once, and whether a neighbour v != 0 is
+//        present (step v);
+//   iii) new key floor(centroid / h);
+//   iv)  the cell's count and count-weighted centroid (Eq. 3-4) added exactly
+//        into the slot of its new key in tab[(t + 1) % 3].
+// The merge is applied before the stop test is known; when the test stops
+// the run, the merge table is cleared instead of used.
+// For t > 0 the same phase links every cell of level t-1 to its cell of level
+// t (the union of resident sets of Eq. 4) and clears level t-1's table.
+template <int D, int GS, bool BT>
+__device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
+                             uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
+                             unsigned& inexact, unsigned& werr) {
+  constexpr int U = ProbeBatch<D, GS>::value;
+  const int lane = threadIdx.x & 31;
+  const int glane = lane & (GS - 1);
+  const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
+  const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / GS;
+  const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
+  const LevelTable G = A.tab[t % 3];
+  const LevelTable M = A.tab[(t + 1) % 3];
+  const Cells c = A.cells[t & 1];
+  uint32_t* pslot = A.pslot[t & 1];
+  const int nprobe = A.P.nprobe, center = A.P.center;
+  // the level's occupancy filter, into shared memory; the filter of level
+  // t-1 is cleared for level t+1
+  extern __shared__ uint4 s_dyn[];
+  uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
+  const int lg = filter_log2(m);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.filter[t & 1]);
+    uint4* dst = reinterpret_cast<uint4*>(s_filter);
+    const uint32_t n4 = (1u << lg) / 128;
+    for (uint32_t w = threadIdx.x; w < n4; w += blockDim.x) dst[w] = __ldcg(src + w);
+    if (t > 0) {
+      uint4* old = reinterpret_cast<uint4*>(A.filter[(t + 1) & 1]);
+      const uint32_t o4 = (1u << filter_log2(m_prev)) / 128;
+      const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (uint32_t w = tid; w < o4; w += gridDim.x * blockDim.x) old[w] = make_uint4(0, 0, 0, 0);
+    }
+    if (BT) {
+      // per-instance flags of the next step start clear
+      const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (uint32_t b = tid; b < (uint32_t)A.B; b += gridDim.x * blockDim.x) {
+        A.I.nbf[(t + 1) & 1][b] = 0;
+        A.I.mt[(t + 1) & 1][b] = 0;
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t j = group; j < m; j += ngroups) {
+    const uint64_t key = c.key[j];
+    const uint32_t cj = c.cnt[j];
+    // batched runs: a cell of an instance that has stopped is carried to the
+    // next level unchanged (same key, its own exact sum)
+    uint32_t inst = 0;
+    bool live = true;
+    if (BT) {
+      inst = (uint32_t)(key >> A.P.inst_off);
+      live = A.I.done[t & 1][inst] == 0;
+    }
+    uint32_t Dc = 0;
+    bool nbc = false;
+    u128 N[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) N[a] = 0;
+    for (int p0 = glane; live && p0 < nprobe; p0 += GS * U) {
+      uint64_t q[U];
+      bool v[U];
+      uint32_t sl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * GS;
+        q[u] = key + (p < nprobe ? __ldg(&A.dtab[p]) : 0ull);
+        const uint32_t fb = filter_bit(q[u], lg);
+        v[u] = p < nprobe && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
+      }
+      table_find_many<U>(G.key, mask, q, v, sl);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (sl[u] == kNone) continue;
+        const ulonglong2* r = G.row + (size_t)sl[u] * (D + 1);
+        Dc += (uint32_t)r[0].x;
+#pragma unroll
+        for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
+        if (p0 + u * GS != center) nbc = true;
+      }
+    }
+    any_nb = any_nb || nbc;
+#pragma unroll
+    for (int o = GS / 2; o > 0; o >>= 1) {
+      Dc += __shfl_xor_sync(gmask, Dc, o);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        uint64_t lo = (uint64_t)N[a], hi = (uint64_t)(N[a] >> 64);
+        lo = __shfl_xor_sync(gmask, lo, o);
+        hi = __shfl_xor_sync(gmask, hi, o);
+        N[a] += (u128)lo | ((u128)hi << 64);
+      }
+    }
+    // lane a < d: coordinate a of the centroid, its key field, its fixed value
+    uint64_t field = 0;
+    u128 V = 0;
+    int La = 0;
+    uint32_t mult = cj;
+    if (BT && !live) {
+      field = key;
+      mult = 1;
+      if (glane < D) V = as_u128(G.row[(size_t)G.list[j] * (D + 1) + 1 + glane]);
+    } else if (glane < D) {
+      u128 Na = 0;
+      int off = 0, span = 1, toff = 0;
+      int64_t kmin = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (a == glane) {
+          Na = N[a];
+          La = A.P.L[a];
+          off = A.P.off[a];
+          span = A.P.span[a];
+          toff = A.P.thr_off[a];
+          kmin = A.P.kmin[a];
+        }
+      const double sv = div_round(Na, Dc, La, inexact);
+      const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
+      field = (uint64_t)(idx + 1) << off;
+      V = to_fixed(bits_of(sv), La, inexact, werr);
+    }
+    if (!BT || live) {
+#pragma unroll
+      for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
+      if (BT) field |= (key >> A.P.inst_off) << A.P.inst_off;  // the instance field
+    }
+    const bool nbg = BT && (__ballot_sync(gmask, nbc) & gmask) != 0u;
+    // iv: merge into the slot of the new key
+    uint32_t ms = kNone;
+    if (glane == 0) {
+      bool won;
+      ms = table_insert(M.key, maskM, field, won, &A.fl->err);
+      if (ms != kNone) {
+        if (won) {
+          const uint32_t id = atomicAdd(&A.st[t + 1].m, 1u);
+          M.list[id] = ms;
+          if (BT) M.id[ms] = j;  // a member, to restore an instance that stops here
+        }
+        atomicAdd((unsigned long long*)&M.row[(size_t)ms * (D + 1)].x, (unsigned long long)cj);
+      }
+      pslot[j] = ms;
+      if (BT && live) {
+        if (nbg && !A.I.nbf[t & 1][inst]) atomicOr(&A.I.nbf[t & 1][inst], 1u);
+        atomicAdd(&A.I.mt[t & 1][inst], 1u);
+      }
+    }
+    ms = __shfl_sync(gmask, ms, 0, GS);
+    if (glane < D && ms != kNone)
+      atomic_add_fixed(M.acc + ((size_t)ms * D + glane) * 4, V * (u128)mult);
+  }
+  if (t > 0) {
+    // level t-1: parent links, then its table is released
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nth = gridDim.x * blockDim.x;
+    const LevelTable Lp = A.tab[(t + 2) % 3];
+    const uint32_t* pp = A.pslot[(t - 1) & 1];
+    for (uint32_t i = tid; i < m_prev; i += nth) {
+      A.forest[base_prev + i] = base + G.id[pp[i]];
+      const uint32_t s = Lp.list[i];
+      Lp.key[s] = kEmpty;
+      Lp.row[(size_t)s * (D + 1)].x = 0;
+    }
+  }
+}
+
+// The cells of level t+1 from the merge table: sums rounded once.
+// Batched runs: a cell of an instance that stops at step t (it had no
+// neighbour) is restored from its single member (no merges happen in such an
+// instance), since the update of step t is not applied to it.
+template <int D, bool BT>
+__device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& inexact,
+                              unsigned& werr) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const LevelTable G = A.tab[t % 3];
+  const LevelTable M = A.tab[(t + 1) % 3];
+  const Cells cur = A.cells[t & 1];
+  const Cells nx = A.cells[(t + 1) & 1];
+  uint32_t* f = A.filter[(t + 1) & 1];
+  const int lg = filter_log2(m1);
+  for (uint32_t id = tid; id < m1; id += nth) {
+    const uint32_t s = M.list[id];
+    ulonglong2* r = M.row + (size_t)s * (D + 1);
+    uint64_t key = M.key[s];
+    bool restored = false;
+    if (BT) {
+      const uint32_t inst = (uint32_t)(key >> A.P.inst_off);
+      if (!A.I.done[t & 1][inst] && !A.I.nbf[t & 1][inst]) {
+        const uint32_t j = M.id[s];
+        const ulonglong2* o = G.row + (size_t)G.list[j] * (D + 1);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          r[1 + a] = o[1 + a];
+          uint64_t* acc = M.acc + ((size_t)s * D + a) * 4;
+          acc[0] = acc[1] = acc[2] = acc[3] = 0;
+        }
+        key = cur.key[j];
+        restored = true;
+      }
+    }
+    if (!restored) {
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
+    }
+    nx.key[id] = key;
+    nx.cnt[id] = (uint32_t)r[0].x;
+    M.id[s] = id;
+    filter_set(f, key, lg);
+  }
+  if (BT) {
+    for (uint32_t b = tid; b < (uint32_t)A.B; b += nth) {
+      const bool act = A.I.done[t & 1][b] == 0, nb = A.I.nbf[t & 1][b] != 0;
+      A.I.done[(t + 1) & 1][b] = act && nb ? 0u : 1u;
+      if (act && nb) A.I.cell_iters[b] += A.I.mt[t & 1][b];
+      if (act && !nb) {
+        A.I.iters[b] = t;
+        A.I.conv[b] = 1;
+      }
+    }
+  }
+}
+
+// Mode of final cell r (row of its table slot) written to its label's row,
+// then the slot is released.
+template <int D>
+__device__ __forceinline__ void mode_and_release(const LevelTable& G, const Plan& P, uint32_t r,
+                                                 uint32_t label, double* modes, bool write,
+                                                 unsigned& inexact) {
+  const uint32_t s = G.list[r];
+  ulonglong2* row = G.row + (size_t)s * (D + 1);
+  if (write) {
+    const double cnt = (double)row[0].x;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      modes[(size_t)label * D + a] = round_fixed(as_u128(row[1 + a]), P.L[a], inexact) / cnt;
+  }
+  row[0].x = 0;
+  G.key[s] = kEmpty;
+}
+
+// ---------------------------------------------------------------------------
+// The float32 mixed-precision variant (GS_FP32_MIXED).  A cell row holds the
+// resident count and, per axis, the mean offset of its residents from the
+// cell's lower face (count-normalised, float32):
+//   row32[s * (d + 1)]      count (uint32)
+//   row32[s * (d + 1) + 1 + a]  float32 bits of the mean offset along axis a
+// Sums are kept as float-float pairs (hi + lo, compensated additions);
+// merges and binning add their partial sums with float32 atomics.  A
+// centroid that falls within kFaceBand * h of a face of its cell is
+// recomputed from the same float32 state in float64 and its key decided
+// against the face table, since that decision sets merges and labels; a
+// recomputed centroid less than kTieBand * h below a face counts as a tie and
+// goes to the upper cell, as an exact tie does in the exact path.
+
+constexpr float kFaceBand = 1e-5f;
+constexpr float kTieBand = 4e-6f;  // below the state error bound of the float32 path
+
+// Float-float number hi + lo with |lo| <= ulp(hi) / 2.
+struct FF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float b) {  // Knuth's TwoSum, then renormalise
+    const float s = hi + b;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (b - bb);
+    const float l = lo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+  }
+  __device__ __forceinline__ void add(const FF& o) {
+    const float s = hi + o.hi;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (o.hi - bb);
+    const float l = lo + o.lo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+  }
+  __device__ __forceinline__ float value() const { return hi + lo; }
+};
+
+__device__ __forceinline__ FF shfl_xor_ff(unsigned mask, const FF& v, int o) {
+  FF r;
+  r.hi = __shfl_xor_sync(mask, v.hi, o);
+  r.lo = __shfl_xor_sync(mask, v.lo, o);
+  return r;
+}
+
+// Lower face (least double >= q h) of the cell with packed key `key` along
+// axis a, from the face table.
+__device__ __forceinline__ double face_of(const Plan& P, const int64_t* __restrict__ thr,
+                                          uint64_t key, int a) {
+  const int top = a == 0 ? P.inst_off : P.off[a - 1];
+  const uint64_t fmask = (1ull << (top - P.off[a])) - 1ull;
+  const int idx = (int)((key >> P.off[a]) & fmask) - 1;
+  const int64_t o = __ldg(&thr[P.thr_off[a] + idx]);
+  return __longlong_as_double((long long)(o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll)));
+}
+
+// Binning, second pass (float32): each cell's sum of offsets from its lower
+// face, over the runs of the counting sort (as phase_cell_sums).
+template <int D, typename T>
+__device__ void phase_cell_sums32(const LoopArgs& A) {
+  constexpr int E = kSumRun;
+  const T* __restrict__ pts = static_cast<const T*>(A.pts);
+  float* __restrict__ tacc = reinterpret_cast<float*>(A.T0.acc);
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gwarp * 32 * E; base < A.n; base += nwarps * 32 * E) {
+    const int64_t p0 = base + (int64_t)lane * E;
+    uint32_t idx[E], s[E];
+    if (p0 + E <= A.n) {
+      const uint4 q = *reinterpret_cast<const uint4*>(A.perm + p0);
+      idx[0] = q.x;
+      idx[1] = q.y;
+      idx[2] = q.z;
+      idx[3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) idx[e] = p0 + e < A.n ? A.perm[p0 + e] : kNone;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) s[e] = idx[e] != kNone ? A.slot0[idx[e]] : kNone;
+    float x[E][D];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        x[e][a] = idx[e] != kNone ? (float)__ldg(pts + (size_t)idx[e] * D + a) : 0.f;
+    uint32_t cur = kNone;
+    float org[D];
+    FF V[D];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (s[e] != cur) {
+        if (cur != kNone) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
+        }
+        cur = s[e];
+        if (cur != kNone) {
+          const uint64_t key = A.T0.key[cur];
+#pragma unroll
+          for (int a = 0; a < D; ++a) org[a] = (float)face_of(A.P, A.thr, key, a);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) V[a] = FF();
+      }
+      if (cur != kNone) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) V[a].add(x[e][a] - org[a]);
+      }
+    }
+    const uint32_t prev = __shfl_up_sync(kFull, cur, 1);
+    const bool head = lane == 0 || prev != cur;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned after = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);
+    const int end = after ? __ffs(after) - 1 : 32;
+    if (__any_sync(kFull, end - lane > 1)) {
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          FF w;
+          w.hi = __shfl_down_sync(kFull, V[a].hi, o);
+          w.lo = __shfl_down_sync(kFull, V[a].lo, o);
+          if (lane + o < end) V[a].add(w);
+        }
+      }
+    }
+    if (head && cur != kNone) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
+    }
+  }
+}
+
+// Level 0 (float32): mean offsets of the initial cells; resets the binning
+// table's slots.
+template <int D>
+__device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const BinTable T0 = A.T0;
+  float* tacc = reinterpret_cast<float*>(T0.acc);
+  const LevelTable G = A.tab[0];
+  uint32_t* row = reinterpret_cast<uint32_t*>(G.row);
+  const Cells c = A.cells[0];
+  const int lg0 = filter_log2(m0);
+  for (uint32_t id = tid; id < m0; id += nth) {
+    const uint32_t s = T0.list[id];
+    const uint64_t key = T0.key[s];
+    const uint32_t cnt = T0.cnt[s];
+    bool won;
+    const uint32_t sa = table_insert(G.key, maskA, key, won, &A.fl->err);
+    if (sa != kNone) {
+      uint32_t* r = row + (size_t)sa * (D + 1);
+      r[0] = cnt;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        r[1 + a] = __float_as_uint(tacc[(size_t)s * D + a] / (float)cnt);
+        tacc[(size_t)s * D + a] = 0.f;
+      }
+      G.id[sa] = id;
+      G.list[id] = sa;
+    }
+    filter_set(A.filter[0], key, lg0);
+    c.key[id] = key;
+    c.cnt[id] = cnt;
+    T0.cnt[s] = 0;
+    T0.key[s] = kEmpty;
+  }
+}
+
+// One update step t (float32), as phase_update: Eq. 1-2 over the neighbours
+// in float-float, centroid relative to the cell's lower face, new key, and
+// the count-weighted centroid merged (Eq. 3-4) relative to the new cell's
+// lower face.  A centroid within kFaceBand * h of a face is recomputed in
+// float64 from the same neighbours and its key decided exactly.
+template <int D, int GS, bool BT>
+__device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t mask,
+                               uint32_t maskM, uint32_t m_prev, uint32_t base_prev,
+                               uint32_t base, bool& any_nb) {
+  constexpr int U = ProbeBatch<D, GS>::value;
+  const int lane = threadIdx.x & 31;
+  const int glane = lane & (GS - 1);
+  const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
+  const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / GS;
+  const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
+  const LevelTable G = A.tab[t % 3];
+  const LevelTable M = A.tab[(t + 1) % 3];
+  const uint32_t* grow = reinterpret_cast<const uint32_t*>(G.row);
+  uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);
+  float* macc = reinterpret_cast<float*>(M.acc);
+  const Cells c = A.cells[t & 1];
+  uint32_t* pslot = A.pslot[t & 1];
+  const int nprobe = A.P.nprobe, center = A.P.center;
+  const float h = A.P.h32;
+  extern __shared__ uint4 s_dyn[];
+  uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
+  const int lg = filter_log2(m);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.filter[t & 1]);
+    uint4* dst = reinterpret_cast<uint4*>(s_filter);
+    const uint32_t n4 = (1u << lg) / 128;
+    for (uint32_t w = threadIdx.x; w < n4; w += blockDim.x) dst[w] = __ldcg(src + w);
+    if (t > 0) {
+      uint4* old = reinterpret_cast<uint4*>(A.filter[(t + 1) & 1]);
+      const uint32_t o4 = (1u << filter_log2(m_prev)) / 128;
+      const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (uint32_t w = tid; w < o4; w += gridDim.x * blockDim.x) old[w] = make_uint4(0, 0, 0, 0);
+    }
+    if (BT) {
+      const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+      for (uint32_t b = tid; b < (uint32_t)A.B; b += gridDim.x * blockDim.x) {
+        A.I.nbf[(t + 1) & 1][b] = 0;
+        A.I.mt[(t + 1) & 1][b] = 0;
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t j = group; j < m; j += ngroups) {
+    const uint64_t key = c.key[j];
+    const uint32_t cj = c.cnt[j];
+    uint32_t inst = 0;
+    bool live = true;
+    if (BT) {
+      inst = (uint32_t)(key >> A.P.inst_off);
+      live = A.I.done[t & 1][inst] == 0;
+    }
+    uint32_t Dc = 0;
+    bool nbc = false;
+    FF N[D];
+    for (int p0 = glane; live && p0 < nprobe; p0 += GS * U) {
+      uint64_t q[U];
+      bool v[U];
+      uint32_t sl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * GS;
+        q[u] = key + (p < nprobe ? __ldg(&A.dtab[p]) : 0ull);
+        const uint32_t fb = filter_bit(q[u], lg);
+        v[u] = p < nprobe && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
+      }
+      table_find_many<U>(G.key, mask, q, v, sl);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (sl[u] == kNone) continue;
+        const int p = p0 + u * GS;
+        const uint32_t* r = grow + (size_t)sl[u] * (D + 1);
+        const uint32_t cn = r[0];
+        const float fc = (float)cn;
+        Dc += cn;
+        float dv[D];  // the probe's offset v in {-1, 0, 1}^d, axis 0 the slowest digit
+        int rest = p;
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+          dv[a] = (float)(rest % 3 - 1);
+          rest /= 3;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) N[a].add(fc * (__uint_as_float(r[1 + a]) + dv[a] * h));
+        if (p != center) nbc = true;
+      }
+    }
+    any_nb = any_nb || nbc;
+#pragma unroll
+    for (int o = GS / 2; o > 0; o >>= 1) {
+      Dc += __shfl_xor_sync(gmask, Dc, o);
+#pragma unroll
+      for (int a = 0; a < D; ++a) N[a].add(shfl_xor_ff(gmask, N[a], o));
+    }
+    // float-float additions are not symmetric in their low parts: every lane
+    // of the group takes the first lane's sums, so all take the same decisions
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      N[a].hi = __shfl_sync(gmask, N[a].hi, 0, GS);
+      N[a].lo = __shfl_sync(gmask, N[a].lo, 0, GS);
+    }
+    // centroid relative to the lower face; move q_a in {-1, 0, 1} per axis
+    uint64_t field = 0;
+    float rel[D];
+    bool near = false;
+    if (BT && !live) {
+      field = key;
+#pragma unroll
+      for (int a = 0; a < D; ++a) rel[a] = 0.f;
+    } else {
+      const float fD = (float)Dc;
+      uint64_t nk = key;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        rel[a] = N[a].hi / fD + N[a].lo / fD;
+        const int qa = rel[a] < 0.f ? -1 : (rel[a] >= h ? 1 : 0);
+        near = near || fabsf(rel[a]) < kFaceBand * h || fabsf(rel[a] - h) < kFaceBand * h;
+        nk += (uint64_t)(int64_t)qa << A.P.off[a];
+      }
+      field = nk;
+    }
+    if (near) {
+      // float64 recheck: the same neighbours, upcast, summed in float64 about
+      // the cell's lower face; the key of N / D decided on the face table
+      double N64[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) N64[a] = 0.0;
+      double org[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) org[a] = (double)(float)face_of(A.P, A.thr, key, a);
+      for (int p = glane; p < nprobe; p += GS) {
+        const uint64_t qk = key + __ldg(&A.dtab[p]);
+        const uint32_t sl = table_find(G.key, mask, qk);
+        if (sl == kNone) continue;
+        const uint32_t* r = grow + (size_t)sl * (D + 1);
+        const double cn = (double)r[0];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const double of = (double)(float)face_of(A.P, A.thr, qk, a);
+          N64[a] += cn * ((of - org[a]) + (double)__uint_as_float(r[1 + a]));
+        }
+      }
+#pragma unroll
+      for (int o = GS / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < D; ++a) N64[a] += __shfl_xor_sync(gmask, N64[a], o);
+      uint64_t nk = (key >> A.P.inst_off) << A.P.inst_off;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const double xa = org[a] + N64[a] / (double)Dc;
+        const int64_t* thr = A.thr + A.P.thr_off[a];
+        int idx = key_index(thr, A.P.span[a], A.P.kmin[a], A.P.inv_h,
+                            (uint64_t)__double_as_longlong(xa));
+        // a centroid this close below a face is taken to lie on it: the
+        // float32 state cannot tell such a value from an exact tie, which the
+        // exact path assigns to the upper cell
+        if (idx + 1 < A.P.span[a]) {
+          const int64_t o = __ldg(&thr[idx + 1]);
+          const double fnext =
+              __longlong_as_double((long long)(o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll)));
+          if (fnext - xa < (double)kTieBand * (double)h) ++idx;
+        }
+        nk |= (uint64_t)(idx + 1) << A.P.off[a];
+        // the centroid relative to its own cell's lower face, in float32
+        rel[a] = (float)(xa - org[a]);
+      }
+      field = nk;
+      if (glane == 0) atomicAdd(&A.fl->rechecks, 1ull);
+    }
+    const bool nbg = BT && (__ballot_sync(gmask, nbc) & gmask) != 0u;
+    uint32_t ms = kNone;
+    if (glane == 0) {
+      bool won;
+      ms = table_insert(M.key, maskM, field, won, &A.fl->err);
+      if (ms != kNone) {
+        if (won) {
+          const uint32_t id = atomicAdd(&A.st[t + 1].m, 1u);
+          M.list[id] = ms;
+          if (BT) M.id[ms] = j;
+        }
+        atomicAdd(&mrow[(size_t)ms * (D + 1)], cj);
+      }
+      pslot[j] = ms;
+      if (BT && live) {
+        if (nbg && !A.I.nbf[t & 1][inst]) atomicOr(&A.I.nbf[t & 1][inst], 1u);
+        atomicAdd(&A.I.mt[t & 1][inst], 1u);
+      }
+    }
+    ms = __shfl_sync(gmask, ms, 0, GS);
+    if (glane < D && ms != kNone) {
+      // this cell's count-weighted centroid about the new cell's lower face
+      float contrib = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (a != glane) continue;
+        if (BT && !live) {
+          contrib = (float)cj * __uint_as_float(grow[(size_t)G.list[j] * (D + 1) + 1 + a]);
+        } else {
+          const int top = a == 0 ? A.P.inst_off : A.P.off[a - 1];
+          const uint64_t fm = (1ull << (top - A.P.off[a])) - 1ull;
+          const int qa = (int)((field >> A.P.off[a]) & fm) - (int)((key >> A.P.off[a]) & fm);
+          contrib = (float)cj * (rel[a] - (float)qa * h);
+        }
+      }
+      atomicAdd(&macc[(size_t)ms * D + glane], contrib);
+    }
+  }
+  if (t > 0) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nth = gridDim.x * blockDim.x;
+    const LevelTable Lp = A.tab[(t + 2) % 3];
+    uint32_t* prow = reinterpret_cast<uint32_t*>(Lp.row);
+    const uint32_t* pp = A.pslot[(t - 1) & 1];
+    for (uint32_t i = tid; i < m_prev; i += nth) {
+      A.forest[base_prev + i] = base + G.id[pp[i]];
+      const uint32_t s = Lp.list[i];
+      Lp.key[s] = kEmpty;
+      prow[(size_t)s * (D + 1)] = 0;
+    }
+  }
+}
+
+// The cells of level t+1 (float32): mean offsets = merged sums / counts.
+template <int D, bool BT>
+__device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const LevelTable G = A.tab[t % 3];
+  const LevelTable M = A.tab[(t + 1) % 3];
+  const uint32_t* grow = reinterpret_cast<const uint32_t*>(G.row);
+  uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);
+  float* macc = reinterpret_cast<float*>(M.acc);
+  const Cells cur = A.cells[t & 1];
+  const Cells nx = A.cells[(t + 1) & 1];
+  uint32_t* f = A.filter[(t + 1) & 1];
+  const int lg = filter_log2(m1);
+  for (uint32_t id = tid; id < m1; id += nth) {
+    const uint32_t s = M.list[id];
+    uint32_t* r = mrow + (size_t)s * (D + 1);
+    uint64_t key = M.key[s];
+    const uint32_t cnt = r[0];
+    bool restored = false;
+    if (BT) {
+      const uint32_t inst = (uint32_t)(key >> A.P.inst_off);
+      if (!A.I.done[t & 1][inst] && !A.I.nbf[t & 1][inst]) {
+        const uint32_t j = M.id[s];
+        const uint32_t* o = grow + (size_t)G.list[j] * (D + 1);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          r[1 + a] = o[1 + a];
+          macc[(size_t)s * D + a] = 0.f;
+        }
+        key = cur.key[j];
+        restored = true;
+      }
+    }
+    if (!restored) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        r[1 + a] = __float_as_uint(macc[(size_t)s * D + a] / (float)cnt);
+        macc[(size_t)s * D + a] = 0.f;
+      }
+    }
+    nx.key[id] = key;
+    nx.cnt[id] = cnt;
+    M.id[s] = id;
+    filter_set(f, key, lg);
+  }
+  if (BT) {
+    for (uint32_t b = tid; b < (uint32_t)A.B; b += nth) {
+      const bool act = A.I.done[t & 1][b] == 0, nb = A.I.nbf[t & 1][b] != 0;
+      A.I.done[(t + 1) & 1][b] = act && nb ? 0u : 1u;
+      if (act && nb) A.I.cell_iters[b] += A.I.mt[t & 1][b];
+      if (act && !nb) {
+        A.I.iters[b] = t;
+        A.I.conv[b] = 1;
+      }
+    }
+  }
+}
+
+// Mode of final cell r (float32 state): its lower face plus its mean offset,
+// in float64; then the slot is released.
+template <int D>
+__device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Plan& P,
+                                                   const int64_t* thr, const uint64_t* keys,
+                                                   uint32_t r, uint32_t label, double* modes,
+                                                   bool write) {
+  const uint32_t s = G.list[r];
+  uint32_t* row = reinterpret_cast<uint32_t*>(G.row) + (size_t)s * (D + 1);
+  if (write) {
+    const uint64_t key = keys[r];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      modes[(size_t)label * D + a] =
+          (double)(float)face_of(P, thr, key, a) + (double)__uint_as_float(row[1 + a]);
+  }
+  row[0] = 0;
+  G.key[s] = kEmpty;
+}
+
+template <int D, bool BT, bool F32>
+__global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
+  unsigned inexact = 0, werr = 0;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  volatile IterState* vst = A.st;
+  SegClock clk;
+  clk.start();
+
+  // step i, second pass: exact cell sums
+  const uint32_t m0 = *(volatile uint32_t*)&A.fl->m0;
+  phase_count_totals(A, m0);
+  if (!grid_sync(A.bar, A.fl)) return;
+  phase_offsets(A, m0);
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegOffsets);
+  phase_scatter(A);
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegScatter);
+  if (F32) {
+    if (A.f32)
+      phase_cell_sums32<D, float>(A);
+    else
+      phase_cell_sums32<D, double>(A);
+  } else {
+    if (A.f32)
+      phase_cell_sums<D, float>(A, inexact, werr);
+    else
+      phase_cell_sums<D, double>(A, inexact, werr);
+  }
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegSums);
+
+  // level 0
+  const uint32_t maskA = mask_for(m0, A.capAB);
+  if (tid == 0) {
+    A.st[0].m = m0;
+    A.st[0].mask = maskA;
+    A.st[0].base = 0;
+  }
+  if (F32)
+    phase_level0_32<D>(A, m0, maskA);
+  else
+    phase_level0<D>(A, m0, maskA, inexact, werr);
+  if (BT) {
+    for (uint32_t id = tid; id < m0; id += nth)
+      atomicAdd(&A.I.m0[(uint32_t)(A.cells[0].key[id] >> A.P.inst_off)], 1u);
+  }
+  if (!grid_sync(A.bar, A.fl)) return;
+  clk.lap(kSegLevel0);
+
+  int t = 0;
+  uint32_t m = m0, mask = maskA, base = 0, m_prev = 0, base_prev = 0;
+  unsigned long long cell_iters = 0;
+  bool converged = false;
+  for (;;) {
+    bool any_nb = false;
+    const uint32_t maskM = mask_for(m, A.capAB);
+    // lanes per cell: the fewest (most cells in flight) while the level has
+    // more cells than warps, else 32
+    constexpr int GSmin = GatherLanes<D>::min;
+    if (F32) {
+      if (GSmin < 32 && m > (nth >> 5))
+        phase_update32<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb);
+      else
+        phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb);
+    } else {
+      if (GSmin < 32 && m > (nth >> 5))
+        phase_update<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact,
+                                   werr);
+      else
+        phase_update<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact,
+                                werr);
+    }
+    if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
+    if (!grid_sync(A.bar, A.fl)) return;
+    clk.lap(t == 0 ? kSegUpdateFirst : kSegUpdateRest);
+    if (!vst[t].has_nb) {
+      converged = true;
+      break;
+    }
+    if (t == A.max_iter) break;
+    const uint32_t m1 = vst[t + 1].m;
+    if (F32)
+      phase_compact32<D, BT>(A, t, m1);
+    else
+      phase_compact<D, BT>(A, t, m1, inexact, werr);
+    if (tid == 0) {
+      A.st[t + 1].mask = maskM;
+      A.st[t + 1].base = base + m;
+    }
+    if (!grid_sync(A.bar, A.fl)) return;
+    clk.lap(kSegCompact);
+    cell_iters += m;
+    m_prev = m;
+    base_prev = base;
+    base += m;
+    m = m1;
+    mask = maskM;
+    ++t;
+  }
+  const int T = t;
+  const uint32_t k = m;
+
+  // the update of step T is not applied: clear its merge table; every final
+  // cell is its own root
+  {
+    const LevelTable Ms = A.tab[(T + 1) % 3];
+    const uint32_t ms = vst[T + 1].m;
+    for (uint32_t id = tid; id < ms; id += nth) {
+      const uint32_t s = Ms.list[id];
+      Ms.key[s] = kEmpty;
+      if (F32) {
+        reinterpret_cast<uint32_t*>(Ms.row)[(size_t)s * (D + 1)] = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) reinterpret_cast<float*>(Ms.acc)[(size_t)s * D + a] = 0.f;
+      } else {
+        Ms.row[(size_t)s * (D + 1)].x = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          uint64_t* acc = Ms.acc + ((size_t)s * D + a) * 4;
+          acc[0] = acc[1] = acc[2] = acc[3] = 0;
+        }
+      }
+    }
+    for (uint32_t j = tid; j < k; j += nth) A.forest[base + j] = base + j;
+    if (BT) {
+      // instances still updating stop at step T (converged unless the step
+      // limit stopped them with a neighbour present); final cells per instance
+      for (uint32_t b = tid; b < (uint32_t)A.B; b += nth) {
+        if (!A.I.done[T & 1][b]) {
+          A.I.iters[b] = T;
+          A.I.conv[b] = A.I.nbf[T & 1][b] ? 0 : 1;
+        }
+      }
+      const Cells c = A.cells[T & 1];
+      for (uint32_t j = tid; j < k; j += nth)
+        atomicAdd(&A.I.k[(uint32_t)(c.key[j] >> A.P.inst_off)], 1u);
+    }
+  }
+  if (!grid_sync(A.bar, A.fl)) return;
+  if (BT && tid == 0) {
+    // labels of instance b start at 0: subtract the final cells of earlier ones
+    uint32_t run = 0;
+    for (int b = 0; b < A.B; ++b) {
+      A.I.koff[b] = run;
+      run += A.I.k[b];
+    }
+  }
+
+  // pointer jumping over the forest of merges: after r rounds every node
+  // points 2^r levels up (or to its root)
+  const uint32_t nodes = base + k;
+  uint32_t* in = A.forest;
+  uint32_t* out = A.forest2;
+  for (int hop = 1; hop < T; hop <<= 1) {
+    for (uint32_t v = tid; v < nodes; v += nth) out[v] = in[in[v]];
+    if (!grid_sync(A.bar, A.fl)) return;
+    uint32_t* tmp = in;
+    in = out;
+    out = tmp;
+  }
+  if (in != A.forest) {
+    for (uint32_t v = tid; v < m0; v += nth) A.forest[v] = in[v];
+    if (!grid_sync(A.bar, A.fl)) return;
+  }
+
+  const bool numbered = k <= A.rank_max;
+  if (numbered) {
+    // label of a final cell = number of final keys below its key (keys are
+    // unique), i.e. ascending lexicographic order of the integer keys
+    const Cells c = A.cells[T & 1];
+    const uint32_t warp = tid >> 5, nwarps = nth >> 5;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t r = warp; r < k; r += nwarps) {
+      const uint64_t kr = c.key[r];
+      uint32_t below = 0;
+      for (uint32_t q = lane; q < k; q += 32) below += c.key[q] < kr ? 1u : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(kFull, below, o);
+      if (lane == 0) A.rank[r] = below;
+    }
+    if (!grid_sync(A.bar, A.fl)) return;
+    for (uint32_t cc = tid; cc < m0; cc += nth) {
+      const uint32_t r = A.forest[cc] - base;
+      uint32_t label = A.rank[r];
+      if (BT) label -= A.I.koff[(uint32_t)(c.key[r] >> A.P.inst_off)];
+      A.labslot[A.T0.list[cc]] = label;
+    }
+    if (!grid_sync(A.bar, A.fl)) return;
+    for (int64_t i = tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
+    const LevelTable G = A.tab[T % 3];
+    const bool write = (int64_t)k <= A.modes_cap;
+    for (uint32_t r = tid; r < k; r += nth) {
+      if (F32)
+        mode_and_release32<D>(G, A.P, A.thr, c.key, r, A.rank[r], A.modes, write);
+      else
+        mode_and_release<D>(G, A.P, r, A.rank[r], A.modes, write, inexact);
+    }
+  }
+  clk.lap(kSegLabels);
+  if (tid == 0) {
+    A.res->iterations = T;
+    A.res->converged = converged ? 1 : 0;
+    A.res->k = k;
+    A.res->base = base;
+    A.res->need_sort = numbered ? 0u : 1u;
+    A.res->cell_iters = cell_iters;
+#pragma unroll
+    for (int i = 0; i < kLoopPhases; ++i) A.res->ns[i] = clk.ns[i];
+  }
+  if (inexact) atomicAdd(&A.fl->inexact, 1ull);
+  if (werr) atomicOr(&A.fl->err, kErrWindow);
+}
+
+template <int D, bool F32>
+__global__ void k_modes_tail(LevelTable G, Plan P, const int64_t* __restrict__ thr,
+                             const uint64_t* __restrict__ keys, const uint32_t* __restrict__ rank,
+                             double* __restrict__ modes, uint32_t k, bool write) {
+  unsigned inexact = 0;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x) {
+    if (F32)
+      mode_and_release32<D>(G, P, thr, keys, r, rank[r], modes, write);
+    else
+      mode_and_release<D>(G, P, r, rank[r], modes, write, inexact);
+  }
+}
+
+
+// Launch helpers, instantiated per precision in gs_loop64.cu / gs_loop32.cu.
+template <int D, bool F32>
+int loop_grid_d() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  const int smem = (int)(kFilterWords * sizeof(uint32_t));
+  if (cudaFuncSetAttribute(k_loop<D, false, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_loop<D, true, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem) != cudaSuccess)
+    return -1;
+  int per_sm_b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_loop<D, true, F32>, kLoopBlock,
+                                                    smem) != cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_loop<D, false, F32>, kLoopBlock,
+                                                    smem) != cudaSuccess)
+    return -1;
+  if (per_sm_b < per_sm) per_sm = per_sm_b;  // one grid size serves both variants
+  if (per_sm < 1) return -1;
+  if (per_sm > 2) per_sm = 2;  // fewer blocks make the grid barriers cheaper
+  const int g = sms * per_sm;
+  return g < kMaxLoopGrid ? g : kMaxLoopGrid;
+}
+
+template <bool F32>
+int loop_grid_t(int d) {
+  switch (d) {
+    case 1: return loop_grid_d<1, F32>();
+    case 2: return loop_grid_d<2, F32>();
+    case 3: return loop_grid_d<3, F32>();
+    case 4: return loop_grid_d<4, F32>();
+    case 5: return loop_grid_d<5, F32>();
+    case 6: return loop_grid_d<6, F32>();
+    case 7: return loop_grid_d<7, F32>();
+    case 8: return loop_grid_d<8, F32>();
+  }
+  return -1;
+}
+
+template <bool F32>
+cudaError_t launch_loop_t(const LoopArgs& a, int grid, cudaStream_t s) {
+  LoopArgs args = a;
+  void* params[] = {&args};
+  const size_t smem = kFilterWords * sizeof(uint32_t);
+  if (a.B > 1) {
+    GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D, true, F32>,
+                                                            dim3(grid), dim3(kLoopBlock), params,
+                                                            smem, s));
+  }
+  GS_DISPATCH_D(a.P.d, return cudaLaunchCooperativeKernel((const void*)k_loop<D, false, F32>,
+                                                          dim3(grid), dim3(kLoopBlock), params,
+                                                          smem, s));
+  return cudaSuccess;
+}
+
+template <bool F32>
+cudaError_t launch_modes_tail_t(const LoopArgs& a, uint32_t k, int T, cudaStream_t s) {
+  const bool write = (int64_t)k <= a.modes_cap;
+  GS_DISPATCH_D(a.P.d, k_modes_tail<D, F32><<<grid_for(k), kBlock, 0, s>>>(
+                           a.tab[T % 3], a.P, a.thr, a.cells[T & 1].key, a.rank, a.modes, k,
+                           write));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace gs

@@ -27,6 +27,7 @@ struct Plan {
   int64_t kmin[kMaxD];      // smallest key of axis a
   float inv_h;              // 1/h rounded to float: first guess of a cell index only
   int inst_off;             // batched runs: bit offset of the instance field (above all axes)
+  float h32;                // h rounded to float (the float32 variant)
 };
 
 // Device-resident state of one level t (the cells before update step t).
@@ -43,6 +44,7 @@ struct DevFlags {
   uint32_t m0;                  // cells created by binning
   unsigned long long inexact;   // values truncated by the fixed-point window
   unsigned long long bad;       // non-finite input coordinates
+  unsigned long long rechecks;  // float32 variant: key decisions redone in float64
   long long min_ord[kMaxD];     // order code of min_i x_ia
   long long max_ord[kMaxD];     // order code of max_i x_ia
   unsigned long long maxabs[kMaxD];  // bits of max_i |x_ia|

@@ -44,7 +44,8 @@ PHASES = ("range", "bin", "loop", "sort", "k_offsets", "k_scatter", "k_sums", "k
 class gs_fit_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("m0", ctypes.c_int64), ("k", ctypes.c_int64), ("inexact", ctypes.c_int64),
-                ("cell_iters", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("cell_iters", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("face_rechecks", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -1,0 +1,136 @@
+"""The float32 mixed-precision variant (GS_FP32_MIXED) against the float64
+oracle.  The bar: at least 99.9% of the points carry the label of the
+oracle's cluster they best overlap, and the modes of matching clusters lie
+within 1e-3 * h of the oracle's (the float32 path is not bit-exact: its sums
+are rounded float32 and merges add in any order)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2206_02200_gb300 import gridshift, synth
+from tests import golden_io
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+AGREE = 0.999
+MODE_TOL = 1e-3  # in units of h
+
+
+def _fit32(X, h, max_iter=50, as_f32=False):
+    pts = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    if as_f32:
+        pts = pts.float()
+    with gridshift.GridShift(X.shape[1], h, max_iter, precision=gridshift.GS_FP32_MIXED) as g:
+        labels, modes, info = g.fit(pts)
+        torch.cuda.synchronize()
+    return labels.cpu().numpy(), modes.cpu().numpy(), info
+
+
+def agreement(lab, ref_lab):
+    """Fraction of points whose cluster's best-overlapping oracle cluster is
+    their own oracle cluster, and the mutual best pairs (ours, oracle's)."""
+    n = lab.size
+    if n == 0:
+        return 1.0, []
+    pairs, counts = np.unique(np.stack([lab, ref_lab], 1), axis=0, return_counts=True)
+    best = {}
+    for (a, b), c in zip(pairs.tolist(), counts.tolist()):
+        if c > best.get(a, (None, -1))[1]:
+            best[a] = (b, c)
+    rbest = {}
+    for (a, b), c in zip(pairs.tolist(), counts.tolist()):
+        if c > rbest.get(b, (None, -1))[1]:
+            rbest[b] = (a, c)
+    agree = sum(c for _, c in best.values()) / n
+    mutual = [(a, b) for a, (b, _) in best.items() if rbest[b][0] == a]
+    return agree, mutual
+
+
+def check32(X, h, max_iter=50, as_f32=False):
+    Xo = X.astype(np.float32).astype(np.float64) if as_f32 else X
+    ref = oracle.fit(Xo, h, max_iter)
+    lab, md, info = _fit32(X, h, max_iter, as_f32)
+    agree, mutual = agreement(lab, ref["labels"])
+    assert agree >= AGREE, agree
+    err = max((np.max(np.abs(md[a] - ref["modes"][b])) for a, b in mutual), default=0.0)
+    assert err <= MODE_TOL * h, err / h
+    return agree, err / h, info, ref
+
+
+@pytest.mark.parametrize("case", golden_io.all_cases(), ids=lambda c: c["name"])
+def test_golden_cases_fp32(case):
+    X = case["points"]
+    lab, md, info = _fit32(X, case["h"], case.get("max_iter", 50))
+    assert list(lab) == case["labels"]
+    for r, row in enumerate(case["modes"]):
+        for a, v in enumerate(row):
+            assert abs(md[r, a] - float(v)) <= 1e-6 * case["h"]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 6, 8])
+def test_random_blobs_fp32(d):
+    rng = np.random.default_rng(500 + d)
+    centres = rng.uniform(-40, 40, size=(5, d))
+    X = centres[rng.integers(0, 5, 20000)] + rng.normal(0, 3.0, size=(20000, d))
+    check32(X, 4.0)
+
+
+def test_images_fp32():
+    for (H, W, R, seed, xy) in [(120, 160, 9, 4, None), (250, 333, 15, 3, 0.1)]:
+        img = synth.voronoi_image(H, W, R, 10.0, seed=seed, gradient=0.02)
+        check32(synth.image_features(img, xy_scale=xy), 10.0 if xy else 16.0)
+
+
+def test_gmm_float32_input_fp32():
+    X = synth.gmm_points(300_000, 6, 40, seed=9)
+    check32(X, 4.0, as_f32=True)
+
+
+def test_max_iter_fp32():
+    X = synth.image_features(synth.voronoi_image(120, 160, 9, 8.0, seed=4))
+    for mi in (0, 1, 2):
+        agree, err, info, ref = check32(X, 16.0, mi)
+        assert info["iterations"] <= mi
+
+
+def test_image_1080p_d5_fp32():
+    w = synth.WORKLOADS["image_1080p_d5"]()
+    agree, err, info, ref = check32(w["points"], w["h"], w["max_iter"])
+    print(f"1080p fp32: label agreement {agree:.6f}, max mode error {err:.2e} h, "
+          f"face rechecks {info['face_rechecks']}")
+
+
+def test_batched_fp32():
+    parts = synth.image_batch(5, 300, hmin=40, hmax=120, wmin=50, wmax=160)
+    offsets = np.concatenate([[0], np.cumsum([len(p) for p in parts])]).tolist()
+    X = np.concatenate(parts, 0)
+    with gridshift.GridShift(3, 16.0, 50, precision=gridshift.GS_FP32_MIXED) as g:
+        labels, modes, infos = g.fit_batched(torch.from_numpy(X).cuda(), offsets)
+        torch.cuda.synchronize()
+    lab = labels.cpu().numpy()
+    for b, p in enumerate(parts):
+        ref = oracle.fit(p, 16.0, 50)
+        agree, mutual = agreement(lab[offsets[b]:offsets[b + 1]], ref["labels"])
+        assert agree >= AGREE
+        md = modes[b].cpu().numpy()
+        err = max((np.max(np.abs(md[a] - ref["modes"][c])) for a, c in mutual), default=0.0)
+        assert err <= MODE_TOL * 16.0
+
+
+def test_switching_precision_on_one_context():
+    X = synth.image_features(synth.voronoi_image(100, 140, 7, 8.0, seed=6))
+    ref = oracle.fit(X, 16.0, 50)
+    pts = torch.from_numpy(X).cuda()
+    with gridshift.GridShift(3, 16.0, 50) as g:
+        for prec in (gridshift.GS_FP64, gridshift.GS_FP32_MIXED, gridshift.GS_FP64):
+            assert gridshift.gs_set_precision(g._ctx, prec) == gridshift.GS_OK
+            labels, modes, info = g.fit(pts)
+            torch.cuda.synchronize()
+            if prec == gridshift.GS_FP64:
+                np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+            else:
+                assert agreement(labels.cpu().numpy(), ref["labels"])[0] >= AGREE
