@@ -4,6 +4,10 @@ Workload (default): a synthetic 1920x1080 image of 40 Voronoi regions, noise
 sigma 10, features (R, G, B, 0.1 x, 0.1 y) in float64 (d = 5), cell side h = 12,
 at most 50 updates, the plain FP64 path.  One step = one complete GridShift run
 (binning, all updates until convergence, labels and modes) over the image.
+``--precision fp32`` runs the float32 mixed-precision path and reports its
+label agreement and mode error against the FP64 path; ``--workload
+batch_64_d3`` runs 64 uneven images in one batched call (and times 64
+sequential plain calls beside it).
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
 reference arm: a plain single-threaded FP64 program written from the paper).
@@ -26,10 +30,23 @@ if ROOT not in sys.path:
 METRIC = "Mpixels/s end-to-end (1080p/4K, d=3/5), FP32 vs FP64, at stated label agreement"
 UNIT = "Mpixels/s"
 
-# Bytes each unit of work must move (algorithmic, not measured):
-#   binning kernel: per point, read d coordinates and write its cell slot (4 B).
+# Bytes each unit of work must move through DRAM (algorithmic, not measured):
+#   k_bin (binning, first pass): per point, read its d coordinates and write
+#     its cell slot (4 B).
+#   k_loop (everything after): per point, read its d coordinates again for the
+#     exact cell sums, and 4-byte words: its slot read by the scatter, written
+#     to and read from the counting-sort permutation, gathered by the sums,
+#     read again for its label, and the label written (6 x 4 B); per active
+#     cell and update step, its row read once and the next level's row and key
+#     written once (rows: count + d sums, 16 (d + 1) B in FP64, 4 (d + 1) B in
+#     FP32; keys 8 B).
 def bin_bytes_per_point(d: int, elem: int) -> int:
     return d * elem + 4
+
+
+def loop_bytes(n: int, d: int, elem: int, cell_steps: int, fp32: bool) -> int:
+    row = (4 if fp32 else 16) * (d + 1)
+    return n * (d * elem + 24) + cell_steps * (2 * row + 8)
 
 
 def peaks() -> dict:
@@ -108,29 +125,53 @@ def load_workload(name: str) -> dict:
     return synth.WORKLOADS[name]()
 
 
-def workload_config(w: dict, name: str) -> dict:
-    n, d = w["points"].shape
-    return {"workload": w["name"], "n": int(n), "d": int(d), "h": w["h"],
-            "max_iter": w["max_iter"], "precision": "fp64",
-            "input_dtype": str(w["points"].dtype),
-            "l2": "flushed between timed steps (256 MiB device write)",
-            "generator": "Voronoi image, seeded (paper_2206_02200_gb300.synth)"}
+def workload_config(w: dict, name: str, precision: str = "fp64") -> dict:
+    if "parts" in w:
+        n, d = sum(len(p) for p in w["parts"]), w["parts"][0].shape[1]
+        dt = w["parts"][0].dtype
+    else:
+        (n, d), dt = w["points"].shape, w["points"].dtype
+    gen = ("GMM points, seeded" if name.startswith("gmm") else "Voronoi image, seeded")
+    cfg = {"workload": w["name"], "n": int(n), "d": int(d), "h": w["h"],
+           "max_iter": w["max_iter"], "precision": precision, "input_dtype": str(dt),
+           "l2": "flushed between timed steps (256 MiB device write)",
+           "generator": gen + " (paper_2206_02200_gb300.synth)"}
+    if "parts" in w:
+        cfg["instances"] = len(w["parts"])
+    return cfg
+
+
+def _oracle_sample(w: dict):
+    """The CPU oracle's share of the workload: the whole point set, or for a
+    batched workload its first instances up to about 1.5 M points."""
+    if "parts" not in w:
+        return [w["points"]]
+    out, tot = [], 0
+    for p in w["parts"]:
+        out.append(p)
+        tot += len(p)
+        if tot >= 1_500_000:
+            break
+    return out
 
 
 def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8) -> dict:
     """Times the CPU oracle (single-threaded, as it stands) on the same workload."""
     from oracle import oracle
     oracle.build()
-    X, h, it = w["points"], w["h"], w["max_iter"]
-    n = X.shape[0]
+    sample = _oracle_sample(w)
+    h, it = w["h"], w["max_iter"]
+    n = sum(len(X) for X in sample)
     runs, total = 0, 0.0
     while runs < max_runs and (runs == 0 or total < budget_s):
         t0 = time.perf_counter()
-        oracle.fit(X, h, it)
+        for X in sample:
+            oracle.fit(X, h, it)
         total += time.perf_counter() - t0
         runs += 1
+    what = "the workload" if "parts" not in w else f"the first {len(sample)} instances"
     return {"value": n * runs / total / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full runs of the workload ({n} points each), {total:.1f} s"}
+            "sample": f"{runs} full runs of {what} ({n} points each), {total:.1f} s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -139,28 +180,53 @@ def run_reference(args, rank: int, world: int):
     w = load_workload(args.workload)
     from oracle import oracle
     oracle.build()
-    X, h, it = w["points"], w["h"], w["max_iter"]
-    n = X.shape[0]
+    sample = _oracle_sample(w)
+    h, it = w["h"], w["max_iter"]
+    n = sum(len(X) for X in sample)
     for _ in range(args.warmup):
-        oracle.fit(X, h, it)
+        for X in sample:
+            oracle.fit(X, h, it)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.fit(X, h, it)
+        for X in sample:
+            oracle.fit(X, h, it)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n * args.steps / total / 1e6
+    what = "the workload" if "parts" not in w else f"the first {len(sample)} instances"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, args.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full runs of the workload ({n} points each)"},
+                             "sample": f"{args.steps} full runs of {what} ({n} points each)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _agreement(lab, ref_lab, modes, ref_modes, h) -> tuple:
+    """Fraction of points in the best-overlapping reference cluster, and the
+    largest mode distance (units of h) over mutually best cluster pairs."""
+    import numpy as np
+    if lab.size == 0:
+        return 1.0, 0.0
+    pairs, counts = np.unique(np.stack([lab, ref_lab], 1), axis=0, return_counts=True)
+    best, rbest = {}, {}
+    for (a, b), c in zip(pairs.tolist(), counts.tolist()):
+        if c > best.get(a, (None, -1))[1]:
+            best[a] = (b, c)
+        if c > rbest.get(b, (None, -1))[1]:
+            rbest[b] = (a, c)
+    agree = sum(c for _, c in best.values()) / lab.size
+    err = 0.0
+    for a, (b, _) in best.items():
+        if rbest[b][0] == a:
+            err = max(err, float(np.max(np.abs(modes[a] - ref_modes[b]))) / h)
+    return agree, err
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -174,21 +240,39 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(dev)
     gridshift.load()
     w = load_workload(args.workload)
-    X = w["points"]
+    batched = "parts" in w
+    if batched:
+        X = np.ascontiguousarray(np.concatenate(w["parts"], 0))
+        offsets = np.concatenate([[0], np.cumsum([len(p) for p in w["parts"]])]).tolist()
+    else:
+        X = w["points"]
     n, d = X.shape
     elem = X.dtype.itemsize
-    g = gridshift.GridShift(d, w["h"], w["max_iter"])
+    fp32 = args.precision == "fp32"
+    prec = gridshift.GS_FP32_MIXED if fp32 else gridshift.GS_FP64
+    g = gridshift.GridShift(d, w["h"], w["max_iter"], precision=prec)
     pts = torch.from_numpy(X).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     modes = torch.empty((max(n // 16, 4096), d), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        st, k, info = g.fit_into(pts, labels, modes)
+    def call(p, lab, md, gg=g):
+        if batched:
+            st, mo, infos = gridshift.gs_fit_batched(gg._ctx, p.data_ptr(), gridshift.GS_IN_F64
+                                                     if p.dtype == torch.float64 else
+                                                     gridshift.GS_IN_F32, offsets,
+                                                     lab.data_ptr(), md.data_ptr(), md.shape[0])
+            if st != gridshift.GS_OK:
+                raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gg._ctx))
+            return mo[-1], [x.as_dict() for x in infos]
+        gridshift.gs_set_stream(gg._ctx, stream.cuda_stream)
+        st, k, info = gg.fit_into(p, lab, md)
         if st != gridshift.GS_OK:
-            raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(g._ctx))
-        return k, info
+            raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gg._ctx))
+        return k, [info.as_dict()]
+
+    gridshift.gs_set_stream(g._ctx, stream.cuda_stream)
 
     def barrier():
         if world > 1:
@@ -196,7 +280,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize(dev)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        call(pts, labels, modes)
 
     # -- device-resident inputs: K timed steps, L2 flushed between them
     g.set_timing(True)
@@ -206,6 +290,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     phase_cnt = {p: 0 for p in gridshift.PHASES}
     launches = 0
     cell_iters = 0
+    m0_total = 0
     vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     clocks = ClockSampler(vis[local_rank] if local_rank < len(vis) else local_rank)
     barrier()
@@ -213,13 +298,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
-        k, info = step()
+        k, infos = call(pts, labels, modes)
         ev[i][1].record(stream)
-        launches += info.launches
-        cell_iters += info.cell_iters
-        for p, (ms, c) in g.phase_times().items():
-            phase_ms[p] += ms
-            phase_cnt[p] += c
+        launches += infos[0]["launches"]
+        cell_iters += sum(x["cell_iters"] for x in infos)
+        m0_total += sum(x["m0"] for x in infos)
+        if not batched:
+            for p, (ms, c) in g.phase_times().items():
+                phase_ms[p] += ms
+                phase_cnt[p] += c
     barrier()
     clk = clocks.stop()
     g.set_timing(False)
@@ -229,6 +316,59 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     value = n * args.steps * world / (total_ms / 1e3) / 1e6
+
+    # -- agreement of the float32 path with the FP64 path (which the tests
+    #    hold bit-identical to the oracle)
+    agreement = None
+    if fp32:
+        lab32 = labels.cpu().numpy().copy()
+        md32 = modes[:k].cpu().numpy().copy()
+        g64 = gridshift.GridShift(d, w["h"], w["max_iter"])
+        gridshift.gs_set_stream(g64._ctx, stream.cuda_stream)
+        lab64 = torch.empty_like(labels)
+        md64 = torch.empty_like(modes)
+        k64, infos64 = call(pts, lab64, md64, g64)
+        torch.cuda.synchronize(dev)
+        l64, m64 = lab64.cpu().numpy(), md64[:k64].cpu().numpy()
+        if batched:
+            agree_n, err = 0.0, 0.0
+            mo32 = np.concatenate([[0], np.cumsum([x["k"] for x in infos])])
+            mo64 = np.concatenate([[0], np.cumsum([x["k"] for x in infos64])])
+            for b in range(len(offsets) - 1):
+                s0, s1 = offsets[b], offsets[b + 1]
+                a_b, e_b = _agreement(lab32[s0:s1], l64[s0:s1], md32[mo32[b]:mo32[b + 1]],
+                                      m64[mo64[b]:mo64[b + 1]], w["h"])
+                agree_n += a_b * (s1 - s0)
+                err = max(err, e_b)
+            agree = agree_n / n
+        else:
+            agree, err = _agreement(lab32, l64, md32, m64, w["h"])
+        agreement = {"labels": agree, "max_mode_error_h": err,
+                     "face_rechecks_per_step": sum(x["face_rechecks"] for x in infos),
+                     "against": "FP64 GPU path (bit-identical to the FP64 oracle in the tests)"}
+        g64.close()
+
+    # -- sequential plain calls beside the batched one
+    sequential = None
+    if batched:
+        gp = gridshift.GridShift(d, w["h"], w["max_iter"])
+        gridshift.gs_set_stream(gp._ctx, stream.cuda_stream)
+        parts_dev = [pts[offsets[b]:offsets[b + 1]] for b in range(len(offsets) - 1)]
+        for P in parts_dev[:3]:
+            gp.fit_into(P, labels, modes)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for P in parts_dev:
+            st, _, _ = gp.fit_into(P, labels, modes)
+            if st != gridshift.GS_OK:
+                raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gp._ctx))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms = e0.elapsed_time(e1)
+        sequential = {"what": f"{len(parts_dev)} sequential gs_fit calls, plain FP64 path",
+                      "ms": seq_ms, "value": n / (seq_ms / 1e3) / 1e6, "unit": UNIT}
+        gp.close()
 
     # -- end to end through the public API: host inputs, host outputs
     h_pts = torch.from_numpy(X).pin_memory()
@@ -241,9 +381,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     kk = 0
     for _ in range(e2e_steps):
         d_pts.copy_(h_pts, non_blocking=True)
-        st, kk, info = g.fit_into(d_pts, labels, modes)
-        if st != gridshift.GS_OK:
-            raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(g._ctx))
+        kk, _ = call(d_pts, labels, modes)
         h_labels.copy_(labels, non_blocking=True)
         h_modes[:kk].copy_(modes[:kk], non_blocking=True)
         stream.synchronize()
@@ -254,31 +392,46 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_value = n * e2e_steps * world / float(t.item()) / 1e6
 
-    # -- roofline of the dominant kernel (binning: one launch per step)
+    # -- roofline of the dominant kernel (the loop kernel: one launch per step)
     pk = peaks()
-    bin_ms = phase_ms["bin"] / max(phase_cnt["bin"], 1)
-    bin_bytes = n * bin_bytes_per_point(d, elem)
-    achieved = bin_bytes / (bin_ms / 1e3) / 1e9
-    roof = {"kernel": "k_bin (binning, step i)", "bound": "hbm", "achieved": achieved,
-            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-            "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": bin_bytes, "avg_launch_ms": bin_ms,
-            "traffic": None}
+    roof = None
+    if not batched:
+        loop_ms = phase_ms["loop"] / max(phase_cnt["loop"], 1)
+        cell_steps = (cell_iters + m0_total) // args.steps
+        lb = loop_bytes(n, d, elem, cell_steps, fp32)
+        achieved = lb / (loop_ms / 1e3) / 1e9
+        bin_ms = phase_ms["bin"] / max(phase_cnt["bin"], 1)
+        bb = n * bin_bytes_per_point(d, elem)
+        roof = {"kernel": "k_loop (exact cell sums, update steps ii-v, labels)", "bound": "hbm",
+                "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"],
+                "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac_of": pk["source"],
+                "algorithmic_bytes_per_launch": lb, "avg_launch_ms": loop_ms, "traffic": None,
+                "second": {"kernel": "k_bin (binning, first pass)", "achieved": bb / (bin_ms / 1e3) / 1e9,
+                           "frac": bb / (bin_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                           "algorithmic_bytes_per_launch": bb, "avg_launch_ms": bin_ms}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": max(args.warmup, 3),
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(w, args.workload),
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+                "data": "synthetic",
+                "config": workload_config(w, args.workload, args.precision),
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": int(X.nbytes),
                         "d2h_bytes_per_step": int(n * 4 + kk * d * 8)},
                 "gpu_launches": int(launches),
                 "roofline": roof,
-                "phases_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms},
                 "active_cell_iterations_per_s": cell_iters * world / (total_ms / 1e3),
                 "clocks": clk}
+        if not batched:
+            line["phases_ms_per_step"] = {p: phase_ms[p] / args.steps for p in phase_ms}
+        if agreement is not None:
+            line["agreement"] = agreement
+        if sequential is not None:
+            line["sequential"] = sequential
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -293,6 +446,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="image_1080p_d5")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -146,10 +146,17 @@ def _cfg_gmm():
                 name="gmm_10M_d6_h4")
 
 
-#: name -> zero-argument builder returning dict(points, h, max_iter, name)
+def _cfg_batch64():
+    parts = image_batch(64, 1000)
+    return dict(parts=parts, h=16.0, max_iter=50, name="voronoi_batch64_uneven_d3_h16")
+
+
+#: name -> zero-argument builder returning dict(points, h, max_iter, name);
+#: batched workloads give dict(parts=[...], h, max_iter, name) instead
 WORKLOADS = {
     "image_321x481_d3": _cfg_image_small,
     "image_1080p_d5": _cfg_1080p,
     "image_4k_d5": _cfg_4k,
     "gmm_10M_d6": _cfg_gmm,
+    "batch_64_d3": _cfg_batch64,
 }
