@@ -211,12 +211,13 @@ gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
  * static array (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.
  *
- * Limits: the point-to-cell map takes 4 bytes per point and 1 MiB is kept
- * for the rest, so n <= 16,515,072; the cell workspace (about 1.5 KB per
- * initial active cell at d = 4 and max_iter = 50, growing with d and
- * max_iter) must fit what the points leave; the cell-face table holds at most
- * 8192 entries (over all axes, the number of cells the data spans plus 3).
- * Beyond these the call returns GS_E_SCRATCH; use gs_fit.
+ * Limits: the per-point arrays (cell slot and counting-sort position) take
+ * 8 bytes per point and 1 MiB is kept for the rest, so n <= 8,257,536; the
+ * cell workspace (about 2.1 KB per initial active cell at d = 4 and
+ * max_iter = 50, growing with d and max_iter, plus 272 KB of fixed buffers)
+ * must fit what the points leave; the cell-face table holds at most 8192
+ * entries (over all axes, the number of cells the data spans plus 3).
+ * Beyond these the call returns GS_E_SCRATCH; use gs_fit.  GS_FP64 only.
  *
  * Sharing: every call uses the same array, which keeps the previous call's
  * contents; the call clears what must start at zero itself.  Calls are
