@@ -117,6 +117,8 @@ typedef enum {
 typedef struct {
   double ms[GS_NPHASES];    /* device time of each phase, summed over its occurrences */
   int32_t count[GS_NPHASES]; /* occurrences timed in each phase */
+  double step_ms[16][2];    /* device clock of the first 16 update steps: the update phase
+                               (ii-iv) and the compaction that follows it */
 } gs_phase_times;
 
 /* Creates a context for d-dimensional points, cell side (bandwidth) h and at

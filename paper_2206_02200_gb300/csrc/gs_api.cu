@@ -45,26 +45,28 @@ struct DBuf {
 // Device storage of the binning table (see gs::BinTable).
 struct BinTableBuf {
   DBuf<uint64_t> key;
-  DBuf<uint32_t> cnt, off, list;
+  DBuf<uint32_t> cnt, off, id, list;
   DBuf<uint64_t> acc;
   uint32_t cap = 0;
   int d = 0;
-  // Allocates capacity c (power of two) for d-dimensional sums and a list of
-  // up to lmax cells; a new or regrown table is cleared.
-  cudaError_t ensure(uint32_t c, int dd, uint32_t lmax, cudaStream_t s) {
+  // Allocates capacity c (power of two) for d-dimensional sums of up to c / 2
+  // cells; a new or regrown table is cleared.
+  cudaError_t ensure(uint32_t c, int dd, cudaStream_t s) {
     cudaError_t e;
     if (c > cap || dd != d) {
-      key.release(); cnt.release(); off.release(); acc.release();
+      key.release(); cnt.release(); off.release(); id.release(); acc.release(); list.release();
       cap = 0;
       if ((e = key.ensure(c)) != cudaSuccess) return e;
       if ((e = cnt.ensure(c)) != cudaSuccess) return e;
       if ((e = off.ensure(c)) != cudaSuccess) return e;
-      if ((e = acc.ensure((size_t)c * dd * 4)) != cudaSuccess) return e;
+      if ((e = id.ensure(c)) != cudaSuccess) return e;
+      if ((e = acc.ensure((size_t)(c / 2) * dd * 4)) != cudaSuccess) return e;
+      if ((e = list.ensure(c / 2)) != cudaSuccess) return e;
       cap = c;
       d = dd;
       if ((e = clear(s)) != cudaSuccess) return e;
     }
-    return list.ensure(lmax);
+    return cudaSuccess;
   }
   cudaError_t clear(cudaStream_t s) {
     cudaError_t e;
@@ -72,9 +74,9 @@ struct BinTableBuf {
     if ((e = cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * cnt.cap, s)) != cudaSuccess) return e;
     return cudaMemsetAsync(acc.p, 0, sizeof(uint64_t) * acc.cap, s);
   }
-  BinTable view() const { return BinTable{key.p, cnt.p, off.p, acc.p, list.p, cap}; }
+  BinTable view() const { return BinTable{key.p, cnt.p, off.p, id.p, acc.p, list.p, cap}; }
   void release() {
-    key.release(); cnt.release(); off.release(); acc.release(); list.release();
+    key.release(); cnt.release(); off.release(); id.release(); acc.release(); list.release();
     cap = 0;
   }
 };
@@ -183,6 +185,7 @@ struct CtxWorkspace : public Workspace {
   int64_t* h_words = nullptr;     // pinned staging of the face and offset tables
   size_t h_words_cap = 0;
   bool dirty = false;             // a call stopped with tables not returned to clean
+  uint64_t last_m0 = 0;           // initial cells of the last call (sizes the binning table)
 
   std::string alloc_err(cudaError_t e, const char* what) {
     return std::string(what) + ": " + cudaGetErrorName(e);
@@ -240,14 +243,18 @@ struct CtxWorkspace : public Workspace {
     WS_CU(slot0.ensure(n), "alloc slot0");
     WS_CU(perm.ensure(n), "alloc perm");
     WS_CU(blocksum.ensure(kMaxLoopGrid), "alloc block sums");
-    uint32_t cap0 = pow2_at_least(2 * m_bound, 1024);
+    // binning table for the cells expected: as many as the last call found
+    // (plus a quarter), else n / 32; an overflow regrows it (regrow_bin)
+    uint64_t est = last_m0 ? last_m0 + last_m0 / 4 + 1024 : (uint64_t)n / 32 + 65536;
+    if (est > m_bound) est = m_bound;
+    uint32_t cap0 = pow2_at_least(2 * est, 1024);
     if (t0.cap > cap0 && t0.d == d) cap0 = t0.cap;
     if (dirty) {
       if (t0.cap) WS_CU(t0.clear(s), "clear T0");
       for (int i = 0; i < 3; ++i)
         if (tab[i].cap) WS_CU(tab[i].clear(s), "clear level table");
     }
-    WS_CU(t0.ensure(cap0, d, cap0 / 2, s), "alloc T0");
+    WS_CU(t0.ensure(cap0, d, s), "alloc T0");
     b.st = st.p;
     b.res = res.p;
     b.bar = bar.p;
@@ -268,7 +275,7 @@ struct CtxWorkspace : public Workspace {
     }
     cudaError_t e;
     WS_CU(t0.clear(s), "clear T0");
-    WS_CU(t0.ensure(t0.cap << 2, d, t0.cap << 1, s), "alloc T0");
+    WS_CU(t0.ensure(t0.cap << 2, d, s), "alloc T0");
     b.t0 = t0.view();
     b.t0_maxcells = t0.cap / 2;
     return GS_OK;
@@ -277,6 +284,7 @@ struct CtxWorkspace : public Workspace {
   gs_status levels(uint32_t m0, int d, int max_iter, cudaStream_t s, Bufs& b,
                    std::string* err) override {
     cudaError_t e;
+    last_m0 = m0;
     const uint32_t capAB = pow2_at_least(4ull * m0, 64);
     const uint32_t m = m0 > 0 ? m0 : 1;
     for (int i = 0; i < 3; ++i) WS_CU(tab[i].ensure(capAB, d, m, s), "alloc level table");
@@ -495,7 +503,7 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   a.modes = modes;
   a.modes_cap = modes_cap;
   a.mixed = ctx->prec == GS_FP32_MIXED;
-  double kms[kLoopPhases] = {};
+  double kms[kLoopPhases + 2 * kClockSteps] = {};
   gs_status st = fit_pipeline(a, ctx->ws, ctx->timing ? &ctx->tm : nullptr, k_out, &inf, kms,
                               &ctx->err);
   if (info) *info = inf;
@@ -513,6 +521,8 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
       ctx->last_times.ms[GS_PHASE_K_OFFSETS + i] = kms[i];
       ctx->last_times.count[GS_PHASE_K_OFFSETS + i] = 1;
     }
+    for (int i = 0; i < kClockSteps; ++i)
+      for (int c = 0; c < 2; ++c) ctx->last_times.step_ms[i][c] = kms[kLoopPhases + 2 * i + c];
   }
   return st;
 }

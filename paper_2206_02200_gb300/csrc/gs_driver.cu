@@ -291,6 +291,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   L.mixed = a.mixed;
   if (a.B > 1) L.I = inst_views(b.inst, a.B);
   GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
+  GS_CU(cudaMemsetAsync(b.res, 0, sizeof(LoopResult), s), "memset result");
   GS_T_BEGIN(GS_PHASE_LOOP);
   GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
   GS_T_END();
@@ -327,8 +328,12 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   info->inexact = (int64_t)hf->inexact;
   info->face_rechecks = (int64_t)hf->rechecks;
   info->cell_iters = (int64_t)hr->cell_iters;
-  if (inkernel_ms)
+  if (inkernel_ms) {
     for (int i = 0; i < kLoopPhases; ++i) inkernel_ms[i] = (double)hr->ns[i] * 1e-6;
+    for (int i = 0; i < kClockSteps; ++i)
+      for (int c = 0; c < 2; ++c)
+        inkernel_ms[kLoopPhases + 2 * i + c] = i < T ? (double)hr->step_ns[i][c] * 1e-6 : 0.0;
+  }
   *k_out = k;
   if (a.B > 1) {
     // per-instance results (the host copy of InstState, same layout)

@@ -116,6 +116,8 @@ InstState inst_views(uint32_t* base, int B);
 // Runs GridShift end to end on the workspace.  Fills *k_out and *info
 // (statistics and in-kernel phase times) and returns a status; err receives a
 // description of any error (may be null).
+// inkernel_ms (optional): kLoopPhases device-clock phase times, then
+// 2 * kClockSteps per-step times (update, compaction).
 gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64_t* k_out,
                        gs_fit_info* info, double* inkernel_ms, std::string* err);
 

@@ -9,17 +9,20 @@
 namespace gs {
 
 // The binning table of step i: packed cell keys with, per slot, the resident
-// count, the offset of the cell's run in the counting sort of the points, and
-// the exact coordinate sums (d x 4 limb accumulators).  key[] is kEmpty where
-// free; cnt[] and acc[] are zero where free (off[] needs no clearing).
-// list[i] is the slot of the i-th key inserted (arrival order).
+// count, the offset of the cell's run in the counting sort of the points and
+// the cell's id (its arrival order).  list[i] is the slot of the cell with
+// id i.  acc holds, per cell id, the exact coordinate sums (d x 4 limb
+// accumulators; float sums in the float32 variant).  key[] is kEmpty where
+// free; cnt[] and acc[] are zero where unused (off[] and id[] need no
+// clearing).
 struct BinTable {
   uint64_t* key;
   uint32_t* cnt;
   uint32_t* off;
-  uint64_t* acc;
-  uint32_t* list;
-  uint32_t cap;  // power of two
+  uint32_t* id;
+  uint64_t* acc;   // maxcells x d x 4
+  uint32_t* list;  // maxcells
+  uint32_t cap;    // power of two
 };
 
 // A table of the cells of one level, also the merge target of the update

@@ -73,23 +73,6 @@ __device__ bool grid_sync(GridBar* bar, DevFlags* fl) {
   return s_ok != 0;
 }
 
-// Device-clock split of the loop kernel, kept by thread 0 of block 0.
-struct SegClock {
-  unsigned long long last = 0;
-  unsigned long long ns[kLoopPhases] = {};
-  bool on = false;
-  __device__ void start() {
-    on = blockIdx.x == 0 && threadIdx.x == 0;
-    if (on) last = global_ns();
-  }
-  __device__ void lap(int seg) {
-    if (!on) return;
-    const unsigned long long now = global_ns();
-    ns[seg] += now - last;
-    last = now;
-  }
-};
-
 enum {
   kSegOffsets = 0,
   kSegScatter = 1,
@@ -100,6 +83,28 @@ enum {
   kSegCompact = 6,
   kSegLabels = 7
 };
+
+// Device-clock split of the loop kernel, kept by thread 0 of block 0.
+struct SegClock {
+  unsigned long long last = 0;
+  unsigned long long ns[kLoopPhases] = {};
+  bool on = false;
+  __device__ void start() {
+    on = blockIdx.x == 0 && threadIdx.x == 0;
+    if (on) last = global_ns();
+  }
+  __device__ void lap(int seg) { lap_step(seg, -1, nullptr); }
+  // also records the lap in step[t] (update steps t < kClockSteps; col 0 the
+  // update phase, col 1 the compaction)
+  __device__ void lap_step(int seg, int t, LoopResult* res) {
+    if (!on) return;
+    const unsigned long long now = global_ns();
+    ns[seg] += now - last;
+    if (res && t >= 0 && t < kClockSteps) res->step_ns[t][seg == kSegCompact ? 1 : 0] = now - last;
+    last = now;
+  }
+};
+
 
 __device__ __forceinline__ u128 as_u128(ulonglong2 v) { return (u128)v.x | ((u128)v.y << 64); }
 
@@ -220,7 +225,10 @@ __device__ void phase_offsets(const LoopArgs& A, uint32_t m0) {
       before += q < w ? t : 0u;
       total += t;
     }
-    if (id < hi) A.T0.off[slot] = run + before + x - v;
+    if (id < hi) {
+      A.T0.off[slot] = run + before + x - v;
+      A.T0.id[slot] = id;
+    }
     run += total;
     __syncthreads();
   }
@@ -270,10 +278,13 @@ __device__ void phase_scatter(const LoopArgs& A) {
 // segment adds the segment's sum.
 constexpr int kSumRun = 4;
 
+// Adds V into the sum accumulators of the cell in binning slot s (they are
+// indexed by the cell's id, so the initial cells' sums are dense).
 template <int D>
 __device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t s, const u128 (&V)[D]) {
+  const uint32_t id = A.T0.id[s];
 #pragma unroll
-  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)s * D + a) * 4, V[a]);
+  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)id * D + a) * 4, V[a]);
 }
 
 template <int D, typename T>
@@ -363,7 +374,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
       r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        r[1 + a] = settle_sum(T0.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
+        r[1 + a] = settle_sum(T0.acc + ((size_t)id * D + a) * 4, A.P.L[a], inexact, werr);
       G.id[sa] = id;
       G.list[id] = sa;
     }
@@ -722,7 +733,9 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
       if (s[e] != cur) {
         if (cur != kNone) {
 #pragma unroll
-          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
+          const uint32_t cid = A.T0.id[cur];
+#pragma unroll
+          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cid * D + a], V[a].value());
         }
         cur = s[e];
         if (cur != kNone) {
@@ -756,8 +769,9 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
       }
     }
     if (head && cur != kNone) {
+      const uint32_t cid = A.T0.id[cur];
 #pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
+      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cid * D + a], V[a].value());
     }
   }
 }
@@ -785,8 +799,8 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
       r[0] = cnt;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        r[1 + a] = __float_as_uint(tacc[(size_t)s * D + a] / (float)cnt);
-        tacc[(size_t)s * D + a] = 0.f;
+        r[1 + a] = __float_as_uint(tacc[(size_t)id * D + a] / (float)cnt);
+        tacc[(size_t)id * D + a] = 0.f;
       }
       G.id[sa] = id;
       G.list[id] = sa;
@@ -1180,7 +1194,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     }
     if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
     if (!grid_sync(A.bar, A.fl)) return;
-    clk.lap(t == 0 ? kSegUpdateFirst : kSegUpdateRest);
+    clk.lap_step(t == 0 ? kSegUpdateFirst : kSegUpdateRest, t, A.res);
     if (!vst[t].has_nb) {
       converged = true;
       break;
@@ -1196,7 +1210,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       A.st[t + 1].base = base + m;
     }
     if (!grid_sync(A.bar, A.fl)) return;
-    clk.lap(kSegCompact);
+    clk.lap_step(kSegCompact, t, A.res);
     cell_iters += m;
     m_prev = m;
     base_prev = base;

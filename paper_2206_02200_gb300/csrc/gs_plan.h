@@ -66,7 +66,10 @@ struct LoopResult {
   uint32_t pad;
   unsigned long long cell_iters;  // sum of m_t over applied updates
   unsigned long long ns[kLoopPhases];  // nanoseconds spent in each segment
+  unsigned long long step_ns[16][2];   // first 16 update steps: update phase, compaction
 };
+
+constexpr int kClockSteps = 16;
 
 // Per-instance state of a batched run (B point sets in one run, each cell
 // key carrying its instance in the field above the axes).  Arrays of B

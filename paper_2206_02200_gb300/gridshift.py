@@ -52,10 +52,15 @@ class gs_fit_info(ctypes.Structure):
 
 
 class gs_phase_times(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("count", ctypes.c_int32 * len(PHASES))]
+    _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("count", ctypes.c_int32 * len(PHASES)),
+                ("step_ms", (ctypes.c_double * 2) * 16)]
 
     def as_dict(self) -> dict:
         return {p: (float(self.ms[i]), int(self.count[i])) for i, p in enumerate(PHASES)}
+
+    def steps(self) -> list:
+        """[(update ms, compaction ms)] of the first 16 update steps."""
+        return [(float(self.step_ms[i][0]), float(self.step_ms[i][1])) for i in range(16)]
 
 
 class GridShiftError(RuntimeError):
@@ -154,13 +159,14 @@ def gs_set_timing(ctx: int, enable: bool) -> int:
     return load().gs_set_timing(ctx, 1 if enable else 0)
 
 
-def gs_get_phase_times(ctx: int) -> dict:
-    """{phase: (device ms, launch groups)} of the context's last gs_fit."""
+def gs_get_phase_times(ctx: int, steps: bool = False):
+    """{phase: (device ms, launch groups)} of the context's last gs_fit; with
+    steps=True also the per-step split [(update ms, compaction ms)]."""
     out = gs_phase_times()
     st = load().gs_get_phase_times(ctx, ctypes.byref(out))
     if st != GS_OK:
         raise GridShiftError(st, "gs_get_phase_times")
-    return out.as_dict()
+    return (out.as_dict(), out.steps()) if steps else out.as_dict()
 
 
 def gs_fit_noalloc(d: int, h: float, max_iter: int, stream: int | None, points_ptr: int,
