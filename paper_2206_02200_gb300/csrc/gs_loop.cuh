@@ -1118,6 +1118,322 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
   G.key[s] = kEmpty;
 }
 
+// ---------------------------------------------------------------------------
+// The tail of the update loop in one block (GS_FP64, plain runs).  Once a
+// level has at most TailCells<D>::value cells, block 0 copies it into shared
+// memory and runs the remaining update steps alone, with block barriers and
+// shared-memory hash tables, while the other blocks wait at one grid barrier.
+// The arithmetic is that of phase_update and phase_compact (exact sums
+// rounded once); a merged cell's sum is added along a list of its members.
+
+constexpr size_t tail_bytes(int d, int mx) {
+  return (size_t)mx * d * 16 * 3       // sums of two levels, centroids
+         + (size_t)mx * 8 * 3          // keys of two levels, new keys
+         + (size_t)4 * mx * 8 * 2      // lookup and merge hash keys
+         + (size_t)mx * 4 * 2          // counts of two levels
+         + (size_t)4 * mx * 4          // merge list heads
+         + (size_t)4 * mx * 2 * 2      // lookup cell index, merge cell id
+         + (size_t)mx * 2 * 3;         // member links, member slots, new-cell slots
+}
+
+template <int D>
+struct TailCells {
+  static constexpr int value = tail_bytes(D, 256) <= kFilterWords * 4 ? 256 : 128;
+  static constexpr int cap = 4 * value;  // hash capacity (power of two), load <= 1/4
+};
+
+// Largest level handed to the one-block tail.  All of a tail step's probes go
+// through one SM's shared memory, so the tail pays off only where a step has
+// too little work to hide the latency of the multi-block path (measured on
+// GB300: about 12 us per step at 45 cells in the tail against 20 us; 39 us
+// against 12 us at 171 cells).
+constexpr uint32_t kTailEnter = 64;
+
+template <int D>
+struct TailMem {
+  static constexpr int Mx = TailCells<D>::value, C = TailCells<D>::cap;
+  ulonglong2 *sum[2], *V;
+  uint64_t *key[2], *nk, *hk, *mk;
+  uint32_t *cnt[2], *mhead;
+  uint16_t *hidx, *mid, *nxt, *myslot, *mlist;
+  __device__ explicit TailMem(void* base) {
+    char* p = static_cast<char*>(base);
+    sum[0] = reinterpret_cast<ulonglong2*>(p); p += (size_t)Mx * D * 16;
+    sum[1] = reinterpret_cast<ulonglong2*>(p); p += (size_t)Mx * D * 16;
+    V = reinterpret_cast<ulonglong2*>(p); p += (size_t)Mx * D * 16;
+    key[0] = reinterpret_cast<uint64_t*>(p); p += (size_t)Mx * 8;
+    key[1] = reinterpret_cast<uint64_t*>(p); p += (size_t)Mx * 8;
+    nk = reinterpret_cast<uint64_t*>(p); p += (size_t)Mx * 8;
+    hk = reinterpret_cast<uint64_t*>(p); p += (size_t)C * 8;
+    mk = reinterpret_cast<uint64_t*>(p); p += (size_t)C * 8;
+    cnt[0] = reinterpret_cast<uint32_t*>(p); p += (size_t)Mx * 4;
+    cnt[1] = reinterpret_cast<uint32_t*>(p); p += (size_t)Mx * 4;
+    mhead = reinterpret_cast<uint32_t*>(p); p += (size_t)C * 4;
+    hidx = reinterpret_cast<uint16_t*>(p); p += (size_t)C * 2;
+    mid = reinterpret_cast<uint16_t*>(p); p += (size_t)C * 2;
+    nxt = reinterpret_cast<uint16_t*>(p); p += (size_t)Mx * 2;
+    myslot = reinterpret_cast<uint16_t*>(p); p += (size_t)Mx * 2;
+    mlist = reinterpret_cast<uint16_t*>(p);
+  }
+};
+
+__device__ __forceinline__ uint32_t tail_home(uint64_t key, int C) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - __popc(C - 1)));
+}
+
+// Slot of key in a shared-memory table of C slots (linear probing), inserting
+// it if absent; won is set for the inserting thread.
+__device__ __forceinline__ uint32_t tail_insert(uint64_t* keys, int C, uint64_t key, bool& won) {
+  uint32_t s = tail_home(key, C);
+  won = false;
+  for (int i = 0; i < C; ++i) {
+    const uint64_t prev = atomicCAS((unsigned long long*)&keys[s], (unsigned long long)kEmpty,
+                                    (unsigned long long)key);
+    if (prev == kEmpty) {
+      won = true;
+      return s;
+    }
+    if (prev == key) return s;
+    s = (s + 1) & (C - 1);
+  }
+  return kNone;  // unreachable: at most C / 4 keys
+}
+
+__device__ __forceinline__ uint32_t tail_find(const uint64_t* keys, int C, uint64_t key) {
+  uint32_t s = tail_home(key, C);
+#pragma unroll 1
+  for (int i = 0; i < C; ++i) {
+    const uint64_t k = keys[s];
+    if (k == key) return s;
+    if (k == kEmpty) return kNone;
+    s = (s + 1) & (C - 1);
+  }
+  return kNone;
+}
+
+// Result of the tail, published by block 0 for the other blocks.
+struct TailOut {
+  int t;
+  uint32_t m, base;
+  int converged;
+  unsigned long long cell_iters;
+};
+
+// Block 0 only.  Level t (m cells, in table tab[t % 3] and cells[t & 1]) is
+// the first level of the tail.  On return level t (the final level) is back
+// in tab[t % 3] and cells[t & 1], and the forest holds the parent links of
+// every level before it.
+template <int D>
+__device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
+                         uint32_t base_prev, uint32_t base, unsigned long long cell_iters,
+                         SegClock& clk, unsigned& inexact, unsigned& werr, TailOut& out) {
+  constexpr int Mx = TailMem<D>::Mx, C = TailMem<D>::C;
+  constexpr int GS = GatherLanes<D>::min;
+  constexpr int U = ProbeBatch<D, GS>::value;
+  extern __shared__ uint4 s_dyn[];
+  TailMem<D> S(s_dyn);
+  __shared__ uint32_t s_nb, s_m1;
+  const uint32_t tid = threadIdx.x, nth = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int glane = lane & (GS - 1);
+  const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
+  const uint32_t group = threadIdx.x / GS, ngroups = blockDim.x / GS;
+  const int nprobe = A.P.nprobe, center = A.P.center;
+  (void)Mx;
+
+  // parent links of level t-1 and release of its table (the update phase of
+  // step t does this in the multi-block path)
+  {
+    const LevelTable G = A.tab[t % 3];
+    if (t > 0) {
+      const LevelTable Lp = A.tab[(t + 2) % 3];
+      const uint32_t* pp = A.pslot[(t - 1) & 1];
+      for (uint32_t i = tid; i < m_prev; i += nth) {
+        A.forest[base_prev + i] = base + G.id[pp[i]];
+        const uint32_t s = Lp.list[i];
+        Lp.key[s] = kEmpty;
+        Lp.row[(size_t)s * (D + 1)].x = 0;
+      }
+    }
+    // level t into shared memory; its table is released
+    const Cells c = A.cells[t & 1];
+    for (uint32_t i = tid; i < m; i += nth) {
+      const uint32_t s = G.list[i];
+      S.key[0][i] = c.key[i];
+      S.cnt[0][i] = c.cnt[i];
+#pragma unroll
+      for (int a = 0; a < D; ++a) S.sum[0][(size_t)i * D + a] = G.row[(size_t)s * (D + 1) + 1 + a];
+      G.key[s] = kEmpty;
+      G.row[(size_t)s * (D + 1)].x = 0;
+    }
+  }
+  __syncthreads();
+
+  int cur = 0;
+  bool converged = false;
+  for (;;) {
+    const uint64_t* key = S.key[cur];
+    const uint32_t* cnt = S.cnt[cur];
+    const ulonglong2* sum = S.sum[cur];
+    // lookup table of the level
+    for (uint32_t s = tid; s < (uint32_t)C; s += nth) {
+      S.hk[s] = kEmpty;
+      S.mk[s] = kEmpty;
+      S.mhead[s] = kNone;
+    }
+    if (tid == 0) {
+      s_nb = 0;
+      s_m1 = 0;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < m; i += nth) {
+      bool won;
+      const uint32_t s = tail_insert(S.hk, C, key[i], won);
+      S.hidx[s] = (uint16_t)i;
+    }
+    __syncthreads();
+    // ii-iii: the update of every cell (as phase_update)
+    for (uint32_t j = group; j < m; j += ngroups) {
+      const uint64_t kj = key[j];
+      uint32_t Dc = 0;
+      bool nb = false;
+      u128 N[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) N[a] = 0;
+      for (int p0 = glane; p0 < nprobe; p0 += GS * U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int p = p0 + u * GS;
+          if (p >= nprobe) continue;
+          const uint32_t s = tail_find(S.hk, C, kj + __ldg(&A.dtab[p]));
+          if (s == kNone) continue;
+          const uint32_t i = S.hidx[s];
+          Dc += cnt[i];
+#pragma unroll
+          for (int a = 0; a < D; ++a) N[a] += as_u128(sum[(size_t)i * D + a]);
+          if (p != center) nb = true;
+        }
+      }
+#pragma unroll
+      for (int o = GS / 2; o > 0; o >>= 1) {
+        Dc += __shfl_xor_sync(gmask, Dc, o);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          uint64_t lo = (uint64_t)N[a], hi = (uint64_t)(N[a] >> 64);
+          lo = __shfl_xor_sync(gmask, lo, o);
+          hi = __shfl_xor_sync(gmask, hi, o);
+          N[a] += (u128)lo | ((u128)hi << 64);
+        }
+      }
+      uint64_t field = 0;
+      if (glane < D) {
+        u128 Na = 0;
+        int La = 0, off = 0, span = 1, toff = 0;
+        int64_t kmin = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          if (a == glane) {
+            Na = N[a];
+            La = A.P.L[a];
+            off = A.P.off[a];
+            span = A.P.span[a];
+            toff = A.P.thr_off[a];
+            kmin = A.P.kmin[a];
+          }
+        const double sv = div_round(Na, Dc, La, inexact);
+        const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
+        field = (uint64_t)(idx + 1) << off;
+        S.V[(size_t)j * D + glane] = pack(to_fixed(bits_of(sv), La, inexact, werr));
+      }
+#pragma unroll
+      for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
+      if (glane == 0) S.nk[j] = field;
+      if (nb) s_nb = 1u;
+    }
+    __syncthreads();
+    clk.lap_step(kSegUpdateRest, t, A.res);
+    if (!s_nb) {
+      converged = true;
+      break;
+    }
+    if (t == A.max_iter) break;
+    // iv: merge (a list of members per new key)
+    for (uint32_t i = tid; i < m; i += nth) {
+      bool won;
+      const uint32_t ms = tail_insert(S.mk, C, S.nk[i], won);
+      if (won) {
+        const uint32_t id = atomicAdd(&s_m1, 1u);
+        S.mid[ms] = (uint16_t)id;
+        S.mlist[id] = (uint16_t)ms;
+      }
+      S.nxt[i] = (uint16_t)atomicExch(&S.mhead[ms], i);
+      S.myslot[i] = (uint16_t)ms;
+    }
+    __syncthreads();
+    const uint32_t m1 = s_m1;
+    const int nxtb = cur ^ 1;
+    for (uint32_t id = tid; id < m1; id += nth) {
+      const uint32_t ms = S.mlist[id];
+      uint32_t c1 = 0;
+      u128 Sx[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) Sx[a] = 0;
+      for (uint32_t i = S.mhead[ms]; i != kNone; i = S.nxt[i] == 0xFFFFu ? kNone : S.nxt[i]) {
+        const uint32_t ci = cnt[i];
+        c1 += ci;
+#pragma unroll
+        for (int a = 0; a < D; ++a) Sx[a] += as_u128(S.V[(size_t)i * D + a]) * (u128)ci;
+      }
+      S.key[nxtb][id] = S.mk[ms];
+      S.cnt[nxtb][id] = c1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const double v = round_fixed(Sx[a], A.P.L[a], inexact);
+        S.sum[nxtb][(size_t)id * D + a] = pack(to_fixed(bits_of(v), A.P.L[a], inexact, werr));
+      }
+    }
+    for (uint32_t i = tid; i < m; i += nth) A.forest[base + i] = base + m + S.mid[S.myslot[i]];
+    __syncthreads();
+    clk.lap_step(kSegCompact, t, A.res);
+    cell_iters += m;
+    base += m;
+    m = m1;
+    cur = nxtb;
+    ++t;
+  }
+
+  // the final level back into its global table and cell list
+  {
+    const LevelTable G = A.tab[t % 3];
+    const Cells c = A.cells[t & 1];
+    const uint32_t maskT = mask_for(m, A.capAB);
+    for (uint32_t i = tid; i < m; i += nth) {
+      bool won;
+      const uint64_t k = S.key[cur][i];
+      const uint32_t s = table_insert(G.key, maskT, k, won, &A.fl->err);
+      c.key[i] = k;
+      c.cnt[i] = S.cnt[cur][i];
+      if (s == kNone) continue;
+      ulonglong2* r = G.row + (size_t)s * (D + 1);
+      r[0] = make_ulonglong2((uint64_t)S.cnt[cur][i], 0ull);
+#pragma unroll
+      for (int a = 0; a < D; ++a) r[1 + a] = S.sum[cur][(size_t)i * D + a];
+      G.id[s] = i;
+      G.list[i] = s;
+    }
+    if (tid == 0) {
+      A.st[t].m = m;
+      A.st[t].mask = maskT;
+      A.st[t].base = base;
+    }
+  }
+  out.t = t;
+  out.m = m;
+  out.base = base;
+  out.converged = converged ? 1 : 0;
+  out.cell_iters = cell_iters;
+}
+
 template <int D, bool BT, bool F32>
 __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   unsigned inexact = 0, werr = 0;
@@ -1174,6 +1490,30 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   unsigned long long cell_iters = 0;
   bool converged = false;
   for (;;) {
+    if constexpr (!F32 && !BT) {
+      // a small level: block 0 finishes the update steps in shared memory
+      if (m <= kTailEnter) {
+        if (blockIdx.x == 0) {
+          TailOut to;
+          run_tail<D>(A, t, m, m_prev, base_prev, base, cell_iters, clk, inexact, werr, to);
+          if (threadIdx.x == 0) {
+            A.res->tail_t = to.t;
+            A.res->tail_m = to.m;
+            A.res->tail_base = to.base;
+            A.res->tail_conv = to.converged;
+            A.res->tail_cells = to.cell_iters;
+          }
+        }
+        if (!grid_sync(A.bar, A.fl)) return;
+        volatile LoopResult* vr = A.res;
+        t = vr->tail_t;
+        m = vr->tail_m;
+        base = vr->tail_base;
+        converged = vr->tail_conv != 0;
+        cell_iters = vr->tail_cells;
+        break;
+      }
+    }
     bool any_nb = false;
     const uint32_t maskM = mask_for(m, A.capAB);
     // lanes per cell: the fewest (most cells in flight) while the level has

@@ -67,6 +67,11 @@ struct LoopResult {
   unsigned long long cell_iters;  // sum of m_t over applied updates
   unsigned long long ns[kLoopPhases];  // nanoseconds spent in each segment
   unsigned long long step_ns[16][2];   // first 16 update steps: update phase, compaction
+  // the state block 0 leaves after finishing the update steps alone
+  int32_t tail_t;
+  uint32_t tail_m, tail_base;
+  int32_t tail_conv;
+  unsigned long long tail_cells;
 };
 
 constexpr int kClockSteps = 16;
