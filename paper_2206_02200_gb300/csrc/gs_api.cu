@@ -284,7 +284,6 @@ struct CtxWorkspace : public Workspace {
   gs_status levels(uint32_t m0, int d, int max_iter, cudaStream_t s, Bufs& b,
                    std::string* err) override {
     cudaError_t e;
-    last_m0 = m0;
     const uint32_t capAB = pow2_at_least(4ull * m0, 64);
     const uint32_t m = m0 > 0 ? m0 : 1;
     for (int i = 0; i < 3; ++i) WS_CU(tab[i].ensure(capAB, d, m, s), "alloc level table");
@@ -342,6 +341,7 @@ struct CtxWorkspace : public Workspace {
 #undef WS_CU
 
   void mark_dirty(bool d) override { dirty = d; }
+  void note_cells(uint32_t m0) override { last_m0 = m0; }
 
   void release() {
     flags.release(); st.release(); res.release(); bar.release(); thr.release(); dtab.release();

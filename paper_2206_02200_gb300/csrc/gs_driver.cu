@@ -225,80 +225,75 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_CU(cudaMemsetAsync(b.inst, 0, sizeof(uint32_t) * inst_words(a.B), s), "memset instances");
   }
 
-  // i: binning (retried with a larger table if the cells overflow it)
+  // i: binning, then at once the loop kernel: the level workspace is sized
+  // for the binning table's cell bound, so no host round trip separates
+  // them.  If binning overflows the table, the loop kernel returns at its
+  // start and both run again with a larger table.
   ws.mark_dirty(true);
-  uint32_t m0 = 0;
+  const int grid = loop_grid(d, a.mixed);
+  if (grid <= 0) return fail(err, GS_E_CUDA, "no co-resident grid for the loop kernel");
+  LoopArgs L;
+  LoopResult* hr = ws.host_result();
   for (int attempt = 0;; ++attempt) {
+    GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
+    std::memset(&L, 0, sizeof(L));
+    L.P = P;
+    L.pts = a.points;
+    L.f32 = a.f32;
+    L.perm = b.perm;
+    L.blocksum = b.blocksum;
+    L.thr = b.thr;
+    L.dtab = b.dtab;
+    L.T0 = b.t0;
+    for (int i = 0; i < 3; ++i) L.tab[i] = b.tab[i];
+    L.capAB = b.capAB;
+    L.cells[0] = b.cells[0];
+    L.cells[1] = b.cells[1];
+    L.pslot[0] = b.pslot[0];
+    L.pslot[1] = b.pslot[1];
+    L.filter[0] = b.filter;
+    L.filter[1] = b.filter + kFilterWords;
+    L.forest = b.forest;
+    L.forest2 = b.forest2;
+    L.labslot = b.labslot;
+    L.rank = b.rank;
+    L.slot0 = b.slot0;
+    L.labels = a.labels;
+    L.n = n;
+    L.modes = a.modes;
+    L.modes_cap = a.modes_cap;
+    L.st = b.st;
+    L.fl = b.flags;
+    L.bar = b.bar;
+    L.res = b.res;
+    L.max_iter = a.max_iter;
+    L.rank_max = kRankMax;
+    L.B = a.B;
+    L.mixed = a.mixed;
+    if (a.B > 1) L.I = inst_views(b.inst, a.B);
+    GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
+    GS_CU(cudaMemsetAsync(b.res, 0, sizeof(LoopResult), s), "memset result");
     GS_T_BEGIN(GS_PHASE_BIN);
     GS_LAUNCH(launch_bin(a.points, a.f32, n, P, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells, b.slot0,
                          b.flags, b.offsets, a.B, s), "k_bin", 1);
     GS_T_END();
+    GS_T_BEGIN(GS_PHASE_LOOP);
+    GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
+    GS_T_END();
+    GS_CU(cudaMemcpyAsync(hr, b.res, sizeof(LoopResult), cudaMemcpyDeviceToHost, s), "D2H result");
     GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
-    GS_CU(cudaStreamSynchronize(s), "sync bin");
+    GS_CU(cudaStreamSynchronize(s), "sync loop");
     const uint32_t regrow = kErrOverflow | kErrTableFull;
-    if (hf->err & ~regrow)
-      return fail(err, GS_E_INTERNAL, "binning hit a device bound (fixed-point window)");
-    if (!(hf->err & regrow)) {
-      m0 = hf->m0;
-      break;
-    }
+    if (!(hf->err & regrow) || !hr->bin_failed) break;
     if (attempt >= 4) return fail(err, GS_E_INTERNAL, "binning table overflow");
     GS_ST(ws.regrow_bin(d, s, b, err));
     hf->err = 0;
     hf->m0 = 0;
     GS_CU(cudaMemcpyAsync(b.flags, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
   }
+  const uint32_t m0 = hf->m0;
   info->m0 = m0;
-
-  // ii-v, labels and modes: one cooperative launch
-  GS_ST(ws.levels(m0, d, a.max_iter, s, b, err));
-  const int grid = loop_grid(d, a.mixed);
-  if (grid <= 0) return fail(err, GS_E_CUDA, "no co-resident grid for the loop kernel");
-  LoopArgs L;
-  std::memset(&L, 0, sizeof(L));
-  L.P = P;
-  L.pts = a.points;
-  L.f32 = a.f32;
-  L.perm = b.perm;
-  L.blocksum = b.blocksum;
-  L.thr = b.thr;
-  L.dtab = b.dtab;
-  L.T0 = b.t0;
-  for (int i = 0; i < 3; ++i) L.tab[i] = b.tab[i];
-  L.capAB = b.capAB;
-  L.cells[0] = b.cells[0];
-  L.cells[1] = b.cells[1];
-  L.pslot[0] = b.pslot[0];
-  L.pslot[1] = b.pslot[1];
-  L.filter[0] = b.filter;
-  L.filter[1] = b.filter + kFilterWords;
-  L.forest = b.forest;
-  L.forest2 = b.forest2;
-  L.labslot = b.labslot;
-  L.rank = b.rank;
-  L.slot0 = b.slot0;
-  L.labels = a.labels;
-  L.n = n;
-  L.modes = a.modes;
-  L.modes_cap = a.modes_cap;
-  L.st = b.st;
-  L.fl = b.flags;
-  L.bar = b.bar;
-  L.res = b.res;
-  L.max_iter = a.max_iter;
-  L.rank_max = kRankMax;
-  L.B = a.B;
-  L.mixed = a.mixed;
-  if (a.B > 1) L.I = inst_views(b.inst, a.B);
-  GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
-  GS_CU(cudaMemsetAsync(b.res, 0, sizeof(LoopResult), s), "memset result");
-  GS_T_BEGIN(GS_PHASE_LOOP);
-  GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
-  GS_T_END();
-  LoopResult* hr = ws.host_result();
-  GS_CU(cudaMemcpyAsync(hr, b.res, sizeof(LoopResult), cudaMemcpyDeviceToHost, s), "D2H result");
-  GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
-  GS_CU(cudaStreamSynchronize(s), "sync loop");
+  ws.note_cells(m0);
   if (hf->err & kErrBarrier) return fail(err, GS_E_INTERNAL, "a grid barrier of the loop timed out");
   if (hf->err) return fail(err, GS_E_INTERNAL, "an update step hit a device bound");
   const uint32_t k = hr->k;

@@ -66,7 +66,7 @@ class Workspace {
   // Binning found more cells than b.t0 holds: a larger clean table in b.t0
   // (and b.t0_maxcells), or an error.
   virtual gs_status regrow_bin(int d, cudaStream_t s, Bufs& b, std::string* err) = 0;
-  // Workspace of the cell levels for m0 initial cells.
+  // Workspace of the cell levels for at most m0 initial cells.
   virtual gs_status levels(uint32_t m0, int d, int max_iter, cudaStream_t s, Bufs& b,
                            std::string* err) = 0;
   // Sort buffers for k final cells.
@@ -76,6 +76,8 @@ class Workspace {
   virtual gs_status batch_space(int B, Bufs& b, uint32_t** host, std::string* err) = 0;
   // The run stopped before the kernels returned every table to clean.
   virtual void mark_dirty(bool dirty) = 0;
+  // The number of initial cells binning found (sizes later binning tables).
+  virtual void note_cells(uint32_t m0) = 0;
 };
 
 // Optional per-phase CUDA-event timing of a run.

@@ -1443,6 +1443,13 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   SegClock clk;
   clk.start();
 
+  // binning overflowed its table: nothing to do (the host regrows it and
+  // runs binning and this kernel again)
+  if (*(volatile uint32_t*)&A.fl->err & (kErrOverflow | kErrTableFull)) {
+    if (tid == 0) A.res->bin_failed = 1;
+    return;
+  }
+
   // step i, second pass: exact cell sums
   const uint32_t m0 = *(volatile uint32_t*)&A.fl->m0;
   phase_count_totals(A, m0);

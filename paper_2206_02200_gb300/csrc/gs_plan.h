@@ -63,7 +63,7 @@ struct LoopResult {
   uint32_t k;           // final cells
   uint32_t base;        // first forest node of the final level
   uint32_t need_sort;   // 1: k too large for the in-loop numbering; labels not written
-  uint32_t pad;
+  uint32_t bin_failed;  // 1: binning overflowed its table; nothing after it ran
   unsigned long long cell_iters;  // sum of m_t over applied updates
   unsigned long long ns[kLoopPhases];  // nanoseconds spent in each segment
   unsigned long long step_ns[16][2];   // first 16 update steps: update phase, compaction

@@ -127,6 +127,25 @@ def test_unaligned_input():
                                       exp["modes"].view(np.int64))
 
 
+def test_binning_table_regrows():
+    # about one cell per point: far more cells than a fresh context's first
+    # binning table holds (n / 32 + 65536), so binning overflows and the
+    # table grows, twice, before the loop kernel runs
+    rng = np.random.default_rng(31)
+    X = rng.uniform(0, 4000, size=(600_000, 2))
+    ref = oracle.fit(X, 1.0, 10)
+    assert ref["m0"] > 400_000
+    g = gridshift.GridShift(2, 1.0, 10)
+    labels, modes, info = g.fit(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    assert info["m0"] == ref["m0"] and info["k"] == ref["k"]
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    np.testing.assert_array_equal(modes.cpu().numpy().view(np.int64), ref["modes"].view(np.int64))
+    # the same context on a small input afterwards
+    check_ctx_reuse(g)
+    g.close()
+
+
 def test_float32_input():
     X = synth.gmm_points(200_000, 6, 40, seed=9)
     ref, _ = check_parity(X.astype(np.float64), 4.0)
