@@ -694,6 +694,117 @@ __device__ __forceinline__ double face_of(const Plan& P, const int64_t* __restri
   return __longlong_as_double((long long)(o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll)));
 }
 
+// ---------------------------------------------------------------------------
+// Float32 level tables keep the key inside the row: a probe reads the whole
+// row (key, count, offsets) with one load and checks the key afterwards.
+// Row words: [key low, key high, count, offset of axis 0, ...], padded to
+// RowW<D> words (16, 32 or 64 bytes, so a row never straddles more sectors
+// than it must).  A free row has key 0 (packed keys are never 0: every field
+// is at least 1).  Linear probing from the key's home slot.
+
+template <int D>
+struct RowW {
+  static constexpr int value = D + 3 <= 4 ? 4 : (D + 3 <= 8 ? 8 : 16);
+  static constexpr int loads = (D + 3 + 3) / 4;  // 16-byte words holding key, count, offsets
+};
+
+constexpr uint32_t kMaxRowProbe = 4 * kMaxProbeBuckets;  // slots
+
+__device__ __forceinline__ uint64_t row_key(uint4 w0) {
+  return (uint64_t)w0.x | ((uint64_t)w0.y << 32);
+}
+
+// Word i (a constant after unrolling) of a row held as 16-byte words.
+template <int N>
+__device__ __forceinline__ uint32_t row_word(const uint4 (&w)[N], int i) {
+  const uint4 v = w[i >> 2];
+  const int j = i & 3;
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Slot of key in the rows (mask = slots - 1), inserting it if absent; won is
+// set for the inserting thread.  kNone (and kErrTableFull) when no free row
+// lies within kMaxRowProbe slots.
+template <int W>
+__device__ __forceinline__ uint32_t row_insert(uint32_t* rows, uint32_t mask, uint64_t key,
+                                               bool& won, uint32_t* err) {
+  uint32_t s = home_bucket(key, mask);
+  won = false;
+  const uint32_t lim = mask < kMaxRowProbe ? mask + 1 : kMaxRowProbe;
+  for (uint32_t i = 0; i < lim; ++i) {
+    unsigned long long* kp = reinterpret_cast<unsigned long long*>(rows + (size_t)s * W);
+    const uint64_t k = __ldcg(kp);
+    if (k == key) return s;
+    if (k == 0) {
+      const uint64_t prev = atomicCAS(kp, 0ull, (unsigned long long)key);
+      if (prev == 0) {
+        won = true;
+        return s;
+      }
+      if (prev == key) return s;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(err, kErrTableFull);
+  return kNone;
+}
+
+// Lookups of U keys at once: the home rows of all of them are loaded before
+// any is examined; dat receives the row of each key found.
+template <int D, int U>
+__device__ __forceinline__ void row_find_many(const uint32_t* rows, uint32_t mask,
+                                              const uint64_t (&key)[U], const bool (&valid)[U],
+                                              uint32_t (&slot)[U],
+                                              uint4 (&dat)[U][RowW<D>::loads]) {
+  constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
+  uint32_t s[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    s[u] = home_bucket(key[u], mask);
+    if (valid[u]) {
+      const uint4* r = reinterpret_cast<const uint4*>(rows + (size_t)s[u] * W);
+#pragma unroll
+      for (int i = 0; i < NL; ++i) dat[u][i] = r[i];
+    }
+  }
+  const uint32_t lim = mask < kMaxRowProbe ? mask + 1 : kMaxRowProbe;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    slot[u] = kNone;
+    if (!valid[u]) continue;
+    uint64_t k = row_key(dat[u][0]);
+    uint32_t sl = s[u];
+    for (uint32_t i = 1; k != key[u] && k != 0 && i < lim; ++i) {
+      sl = (sl + 1) & mask;
+      const uint4* r = reinterpret_cast<const uint4*>(rows + (size_t)sl * W);
+#pragma unroll
+      for (int j = 0; j < NL; ++j) dat[u][j] = r[j];
+      k = row_key(dat[u][0]);
+    }
+    if (k == key[u]) slot[u] = sl;
+  }
+}
+
+// Slot of key (single lookup), or kNone.
+template <int D>
+__device__ __forceinline__ uint32_t row_find(const uint32_t* rows, uint32_t mask, uint64_t key) {
+  constexpr int W = RowW<D>::value;
+  uint32_t s = home_bucket(key, mask);
+  const uint32_t lim = mask < kMaxRowProbe ? mask + 1 : kMaxRowProbe;
+  for (uint32_t i = 0; i < lim; ++i) {
+    const uint64_t k = *reinterpret_cast<const unsigned long long*>(rows + (size_t)s * W);
+    if (k == key) return s;
+    if (k == 0) return kNone;
+    s = (s + 1) & mask;
+  }
+  return kNone;
+}
+
+__device__ __forceinline__ void row_release(uint32_t* r) {
+  *reinterpret_cast<unsigned long long*>(r) = 0ull;
+  r[2] = 0;
+}
+
 // Binning, second pass (float32): each cell's sum of offsets from its lower
 // face, over the runs of the counting sort (as phase_cell_sums).
 template <int D, typename T>
@@ -786,6 +897,7 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
   float* tacc = reinterpret_cast<float*>(T0.acc);
   const LevelTable G = A.tab[0];
   uint32_t* row = reinterpret_cast<uint32_t*>(G.row);
+  constexpr int W = RowW<D>::value;
   const Cells c = A.cells[0];
   const int lg0 = filter_log2(m0);
   for (uint32_t id = tid; id < m0; id += nth) {
@@ -793,13 +905,13 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
     const uint64_t key = T0.key[s];
     const uint32_t cnt = T0.cnt[s];
     bool won;
-    const uint32_t sa = table_insert(G.key, maskA, key, won, &A.fl->err);
+    const uint32_t sa = row_insert<W>(row, maskA, key, won, &A.fl->err);
     if (sa != kNone) {
-      uint32_t* r = row + (size_t)sa * (D + 1);
-      r[0] = cnt;
+      uint32_t* r = row + (size_t)sa * W;
+      r[2] = cnt;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        r[1 + a] = __float_as_uint(tacc[(size_t)id * D + a] / (float)cnt);
+        r[3 + a] = __float_as_uint(tacc[(size_t)id * D + a] / (float)cnt);
         tacc[(size_t)id * D + a] = 0.f;
       }
       G.id[sa] = id;
@@ -823,6 +935,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
                                uint32_t maskM, uint32_t m_prev, uint32_t base_prev,
                                uint32_t base, bool& any_nb) {
   constexpr int U = ProbeBatch<D, GS>::value;
+  constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
@@ -831,7 +944,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
   const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
   const uint32_t* grow = reinterpret_cast<const uint32_t*>(G.row);
-  uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);
+  uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);  // rows with the key inside (RowW)
   float* macc = reinterpret_cast<float*>(M.acc);
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
@@ -876,6 +989,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       uint64_t q[U];
       bool v[U];
       uint32_t sl[U];
+      uint4 dat[U][NL];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int p = p0 + u * GS;
@@ -883,13 +997,12 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         const uint32_t fb = filter_bit(q[u], lg);
         v[u] = p < nprobe && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
       }
-      table_find_many<U>(G.key, mask, q, v, sl);
+      row_find_many<D, U>(grow, mask, q, v, sl, dat);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (sl[u] == kNone) continue;
         const int p = p0 + u * GS;
-        const uint32_t* r = grow + (size_t)sl[u] * (D + 1);
-        const uint32_t cn = r[0];
+        const uint32_t cn = row_word(dat[u], 2);
         const float fc = (float)cn;
         Dc += cn;
         float dv[D];  // the probe's offset v in {-1, 0, 1}^d, axis 0 the slowest digit
@@ -900,7 +1013,8 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
           rest /= 3;
         }
 #pragma unroll
-        for (int a = 0; a < D; ++a) N[a].add(fc * (__uint_as_float(r[1 + a]) + dv[a] * h));
+        for (int a = 0; a < D; ++a)
+          N[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) + dv[a] * h));
         if (p != center) nbc = true;
       }
     }
@@ -949,14 +1063,14 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       for (int a = 0; a < D; ++a) org[a] = (double)(float)face_of(A.P, A.thr, key, a);
       for (int p = glane; p < nprobe; p += GS) {
         const uint64_t qk = key + __ldg(&A.dtab[p]);
-        const uint32_t sl = table_find(G.key, mask, qk);
+        const uint32_t sl = row_find<D>(grow, mask, qk);
         if (sl == kNone) continue;
-        const uint32_t* r = grow + (size_t)sl * (D + 1);
-        const double cn = (double)r[0];
+        const uint32_t* r = grow + (size_t)sl * W;
+        const double cn = (double)r[2];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const double of = (double)(float)face_of(A.P, A.thr, qk, a);
-          N64[a] += cn * ((of - org[a]) + (double)__uint_as_float(r[1 + a]));
+          N64[a] += cn * ((of - org[a]) + (double)__uint_as_float(r[3 + a]));
         }
       }
 #pragma unroll
@@ -990,14 +1104,14 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
     uint32_t ms = kNone;
     if (glane == 0) {
       bool won;
-      ms = table_insert(M.key, maskM, field, won, &A.fl->err);
+      ms = row_insert<W>(mrow, maskM, field, won, &A.fl->err);
       if (ms != kNone) {
         if (won) {
           const uint32_t id = atomicAdd(&A.st[t + 1].m, 1u);
           M.list[id] = ms;
           if (BT) M.id[ms] = j;
         }
-        atomicAdd(&mrow[(size_t)ms * (D + 1)], cj);
+        atomicAdd(&mrow[(size_t)ms * W + 2], cj);
       }
       pslot[j] = ms;
       if (BT && live) {
@@ -1013,7 +1127,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       for (int a = 0; a < D; ++a) {
         if (a != glane) continue;
         if (BT && !live) {
-          contrib = (float)cj * __uint_as_float(grow[(size_t)G.list[j] * (D + 1) + 1 + a]);
+          contrib = (float)cj * __uint_as_float(grow[(size_t)G.list[j] * W + 3 + a]);
         } else {
           const int top = a == 0 ? A.P.inst_off : A.P.off[a - 1];
           const uint64_t fm = (1ull << (top - A.P.off[a])) - 1ull;
@@ -1032,9 +1146,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
     const uint32_t* pp = A.pslot[(t - 1) & 1];
     for (uint32_t i = tid; i < m_prev; i += nth) {
       A.forest[base_prev + i] = base + G.id[pp[i]];
-      const uint32_t s = Lp.list[i];
-      Lp.key[s] = kEmpty;
-      prow[(size_t)s * (D + 1)] = 0;
+      row_release(prow + (size_t)Lp.list[i] * W);
     }
   }
 }
@@ -1046,6 +1158,7 @@ __device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
+  constexpr int W = RowW<D>::value;
   const uint32_t* grow = reinterpret_cast<const uint32_t*>(G.row);
   uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);
   float* macc = reinterpret_cast<float*>(M.acc);
@@ -1055,18 +1168,18 @@ __device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
   const int lg = filter_log2(m1);
   for (uint32_t id = tid; id < m1; id += nth) {
     const uint32_t s = M.list[id];
-    uint32_t* r = mrow + (size_t)s * (D + 1);
-    uint64_t key = M.key[s];
-    const uint32_t cnt = r[0];
+    uint32_t* r = mrow + (size_t)s * W;
+    uint64_t key = *reinterpret_cast<const unsigned long long*>(r);
+    const uint32_t cnt = r[2];
     bool restored = false;
     if (BT) {
       const uint32_t inst = (uint32_t)(key >> A.P.inst_off);
       if (!A.I.done[t & 1][inst] && !A.I.nbf[t & 1][inst]) {
         const uint32_t j = M.id[s];
-        const uint32_t* o = grow + (size_t)G.list[j] * (D + 1);
+        const uint32_t* o = grow + (size_t)G.list[j] * W;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          r[1 + a] = o[1 + a];
+          r[3 + a] = o[3 + a];
           macc[(size_t)s * D + a] = 0.f;
         }
         key = cur.key[j];
@@ -1076,7 +1189,7 @@ __device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
     if (!restored) {
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        r[1 + a] = __float_as_uint(macc[(size_t)s * D + a] / (float)cnt);
+        r[3 + a] = __float_as_uint(macc[(size_t)s * D + a] / (float)cnt);
         macc[(size_t)s * D + a] = 0.f;
       }
     }
@@ -1106,16 +1219,15 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
                                                    uint32_t r, uint32_t label, double* modes,
                                                    bool write) {
   const uint32_t s = G.list[r];
-  uint32_t* row = reinterpret_cast<uint32_t*>(G.row) + (size_t)s * (D + 1);
+  uint32_t* row = reinterpret_cast<uint32_t*>(G.row) + (size_t)s * RowW<D>::value;
   if (write) {
     const uint64_t key = keys[r];
 #pragma unroll
     for (int a = 0; a < D; ++a)
       modes[(size_t)label * D + a] =
-          (double)(float)face_of(P, thr, key, a) + (double)__uint_as_float(row[1 + a]);
+          (double)(float)face_of(P, thr, key, a) + (double)__uint_as_float(row[3 + a]);
   }
-  row[0] = 0;
-  G.key[s] = kEmpty;
+  row_release(row);
 }
 
 // ---------------------------------------------------------------------------
@@ -1576,12 +1688,12 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     const uint32_t ms = vst[T + 1].m;
     for (uint32_t id = tid; id < ms; id += nth) {
       const uint32_t s = Ms.list[id];
-      Ms.key[s] = kEmpty;
       if (F32) {
-        reinterpret_cast<uint32_t*>(Ms.row)[(size_t)s * (D + 1)] = 0;
+        row_release(reinterpret_cast<uint32_t*>(Ms.row) + (size_t)s * RowW<D>::value);
 #pragma unroll
         for (int a = 0; a < D; ++a) reinterpret_cast<float*>(Ms.acc)[(size_t)s * D + a] = 0.f;
       } else {
+        Ms.key[s] = kEmpty;
         Ms.row[(size_t)s * (D + 1)].x = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
