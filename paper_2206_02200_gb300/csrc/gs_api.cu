@@ -239,7 +239,7 @@ struct CtxWorkspace : public Workspace {
     WS_CU(res.ensure(1), "alloc result");
     WS_CU(bar.ensure(1), "alloc barrier");
     WS_CU(thr.ensure(thr_words), "alloc face table");
-    WS_CU(dtab.ensure(nprobe), "alloc offsets");
+    WS_CU(dtab.ensure(2 * (size_t)nprobe), "alloc offsets");
     WS_CU(slot0.ensure(n), "alloc slot0");
     WS_CU(perm.ensure(n), "alloc perm");
     WS_CU(blocksum.ensure(kMaxLoopGrid), "alloc block sums");

@@ -138,18 +138,21 @@ gs_status make_plan(int d, double h, int64_t n, int B, const DevFlags& fl, Plan&
 
 // Face tables (order codes of the least doubles >= q h) and the packed-key
 // offsets of the 3^d neighbours v in {-1,0,1}^d (axis 0 the slowest digit).
-void fill_tables(const Plan& P, double h, int64_t* thr, uint64_t* dtab) {
+void fill_tables(const Plan& P, double h, int64_t* thr, uint64_t* dtab, uint32_t* vpack) {
   for (int a = 0; a < P.d; ++a)
     for (int64_t j = 0; j <= P.span[a]; ++j) thr[P.thr_off[a] + j] = ord_of(face(P.kmin[a] + j, h));
   for (int p = 0; p < P.nprobe; ++p) {
     int64_t delta = 0;
+    uint32_t vp = 0;
     int rest = p;
     for (int a = P.d - 1; a >= 0; --a) {
       const int v = rest % 3 - 1;
       rest /= 3;
       delta += (int64_t)v * (int64_t)(1ull << P.off[a]);
+      vp |= (uint32_t)(v + 1) << (2 * a);
     }
     dtab[p] = (uint64_t)delta;
+    vpack[p] = vp;
   }
 }
 
@@ -207,12 +210,14 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   GS_ST(ws.prepare(n, d, a.max_iter, thr_words, P.nprobe, m_bound, s, b, err));
 
   // face table and neighbour offsets, through host staging
+  // (dtab holds nprobe offsets, then nprobe 32-bit packed offset vectors)
   int64_t* stage = nullptr;
-  GS_ST(ws.host_words(thr_words + P.nprobe, &stage, err));
-  fill_tables(P, a.h, stage, reinterpret_cast<uint64_t*>(stage + thr_words));
+  GS_ST(ws.host_words(thr_words + 2 * P.nprobe, &stage, err));
+  fill_tables(P, a.h, stage, reinterpret_cast<uint64_t*>(stage + thr_words),
+              reinterpret_cast<uint32_t*>(stage + thr_words + P.nprobe));
   GS_CU(cudaMemcpyAsync(b.thr, stage, sizeof(int64_t) * thr_words, cudaMemcpyHostToDevice, s),
         "H2D thr");
-  GS_CU(cudaMemcpyAsync(b.dtab, stage + thr_words, sizeof(uint64_t) * P.nprobe,
+  GS_CU(cudaMemcpyAsync(b.dtab, stage + thr_words, sizeof(uint64_t) * 2 * P.nprobe,
                         cudaMemcpyHostToDevice, s), "H2D dtab");
   GS_CU(cudaMemsetAsync(b.st, 0, sizeof(IterState) * (a.max_iter + 2), s), "memset state");
   GS_CU(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), s), "memset barrier");
@@ -244,6 +249,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.blocksum = b.blocksum;
     L.thr = b.thr;
     L.dtab = b.dtab;
+    L.vpack = reinterpret_cast<const uint32_t*>(b.dtab + P.nprobe);
     L.T0 = b.t0;
     for (int i = 0; i < 3; ++i) L.tab[i] = b.tab[i];
     L.capAB = b.capAB;

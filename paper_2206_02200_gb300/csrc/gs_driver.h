@@ -21,7 +21,7 @@ struct Bufs {
   LoopResult* res = nullptr;
   GridBar* bar = nullptr;
   int64_t* thr = nullptr;      // cell-face table
-  uint64_t* dtab = nullptr;    // neighbour offsets
+  uint64_t* dtab = nullptr;    // neighbour offsets (nprobe words), then nprobe packed offset vectors
   uint32_t* slot0 = nullptr;   // n
   uint32_t* perm = nullptr;    // n
   uint32_t* blocksum = nullptr;  // kMaxLoopGrid

@@ -65,6 +65,7 @@ struct LoopArgs {
   uint32_t* blocksum;    // one word per block of the loop kernel
   const int64_t* thr;    // cell-face table (order codes)
   const uint64_t* dtab;  // packed-key offsets of the 3^d neighbours
+  const uint32_t* vpack; // the same offsets v as 2 bits per axis (v_a + 1 at bit 2a)
   BinTable T0;           // binning table (its slots are the points' cell slots)
   LevelTable tab[3];     // level t uses tab[t % 3]; its update merges into tab[(t + 1) % 3]
   uint32_t capAB;        // capacity of each of tab[0..2]

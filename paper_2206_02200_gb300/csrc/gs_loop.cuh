@@ -676,6 +676,24 @@ struct FF {
   __device__ __forceinline__ float value() const { return hi + lo; }
 };
 
+// Kahan-compensated sum: s holds the sum, c the (negated) low part lost so far.
+struct KS {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ FF ff() const {
+    FF r;
+    r.hi = s;
+    r.lo = 0.f;
+    r.add(-c);
+    return r;
+  }
+};
+
 __device__ __forceinline__ FF shfl_xor_ff(unsigned mask, const FF& v, int o) {
   FF r;
   r.hi = __shfl_xor_sync(mask, v.hi, o);
@@ -984,7 +1002,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
     }
     uint32_t Dc = 0;
     bool nbc = false;
-    FF N[D];
+    KS Nk[D];
     for (int p0 = glane; live && p0 < nprobe; p0 += GS * U) {
       uint64_t q[U];
       bool v[U];
@@ -1005,20 +1023,20 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         const uint32_t cn = row_word(dat[u], 2);
         const float fc = (float)cn;
         Dc += cn;
-        float dv[D];  // the probe's offset v in {-1, 0, 1}^d, axis 0 the slowest digit
-        int rest = p;
+        // the probe's offset v in {-1, 0, 1}^d: 2 bits per axis, v_a + 1
+        const uint32_t vp = __ldg(&A.vpack[p]);
 #pragma unroll
-        for (int a = D - 1; a >= 0; --a) {
-          dv[a] = (float)(rest % 3 - 1);
-          rest /= 3;
+        for (int a = 0; a < D; ++a) {
+          const float dv = (float)((int)((vp >> (2 * a)) & 3u) - 1);
+          Nk[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) + dv * h));
         }
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-          N[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) + dv[a] * h));
         if (p != center) nbc = true;
       }
     }
     any_nb = any_nb || nbc;
+    FF N[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) N[a] = Nk[a].ff();
 #pragma unroll
     for (int o = GS / 2; o > 0; o >>= 1) {
       Dc += __shfl_xor_sync(gmask, Dc, o);

@@ -26,7 +26,7 @@ constexpr size_t kProbeMax = 6561; // 3^8 neighbour offsets
 
 std::mutex g_mu;  // serialises calls: they share g_scratch and the host buffers below
 unsigned char* g_dev_ptr[kMaxDevices] = {};
-int64_t g_words[kThrMax + kProbeMax];
+int64_t g_words[kThrMax + 2 * kProbeMax];
 DevFlags g_hflags;
 LoopResult g_hres;
 
@@ -78,7 +78,7 @@ size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, s
   B.res = c.take<LoopResult>(1);
   B.bar = c.take<GridBar>(1);
   B.thr = c.take<int64_t>(thr_words);
-  B.dtab = c.take<uint64_t>(nprobe);
+  B.dtab = c.take<uint64_t>(2 * (size_t)nprobe);
   B.slot0 = c.take<uint32_t>(n);
   B.perm = c.take<uint32_t>(n);
   B.blocksum = c.take<uint32_t>(kMaxLoopGrid);
@@ -128,7 +128,7 @@ struct StaticWorkspace : public Workspace {
   DevFlags* host_flags() override { return &g_hflags; }
   LoopResult* host_result() override { return &g_hres; }
   gs_status host_words(size_t words, int64_t** out, std::string*) override {
-    if (words > kThrMax + kProbeMax) return GS_E_SCRATCH;
+    if (words > kThrMax + 2 * kProbeMax) return GS_E_SCRATCH;
     *out = g_words;
     return GS_OK;
   }
