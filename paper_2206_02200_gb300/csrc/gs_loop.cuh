@@ -861,7 +861,6 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
     for (int e = 0; e < E; ++e) {
       if (s[e] != cur) {
         if (cur != kNone) {
-#pragma unroll
           const uint32_t cid = A.T0.id[cur];
 #pragma unroll
           for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cid * D + a], V[a].value());
@@ -1250,95 +1249,68 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
 
 // ---------------------------------------------------------------------------
 // The tail of the update loop in one block (GS_FP64, plain runs).  Once a
-// level has at most TailCells<D>::value cells, block 0 copies it into shared
-// memory and runs the remaining update steps alone, with block barriers and
-// shared-memory hash tables, while the other blocks wait at one grid barrier.
+// level has at most kTailEnter cells, block 0 copies it into shared memory
+// and runs the remaining update steps alone, with block barriers, while the
+// other blocks wait at one grid barrier.  With so few cells, neighbours are
+// found by comparing every pair of cells (|k_i - k_j| <= 1 on every axis is
+// the same test as k_i = k_j + v for some v in {-1,0,1}^d, Eq. 1), and the
+// cells sharing a new key by comparing new keys, so no hash table is needed.
 // The arithmetic is that of phase_update and phase_compact (exact sums
-// rounded once); a merged cell's sum is added along a list of its members.
+// rounded once); a merged cell's sum is added over its members.
+
+// Largest level handed to the one-block tail.  A tail step costs about
+// m^2 d / 512 pair tests per thread of one SM; up to a few hundred cells that
+// is less than the grid barriers and dependent L2 loads of a multi-block step.
+constexpr uint32_t kTailEnter = 256;
+constexpr int kTailLanes = 8;  // lanes comparing one cell against the level
 
 constexpr size_t tail_bytes(int d, int mx) {
-  return (size_t)mx * d * 16 * 3       // sums of two levels, centroids
-         + (size_t)mx * 8 * 3          // keys of two levels, new keys
-         + (size_t)4 * mx * 8 * 2      // lookup and merge hash keys
-         + (size_t)mx * 4 * 2          // counts of two levels
-         + (size_t)4 * mx * 4          // merge list heads
-         + (size_t)4 * mx * 2 * 2      // lookup cell index, merge cell id
-         + (size_t)mx * 2 * 3;         // member links, member slots, new-cell slots
+  return (size_t)mx * d * 16 * 3   // sums of two levels; neighbour sums, then centroids
+         + (size_t)mx * 8 * 3      // keys of two levels, new keys
+         + (size_t)mx * 4 * 3      // counts of two levels, neighbour counts
+         + (size_t)mx * d * 4      // key fields of the level (axis-major)
+         + (size_t)mx * 2 * 4;     // first member, member count, new id, member of a new id
 }
 
-template <int D>
-struct TailCells {
-  static constexpr int value = tail_bytes(D, 256) <= kFilterWords * 4 ? 256 : 128;
-  static constexpr int cap = 4 * value;  // hash capacity (power of two), load <= 1/4
-};
-
-// Largest level handed to the one-block tail.  All of a tail step's probes go
-// through one SM's shared memory, so the tail pays off only where a step has
-// too little work to hide the latency of the multi-block path (measured on
-// GB300: about 12 us per step at 45 cells in the tail against 20 us; 39 us
-// against 12 us at 171 cells).
-constexpr uint32_t kTailEnter = 64;
-
+// Shared-memory layout of the tail.  The two levels' arrays are reached by
+// offset arithmetic (no runtime-indexed pointer array), so every access stays
+// a shared-memory access.
 template <int D>
 struct TailMem {
-  static constexpr int Mx = TailCells<D>::value, C = TailCells<D>::cap;
-  ulonglong2 *sum[2], *V;
-  uint64_t *key[2], *nk, *hk, *mk;
-  uint32_t *cnt[2], *mhead;
-  uint16_t *hidx, *mid, *nxt, *myslot, *mlist;
-  __device__ explicit TailMem(void* base) {
-    char* p = static_cast<char*>(base);
-    sum[0] = reinterpret_cast<ulonglong2*>(p); p += (size_t)Mx * D * 16;
-    sum[1] = reinterpret_cast<ulonglong2*>(p); p += (size_t)Mx * D * 16;
-    V = reinterpret_cast<ulonglong2*>(p); p += (size_t)Mx * D * 16;
-    key[0] = reinterpret_cast<uint64_t*>(p); p += (size_t)Mx * 8;
-    key[1] = reinterpret_cast<uint64_t*>(p); p += (size_t)Mx * 8;
-    nk = reinterpret_cast<uint64_t*>(p); p += (size_t)Mx * 8;
-    hk = reinterpret_cast<uint64_t*>(p); p += (size_t)C * 8;
-    mk = reinterpret_cast<uint64_t*>(p); p += (size_t)C * 8;
-    cnt[0] = reinterpret_cast<uint32_t*>(p); p += (size_t)Mx * 4;
-    cnt[1] = reinterpret_cast<uint32_t*>(p); p += (size_t)Mx * 4;
-    mhead = reinterpret_cast<uint32_t*>(p); p += (size_t)C * 4;
-    hidx = reinterpret_cast<uint16_t*>(p); p += (size_t)C * 2;
-    mid = reinterpret_cast<uint16_t*>(p); p += (size_t)C * 2;
-    nxt = reinterpret_cast<uint16_t*>(p); p += (size_t)Mx * 2;
-    myslot = reinterpret_cast<uint16_t*>(p); p += (size_t)Mx * 2;
-    mlist = reinterpret_cast<uint16_t*>(p);
+  static constexpr int Mx = (int)kTailEnter;
+  static constexpr size_t kSum = (size_t)Mx * D * 16, kKey = (size_t)Mx * 8,
+                          kCnt = (size_t)Mx * 4;
+  char* p;
+  __device__ explicit TailMem(void* base) : p(static_cast<char*>(base)) {}
+  // level c (0 or 1): sums, keys, counts
+  __device__ ulonglong2* sum(int c) const { return reinterpret_cast<ulonglong2*>(p + c * kSum); }
+  __device__ uint64_t* key(int c) const {
+    return reinterpret_cast<uint64_t*>(p + 3 * kSum + c * kKey);
+  }
+  __device__ uint32_t* cnt(int c) const {
+    return reinterpret_cast<uint32_t*>(p + 3 * kSum + 3 * kKey + c * kCnt);
+  }
+  // neighbour sums, then centroids; new keys; neighbour counts; key fields
+  __device__ ulonglong2* V() const { return reinterpret_cast<ulonglong2*>(p + 2 * kSum); }
+  __device__ uint64_t* nk() const { return reinterpret_cast<uint64_t*>(p + 3 * kSum + 2 * kKey); }
+  __device__ uint32_t* dc() const {
+    return reinterpret_cast<uint32_t*>(p + 3 * kSum + 3 * kKey + 2 * kCnt);
+  }
+  __device__ int32_t* F() const {
+    return reinterpret_cast<int32_t*>(p + 3 * kSum + 3 * kKey + 3 * kCnt);
+  }
+  // first member, member count, new id, first member of a new id
+  __device__ uint16_t* u16(int which) const {
+    return reinterpret_cast<uint16_t*>(p + 3 * kSum + 3 * kKey + 3 * kCnt + (size_t)Mx * D * 4 +
+                                       (size_t)which * Mx * 2);
   }
 };
+static_assert(tail_bytes(kMaxD, (int)kTailEnter) <= (size_t)kFilterWords * 4,
+              "the tail's shared memory must fit in the filter's");
 
-__device__ __forceinline__ uint32_t tail_home(uint64_t key, int C) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - __popc(C - 1)));
-}
-
-// Slot of key in a shared-memory table of C slots (linear probing), inserting
-// it if absent; won is set for the inserting thread.
-__device__ __forceinline__ uint32_t tail_insert(uint64_t* keys, int C, uint64_t key, bool& won) {
-  uint32_t s = tail_home(key, C);
-  won = false;
-  for (int i = 0; i < C; ++i) {
-    const uint64_t prev = atomicCAS((unsigned long long*)&keys[s], (unsigned long long)kEmpty,
-                                    (unsigned long long)key);
-    if (prev == kEmpty) {
-      won = true;
-      return s;
-    }
-    if (prev == key) return s;
-    s = (s + 1) & (C - 1);
-  }
-  return kNone;  // unreachable: at most C / 4 keys
-}
-
-__device__ __forceinline__ uint32_t tail_find(const uint64_t* keys, int C, uint64_t key) {
-  uint32_t s = tail_home(key, C);
-#pragma unroll 1
-  for (int i = 0; i < C; ++i) {
-    const uint64_t k = keys[s];
-    if (k == key) return s;
-    if (k == kEmpty) return kNone;
-    s = (s + 1) & (C - 1);
-  }
-  return kNone;
+// Width of axis a's key field (axis 0 most significant).
+__device__ __forceinline__ int field_width(const Plan& P, int a) {
+  return (a == 0 ? 64 : P.off[a - 1]) - P.off[a];
 }
 
 // Result of the tail, published by block 0 for the other blocks.
@@ -1357,19 +1329,23 @@ template <int D>
 __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
                          uint32_t base_prev, uint32_t base, unsigned long long cell_iters,
                          SegClock& clk, unsigned& inexact, unsigned& werr, TailOut& out) {
-  constexpr int Mx = TailMem<D>::Mx, C = TailMem<D>::C;
-  constexpr int GS = GatherLanes<D>::min;
-  constexpr int U = ProbeBatch<D, GS>::value;
+  constexpr int Mx = TailMem<D>::Mx;
+  constexpr int GS = kTailLanes;
   extern __shared__ uint4 s_dyn[];
-  TailMem<D> S(s_dyn);
-  __shared__ uint32_t s_nb, s_m1;
+  const TailMem<D> S(s_dyn);
+  ulonglong2* const V = S.V();
+  uint64_t* const nk = S.nk();
+  uint32_t* const dc = S.dc();
+  int32_t* const F = S.F();
+  uint16_t* const lead = S.u16(0);
+  uint16_t* const mcnt = S.u16(1);
+  uint16_t* const nid = S.u16(2);
+  uint16_t* const lidx = S.u16(3);
+  __shared__ uint32_t s_nb, s_wc[kLoopBlock / 32];
   const uint32_t tid = threadIdx.x, nth = blockDim.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int glane = lane & (GS - 1);
-  const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
   const uint32_t group = threadIdx.x / GS, ngroups = blockDim.x / GS;
-  const int nprobe = A.P.nprobe, center = A.P.center;
-  (void)Mx;
 
   // parent links of level t-1 and release of its table (the update phase of
   // step t does this in the multi-block path)
@@ -1389,10 +1365,10 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
     const Cells c = A.cells[t & 1];
     for (uint32_t i = tid; i < m; i += nth) {
       const uint32_t s = G.list[i];
-      S.key[0][i] = c.key[i];
-      S.cnt[0][i] = c.cnt[i];
+      S.key(0)[i] = c.key[i];
+      S.cnt(0)[i] = c.cnt[i];
 #pragma unroll
-      for (int a = 0; a < D; ++a) S.sum[0][(size_t)i * D + a] = G.row[(size_t)s * (D + 1) + 1 + a];
+      for (int a = 0; a < D; ++a) S.sum(0)[(size_t)i * D + a] = G.row[(size_t)s * (D + 1) + 1 + a];
       G.key[s] = kEmpty;
       G.row[(size_t)s * (D + 1)].x = 0;
     }
@@ -1402,83 +1378,81 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
   int cur = 0;
   bool converged = false;
   for (;;) {
-    const uint64_t* key = S.key[cur];
-    const uint32_t* cnt = S.cnt[cur];
-    const ulonglong2* sum = S.sum[cur];
-    // lookup table of the level
-    for (uint32_t s = tid; s < (uint32_t)C; s += nth) {
-      S.hk[s] = kEmpty;
-      S.mk[s] = kEmpty;
-      S.mhead[s] = kNone;
-    }
-    if (tid == 0) {
-      s_nb = 0;
-      s_m1 = 0;
-    }
-    __syncthreads();
+    const uint64_t* key = S.key(cur);
+    const uint32_t* cnt = S.cnt(cur);
+    const ulonglong2* sum = S.sum(cur);
+    // the key fields of the level, axis-major
     for (uint32_t i = tid; i < m; i += nth) {
-      bool won;
-      const uint32_t s = tail_insert(S.hk, C, key[i], won);
-      S.hidx[s] = (uint16_t)i;
+      const uint64_t k = key[i];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int w = field_width(A.P, a);
+        const uint64_t f = k >> A.P.off[a];
+        F[a * Mx + i] = (int32_t)(w >= 64 ? f : (f & ((1ull << w) - 1ull)));
+      }
+      nk[i] = 0;
     }
+    if (tid == 0) s_nb = 0;
     __syncthreads();
-    // ii-iii: the update of every cell (as phase_update)
-    for (uint32_t j = group; j < m; j += ngroups) {
-      const uint64_t kj = key[j];
+    // ii: D and N over the cells within one cell on every axis (Eq. 1-2);
+    // GS lanes per cell, each comparing a share of the level
+    for (uint32_t j0 = 0; j0 < m; j0 += ngroups) {
+      const uint32_t j = j0 + group;
+      const bool live = j < m;
+      int32_t fj[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) fj[a] = live ? F[a * Mx + j] : 0;
       uint32_t Dc = 0;
       bool nb = false;
       u128 N[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) N[a] = 0;
-      for (int p0 = glane; p0 < nprobe; p0 += GS * U) {
+      for (uint32_t i = glane; live && i < m; i += GS) {
+        bool adj = true;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int p = p0 + u * GS;
-          if (p >= nprobe) continue;
-          const uint32_t s = tail_find(S.hk, C, kj + __ldg(&A.dtab[p]));
-          if (s == kNone) continue;
-          const uint32_t i = S.hidx[s];
+        for (int a = 0; a < D; ++a) adj &= (uint32_t)(F[a * Mx + i] - fj[a] + 1) <= 2u;
+        if (adj) {
           Dc += cnt[i];
 #pragma unroll
           for (int a = 0; a < D; ++a) N[a] += as_u128(sum[(size_t)i * D + a]);
-          if (p != center) nb = true;
+          if (i != j) nb = true;
         }
       }
 #pragma unroll
       for (int o = GS / 2; o > 0; o >>= 1) {
-        Dc += __shfl_xor_sync(gmask, Dc, o);
+        Dc += __shfl_xor_sync(kFull, Dc, o);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          uint64_t lo = (uint64_t)N[a], hi = (uint64_t)(N[a] >> 64);
-          lo = __shfl_xor_sync(gmask, lo, o);
-          hi = __shfl_xor_sync(gmask, hi, o);
-          N[a] += (u128)lo | ((u128)hi << 64);
-        }
+        for (int a = 0; a < D; ++a) N[a] += shfl_xor_u128(N[a], o);
       }
-      uint64_t field = 0;
-      if (glane < D) {
-        u128 Na = 0;
-        int La = 0, off = 0, span = 1, toff = 0;
-        int64_t kmin = 0;
+      if (live) {
+        if (glane == 0) dc[j] = Dc;
 #pragma unroll
         for (int a = 0; a < D; ++a)
-          if (a == glane) {
-            Na = N[a];
-            La = A.P.L[a];
-            off = A.P.off[a];
-            span = A.P.span[a];
-            toff = A.P.thr_off[a];
-            kmin = A.P.kmin[a];
-          }
-        const double sv = div_round(Na, Dc, La, inexact);
-        const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
-        field = (uint64_t)(idx + 1) << off;
-        S.V[(size_t)j * D + glane] = pack(to_fixed(bits_of(sv), La, inexact, werr));
+          if (a == glane) V[(size_t)j * D + a] = pack(N[a]);
       }
+      if (__any_sync(kFull, nb) && lane == 0) s_nb = 1u;
+    }
+    __syncthreads();
+    // ii-iii: one thread per (cell, axis): centroid N / D rounded once, its
+    // key field, its fixed-point value
+    for (uint32_t w = tid; w < m * D; w += nth) {
+      const uint32_t j = w / D;
+      const int ax = (int)(w - j * D);
+      int La = 0, off = 0, span = 1, toff = 0;
+      int64_t kmin = 0;
 #pragma unroll
-      for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
-      if (glane == 0) S.nk[j] = field;
-      if (nb) s_nb = 1u;
+      for (int a = 0; a < D; ++a)
+        if (a == ax) {
+          La = A.P.L[a];
+          off = A.P.off[a];
+          span = A.P.span[a];
+          toff = A.P.thr_off[a];
+          kmin = A.P.kmin[a];
+        }
+      const double sv = div_round(as_u128(V[w]), dc[j], La, inexact);
+      const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
+      atomicOr((unsigned long long*)&nk[j], (unsigned long long)(idx + 1) << off);
+      V[w] = pack(to_fixed(bits_of(sv), La, inexact, werr));
     }
     __syncthreads();
     clk.lap_step(kSegUpdateRest, t, A.res);
@@ -1487,42 +1461,98 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
       break;
     }
     if (t == A.max_iter) break;
-    // iv: merge (a list of members per new key)
-    for (uint32_t i = tid; i < m; i += nth) {
-      bool won;
-      const uint32_t ms = tail_insert(S.mk, C, S.nk[i], won);
-      if (won) {
-        const uint32_t id = atomicAdd(&s_m1, 1u);
-        S.mid[ms] = (uint16_t)id;
-        S.mlist[id] = (uint16_t)ms;
+    // iv: merge.  A cell's first member is the lowest-indexed cell with its
+    // new key; new cells are numbered in the order of their first members.
+    // GS lanes per cell compare its new key with a share of the level's.
+    for (uint32_t j0 = 0; j0 < m; j0 += ngroups) {
+      const uint32_t i = j0 + group;
+      const bool live = i < m;
+      const uint64_t k = live ? nk[i] : 0ull;
+      uint32_t l = kNone, c = 0;
+      for (uint32_t q = glane; live && q < m; q += GS) {
+        if (nk[q] == k) {
+          l = min(l, q);
+          ++c;
+        }
       }
-      S.nxt[i] = (uint16_t)atomicExch(&S.mhead[ms], i);
-      S.myslot[i] = (uint16_t)ms;
+#pragma unroll
+      for (int o = GS / 2; o > 0; o >>= 1) {
+        l = min(l, __shfl_xor_sync(kFull, l, o));
+        c += __shfl_xor_sync(kFull, c, o);
+      }
+      if (live && glane == 0) {
+        lead[i] = (uint16_t)l;
+        mcnt[i] = (uint16_t)c;
+      }
     }
     __syncthreads();
-    const uint32_t m1 = s_m1;
+    uint32_t m1 = 0;
+    {
+      uint32_t base_w = 0;
+      for (uint32_t i0 = 0; i0 < m; i0 += nth) {
+        const uint32_t i = i0 + tid;
+        const bool first = i < m && lead[i] == i;
+        const unsigned bal = __ballot_sync(kFull, first);
+        if (lane == 0) s_wc[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t before = base_w;
+        for (int w = 0; w < warp; ++w) before += s_wc[w];
+        if (first) {
+          const uint32_t id = before + __popc(bal & ((1u << lane) - 1u));
+          nid[i] = (uint16_t)id;
+          lidx[id] = (uint16_t)i;
+        }
+        for (int w = 0; w < (int)(nth >> 5); ++w) base_w += s_wc[w];
+        __syncthreads();
+      }
+      m1 = base_w;
+    }
     const int nxtb = cur ^ 1;
-    for (uint32_t id = tid; id < m1; id += nth) {
-      const uint32_t ms = S.mlist[id];
+    // GS lanes per new cell: the count-weighted sum of its members'
+    // centroids (Eq. 3-4), exact, rounded once; a cell alone under its new
+    // key is its only member
+    for (uint32_t id0 = 0; id0 < m1; id0 += ngroups) {
+      const uint32_t id = id0 + group;
+      const bool live = id < m1;
+      const uint32_t l = live ? lidx[id] : 0u;
+      const bool many = live && mcnt[l] > 1;
       uint32_t c1 = 0;
       u128 Sx[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) Sx[a] = 0;
-      for (uint32_t i = S.mhead[ms]; i != kNone; i = S.nxt[i] == 0xFFFFu ? kNone : S.nxt[i]) {
+      for (uint32_t i = l + glane; live && i < m && (many || i == l); i += GS) {
+        if (lead[i] != l) continue;
         const uint32_t ci = cnt[i];
         c1 += ci;
 #pragma unroll
-        for (int a = 0; a < D; ++a) Sx[a] += as_u128(S.V[(size_t)i * D + a]) * (u128)ci;
+        for (int a = 0; a < D; ++a) Sx[a] += as_u128(V[(size_t)i * D + a]) * (u128)ci;
       }
-      S.key[nxtb][id] = S.mk[ms];
-      S.cnt[nxtb][id] = c1;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const double v = round_fixed(Sx[a], A.P.L[a], inexact);
-        S.sum[nxtb][(size_t)id * D + a] = pack(to_fixed(bits_of(v), A.P.L[a], inexact, werr));
+      for (int o = GS / 2; o > 0; o >>= 1) {
+        c1 += __shfl_xor_sync(kFull, c1, o);
+#pragma unroll
+        for (int a = 0; a < D; ++a) Sx[a] += shfl_xor_u128(Sx[a], o);
+      }
+      if (live && glane < D) {
+        u128 Sa = 0;
+        int La = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          if (a == glane) {
+            Sa = Sx[a];
+            La = A.P.L[a];
+          }
+        const double v = round_fixed(Sa, La, inexact);
+        S.sum(nxtb)[(size_t)id * D + glane] = pack(to_fixed(bits_of(v), La, inexact, werr));
+      }
+      if (live) {
+        if (glane == 0) {
+          S.key(nxtb)[id] = nk[l];
+          S.cnt(nxtb)[id] = c1;
+        }
       }
     }
-    for (uint32_t i = tid; i < m; i += nth) A.forest[base + i] = base + m + S.mid[S.myslot[i]];
+    for (uint32_t i = tid; i < m; i += nth) A.forest[base + i] = base + m + nid[lead[i]];
     __syncthreads();
     clk.lap_step(kSegCompact, t, A.res);
     cell_iters += m;
@@ -1539,15 +1569,15 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
     const uint32_t maskT = mask_for(m, A.capAB);
     for (uint32_t i = tid; i < m; i += nth) {
       bool won;
-      const uint64_t k = S.key[cur][i];
+      const uint64_t k = S.key(cur)[i];
       const uint32_t s = table_insert(G.key, maskT, k, won, &A.fl->err);
       c.key[i] = k;
-      c.cnt[i] = S.cnt[cur][i];
+      c.cnt[i] = S.cnt(cur)[i];
       if (s == kNone) continue;
       ulonglong2* r = G.row + (size_t)s * (D + 1);
-      r[0] = make_ulonglong2((uint64_t)S.cnt[cur][i], 0ull);
+      r[0] = make_ulonglong2((uint64_t)S.cnt(cur)[i], 0ull);
 #pragma unroll
-      for (int a = 0; a < D; ++a) r[1 + a] = S.sum[cur][(size_t)i * D + a];
+      for (int a = 0; a < D; ++a) r[1 + a] = S.sum(cur)[(size_t)i * D + a];
       G.id[s] = i;
       G.list[i] = s;
     }
