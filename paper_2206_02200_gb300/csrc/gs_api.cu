@@ -224,6 +224,8 @@ struct CtxWorkspace : public Workspace {
     return GS_OK;
   }
 
+  size_t plan_thr_cap() const override { return size_t(1) << 16; }
+
   gs_status prepare(int64_t n, int d, int max_iter, size_t thr_words, int nprobe,
                     uint64_t m_bound, cudaStream_t s, Bufs& b, std::string* err) override {
     cudaError_t e;

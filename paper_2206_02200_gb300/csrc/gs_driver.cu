@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "gs_driver.h"
+#include "gs_planner.cuh"
 
 namespace gs {
 
@@ -36,44 +37,6 @@ uint32_t pow2_at_least(uint64_t v, uint32_t lo) {
 
 namespace {
 
-int64_t ord_of(double x) {
-  if (x == 0.0) x = 0.0;
-  int64_t s;
-  std::memcpy(&s, &x, 8);
-  return s ^ ((s >> 63) & 0x7FFFFFFFFFFFFFFFll);
-}
-
-double from_ord(int64_t o) {
-  int64_t s = o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll);
-  double x;
-  std::memcpy(&x, &s, 8);
-  return x;
-}
-
-// The least double t with t >= q * h (exactly); the error of the rounded
-// product q * h is itself a double, obtained exactly by one fused multiply-add.
-double face(int64_t q, double h) {
-  double qd = (double)q;
-  double p = qd * h;
-  double r = std::fma(qd, h, -p);
-  if (r > 0) p = std::nextafter(p, INFINITY);
-  return p;
-}
-
-// floor(x / h) of the exact quotient: the q with face(q) <= x < face(q + 1).
-int64_t floor_div(double x, double h) {
-  int64_t q = (int64_t)std::floor(x / h);
-  for (int i = 0; i < 4 && face(q, h) > x; ++i) --q;
-  for (int i = 0; i < 4 && face(q + 1, h) <= x; ++i) ++q;
-  return q;
-}
-
-int bitlen(uint64_t v) {
-  int b = 0;
-  for (; v; v >>= 1) ++b;
-  return b;
-}
-
 gs_status fail(std::string* err, gs_status s, const char* msg) {
   if (err) *err = msg;
   return s;
@@ -84,75 +47,14 @@ gs_status cuda_fail(std::string* err, cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA;
 }
 
-// Packed-key layout and fixed-point windows from the key range (Sec. 2.1 i):
-// per axis the data's key box widened by one cell each side (centroids are
-// convex combinations of the points, Eq. 1 and Eq. 3, and leave that box by a
-// few roundings at most), packed axis 0 most significant.
-gs_status make_plan(int d, double h, int64_t n, int B, const DevFlags& fl, Plan& P,
-                    size_t& thr_words, uint64_t& span_prod, int& total_bits, std::string* err) {
-  std::memset(&P, 0, sizeof(P));
-  P.d = d;
-  P.inv_h = (float)(1.0 / h);
-  P.h32 = (float)h;
-  int bits[kMaxD];
-  int clog2n = 0;
-  while ((1ll << clog2n) < n) ++clog2n;
-  span_prod = 1;
-  thr_words = 0;
-  for (int a = 0; a < d; ++a) {
-    const double lo = from_ord(fl.min_ord[a]), hi = from_ord(fl.max_ord[a]);
-    if (!(std::fabs(lo / h) < 4.0e15) || !(std::fabs(hi / h) < 4.0e15))
-      return fail(err, GS_E_KEYRANGE, "a coordinate divided by h exceeds 2^52");
-    const int64_t kmin = floor_div(lo, h) - 1, kmax = floor_div(hi, h) + 1;
-    const int64_t span = kmax - kmin + 1;
-    if (span > (1ll << 22)) return fail(err, GS_E_KEYRANGE, "more than 2^22 cells along one axis");
-    P.kmin[a] = kmin;
-    P.span[a] = (int)span;
-    bits[a] = bitlen((uint64_t)span + 1);
-    P.thr_off[a] = (int)thr_words;
-    thr_words += (size_t)span + 1;
-    span_prod = span_prod > (1ull << 40) ? span_prod : span_prod * (uint64_t)span;
-    double ma;
-    const uint64_t mb = fl.maxabs[a];
-    std::memcpy(&ma, &mb, 8);
-    int e = 0;
-    if (ma > 0) std::frexp(ma, &e);  // ma < 2^e
-    P.L[a] = e + clog2n - 126;
-  }
-  total_bits = 0;
-  for (int a = d - 1; a >= 0; --a) {
-    P.off[a] = total_bits;
-    total_bits += bits[a];
-  }
-  // batched runs: the instance index in the field above all axes (it is
-  // never probed, so cells of different instances never meet)
-  P.inst_off = total_bits;
-  if (B > 1) total_bits += bitlen((uint64_t)(B - 1));
-  if (total_bits > 63) return fail(err, GS_E_KEYRANGE, "packed cell key needs more than 63 bits");
-  int np = 1;
-  for (int a = 0; a < d; ++a) np *= 3;
-  P.nprobe = np;
-  P.center = (np - 1) / 2;
-  return GS_OK;
-}
-
-// Face tables (order codes of the least doubles >= q h) and the packed-key
-// offsets of the 3^d neighbours v in {-1,0,1}^d (axis 0 the slowest digit).
-void fill_tables(const Plan& P, double h, int64_t* thr, uint64_t* dtab, uint32_t* vpack) {
-  for (int a = 0; a < P.d; ++a)
-    for (int64_t j = 0; j <= P.span[a]; ++j) thr[P.thr_off[a] + j] = ord_of(face(P.kmin[a] + j, h));
-  for (int p = 0; p < P.nprobe; ++p) {
-    int64_t delta = 0;
-    uint32_t vp = 0;
-    int rest = p;
-    for (int a = P.d - 1; a >= 0; --a) {
-      const int v = rest % 3 - 1;
-      rest /= 3;
-      delta += (int64_t)v * (int64_t)(1ull << P.off[a]);
-      vp |= (uint32_t)(v + 1) << (2 * a);
-    }
-    dtab[p] = (uint64_t)delta;
-    vpack[p] = vp;
+// The error of a plan status other than kPlanOK.
+gs_status plan_fail(std::string* err, uint32_t st) {
+  switch (st) {
+    case kPlanNonFinite: return fail(err, GS_E_INVALID, "non-finite input coordinate");
+    case kPlanRangeH: return fail(err, GS_E_KEYRANGE, "a coordinate divided by h exceeds 2^52");
+    case kPlanSpan: return fail(err, GS_E_KEYRANGE, "more than 2^22 cells along one axis");
+    case kPlanBits: return fail(err, GS_E_KEYRANGE, "packed cell key needs more than 63 bits");
+    default: return fail(err, GS_E_INTERNAL, "invalid plan");
   }
 }
 
@@ -186,7 +88,9 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   Bufs b;
   GS_ST(ws.begin(b, err));
 
-  // a0: key range, fixed-point window, finiteness
+  // a0: key range, fixed-point window, finiteness (k_range), then the plan
+  // on the device (k_plan: no host round trip before binning); the face
+  // table gets the workspace's device-side capacity
   DevFlags* hf = ws.host_flags();
   std::memset(hf, 0, sizeof(DevFlags));
   for (int i = 0; i < kMaxD; ++i) {
@@ -194,33 +98,16 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     hf->max_ord[i] = INT64_MIN;
   }
   GS_CU(cudaMemcpyAsync(b.flags, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
+  const size_t thr_cap = ws.plan_thr_cap();
+  int nprobe = 1;
+  for (int i = 0; i < d; ++i) nprobe *= 3;
+  GS_ST(ws.prepare(n, d, a.max_iter, thr_cap, nprobe, (uint64_t)n, s, b, err));
+  GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
   GS_T_BEGIN(GS_PHASE_RANGE);
   GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, s), "k_range", 1);
+  GS_LAUNCH(launch_plan(d, a.h, n, a.B, b.flags, b.thr, thr_cap, b.dtab, b.filter, b.st,
+                        (uint32_t)(a.max_iter + 2), b.bar, b.res, s), "k_plan", 1);
   GS_T_END();
-  GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
-  GS_CU(cudaStreamSynchronize(s), "sync range");
-  if (hf->bad) return fail(err, GS_E_INVALID, "non-finite input coordinate");
-
-  Plan P;
-  size_t thr_words = 0;
-  uint64_t span_prod = 0;
-  int total_bits = 0;
-  GS_ST(make_plan(d, a.h, n, a.B, *hf, P, thr_words, span_prod, total_bits, err));
-  const uint64_t m_bound = (uint64_t)n < span_prod ? (uint64_t)n : span_prod;
-  GS_ST(ws.prepare(n, d, a.max_iter, thr_words, P.nprobe, m_bound, s, b, err));
-
-  // face table and neighbour offsets, through host staging
-  // (dtab holds nprobe offsets, then nprobe 32-bit packed offset vectors)
-  int64_t* stage = nullptr;
-  GS_ST(ws.host_words(thr_words + 2 * P.nprobe, &stage, err));
-  fill_tables(P, a.h, stage, reinterpret_cast<uint64_t*>(stage + thr_words),
-              reinterpret_cast<uint32_t*>(stage + thr_words + P.nprobe));
-  GS_CU(cudaMemcpyAsync(b.thr, stage, sizeof(int64_t) * thr_words, cudaMemcpyHostToDevice, s),
-        "H2D thr");
-  GS_CU(cudaMemcpyAsync(b.dtab, stage + thr_words, sizeof(uint64_t) * 2 * P.nprobe,
-                        cudaMemcpyHostToDevice, s), "H2D dtab");
-  GS_CU(cudaMemsetAsync(b.st, 0, sizeof(IterState) * (a.max_iter + 2), s), "memset state");
-  GS_CU(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), s), "memset barrier");
   uint32_t* hinst = nullptr;
   if (a.B > 1) {
     // batched: instance offsets, cleared per-instance state
@@ -233,23 +120,35 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   // i: binning, then at once the loop kernel: the level workspace is sized
   // for the binning table's cell bound, so no host round trip separates
   // them.  If binning overflows the table, the loop kernel returns at its
-  // start and both run again with a larger table.
+  // start and both run again with a larger table; if the face table did not
+  // fit the device-side capacity, neither ran, and the host makes the plan
+  // and runs them again.
   ws.mark_dirty(true);
   const int grid = loop_grid(d, a.mixed);
   if (grid <= 0) return fail(err, GS_E_CUDA, "no co-resident grid for the loop kernel");
   LoopArgs L;
   LoopResult* hr = ws.host_result();
+  bool host_planned = false;
   for (int attempt = 0;; ++attempt) {
-    GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
+    if (attempt > 0) {
+      // a second binning (larger table, or the host's plan): the level
+      // workspace for its cell bound, and the start state k_plan cleared
+      GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
+      GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s),
+            "memset filters");
+      GS_CU(cudaMemsetAsync(b.res, 0, sizeof(LoopResult), s), "memset result");
+      GS_CU(cudaMemsetAsync(b.st, 0, sizeof(IterState) * (a.max_iter + 2), s), "memset state");
+      GS_CU(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), s), "memset barrier");
+    }
     std::memset(&L, 0, sizeof(L));
-    L.P = P;
+    L.P.d = d;  // the loop kernel reads the plan from b.flags
     L.pts = a.points;
     L.f32 = a.f32;
     L.perm = b.perm;
     L.blocksum = b.blocksum;
     L.thr = b.thr;
     L.dtab = b.dtab;
-    L.vpack = reinterpret_cast<const uint32_t*>(b.dtab + P.nprobe);
+    L.vpack = reinterpret_cast<const uint32_t*>(b.dtab + nprobe);
     L.T0 = b.t0;
     for (int i = 0; i < 3; ++i) L.tab[i] = b.tab[i];
     L.capAB = b.capAB;
@@ -277,11 +176,9 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.B = a.B;
     L.mixed = a.mixed;
     if (a.B > 1) L.I = inst_views(b.inst, a.B);
-    GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
-    GS_CU(cudaMemsetAsync(b.res, 0, sizeof(LoopResult), s), "memset result");
     GS_T_BEGIN(GS_PHASE_BIN);
-    GS_LAUNCH(launch_bin(a.points, a.f32, n, P, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells, b.slot0,
-                         b.flags, b.offsets, a.B, s), "k_bin", 1);
+    GS_LAUNCH(launch_bin(a.points, a.f32, n, d, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells,
+                         b.slot0, b.flags, b.offsets, a.B, s), "k_bin", 1);
     GS_T_END();
     GS_T_BEGIN(GS_PHASE_LOOP);
     GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
@@ -289,6 +186,35 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_CU(cudaMemcpyAsync(hr, b.res, sizeof(LoopResult), cudaMemcpyDeviceToHost, s), "D2H result");
     GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
     GS_CU(cudaStreamSynchronize(s), "sync loop");
+    if (hf->plan_status != kPlanOK) {
+      if (hf->plan_status != kPlanTable || host_planned) return plan_fail(err, hf->plan_status);
+      // the face table is larger than the device-side capacity: the plan,
+      // face table and offsets from the host, then binning and the loop
+      Plan P;
+      PlanSizes z;
+      const uint32_t st = plan_from_range(d, a.h, n, a.B, *hf, P, z);
+      if (st != kPlanOK) return plan_fail(err, st);
+      const uint64_t m_bound = (uint64_t)n < z.span_prod ? (uint64_t)n : z.span_prod;
+      GS_ST(ws.prepare(n, d, a.max_iter, z.thr_words, nprobe, m_bound, s, b, err));
+      int64_t* stage = nullptr;
+      GS_ST(ws.host_words(z.thr_words + 2 * (size_t)nprobe, &stage, err));
+      for (uint64_t j = 0; j < z.thr_words; ++j) stage[j] = plan_face_entry(P, a.h, j);
+      uint64_t* hd = reinterpret_cast<uint64_t*>(stage + z.thr_words);
+      uint32_t* hv = reinterpret_cast<uint32_t*>(hd + nprobe);
+      for (int p = 0; p < nprobe; ++p) plan_probe(P, p, hd + p, hv + p);
+      GS_CU(cudaMemcpyAsync(b.thr, stage, sizeof(int64_t) * z.thr_words, cudaMemcpyHostToDevice,
+                            s), "H2D thr");
+      GS_CU(cudaMemcpyAsync(b.dtab, hd, sizeof(uint64_t) * 2 * nprobe, cudaMemcpyHostToDevice, s),
+            "H2D dtab");
+      hf->plan = P;
+      hf->plan_sizes = z;
+      hf->plan_status = kPlanOK;
+      hf->err = 0;
+      hf->m0 = 0;
+      GS_CU(cudaMemcpyAsync(b.flags, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
+      host_planned = true;
+      continue;
+    }
     const uint32_t regrow = kErrOverflow | kErrTableFull;
     if (!(hf->err & regrow) || !hr->bin_failed) break;
     if (attempt >= 4) return fail(err, GS_E_INTERNAL, "binning table overflow");
@@ -297,6 +223,9 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     hf->m0 = 0;
     GS_CU(cudaMemcpyAsync(b.flags, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
   }
+  // the plan the kernels ran with, for the kernels after the loop
+  L.P = hf->plan;
+  const int total_bits = hf->plan_sizes.total_bits;
   const uint32_t m0 = hf->m0;
   info->m0 = m0;
   ws.note_cells(m0);

@@ -57,6 +57,9 @@ class Workspace {
   virtual gs_status host_words(size_t words, int64_t** out, std::string* err) = 0;
   // b.flags (needed before the plan).
   virtual gs_status begin(Bufs& b, std::string* err) = 0;
+  // Face-table entries the device-side plan may use (prepare is first called
+  // with this many; a plan that needs more is made on the host).
+  virtual size_t plan_thr_cap() const = 0;
   // Everything up to and including binning, for n points, a face table of
   // thr_words entries, 3^d offsets, and a binning table for at most m_bound
   // cells (load factor <= 1/2).  Tables handed out are clean (keys empty,

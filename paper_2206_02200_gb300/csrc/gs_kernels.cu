@@ -1,11 +1,15 @@
 // gs_kernels.cu -- the per-point kernels of the GridShift hot path on sm_103a
 // (Kumar et al., arXiv 2206.02200, Sec. 2.1 and Algorithm 1):
 //   k_range  key range, fixed-point window and finiteness of the input
+//   k_plan   the plan of the call (key packing, face table, offsets)
 //   k_bin    step i, first pass: cell key and count of every point
 // and the kernels that finish the labels when the final cells are numbered
 // by a radix sort.  Everything between binning and the labels runs in the
 // loop kernel (gs_loop.cuh).
+#include <atomic>
+
 #include "gs_common.cuh"
+#include "gs_planner.cuh"
 
 namespace gs {
 
@@ -180,12 +184,76 @@ __device__ __forceinline__ uint32_t instance_of(const int64_t* __restrict__ offs
   return (uint32_t)lo;
 }
 
+// The plan of a call (Sec. 2.1 i) from its key range, on the device.  Block
+// 0: one thread per axis, then one thread for the key layout, into fl->plan;
+// then the block fills the face table and the neighbour offsets.  A
+// non-finite input, a key range the packing cannot hold, or a face table
+// above thr_cap entries sets fl->plan_status instead (binning and the loop
+// kernel then do nothing; the host reads the status).  Every block also
+// clears part of the loop kernel's start state (the occupancy filters, the
+// per-level state, the grid barrier, the result).
+__global__ void __launch_bounds__(kBlock)
+    k_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t* __restrict__ thr,
+           uint64_t thr_cap, uint64_t* __restrict__ dtab, uint4* filters, uint32_t filter_vec,
+           IterState* st, uint32_t n_st, GridBar* bar, LoopResult* res) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < filter_vec;
+       w += gridDim.x * blockDim.x)
+    filters[w] = make_uint4(0, 0, 0, 0);
+  if (blockIdx.x != 0) return;
+  for (uint32_t i = threadIdx.x; i < n_st; i += blockDim.x) st[i] = IterState{};
+  if (threadIdx.x == 0) {
+    *bar = GridBar{};
+    *res = LoopResult{};
+  }
+  __shared__ Plan s_plan;
+  __shared__ PlanSizes s_z;
+  __shared__ uint32_t s_st, s_ax[kMaxD];
+  if (threadIdx.x == 0) memset(&s_plan, 0, sizeof(s_plan));
+  __syncthreads();
+  if ((int)threadIdx.x < d) s_ax[threadIdx.x] = plan_axis(threadIdx.x, h, n, *fl, s_plan);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t status = fl->bad ? kPlanNonFinite : kPlanOK;
+    for (int a = 0; a < d && status == kPlanOK; ++a) status = s_ax[a];
+    if (status == kPlanOK) status = plan_finish(d, h, B, s_plan, s_z);
+    if (status == kPlanOK && s_z.thr_words > thr_cap) status = kPlanTable;
+    fl->plan = s_plan;
+    fl->plan_sizes = s_z;
+    fl->plan_status = status;
+    s_st = status;
+  }
+  __syncthreads();
+  if (s_st != kPlanOK) return;
+  for (uint64_t j = threadIdx.x; j < s_z.thr_words; j += blockDim.x)
+    thr[j] = plan_face_entry(s_plan, h, j);
+  // dtab: nprobe packed-key offsets, then nprobe 32-bit offset vectors
+  uint32_t* vpack = reinterpret_cast<uint32_t*>(dtab + s_plan.nprobe);
+  for (int p = threadIdx.x; p < s_plan.nprobe; p += blockDim.x)
+    plan_probe(s_plan, p, dtab + p, vpack + p);
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock)
-    k_bin(const T* __restrict__ pts, int64_t n, Plan P, const int64_t* __restrict__ thr,
+    k_bin(const T* __restrict__ pts, int64_t n, const int64_t* __restrict__ thr,
           BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
           DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B) {
   __shared__ __align__(16) T s_pts[kWarps][32 * D];
+  __shared__ uint32_t s_ok;
+  // the plan, into registers (nothing runs unless it is valid)
+  if (threadIdx.x == 0) s_ok = *(volatile uint32_t*)&fl->plan_status == kPlanOK;
+  __syncthreads();
+  if (!s_ok) return;
+  int thr_off[D], span[D], off[D];
+  int64_t kmin[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    thr_off[a] = fl->plan.thr_off[a];
+    span[a] = fl->plan.span[a];
+    off[a] = fl->plan.off[a];
+    kmin[a] = fl->plan.kmin[a];
+  }
+  const float inv_h = fl->plan.inv_h;
+  const int inst_off = fl->plan.inst_off;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -196,12 +264,12 @@ __global__ void __launch_bounds__(kBlock)
     const bool valid = lane < cnt;
     uint64_t key = kEmpty;
     if (valid) {
-      key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << P.inst_off : 0ull;
+      key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << inst_off : 0ull;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const uint64_t b = bits_of(s_pts[w][lane * D + a]);
-        const int idx = key_index(thr + P.thr_off[a], P.span[a], P.kmin[a], P.inv_h, b);
-        key |= (uint64_t)(idx + 1) << P.off[a];
+        const int idx = key_index(thr + thr_off[a], span[a], kmin[a], inv_h, b);
+        key |= (uint64_t)(idx + 1) << off[a];
       }
     }
     __syncwarp();
@@ -289,17 +357,26 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
+cudaError_t launch_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t* thr,
+                        uint64_t thr_cap, uint64_t* dtab, uint32_t* filters, IterState* st,
+                        uint32_t n_st, GridBar* bar, LoopResult* res, cudaStream_t s) {
+  const uint32_t vec = 2 * kFilterWords / 4;
+  k_plan<<<32, kBlock, 0, s>>>(d, h, n, B, fl, thr, thr_cap, dtab,
+                               reinterpret_cast<uint4*>(filters), vec, st, n_st, bar, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s) {
   const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * 6u);
   const bool vec_ok = ((uintptr_t)pts & 15u) == 0;
   if (f32) {
-    GS_DISPATCH_D(P.d, k_bin<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, P, thr, T0,
+    GS_DISPATCH_D(d, k_bin<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, thr, T0,
                                                             mask0, maxcells, slot0, fl, vec_ok,
                                                             offsets, B));
   } else {
-    GS_DISPATCH_D(P.d, k_bin<D, double><<<g, kBlock, 0, s>>>((const double*)pts, n, P, thr, T0,
+    GS_DISPATCH_D(d, k_bin<D, double><<<g, kBlock, 0, s>>>((const double*)pts, n, thr, T0,
                                                              mask0, maxcells, slot0, fl, vec_ok,
                                                              offsets, B));
   }
@@ -337,7 +414,22 @@ cudaError_t launch_modes_tail(const LoopArgs& a, uint32_t k, int T, cudaStream_t
   return a.mixed ? launch_modes_tail_fp32(a, k, T, s) : launch_modes_tail_fp64(a, k, T, s);
 }
 
-int loop_grid(int d, bool mixed) { return mixed ? loop_grid_fp32(d) : loop_grid_fp64(d); }
+// The loop kernel's co-resident grid for (device, d, precision), found once
+// (function attributes and occupancy queries cost tens of microseconds).
+int loop_grid(int d, bool mixed) {
+  constexpr int kDevices = 64;
+  static std::atomic<int> cache[kDevices][kMaxD + 1][2];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (dev < 0 || dev >= kDevices || d < 1 || d > kMaxD)
+    return mixed ? loop_grid_fp32(d) : loop_grid_fp64(d);
+  std::atomic<int>& c = cache[dev][d][mixed ? 1 : 0];
+  int g = c.load(std::memory_order_acquire);
+  if (g > 0) return g;
+  g = mixed ? loop_grid_fp32(d) : loop_grid_fp64(d);
+  if (g > 0) c.store(g, std::memory_order_release);
+  return g;
+}
 
 cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s) {
   return a.mixed ? launch_loop_fp32(a, grid, s) : launch_loop_fp64(a, grid, s);

@@ -97,7 +97,15 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
                          cudaStream_t s);
 // Binning, first pass.  offsets (device, B + 1 entries) give the points of
 // each instance of a batched run (B > 1); ignored when B == 1.
-cudaError_t launch_bin(const void* pts, bool f32, int64_t n, const Plan& P, const int64_t* thr,
+// The plan from the key range in fl, into fl->plan (and fl->plan_status),
+// with the face table (at most thr_cap entries) and the neighbour offsets;
+// also clears the loop kernel's start state: both occupancy filters
+// (2 * kFilterWords words), n_st level states, the grid barrier, the result.
+cudaError_t launch_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t* thr,
+                        uint64_t thr_cap, uint64_t* dtab, uint32_t* filters, IterState* st,
+                        uint32_t n_st, GridBar* bar, LoopResult* res, cudaStream_t s);
+// Binning with the plan in fl->plan (nothing runs unless fl->plan_status is 0).
+cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s);
 

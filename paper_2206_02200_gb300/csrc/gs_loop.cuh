@@ -24,6 +24,10 @@ namespace gs {
 
 namespace {
 
+// The plan of the call (DevFlags::plan), copied into shared memory by every
+// block of the loop kernel at its start.
+__shared__ Plan g_plan;
+
 // ---------------------------------------------------------------------------
 // Software grid barrier for the cooperative loop kernel.  All blocks are
 // co-resident (cooperative launch).  Block leaders arrive on a counter; the
@@ -319,7 +323,7 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
     uint32_t cur = s[0];
     u128 V[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], A.P.L[a], inexact, werr);
+    for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], g_plan.L[a], inexact, werr);
 #pragma unroll
     for (int e = 1; e < E; ++e) {
       if (s[e] != cur) {
@@ -329,7 +333,7 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
         for (int a = 0; a < D; ++a) V[a] = 0;
       }
 #pragma unroll
-      for (int a = 0; a < D; ++a) V[a] += to_fixed(raw[e][a], A.P.L[a], inexact, werr);
+      for (int a = 0; a < D; ++a) V[a] += to_fixed(raw[e][a], g_plan.L[a], inexact, werr);
     }
     // the lanes' last runs: lane l ends with the sum of [l, end of its segment)
     const uint32_t prev = __shfl_up_sync(kFull, cur, 1);
@@ -374,7 +378,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
       r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        r[1 + a] = settle_sum(T0.acc + ((size_t)id * D + a) * 4, A.P.L[a], inexact, werr);
+        r[1 + a] = settle_sum(T0.acc + ((size_t)id * D + a) * 4, g_plan.L[a], inexact, werr);
       G.id[sa] = id;
       G.list[id] = sa;
     }
@@ -412,7 +416,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   const LevelTable M = A.tab[(t + 1) % 3];
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
-  const int nprobe = A.P.nprobe, center = A.P.center;
+  const int nprobe = g_plan.nprobe, center = g_plan.center;
   // the level's occupancy filter, into shared memory; the filter of level
   // t-1 is cleared for level t+1
   extern __shared__ uint4 s_dyn[];
@@ -447,7 +451,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
     uint32_t inst = 0;
     bool live = true;
     if (BT) {
-      inst = (uint32_t)(key >> A.P.inst_off);
+      inst = (uint32_t)(key >> g_plan.inst_off);
       live = A.I.done[t & 1][inst] == 0;
     }
     uint32_t Dc = 0;
@@ -506,21 +510,21 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
       for (int a = 0; a < D; ++a)
         if (a == glane) {
           Na = N[a];
-          La = A.P.L[a];
-          off = A.P.off[a];
-          span = A.P.span[a];
-          toff = A.P.thr_off[a];
-          kmin = A.P.kmin[a];
+          La = g_plan.L[a];
+          off = g_plan.off[a];
+          span = g_plan.span[a];
+          toff = g_plan.thr_off[a];
+          kmin = g_plan.kmin[a];
         }
       const double sv = div_round(Na, Dc, La, inexact);
-      const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
+      const int idx = key_index(A.thr + toff, span, kmin, g_plan.inv_h, bits_of(sv));
       field = (uint64_t)(idx + 1) << off;
       V = to_fixed(bits_of(sv), La, inexact, werr);
     }
     if (!BT || live) {
 #pragma unroll
       for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
-      if (BT) field |= (key >> A.P.inst_off) << A.P.inst_off;  // the instance field
+      if (BT) field |= (key >> g_plan.inst_off) << g_plan.inst_off;  // the instance field
     }
     const bool nbg = BT && (__ballot_sync(gmask, nbc) & gmask) != 0u;
     // iv: merge into the slot of the new key
@@ -582,7 +586,7 @@ __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& i
     uint64_t key = M.key[s];
     bool restored = false;
     if (BT) {
-      const uint32_t inst = (uint32_t)(key >> A.P.inst_off);
+      const uint32_t inst = (uint32_t)(key >> g_plan.inst_off);
       if (!A.I.done[t & 1][inst] && !A.I.nbf[t & 1][inst]) {
         const uint32_t j = M.id[s];
         const ulonglong2* o = G.row + (size_t)G.list[j] * (D + 1);
@@ -599,7 +603,7 @@ __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& i
     if (!restored) {
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, A.P.L[a], inexact, werr);
+        r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, g_plan.L[a], inexact, werr);
     }
     nx.key[id] = key;
     nx.cnt[id] = (uint32_t)r[0].x;
@@ -869,7 +873,7 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
         if (cur != kNone) {
           const uint64_t key = A.T0.key[cur];
 #pragma unroll
-          for (int a = 0; a < D; ++a) org[a] = (float)face_of(A.P, A.thr, key, a);
+          for (int a = 0; a < D; ++a) org[a] = (float)face_of(g_plan, A.thr, key, a);
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) V[a] = FF();
@@ -965,8 +969,8 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
   float* macc = reinterpret_cast<float*>(M.acc);
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
-  const int nprobe = A.P.nprobe, center = A.P.center;
-  const float h = A.P.h32;
+  const int nprobe = g_plan.nprobe, center = g_plan.center;
+  const float h = g_plan.h32;
   extern __shared__ uint4 s_dyn[];
   uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
   const int lg = filter_log2(m);
@@ -996,7 +1000,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
     uint32_t inst = 0;
     bool live = true;
     if (BT) {
-      inst = (uint32_t)(key >> A.P.inst_off);
+      inst = (uint32_t)(key >> g_plan.inst_off);
       live = A.I.done[t & 1][inst] == 0;
     }
     uint32_t Dc = 0;
@@ -1065,7 +1069,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         rel[a] = N[a].hi / fD + N[a].lo / fD;
         const int qa = rel[a] < 0.f ? -1 : (rel[a] >= h ? 1 : 0);
         near = near || fabsf(rel[a]) < kFaceBand * h || fabsf(rel[a] - h) < kFaceBand * h;
-        nk += (uint64_t)(int64_t)qa << A.P.off[a];
+        nk += (uint64_t)(int64_t)qa << g_plan.off[a];
       }
       field = nk;
     }
@@ -1077,7 +1081,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       for (int a = 0; a < D; ++a) N64[a] = 0.0;
       double org[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) org[a] = (double)(float)face_of(A.P, A.thr, key, a);
+      for (int a = 0; a < D; ++a) org[a] = (double)(float)face_of(g_plan, A.thr, key, a);
       for (int p = glane; p < nprobe; p += GS) {
         const uint64_t qk = key + __ldg(&A.dtab[p]);
         const uint32_t sl = row_find<D>(grow, mask, qk);
@@ -1086,7 +1090,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         const double cn = (double)r[2];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          const double of = (double)(float)face_of(A.P, A.thr, qk, a);
+          const double of = (double)(float)face_of(g_plan, A.thr, qk, a);
           N64[a] += cn * ((of - org[a]) + (double)__uint_as_float(r[3 + a]));
         }
       }
@@ -1094,23 +1098,23 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       for (int o = GS / 2; o > 0; o >>= 1)
 #pragma unroll
         for (int a = 0; a < D; ++a) N64[a] += __shfl_xor_sync(gmask, N64[a], o);
-      uint64_t nk = (key >> A.P.inst_off) << A.P.inst_off;
+      uint64_t nk = (key >> g_plan.inst_off) << g_plan.inst_off;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const double xa = org[a] + N64[a] / (double)Dc;
-        const int64_t* thr = A.thr + A.P.thr_off[a];
-        int idx = key_index(thr, A.P.span[a], A.P.kmin[a], A.P.inv_h,
+        const int64_t* thr = A.thr + g_plan.thr_off[a];
+        int idx = key_index(thr, g_plan.span[a], g_plan.kmin[a], g_plan.inv_h,
                             (uint64_t)__double_as_longlong(xa));
         // a centroid this close below a face is taken to lie on it: the
         // float32 state cannot tell such a value from an exact tie, which the
         // exact path assigns to the upper cell
-        if (idx + 1 < A.P.span[a]) {
+        if (idx + 1 < g_plan.span[a]) {
           const int64_t o = __ldg(&thr[idx + 1]);
           const double fnext =
               __longlong_as_double((long long)(o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFFll)));
           if (fnext - xa < (double)kTieBand * (double)h) ++idx;
         }
-        nk |= (uint64_t)(idx + 1) << A.P.off[a];
+        nk |= (uint64_t)(idx + 1) << g_plan.off[a];
         // the centroid relative to its own cell's lower face, in float32
         rel[a] = (float)(xa - org[a]);
       }
@@ -1146,9 +1150,9 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         if (BT && !live) {
           contrib = (float)cj * __uint_as_float(grow[(size_t)G.list[j] * W + 3 + a]);
         } else {
-          const int top = a == 0 ? A.P.inst_off : A.P.off[a - 1];
-          const uint64_t fm = (1ull << (top - A.P.off[a])) - 1ull;
-          const int qa = (int)((field >> A.P.off[a]) & fm) - (int)((key >> A.P.off[a]) & fm);
+          const int top = a == 0 ? g_plan.inst_off : g_plan.off[a - 1];
+          const uint64_t fm = (1ull << (top - g_plan.off[a])) - 1ull;
+          const int qa = (int)((field >> g_plan.off[a]) & fm) - (int)((key >> g_plan.off[a]) & fm);
           contrib = (float)cj * (rel[a] - (float)qa * h);
         }
       }
@@ -1190,7 +1194,7 @@ __device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
     const uint32_t cnt = r[2];
     bool restored = false;
     if (BT) {
-      const uint32_t inst = (uint32_t)(key >> A.P.inst_off);
+      const uint32_t inst = (uint32_t)(key >> g_plan.inst_off);
       if (!A.I.done[t & 1][inst] && !A.I.nbf[t & 1][inst]) {
         const uint32_t j = M.id[s];
         const uint32_t* o = grow + (size_t)G.list[j] * W;
@@ -1258,10 +1262,12 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
 // The arithmetic is that of phase_update and phase_compact (exact sums
 // rounded once); a merged cell's sum is added over its members.
 
-// Largest level handed to the one-block tail.  A tail step costs about
-// m^2 d / 512 pair tests per thread of one SM; up to a few hundred cells that
-// is less than the grid barriers and dependent L2 loads of a multi-block step.
-constexpr uint32_t kTailEnter = 256;
+// Largest level handed to the one-block tail.  A tail step makes m^2 pair
+// tests on one SM; measured on GB300 (d = 3 and 5), it beats a multi-block
+// step (grid barriers, dependent L2 loads) up to about 110 cells and loses
+// from about 150 (14 against 20 us at 107 cells, 31 against 21 us at 149).
+constexpr uint32_t kTailEnter = 128;
+constexpr int kTailMax = 256;  // cells the tail's shared memory holds
 constexpr int kTailLanes = 8;  // lanes comparing one cell against the level
 
 constexpr size_t tail_bytes(int d, int mx) {
@@ -1277,7 +1283,7 @@ constexpr size_t tail_bytes(int d, int mx) {
 // a shared-memory access.
 template <int D>
 struct TailMem {
-  static constexpr int Mx = (int)kTailEnter;
+  static constexpr int Mx = kTailMax;
   static constexpr size_t kSum = (size_t)Mx * D * 16, kKey = (size_t)Mx * 8,
                           kCnt = (size_t)Mx * 4;
   char* p;
@@ -1305,7 +1311,8 @@ struct TailMem {
                                        (size_t)which * Mx * 2);
   }
 };
-static_assert(tail_bytes(kMaxD, (int)kTailEnter) <= (size_t)kFilterWords * 4,
+static_assert(kTailEnter <= (uint32_t)kTailMax &&
+                  tail_bytes(kMaxD, kTailMax) <= (size_t)kFilterWords * 4,
               "the tail's shared memory must fit in the filter's");
 
 // Width of axis a's key field (axis 0 most significant).
@@ -1386,8 +1393,8 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
       const uint64_t k = key[i];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const int w = field_width(A.P, a);
-        const uint64_t f = k >> A.P.off[a];
+        const int w = field_width(g_plan, a);
+        const uint64_t f = k >> g_plan.off[a];
         F[a * Mx + i] = (int32_t)(w >= 64 ? f : (f & ((1ull << w) - 1ull)));
       }
       nk[i] = 0;
@@ -1443,14 +1450,14 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
 #pragma unroll
       for (int a = 0; a < D; ++a)
         if (a == ax) {
-          La = A.P.L[a];
-          off = A.P.off[a];
-          span = A.P.span[a];
-          toff = A.P.thr_off[a];
-          kmin = A.P.kmin[a];
+          La = g_plan.L[a];
+          off = g_plan.off[a];
+          span = g_plan.span[a];
+          toff = g_plan.thr_off[a];
+          kmin = g_plan.kmin[a];
         }
       const double sv = div_round(as_u128(V[w]), dc[j], La, inexact);
-      const int idx = key_index(A.thr + toff, span, kmin, A.P.inv_h, bits_of(sv));
+      const int idx = key_index(A.thr + toff, span, kmin, g_plan.inv_h, bits_of(sv));
       atomicOr((unsigned long long*)&nk[j], (unsigned long long)(idx + 1) << off);
       V[w] = pack(to_fixed(bits_of(sv), La, inexact, werr));
     }
@@ -1540,7 +1547,7 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
         for (int a = 0; a < D; ++a)
           if (a == glane) {
             Sa = Sx[a];
-            La = A.P.L[a];
+            La = g_plan.L[a];
           }
         const double v = round_fixed(Sa, La, inexact);
         S.sum(nxtb)[(size_t)id * D + glane] = pack(to_fixed(bits_of(v), La, inexact, werr));
@@ -1603,8 +1610,12 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   SegClock clk;
   clk.start();
 
-  // binning overflowed its table: nothing to do (the host regrows it and
-  // runs binning and this kernel again)
+  // no valid plan (the host reads the status), or binning overflowed its
+  // table (the host regrows it and runs binning and this kernel again):
+  // nothing to do
+  if (*(volatile uint32_t*)&A.fl->plan_status != kPlanOK) return;
+  if (threadIdx.x == 0) g_plan = A.fl->plan;
+  __syncthreads();
   if (*(volatile uint32_t*)&A.fl->err & (kErrOverflow | kErrTableFull)) {
     if (tid == 0) A.res->bin_failed = 1;
     return;
@@ -1647,7 +1658,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     phase_level0<D>(A, m0, maskA, inexact, werr);
   if (BT) {
     for (uint32_t id = tid; id < m0; id += nth)
-      atomicAdd(&A.I.m0[(uint32_t)(A.cells[0].key[id] >> A.P.inst_off)], 1u);
+      atomicAdd(&A.I.m0[(uint32_t)(A.cells[0].key[id] >> g_plan.inst_off)], 1u);
   }
   if (!grid_sync(A.bar, A.fl)) return;
   clk.lap(kSegLevel0);
@@ -1762,7 +1773,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       }
       const Cells c = A.cells[T & 1];
       for (uint32_t j = tid; j < k; j += nth)
-        atomicAdd(&A.I.k[(uint32_t)(c.key[j] >> A.P.inst_off)], 1u);
+        atomicAdd(&A.I.k[(uint32_t)(c.key[j] >> g_plan.inst_off)], 1u);
     }
   }
   if (!grid_sync(A.bar, A.fl)) return;
@@ -1811,7 +1822,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     for (uint32_t cc = tid; cc < m0; cc += nth) {
       const uint32_t r = A.forest[cc] - base;
       uint32_t label = A.rank[r];
-      if (BT) label -= A.I.koff[(uint32_t)(c.key[r] >> A.P.inst_off)];
+      if (BT) label -= A.I.koff[(uint32_t)(c.key[r] >> g_plan.inst_off)];
       A.labslot[A.T0.list[cc]] = label;
     }
     if (!grid_sync(A.bar, A.fl)) return;
@@ -1820,9 +1831,9 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     const bool write = (int64_t)k <= A.modes_cap;
     for (uint32_t r = tid; r < k; r += nth) {
       if (F32)
-        mode_and_release32<D>(G, A.P, A.thr, c.key, r, A.rank[r], A.modes, write);
+        mode_and_release32<D>(G, g_plan, A.thr, c.key, r, A.rank[r], A.modes, write);
       else
-        mode_and_release<D>(G, A.P, r, A.rank[r], A.modes, write, inexact);
+        mode_and_release<D>(G, g_plan, r, A.rank[r], A.modes, write, inexact);
     }
   }
   clk.lap(kSegLabels);

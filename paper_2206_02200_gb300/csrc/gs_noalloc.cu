@@ -136,6 +136,8 @@ struct StaticWorkspace : public Workspace {
     b.flags = reinterpret_cast<DevFlags*>(base);  // where layout() puts them
     return GS_OK;
   }
+  size_t plan_thr_cap() const override { return kThrMax; }
+
   gs_status prepare(int64_t n, int d, int max_iter, size_t thr_words, int nprobe,
                     uint64_t m_bound, cudaStream_t s, Bufs& b, std::string*) override {
     if (thr_words > kThrMax || (size_t)nprobe > kProbeMax) return GS_E_SCRATCH;

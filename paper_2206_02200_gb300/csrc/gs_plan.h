@@ -38,6 +38,22 @@ struct IterState {
   uint32_t base;    // first node of level t in the forest of merges
 };
 
+// Plan status (DevFlags::plan_status).
+constexpr uint32_t kPlanOK = 0;
+constexpr uint32_t kPlanNonFinite = 1;  // a coordinate is NaN or infinite
+constexpr uint32_t kPlanRangeH = 2;     // a coordinate divided by h exceeds 2^52
+constexpr uint32_t kPlanSpan = 3;       // more than 2^22 cells along one axis
+constexpr uint32_t kPlanBits = 4;       // the packed key needs more than 63 bits
+constexpr uint32_t kPlanTable = 5;      // face table above the device-side capacity
+
+// Sizes that follow from a plan.
+struct PlanSizes {
+  uint64_t thr_words;  // face-table entries (sum over axes of span + 1)
+  uint64_t span_prod;  // product of the spans (saturating above 2^40)
+  int32_t total_bits;  // width of the packed key
+  int32_t pad;
+};
+
 // Global device flags and counters of a call.
 struct DevFlags {
   uint32_t err;                 // kErr* bits
@@ -48,6 +64,13 @@ struct DevFlags {
   long long min_ord[kMaxD];     // order code of min_i x_ia
   long long max_ord[kMaxD];     // order code of max_i x_ia
   unsigned long long maxabs[kMaxD];  // bits of max_i |x_ia|
+  // the plan of the call (written by k_plan, or by the host), read by
+  // binning and the loop kernel; nothing after the key range runs unless
+  // plan_status is 0
+  Plan plan;
+  PlanSizes plan_sizes;
+  uint32_t plan_status;
+  uint32_t pad;
 };
 
 // Segments of the loop kernel timed on the device clock by block 0 (between

@@ -260,6 +260,15 @@ def test_key_range_error():
     assert e.value.status == gridshift.GS_E_KEYRANGE
 
 
+@pytest.mark.parametrize("d,width", [(1, 200_000.0), (2, 40_000.0)])
+def test_face_table_above_device_capacity(d, width):
+    # more than 2^16 face-table entries in all: the plan is made on the host
+    X = np.random.default_rng(11).uniform(0.0, width, size=(4000, d))
+    check_parity(X, 1.0)
+    X[:2000] = X[:2000] * 1e-3 + 5.0  # and a dense corner that merges
+    check_parity(X, 1.0)
+
+
 def test_capacity_error_leaves_labels_valid():
     X = synth.image_features(synth.voronoi_image(64, 64, 8, 8.0, seed=3))
     ref = oracle.fit(X, 16.0, 50)
