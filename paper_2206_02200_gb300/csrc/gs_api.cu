@@ -173,7 +173,7 @@ struct CtxWorkspace : public Workspace {
   BinTableBuf t0;
   LevelTableBuf tab[3];
   CellBuf cells[2];
-  DBuf<uint32_t> pslot[2], forest, forest2, labslot, rank, filter;
+  DBuf<uint32_t> pslot[2], qlist, forest, forest2, labslot, rank, filter;
   DBuf<uint64_t> skey, skey2;
   DBuf<uint32_t> sval, sval2, shist;
   DBuf<int64_t> offsets;
@@ -293,6 +293,7 @@ struct CtxWorkspace : public Workspace {
       WS_CU(cells[i].ensure(m), "alloc cells");
       WS_CU(pslot[i].ensure(m), "alloc pslot");
     }
+    WS_CU(qlist.ensure((size_t)m * 3), "alloc pencil list");
     WS_CU(forest.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(forest2.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(labslot.ensure(t0.cap), "alloc labslot");
@@ -308,6 +309,7 @@ struct CtxWorkspace : public Workspace {
       b.cells[i] = cells[i].view();
       b.pslot[i] = pslot[i].p;
     }
+    b.qlist = qlist.p;
     b.forest = forest.p;
     b.forest2 = forest2.p;
     b.labslot = labslot.p;
@@ -353,7 +355,7 @@ struct CtxWorkspace : public Workspace {
       cells[i].release();
       pslot[i].release();
     }
-    forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
+    qlist.release(); forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
     offsets.release(); inst.release();
     if (h_flags) cudaFreeHost(h_flags);

@@ -158,6 +158,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.pslot[1] = b.pslot[1];
     L.filter[0] = b.filter;
     L.filter[1] = b.filter + kFilterWords;
+    L.qlist = b.qlist;
     L.forest = b.forest;
     L.forest2 = b.forest2;
     L.labslot = b.labslot;

@@ -72,7 +72,8 @@ struct LoopArgs {
   Cells cells[2];        // cells of alternate levels
   uint32_t* pslot[2];    // merge slot of every cell of alternate levels
   uint32_t* filter[2];   // occupancy filters of alternate levels, kFilterWords each,
-                         // zeroed by the host
+                         // zeroed before the launch
+  uint32_t* qlist;       // 3 x (level-0 cell bound): slots of the pencil set of step 0
   uint32_t* forest;      // parent of every cell of every level, then its final cell
   uint32_t* forest2;     // pointer-jumping buffer
   uint32_t* labslot;     // label of every binning slot
@@ -82,9 +83,9 @@ struct LoopArgs {
   int64_t n;
   double* modes;          // output: k x d modes (written if k <= modes_cap)
   int64_t modes_cap;
-  IterState* st;          // max_iter + 2 levels, zeroed by the host
+  IterState* st;          // max_iter + 2 levels, zeroed before the launch
   DevFlags* fl;
-  GridBar* bar;           // zeroed by the host
+  GridBar* bar;           // zeroed before the launch
   LoopResult* res;
   int max_iter;
   uint32_t rank_max;      // largest k numbered inside the loop kernel

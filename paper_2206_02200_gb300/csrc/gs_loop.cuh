@@ -390,6 +390,101 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
   }
 }
 
+// ---------------------------------------------------------------------------
+// The pencil form of the first update step.  The 3^d-neighbour sums of Eq. 1
+// are sums over v_0 in {-1,0,1} inside sums over the other d - 1 axes, so
+// they are taken in two passes: first, for every position q of the level-0
+// cells dilated by one cell along axis 0 (the pencil set Q), the count and
+// the coordinate sums of the up to three cells q - e_0, q, q + e_0; then, per
+// cell, the sum of those over its 3^(d-1) offsets with v_0 = 0.  The sums are
+// exact integers, so the result is the direct sum's, in about a third of the
+// probes.  Q lives in tab[2] (free during step 0) with its slots listed in
+// qlist, and its keys join the level-0 occupancy filter.
+
+// Minimum level-0 cells for the pencil form (below it the two extra grid
+// barriers cost more than the probes they save).
+constexpr uint32_t kPencilMin = 4096;
+
+// Q's keys: every level-0 cell and its two neighbours along axis 0 (plain
+// runs only: no field above axis 0).
+template <int D>
+__device__ void phase_pencil_keys(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const LevelTable Q = A.tab[2];
+  const Cells c = A.cells[0];
+  const int lg0 = filter_log2(m0);
+  const uint64_t e0 = 1ull << g_plan.off[0];
+  for (uint32_t w = tid; w < 3 * m0; w += nth) {
+    const uint32_t id = w / 3;
+    const uint32_t u = w - 3 * id;  // 0, 1, 2: offsets -1, 0, +1
+    const uint64_t key = c.key[id];
+    // only positions the update probes: axis 0's field in [1, span_0]
+    const int64_t f0 = (int64_t)(key >> g_plan.off[0]) + (int64_t)u - 1;
+    if (f0 < 1 || f0 > g_plan.span[0]) continue;
+    const uint64_t q = key + (u == 0 ? (uint64_t)0 - e0 : u == 2 ? e0 : 0ull);
+    bool won;
+    const uint32_t s = table_insert(Q.key, maskQ, q, won, &A.fl->err);
+    if (s != kNone && won) {
+      const uint32_t j = atomicAdd(&A.st[0].qn, 1u);
+      A.qlist[j] = s;
+      if (u != 1) filter_set(A.filter[0], q, lg0);
+    }
+  }
+}
+
+// Count and coordinate sums of the three cells q - e_0, q, q + e_0 of every
+// q in Q, into Q's row (the layout of a level row).  Plain runs only: no
+// field above axis 0.
+template <int D>
+__device__ void phase_pencil_sums(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const LevelTable G = A.tab[0];
+  const LevelTable Q = A.tab[2];
+  const uint64_t e0 = 1ull << g_plan.off[0];
+  for (uint32_t j = tid; j < qn; j += nth) {
+    const uint32_t s = A.qlist[j];
+    const uint64_t q = Q.key[s];
+    // axis 0's field of a cell lies in [1, span_0]: probe only there (the key
+    // arithmetic then never borrows or carries out of the field)
+    const int64_t f0 = (int64_t)(q >> g_plan.off[0]);
+    const uint64_t keys[3] = {q - e0, q, q + e0};
+    const bool valid[3] = {f0 >= 2, f0 >= 1 && f0 <= g_plan.span[0], f0 + 1 <= g_plan.span[0]};
+    uint32_t sl[3];
+    table_find_many<3>(G.key, maskA, keys, valid, sl);
+    uint64_t cnt = 0;
+    u128 N[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) N[a] = 0;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (sl[u] == kNone) continue;
+      const ulonglong2* r = G.row + (size_t)sl[u] * (D + 1);
+      cnt += r[0].x;
+#pragma unroll
+      for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
+    }
+    ulonglong2* r = Q.row + (size_t)s * (D + 1);
+    r[0] = make_ulonglong2(cnt, 0ull);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r[1 + a] = pack(N[a]);
+  }
+}
+
+// Q's table back to clean (keys empty, counts zero) once step 0 has read it.
+template <int D>
+__device__ void pencil_release(const LoopArgs& A, uint32_t qn) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const LevelTable Q = A.tab[2];
+  for (uint32_t j = tid; j < qn; j += nth) {
+    const uint32_t s = A.qlist[j];
+    Q.key[s] = kEmpty;
+    Q.row[(size_t)s * (D + 1)].x = 0;
+  }
+}
+
 // One update step t for every cell of level t (table tab[t % 3]):
 //   ii)  D = sum of the counts and N = sum of the coordinate sums over the
 //        3^d neighbours present (Eq. 1-2, all cells reading level t: Eq. 6),
@@ -402,21 +497,27 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
 // the run, the merge table is cleared instead of used.
 // For t > 0 the same phase links every cell of level t-1 to its cell of level
 // t (the union of resident sets of Eq. 4) and clears level t-1's table.
+// With pen (step 0 only) the sums over the 3^d neighbours are taken as sums
+// over the 3^(d-1) offsets with v_0 = 0 of the pencil table tab[2] (mask
+// `mask`), each entry of which already holds the three cells along axis 0.
+// A neighbour v != 0 is present iff D exceeds the cell's own count.
 template <int D, int GS, bool BT>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
-                             unsigned& inexact, unsigned& werr) {
+                             unsigned& inexact, unsigned& werr, bool pen = false) {
   constexpr int U = ProbeBatch<D, GS>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
   const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / GS;
   const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
-  const LevelTable G = A.tab[t % 3];
+  const LevelTable G = A.tab[pen ? 2 : t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
-  const int nprobe = g_plan.nprobe, center = g_plan.center;
+  // probes pbase .. pbase + np - 1 of the offset table (axis 0 the slowest
+  // digit: v_0 = 0 is its middle third)
+  const int np = pen ? g_plan.nprobe / 3 : g_plan.nprobe, pbase = pen ? np : 0;
   // the level's occupancy filter, into shared memory; the filter of level
   // t-1 is cleared for level t+1
   extern __shared__ uint4 s_dyn[];
@@ -455,20 +556,19 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
       live = A.I.done[t & 1][inst] == 0;
     }
     uint32_t Dc = 0;
-    bool nbc = false;
     u128 N[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) N[a] = 0;
-    for (int p0 = glane; live && p0 < nprobe; p0 += GS * U) {
+    for (int p0 = glane; live && p0 < np; p0 += GS * U) {
       uint64_t q[U];
       bool v[U];
       uint32_t sl[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int p = p0 + u * GS;
-        q[u] = key + (p < nprobe ? __ldg(&A.dtab[p]) : 0ull);
+        q[u] = key + (p < np ? __ldg(&A.dtab[pbase + p]) : 0ull);
         const uint32_t fb = filter_bit(q[u], lg);
-        v[u] = p < nprobe && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
+        v[u] = p < np && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
       }
       table_find_many<U>(G.key, mask, q, v, sl);
 #pragma unroll
@@ -478,10 +578,8 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         Dc += (uint32_t)r[0].x;
 #pragma unroll
         for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
-        if (p0 + u * GS != center) nbc = true;
       }
     }
-    any_nb = any_nb || nbc;
 #pragma unroll
     for (int o = GS / 2; o > 0; o >>= 1) {
       Dc += __shfl_xor_sync(gmask, Dc, o);
@@ -493,6 +591,9 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         N[a] += (u128)lo | ((u128)hi << 64);
       }
     }
+    // a neighbour other than the cell itself (counts are at least 1)
+    const bool nbc = live && Dc > cj;
+    any_nb = any_nb || nbc;
     // lane a < d: coordinate a of the centroid, its key field, its fixed value
     uint64_t field = 0;
     u128 V = 0;
@@ -526,7 +627,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
       for (int o = GS / 2; o > 0; o >>= 1) field |= __shfl_xor_sync(gmask, field, o);
       if (BT) field |= (key >> g_plan.inst_off) << g_plan.inst_off;  // the instance field
     }
-    const bool nbg = BT && (__ballot_sync(gmask, nbc) & gmask) != 0u;
+    const bool nbg = BT && nbc;
     // iv: merge into the slot of the new key
     uint32_t ms = kNone;
     if (glane == 0) {
@@ -1663,6 +1764,22 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   if (!grid_sync(A.bar, A.fl)) return;
   clk.lap(kSegLevel0);
 
+  // the pencil form of step 0 (FP64 plain runs with enough cells)
+  bool pen = false;
+  uint32_t maskQ = 0, qn = 0;
+  if constexpr (!F32 && !BT && D >= 3) {
+    if (m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr) {
+      pen = true;
+      maskQ = mask_for(3 * m0, A.capAB);
+      phase_pencil_keys<D>(A, m0, maskQ);
+      if (!grid_sync(A.bar, A.fl)) return;
+      qn = vst[0].qn;
+      phase_pencil_sums<D>(A, qn, maskA);
+      if (!grid_sync(A.bar, A.fl)) return;
+      clk.lap(kSegUpdateFirst);
+    }
+  }
+
   int t = 0;
   uint32_t m = m0, mask = maskA, base = 0, m_prev = 0, base_prev = 0;
   unsigned long long cell_iters = 0;
@@ -1703,16 +1820,20 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       else
         phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb);
     } else {
+      const bool pt = pen && t == 0;
       if (GSmin < 32 && m > (nth >> 5))
-        phase_update<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact,
-                                   werr);
+        phase_update<D, GSmin, BT>(A, t, m, pt ? maskQ : mask, maskM, m_prev, base_prev, base,
+                                   any_nb, inexact, werr, pt);
       else
-        phase_update<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, inexact,
-                                werr);
+        phase_update<D, 32, BT>(A, t, m, pt ? maskQ : mask, maskM, m_prev, base_prev, base,
+                                any_nb, inexact, werr, pt);
     }
     if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
     if (!grid_sync(A.bar, A.fl)) return;
     clk.lap_step(t == 0 ? kSegUpdateFirst : kSegUpdateRest, t, A.res);
+    // the pencil table is read: back to clean (the next use of tab[2], as
+    // step 1's merge table, is a grid barrier away)
+    if (!F32 && pen && t == 0) pencil_release<D>(A, qn);
     if (!vst[t].has_nb) {
       converged = true;
       break;

@@ -91,6 +91,7 @@ size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, s
     B.cells[i].cnt = c.take<uint32_t>(M);
     B.pslot[i] = c.take<uint32_t>(M);
   }
+  B.qlist = c.take<uint32_t>((size_t)M * 3);
   B.forest = c.take<uint32_t>((size_t)M * (max_iter + 1));
   B.forest2 = c.take<uint32_t>((size_t)M * (max_iter + 1));
   B.labslot = c.take<uint32_t>(cap);

@@ -108,6 +108,17 @@ def test_uniform_noise_many_cells(seed):
     check_parity(X, float(rng.uniform(2, 9)))
 
 
+@pytest.mark.parametrize("d,n,side", [(3, 60_000, 25.0), (4, 60_000, 12.0), (5, 60_000, 12.0),
+                                        (6, 60_000, 6.0), (7, 15_000, 4.0), (8, 12_000, 3.0)])
+def test_pencil_first_step(d, n, side):
+    # enough level-0 cells (>= 4096) for the two-pass form of the first update,
+    # dense enough that most neighbourhoods are full, with edges on every axis
+    rng = np.random.default_rng(77 + d)
+    X = rng.uniform(0.0, side, size=(n, d))
+    X[: n // 4] = rng.normal(3.0, 0.7, size=(n // 4, d))
+    check_parity(X, 1.0, max_iter=8)
+
+
 def test_unaligned_input():
     # points starting 8 bytes (float64) or 4 bytes (float32) past a 16-byte
     # boundary take the scalar load paths
