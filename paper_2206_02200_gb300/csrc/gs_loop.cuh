@@ -1047,15 +1047,99 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
   }
 }
 
+// The pencil form of step 0 in float32 (as phase_pencil_keys and
+// phase_pencil_sums): Q's rows hold the key, the count of the up to three
+// cells q - e_0, q, q + e_0, and their count-weighted mean offset from q's
+// lower face.
+template <int D>
+__device__ void phase_pencil_keys32(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
+  constexpr int W = RowW<D>::value;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
+  const Cells c = A.cells[0];
+  const int lg0 = filter_log2(m0);
+  const uint64_t e0 = 1ull << g_plan.off[0];
+  for (uint32_t w = tid; w < 3 * m0; w += nth) {
+    const uint32_t id = w / 3;
+    const uint32_t u = w - 3 * id;  // 0, 1, 2: offsets -1, 0, +1
+    const uint64_t key = c.key[id];
+    const int64_t f0 = (int64_t)(key >> g_plan.off[0]) + (int64_t)u - 1;
+    if (f0 < 1 || f0 > g_plan.span[0]) continue;
+    const uint64_t q = key + (u == 0 ? (uint64_t)0 - e0 : u == 2 ? e0 : 0ull);
+    bool won;
+    const uint32_t s = row_insert<W>(qrow, maskQ, q, won, &A.fl->err);
+    if (s != kNone && won) {
+      const uint32_t j = atomicAdd(&A.st[0].qn, 1u);
+      A.qlist[j] = s;
+      if (u != 1) filter_set(A.filter[0], q, lg0);
+    }
+  }
+}
+
+template <int D>
+__device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
+  constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  const uint32_t* grow = reinterpret_cast<const uint32_t*>(A.tab[0].row);
+  uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
+  const uint64_t e0 = 1ull << g_plan.off[0];
+  const float h = g_plan.h32;
+  for (uint32_t j = tid; j < qn; j += nth) {
+    const uint32_t s = A.qlist[j];
+    uint32_t* r = qrow + (size_t)s * W;
+    const uint64_t q = *reinterpret_cast<const unsigned long long*>(r);
+    const int64_t f0 = (int64_t)(q >> g_plan.off[0]);
+    const uint64_t keys[3] = {q - e0, q, q + e0};
+    const bool valid[3] = {f0 >= 2, f0 >= 1 && f0 <= g_plan.span[0], f0 + 1 <= g_plan.span[0]};
+    uint32_t sl[3];
+    uint4 dat[3][NL];
+    row_find_many<D, 3>(grow, maskA, keys, valid, sl, dat);
+    uint32_t cnt = 0;
+    KS S[D];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (sl[u] == kNone) continue;
+      const uint32_t cn = row_word(dat[u], 2);
+      const float fc = (float)cn;
+      cnt += cn;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        S[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) + (a == 0 ? (float)(u - 1) * h : 0.f)));
+    }
+    const float fC = (float)cnt;
+    r[2] = cnt;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const FF v = S[a].ff();
+      r[3 + a] = __float_as_uint(v.hi / fC + v.lo / fC);
+    }
+  }
+}
+
+template <int D>
+__device__ void pencil_release32(const LoopArgs& A, uint32_t qn) {
+  constexpr int W = RowW<D>::value;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
+  for (uint32_t j = tid; j < qn; j += nth) row_release(qrow + (size_t)A.qlist[j] * W);
+}
+
 // One update step t (float32), as phase_update: Eq. 1-2 over the neighbours
 // in float-float, centroid relative to the cell's lower face, new key, and
 // the count-weighted centroid merged (Eq. 3-4) relative to the new cell's
 // lower face.  A centroid within kFaceBand * h of a face is recomputed in
-// float64 from the same neighbours and its key decided exactly.
+// float64 from the same neighbours and its key decided exactly.  With pen
+// (step 0 only) the neighbour sums come from the pencil rows of tab[2] (mask
+// maskQ) over the 3^(d-1) offsets with v_0 = 0; the float64 recheck still
+// reads the level's own rows.
 template <int D, int GS, bool BT>
 __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t mask,
                                uint32_t maskM, uint32_t m_prev, uint32_t base_prev,
-                               uint32_t base, bool& any_nb) {
+                               uint32_t base, bool& any_nb, bool pen = false,
+                               uint32_t maskQ = 0) {
   constexpr int U = ProbeBatch<D, GS>::value;
   constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
   const int lane = threadIdx.x & 31;
@@ -1066,11 +1150,16 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
   const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
   const uint32_t* grow = reinterpret_cast<const uint32_t*>(G.row);
+  // the rows the neighbour sums read: the level's, or the pencil rows
+  const uint32_t* prow = reinterpret_cast<const uint32_t*>(A.tab[pen ? 2 : t % 3].row);
+  const uint32_t maskP = pen ? maskQ : mask;
   uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);  // rows with the key inside (RowW)
   float* macc = reinterpret_cast<float*>(M.acc);
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
-  const int nprobe = g_plan.nprobe, center = g_plan.center;
+  const int nprobe = g_plan.nprobe;
+  // probes pbase .. pbase + np - 1 of the offset table (v_0 = 0: the middle third)
+  const int np = pen ? nprobe / 3 : nprobe, pbase = pen ? np : 0;
   const float h = g_plan.h32;
   extern __shared__ uint4 s_dyn[];
   uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
@@ -1105,9 +1194,8 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       live = A.I.done[t & 1][inst] == 0;
     }
     uint32_t Dc = 0;
-    bool nbc = false;
     KS Nk[D];
-    for (int p0 = glane; live && p0 < nprobe; p0 += GS * U) {
+    for (int p0 = glane; live && p0 < np; p0 += GS * U) {
       uint64_t q[U];
       bool v[U];
       uint32_t sl[U];
@@ -1115,11 +1203,11 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int p = p0 + u * GS;
-        q[u] = key + (p < nprobe ? __ldg(&A.dtab[p]) : 0ull);
+        q[u] = key + (p < np ? __ldg(&A.dtab[pbase + p]) : 0ull);
         const uint32_t fb = filter_bit(q[u], lg);
-        v[u] = p < nprobe && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
+        v[u] = p < np && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
       }
-      row_find_many<D, U>(grow, mask, q, v, sl, dat);
+      row_find_many<D, U>(prow, maskP, q, v, sl, dat);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (sl[u] == kNone) continue;
@@ -1128,16 +1216,14 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         const float fc = (float)cn;
         Dc += cn;
         // the probe's offset v in {-1, 0, 1}^d: 2 bits per axis, v_a + 1
-        const uint32_t vp = __ldg(&A.vpack[p]);
+        const uint32_t vp = __ldg(&A.vpack[pbase + p]);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const float dv = (float)((int)((vp >> (2 * a)) & 3u) - 1);
           Nk[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) + dv * h));
         }
-        if (p != center) nbc = true;
       }
     }
-    any_nb = any_nb || nbc;
     FF N[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) N[a] = Nk[a].ff();
@@ -1154,6 +1240,9 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       N[a].hi = __shfl_sync(gmask, N[a].hi, 0, GS);
       N[a].lo = __shfl_sync(gmask, N[a].lo, 0, GS);
     }
+    // a neighbour other than the cell itself (counts are at least 1)
+    const bool nbc = live && Dc > cj;
+    any_nb = any_nb || nbc;
     // centroid relative to the lower face; move q_a in {-1, 0, 1} per axis
     uint64_t field = 0;
     float rel[D];
@@ -1222,7 +1311,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       field = nk;
       if (glane == 0) atomicAdd(&A.fl->rechecks, 1ull);
     }
-    const bool nbg = BT && (__ballot_sync(gmask, nbc) & gmask) != 0u;
+    const bool nbg = BT && nbc;
     uint32_t ms = kNone;
     if (glane == 0) {
       bool won;
@@ -1764,17 +1853,23 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   if (!grid_sync(A.bar, A.fl)) return;
   clk.lap(kSegLevel0);
 
-  // the pencil form of step 0 (FP64 plain runs with enough cells)
+  // the pencil form of step 0 (plain runs with enough cells)
   bool pen = false;
   uint32_t maskQ = 0, qn = 0;
-  if constexpr (!F32 && !BT && D >= 3) {
+  if constexpr (!BT && D >= 3) {
     if (m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr) {
       pen = true;
       maskQ = mask_for(3 * m0, A.capAB);
-      phase_pencil_keys<D>(A, m0, maskQ);
+      if (F32)
+        phase_pencil_keys32<D>(A, m0, maskQ);
+      else
+        phase_pencil_keys<D>(A, m0, maskQ);
       if (!grid_sync(A.bar, A.fl)) return;
       qn = vst[0].qn;
-      phase_pencil_sums<D>(A, qn, maskA);
+      if (F32)
+        phase_pencil_sums32<D>(A, qn, maskA);
+      else
+        phase_pencil_sums<D>(A, qn, maskA);
       if (!grid_sync(A.bar, A.fl)) return;
       clk.lap(kSegUpdateFirst);
     }
@@ -1814,13 +1909,15 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     // lanes per cell: the fewest (most cells in flight) while the level has
     // more cells than warps, else 32
     constexpr int GSmin = GatherLanes<D>::min;
+    const bool pt = pen && t == 0;
     if (F32) {
       if (GSmin < 32 && m > (nth >> 5))
-        phase_update32<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb);
+        phase_update32<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
+                                     maskQ);
       else
-        phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb);
+        phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
+                                  maskQ);
     } else {
-      const bool pt = pen && t == 0;
       if (GSmin < 32 && m > (nth >> 5))
         phase_update<D, GSmin, BT>(A, t, m, pt ? maskQ : mask, maskM, m_prev, base_prev, base,
                                    any_nb, inexact, werr, pt);
@@ -1833,7 +1930,12 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     clk.lap_step(t == 0 ? kSegUpdateFirst : kSegUpdateRest, t, A.res);
     // the pencil table is read: back to clean (the next use of tab[2], as
     // step 1's merge table, is a grid barrier away)
-    if (!F32 && pen && t == 0) pencil_release<D>(A, qn);
+    if (pen && t == 0) {
+      if (F32)
+        pencil_release32<D>(A, qn);
+      else
+        pencil_release<D>(A, qn);
+    }
     if (!vst[t].has_nb) {
       converged = true;
       break;

@@ -79,6 +79,20 @@ def test_random_blobs_fp32(d):
     check32(X, 4.0)
 
 
+def test_pencil_first_step_fp32():
+    # enough level-0 cells (>= 4096) for the two-pass form of the first
+    # update, on inputs that converge to few clusters (with thousands of
+    # small clusters one float32 near-tie moves a cell and a mode with it)
+    X = synth.image_features(synth.voronoi_image(480, 640, 20, 4.0, seed=9))
+    _, _, _, ref = check32(X, 4.0)
+    assert ref["m0"] >= 4096
+    rng = np.random.default_rng(84)
+    X = rng.uniform(0.0, 4.0, size=(15_000, 7))
+    X[: 15_000 // 4] = rng.normal(3.0, 0.7, size=(15_000 // 4, 7))
+    _, _, _, ref = check32(X, 1.0, max_iter=8)
+    assert ref["m0"] >= 4096
+
+
 def test_images_fp32():
     for (H, W, R, seed, xy) in [(120, 160, 9, 4, None), (250, 333, 15, 3, 0.1)]:
         img = synth.voronoi_image(H, W, R, 10.0, seed=seed, gradient=0.02)
