@@ -233,27 +233,21 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 6)
     k_bin(const T* __restrict__ pts, int64_t n, const int64_t* __restrict__ thr,
           BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
           DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B) {
   __shared__ __align__(16) T s_pts[kWarps][32 * D];
+  __shared__ Plan s_plan;
   __shared__ uint32_t s_ok;
-  // the plan, into registers (nothing runs unless it is valid)
-  if (threadIdx.x == 0) s_ok = *(volatile uint32_t*)&fl->plan_status == kPlanOK;
+  // the plan, into shared memory (nothing runs unless it is valid)
+  if (threadIdx.x == 0) {
+    s_ok = *(volatile uint32_t*)&fl->plan_status == kPlanOK;
+    if (s_ok) s_plan = fl->plan;
+  }
   __syncthreads();
   if (!s_ok) return;
-  int thr_off[D], span[D], off[D];
-  int64_t kmin[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    thr_off[a] = fl->plan.thr_off[a];
-    span[a] = fl->plan.span[a];
-    off[a] = fl->plan.off[a];
-    kmin[a] = fl->plan.kmin[a];
-  }
-  const float inv_h = fl->plan.inv_h;
-  const int inst_off = fl->plan.inst_off;
+  const Plan& P = s_plan;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -264,12 +258,12 @@ __global__ void __launch_bounds__(kBlock)
     const bool valid = lane < cnt;
     uint64_t key = kEmpty;
     if (valid) {
-      key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << inst_off : 0ull;
+      key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << P.inst_off : 0ull;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const uint64_t b = bits_of(s_pts[w][lane * D + a]);
-        const int idx = key_index(thr + thr_off[a], span[a], kmin[a], inv_h, b);
-        key |= (uint64_t)(idx + 1) << off[a];
+        const int idx = key_index(thr + P.thr_off[a], P.span[a], P.kmin[a], P.inv_h, b);
+        key |= (uint64_t)(idx + 1) << P.off[a];
       }
     }
     __syncwarp();

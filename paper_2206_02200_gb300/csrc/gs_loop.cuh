@@ -110,6 +110,23 @@ struct SegClock {
 };
 
 
+// This thread's first item of a grid-stride loop over `items` items.  With
+// at least as many items as threads, consecutive threads take consecutive
+// items (coalesced); with fewer, consecutive items go to consecutive blocks
+// (so to different SMs) and the loop spreads over the whole grid instead of
+// filling the first blocks.  Either way a bijection of the grid's threads.
+__device__ __forceinline__ uint32_t item_tid(uint32_t items) {
+  return items >= gridDim.x * blockDim.x ? blockIdx.x * blockDim.x + threadIdx.x
+                                         : threadIdx.x * gridDim.x + blockIdx.x;
+}
+
+// The same for groups of GS consecutive lanes of a warp.
+template <int GS>
+__device__ __forceinline__ uint32_t item_group(uint32_t items) {
+  return items >= gridDim.x * (blockDim.x / GS) ? (blockIdx.x * blockDim.x + threadIdx.x) / GS
+                                                : (threadIdx.x / GS) * gridDim.x + blockIdx.x;
+}
+
 __device__ __forceinline__ u128 as_u128(ulonglong2 v) { return (u128)v.x | ((u128)v.y << 64); }
 
 __device__ __forceinline__ ulonglong2 pack(u128 v) {
@@ -361,7 +378,7 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
 template <int D>
 __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, unsigned& inexact,
                              unsigned& werr) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(m0);
   const uint32_t nth = gridDim.x * blockDim.x;
   const BinTable T0 = A.T0;
   const LevelTable G = A.tab[0];
@@ -409,7 +426,7 @@ constexpr uint32_t kPencilMin = 4096;
 // runs only: no field above axis 0).
 template <int D>
 __device__ void phase_pencil_keys(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(3 * m0);
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable Q = A.tab[2];
   const Cells c = A.cells[0];
@@ -438,7 +455,7 @@ __device__ void phase_pencil_keys(const LoopArgs& A, uint32_t m0, uint32_t maskQ
 // field above axis 0.
 template <int D>
 __device__ void phase_pencil_sums(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(qn);
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable G = A.tab[0];
   const LevelTable Q = A.tab[2];
@@ -475,7 +492,7 @@ __device__ void phase_pencil_sums(const LoopArgs& A, uint32_t qn, uint32_t maskA
 // Q's table back to clean (keys empty, counts zero) once step 0 has read it.
 template <int D>
 __device__ void pencil_release(const LoopArgs& A, uint32_t qn) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(qn);
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable Q = A.tab[2];
   for (uint32_t j = tid; j < qn; j += nth) {
@@ -509,7 +526,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
-  const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / GS;
+  const uint32_t group = item_group<GS>(m);
   const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
   const LevelTable G = A.tab[pen ? 2 : t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
@@ -653,7 +670,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   }
   if (t > 0) {
     // level t-1: parent links, then its table is released
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t tid = item_tid(m_prev);
     const uint32_t nth = gridDim.x * blockDim.x;
     const LevelTable Lp = A.tab[(t + 2) % 3];
     const uint32_t* pp = A.pslot[(t - 1) & 1];
@@ -673,7 +690,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
 template <int D, bool BT>
 __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& inexact,
                               unsigned& werr) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(m1);
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
@@ -1013,7 +1030,7 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
 // table's slots.
 template <int D>
 __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(m0);
   const uint32_t nth = gridDim.x * blockDim.x;
   const BinTable T0 = A.T0;
   float* tacc = reinterpret_cast<float*>(T0.acc);
@@ -1054,7 +1071,7 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
 template <int D>
 __device__ void phase_pencil_keys32(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
   constexpr int W = RowW<D>::value;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(3 * m0);
   const uint32_t nth = gridDim.x * blockDim.x;
   uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
   const Cells c = A.cells[0];
@@ -1080,7 +1097,7 @@ __device__ void phase_pencil_keys32(const LoopArgs& A, uint32_t m0, uint32_t mas
 template <int D>
 __device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
   constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(qn);
   const uint32_t nth = gridDim.x * blockDim.x;
   const uint32_t* grow = reinterpret_cast<const uint32_t*>(A.tab[0].row);
   uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
@@ -1121,7 +1138,7 @@ __device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t mas
 template <int D>
 __device__ void pencil_release32(const LoopArgs& A, uint32_t qn) {
   constexpr int W = RowW<D>::value;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(qn);
   const uint32_t nth = gridDim.x * blockDim.x;
   uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
   for (uint32_t j = tid; j < qn; j += nth) row_release(qrow + (size_t)A.qlist[j] * W);
@@ -1145,7 +1162,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
-  const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) / GS;
+  const uint32_t group = item_group<GS>(m);
   const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
   const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
@@ -1350,7 +1367,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
     }
   }
   if (t > 0) {
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t tid = item_tid(m_prev);
     const uint32_t nth = gridDim.x * blockDim.x;
     const LevelTable Lp = A.tab[(t + 2) % 3];
     uint32_t* prow = reinterpret_cast<uint32_t*>(Lp.row);
@@ -1365,7 +1382,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
 // The cells of level t+1 (float32): mean offsets = merged sums / counts.
 template <int D, bool BT>
 __device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t tid = item_tid(m1);
   const uint32_t nth = gridDim.x * blockDim.x;
   const LevelTable G = A.tab[t % 3];
   const LevelTable M = A.tab[(t + 1) % 3];
@@ -1847,7 +1864,9 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   else
     phase_level0<D>(A, m0, maskA, inexact, werr);
   if (BT) {
-    for (uint32_t id = tid; id < m0; id += nth)
+    // the same threads as phase_level0 (no barrier between): each reads the
+    // keys it wrote
+    for (uint32_t id = item_tid(m0); id < m0; id += nth)
       atomicAdd(&A.I.m0[(uint32_t)(A.cells[0].key[id] >> g_plan.inst_off)], 1u);
   }
   if (!grid_sync(A.bar, A.fl)) return;
