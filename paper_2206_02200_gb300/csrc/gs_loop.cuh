@@ -1469,6 +1469,10 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
 // The arithmetic is that of phase_update and phase_compact (exact sums
 // rounded once); a merged cell's sum is added over its members.
 
+// Longest run whose labels walk the chain of merges directly (one dependent
+// load per step) instead of pointer jumping (one grid barrier per round).
+constexpr int kWalkMax = 16;
+
 // Largest level handed to the one-block tail.  A tail step makes m^2 pair
 // tests on one SM; measured on GB300 (d = 3 and 5), it beats a multi-block
 // step (grid barriers, dependent L2 loads) up to about 110 cells and loses
@@ -2355,38 +2359,11 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
         atomicAdd(&A.I.k[(uint32_t)(c.key[j] >> g_plan.inst_off)], 1u);
     }
   }
-  if (!grid_sync(A.bar, A.fl)) return;
-  if (BT && tid == 0) {
-    // labels of instance b start at 0: subtract the final cells of earlier ones
-    uint32_t run = 0;
-    for (int b = 0; b < A.B; ++b) {
-      A.I.koff[b] = run;
-      run += A.I.k[b];
-    }
-  }
-
-  // pointer jumping over the forest of merges: after r rounds every node
-  // points 2^r levels up (or to its root)
-  const uint32_t nodes = base + k;
-  uint32_t* in = A.forest;
-  uint32_t* out = A.forest2;
-  for (int hop = 1; hop < T; hop <<= 1) {
-    for (uint32_t v = tid; v < nodes; v += nth) out[v] = in[in[v]];
-    if (!grid_sync(A.bar, A.fl)) return;
-    uint32_t* tmp = in;
-    in = out;
-    out = tmp;
-  }
-  if (in != A.forest) {
-    for (uint32_t v = tid; v < m0; v += nth) A.forest[v] = in[v];
-    if (!grid_sync(A.bar, A.fl)) return;
-  }
-
+  // numbering: label of a final cell = number of final keys below its key
+  // (keys are unique), i.e. ascending lexicographic order of the integer keys
   const bool numbered = k <= A.rank_max;
+  const Cells c = A.cells[T & 1];
   if (numbered) {
-    // label of a final cell = number of final keys below its key (keys are
-    // unique), i.e. ascending lexicographic order of the integer keys
-    const Cells c = A.cells[T & 1];
     const uint32_t warp = tid >> 5, nwarps = nth >> 5;
     const int lane = threadIdx.x & 31;
     for (uint32_t r = warp; r < k; r += nwarps) {
@@ -2397,14 +2374,57 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(kFull, below, o);
       if (lane == 0) A.rank[r] = below;
     }
+  }
+  if (!grid_sync(A.bar, A.fl)) return;
+  if (BT) {
+    if (tid == 0) {
+      // labels of instance b start at 0: subtract the final cells of earlier ones
+      uint32_t run = 0;
+      for (int b = 0; b < A.B; ++b) {
+        A.I.koff[b] = run;
+        run += A.I.k[b];
+      }
+    }
     if (!grid_sync(A.bar, A.fl)) return;
-    for (uint32_t cc = tid; cc < m0; cc += nth) {
-      const uint32_t r = A.forest[cc] - base;
+  }
+
+  // the final cell of every initial cell: its chain of T merges walked
+  // directly (T dependent loads, no barrier) for short runs, else pointer
+  // jumping over the forest (after r rounds every node points 2^r levels up)
+  const bool walk = T <= kWalkMax;
+  if (!walk) {
+    const uint32_t nodes = base + k;
+    uint32_t* in = A.forest;
+    uint32_t* out = A.forest2;
+    for (int hop = 1; hop < T; hop <<= 1) {
+      for (uint32_t v = tid; v < nodes; v += nth) out[v] = in[in[v]];
+      if (!grid_sync(A.bar, A.fl)) return;
+      uint32_t* tmp = in;
+      in = out;
+      out = tmp;
+    }
+    if (in != A.forest) {
+      for (uint32_t v = tid; v < m0; v += nth) A.forest[v] = in[v];
+      if (!grid_sync(A.bar, A.fl)) return;
+    }
+  }
+  for (uint32_t cc = tid; cc < m0; cc += nth) {
+    uint32_t v = cc;
+    if (walk) {
+      for (int s = 0; s < T; ++s) v = A.forest[v];
+      if (!numbered) A.forest[cc] = v;  // roots for the numbering after the kernel
+    } else {
+      v = A.forest[cc];
+    }
+    if (numbered) {
+      const uint32_t r = v - base;
       uint32_t label = A.rank[r];
       if (BT) label -= A.I.koff[(uint32_t)(c.key[r] >> g_plan.inst_off)];
       A.labslot[A.T0.list[cc]] = label;
     }
-    if (!grid_sync(A.bar, A.fl)) return;
+  }
+  if (!grid_sync(A.bar, A.fl)) return;
+  if (numbered) {
     for (int64_t i = tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
     const LevelTable G = A.tab[T % 3];
     const bool write = (int64_t)k <= A.modes_cap;
