@@ -119,6 +119,16 @@ def test_pencil_first_step(d, n, side):
     check_parity(X, 1.0, max_iter=8)
 
 
+@pytest.mark.parametrize("seed", [0, 2])
+def test_long_runs_label_by_pointer_jumping(seed):
+    # more than 16 update steps: labels through pointer jumping rather than a
+    # walk of the chain of merges
+    rng = np.random.default_rng(seed)
+    X = np.concatenate([rng.normal(0, 30, size=(3000, 2)), rng.normal(100, 30, size=(3000, 2))])
+    ref, _ = check_parity(X, 2.0)
+    assert ref["iterations"] > 16
+
+
 def test_unaligned_input():
     # points starting 8 bytes (float64) or 4 bytes (float32) past a 16-byte
     # boundary take the scalar load paths
