@@ -299,11 +299,10 @@ __device__ void phase_scatter(const LoopArgs& A) {
 // segment adds the segment's sum.
 constexpr int kSumRun = 4;
 
-// Adds V into the sum accumulators of the cell in binning slot s (they are
-// indexed by the cell's id, so the initial cells' sums are dense).
+// Adds V into the sum accumulators of the cell of id `id` (they are indexed
+// by the cell's id, so the initial cells' sums are dense).
 template <int D>
-__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t s, const u128 (&V)[D]) {
-  const uint32_t id = A.T0.id[s];
+__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t id, const u128 (&V)[D]) {
 #pragma unroll
   for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)id * D + a) * 4, V[a]);
 }
@@ -336,16 +335,21 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
 #pragma unroll
       for (int a = 0; a < D; ++a)
         raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)idx[e] * D + a) : 0ull;
+    // the cells' ids, loaded while the coordinates are in flight
+    uint32_t cid[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) cid[e] = s[e] != kNone ? A.T0.id[s[e]] : 0u;
     // runs within the lane
-    uint32_t cur = s[0];
+    uint32_t cur = s[0], curid = cid[0];
     u128 V[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], g_plan.L[a], inexact, werr);
 #pragma unroll
     for (int e = 1; e < E; ++e) {
       if (s[e] != cur) {
-        if (cur != kNone) add_cell_sum<D>(A, cur, V);
+        if (cur != kNone) add_cell_sum<D>(A, curid, V);
         cur = s[e];
+        curid = cid[e];
 #pragma unroll
         for (int a = 0; a < D; ++a) V[a] = 0;
       }
@@ -369,7 +373,7 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
         }
       }
     }
-    if (head && cur != kNone) add_cell_sum<D>(A, cur, V);
+    if (head && cur != kNone) add_cell_sum<D>(A, curid, V);
   }
 }
 
@@ -976,22 +980,29 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
 #pragma unroll
       for (int a = 0; a < D; ++a)
         x[e][a] = idx[e] != kNone ? (float)__ldg(pts + (size_t)idx[e] * D + a) : 0.f;
-    uint32_t cur = kNone;
+    // the cells' ids and keys, loaded while the coordinates are in flight
+    uint32_t cid[E];
+    uint64_t ckey[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      cid[e] = s[e] != kNone ? A.T0.id[s[e]] : 0u;
+      ckey[e] = s[e] != kNone ? A.T0.key[s[e]] : 0ull;
+    }
+    uint32_t cur = kNone, curid = 0;
     float org[D];
     FF V[D];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (s[e] != cur) {
         if (cur != kNone) {
-          const uint32_t cid = A.T0.id[cur];
 #pragma unroll
-          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cid * D + a], V[a].value());
+          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)curid * D + a], V[a].value());
         }
         cur = s[e];
+        curid = cid[e];
         if (cur != kNone) {
-          const uint64_t key = A.T0.key[cur];
 #pragma unroll
-          for (int a = 0; a < D; ++a) org[a] = (float)face_of(g_plan, A.thr, key, a);
+          for (int a = 0; a < D; ++a) org[a] = (float)face_of(g_plan, A.thr, ckey[e], a);
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) V[a] = FF();
@@ -1019,9 +1030,8 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
       }
     }
     if (head && cur != kNone) {
-      const uint32_t cid = A.T0.id[cur];
 #pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cid * D + a], V[a].value());
+      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)curid * D + a], V[a].value());
     }
   }
 }
