@@ -117,6 +117,39 @@ struct LevelTableBuf {
   }
 };
 
+// A table of keys and rows without merge accumulators (the second pencil
+// table of step 0).
+struct PencilTableBuf {
+  DBuf<uint64_t> key;
+  DBuf<uint32_t> list;
+  DBuf<ulonglong2> row;
+  uint32_t cap = 0;
+  int d = 0;
+  cudaError_t ensure(uint32_t c, int dd, size_t lmax, cudaStream_t s) {
+    cudaError_t e;
+    if (c > cap || dd != d) {
+      key.release(); row.release();
+      cap = 0;
+      if ((e = key.ensure(c)) != cudaSuccess) return e;
+      if ((e = row.ensure((size_t)c * (dd + 1))) != cudaSuccess) return e;
+      cap = c;
+      d = dd;
+      if ((e = clear(s)) != cudaSuccess) return e;
+    }
+    return list.ensure(lmax);
+  }
+  cudaError_t clear(cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(key.p, 0xFF, sizeof(uint64_t) * key.cap, s)) != cudaSuccess) return e;
+    return cudaMemsetAsync(row.p, 0, sizeof(ulonglong2) * row.cap, s);
+  }
+  LevelTable view() const { return LevelTable{key.p, nullptr, row.p, nullptr, list.p, cap}; }
+  void release() {
+    key.release(); row.release(); list.release();
+    cap = 0;
+  }
+};
+
 struct CellBuf {
   DBuf<uint64_t> key;
   DBuf<uint32_t> cnt;
@@ -172,6 +205,7 @@ struct CtxWorkspace : public Workspace {
   DBuf<uint32_t> slot0, perm, blocksum;
   BinTableBuf t0;
   LevelTableBuf tab[3];
+  PencilTableBuf ptab;
   CellBuf cells[2];
   DBuf<uint32_t> pslot[2], qlist, forest, forest2, labslot, rank, filter;
   DBuf<uint64_t> skey, skey2;
@@ -255,6 +289,7 @@ struct CtxWorkspace : public Workspace {
       if (t0.cap) WS_CU(t0.clear(s), "clear T0");
       for (int i = 0; i < 3; ++i)
         if (tab[i].cap) WS_CU(tab[i].clear(s), "clear level table");
+      if (ptab.cap) WS_CU(ptab.clear(s), "clear pencil table");
     }
     WS_CU(t0.ensure(cap0, d, s), "alloc T0");
     b.st = st.p;
@@ -294,6 +329,9 @@ struct CtxWorkspace : public Workspace {
       WS_CU(pslot[i].ensure(m), "alloc pslot");
     }
     WS_CU(qlist.ensure((size_t)m * 3), "alloc pencil list");
+    if (d >= kPencil2MinD)
+      WS_CU(ptab.ensure(pow2_at_least(12ull * m, 64), d, (size_t)m * 9, s), "alloc pencil table");
+    b.ptab = ptab.view();
     WS_CU(forest.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(forest2.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(labslot.ensure(t0.cap), "alloc labslot");
@@ -355,7 +393,7 @@ struct CtxWorkspace : public Workspace {
       cells[i].release();
       pslot[i].release();
     }
-    qlist.release(); forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
+    qlist.release(); ptab.release(); forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
     offsets.release(); inst.release();
     if (h_flags) cudaFreeHost(h_flags);

@@ -159,6 +159,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.filter[0] = b.filter;
     L.filter[1] = b.filter + kFilterWords;
     L.qlist = b.qlist;
+    L.ptab = b.ptab;
     L.forest = b.forest;
     L.forest2 = b.forest2;
     L.labslot = b.labslot;

@@ -35,6 +35,7 @@ struct Bufs {
   int64_t* offsets = nullptr;  // batched runs: B + 1 point offsets
   uint32_t* inst = nullptr;    // batched runs: per-instance state (inst_words(B) words)
   uint32_t* qlist = nullptr;   // 3 * m0 (pencil set of step 0)
+  LevelTable ptab{};           // second pencil table (optional; cap 0: none)
   uint32_t* forest = nullptr;  // m0 * (max_iter + 1)
   uint32_t* forest2 = nullptr; // m0 * (max_iter + 1)
   uint32_t* labslot = nullptr; // t0.cap

@@ -46,6 +46,10 @@ struct LevelTable {
   uint32_t cap;  // power of two
 };
 
+// Least d for the second stage of the pencil form of step 0 (the loop
+// kernel), which needs the second pencil table (LoopArgs::ptab).
+constexpr int kPencil2MinD = 6;
+
 // Occupancy filter of a level (see the loop kernel): at most 2^20 bits.
 constexpr int kFilterLog2Max = 20;
 constexpr uint32_t kFilterWords = (1u << kFilterLog2Max) / 32;
@@ -74,6 +78,8 @@ struct LoopArgs {
   uint32_t* filter[2];   // occupancy filters of alternate levels, kFilterWords each,
                          // zeroed before the launch
   uint32_t* qlist;       // 3 x (level-0 cell bound): slots of the pencil set of step 0
+  LevelTable ptab;       // second pencil table of step 0 (key, row, list of 9 x the
+                         // level-0 cell bound; cap 0: none)
   uint32_t* forest;      // parent of every cell of every level, then its final cell
   uint32_t* forest2;     // pointer-jumping buffer
   uint32_t* labslot;     // label of every binning slot

@@ -426,54 +426,73 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
 // barriers cost more than the probes they save).
 constexpr uint32_t kPencilMin = 4096;
 
-// Q's keys: every level-0 cell and its two neighbours along axis 0 (plain
-// runs only: no field above axis 0).
-template <int D>
-__device__ void phase_pencil_keys(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
-  const uint32_t tid = item_tid(3 * m0);
+// Field of axis a of a packed key (plain runs: nothing above axis 0).
+__device__ __forceinline__ int64_t key_field(uint64_t key, int a) {
+  const int w = (a == 0 ? 64 : g_plan.off[a - 1]) - g_plan.off[a];
+  const uint64_t f = key >> g_plan.off[a];
+  return (int64_t)(w >= 64 ? f : (f & ((1ull << w) - 1ull)));
+}
+
+// Keys of a pencil set: every key of the source (n keys: skey[i], or
+// skey[via[i]]) and its two neighbours along `axis`, where that axis's field
+// stays in [1, span] (the only positions the update probes); each new key is
+// listed in dlist (count in *dcount) and joins the level-0 filter.
+__device__ __forceinline__ void pencil_keys_into(const LoopArgs& A, int axis, const uint64_t* skey,
+                                                 const uint32_t* via, uint32_t n, uint64_t* dkey,
+                                                 uint32_t dmask, uint32_t* dlist, uint32_t* dcount,
+                                                 int lg0) {
+  const uint32_t tid = item_tid(3 * n);
   const uint32_t nth = gridDim.x * blockDim.x;
-  const LevelTable Q = A.tab[2];
-  const Cells c = A.cells[0];
-  const int lg0 = filter_log2(m0);
-  const uint64_t e0 = 1ull << g_plan.off[0];
-  for (uint32_t w = tid; w < 3 * m0; w += nth) {
-    const uint32_t id = w / 3;
-    const uint32_t u = w - 3 * id;  // 0, 1, 2: offsets -1, 0, +1
-    const uint64_t key = c.key[id];
-    // only positions the update probes: axis 0's field in [1, span_0]
-    const int64_t f0 = (int64_t)(key >> g_plan.off[0]) + (int64_t)u - 1;
-    if (f0 < 1 || f0 > g_plan.span[0]) continue;
-    const uint64_t q = key + (u == 0 ? (uint64_t)0 - e0 : u == 2 ? e0 : 0ull);
+  const uint64_t e = 1ull << g_plan.off[axis];
+  for (uint32_t w = tid; w < 3 * n; w += nth) {
+    const uint32_t i = w / 3;
+    const uint32_t u = w - 3 * i;  // 0, 1, 2: offsets -1, 0, +1
+    const uint64_t key = via ? skey[via[i]] : skey[i];
+    const int64_t f = key_field(key, axis) + (int64_t)u - 1;
+    if (f < 1 || f > g_plan.span[axis]) continue;
+    const uint64_t q = key + (u == 0 ? (uint64_t)0 - e : u == 2 ? e : 0ull);
     bool won;
-    const uint32_t s = table_insert(Q.key, maskQ, q, won, &A.fl->err);
-    if (s != kNone && won) {
-      const uint32_t j = atomicAdd(&A.st[0].qn, 1u);
-      A.qlist[j] = s;
+    const uint32_t sl = table_insert(dkey, dmask, q, won, &A.fl->err);
+    if (sl != kNone && won) {
+      dlist[atomicAdd(dcount, 1u)] = sl;
       if (u != 1) filter_set(A.filter[0], q, lg0);
     }
   }
 }
 
-// Count and coordinate sums of the three cells q - e_0, q, q + e_0 of every
-// q in Q, into Q's row (the layout of a level row).  Plain runs only: no
-// field above axis 0.
+// Stage 1: Q (tab[2], listed in qlist) from the level-0 cells along axis 0.
 template <int D>
-__device__ void phase_pencil_sums(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
-  const uint32_t tid = item_tid(qn);
+__device__ void phase_pencil_keys(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
+  pencil_keys_into(A, 0, A.cells[0].key, nullptr, m0, A.tab[2].key, maskQ, A.qlist, &A.st[0].qn,
+                   filter_log2(m0));
+}
+
+// Stage 2: Q2 (ptab, listed in ptab.list) from Q along axis 1.
+template <int D>
+__device__ void phase_pencil_keys2(const LoopArgs& A, uint32_t qn, uint32_t m0, uint32_t maskQ2) {
+  pencil_keys_into(A, 1, A.tab[2].key, A.qlist, qn, A.ptab.key, maskQ2, A.ptab.list,
+                   &A.st[0].qn2, filter_log2(m0));
+}
+
+// Count and coordinate sums of the three entries q - e, q, q + e (e along
+// `axis`) of the source table, for every q listed in dlist, into the row of q
+// in the destination table (the layout of a level row).
+template <int D>
+__device__ void pencil_sums_into(int axis, const uint32_t* dlist, uint32_t n, const LevelTable& dst,
+                                 const LevelTable& src, uint32_t smask) {
+  const uint32_t tid = item_tid(n);
   const uint32_t nth = gridDim.x * blockDim.x;
-  const LevelTable G = A.tab[0];
-  const LevelTable Q = A.tab[2];
-  const uint64_t e0 = 1ull << g_plan.off[0];
-  for (uint32_t j = tid; j < qn; j += nth) {
-    const uint32_t s = A.qlist[j];
-    const uint64_t q = Q.key[s];
-    // axis 0's field of a cell lies in [1, span_0]: probe only there (the key
-    // arithmetic then never borrows or carries out of the field)
-    const int64_t f0 = (int64_t)(q >> g_plan.off[0]);
-    const uint64_t keys[3] = {q - e0, q, q + e0};
-    const bool valid[3] = {f0 >= 2, f0 >= 1 && f0 <= g_plan.span[0], f0 + 1 <= g_plan.span[0]};
+  const uint64_t e = 1ull << g_plan.off[axis];
+  for (uint32_t j = tid; j < n; j += nth) {
+    const uint32_t sl0 = dlist[j];
+    const uint64_t q = dst.key[sl0];
+    // the field stays in [1, span] (the key arithmetic then never borrows
+    // or carries out of it)
+    const int64_t f = key_field(q, axis);
+    const uint64_t keys[3] = {q - e, q, q + e};
+    const bool valid[3] = {f >= 2, f >= 1 && f <= g_plan.span[axis], f + 1 <= g_plan.span[axis]};
     uint32_t sl[3];
-    table_find_many<3>(G.key, maskA, keys, valid, sl);
+    table_find_many<3>(src.key, smask, keys, valid, sl);
     uint64_t cnt = 0;
     u128 N[D];
 #pragma unroll
@@ -481,28 +500,45 @@ __device__ void phase_pencil_sums(const LoopArgs& A, uint32_t qn, uint32_t maskA
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       if (sl[u] == kNone) continue;
-      const ulonglong2* r = G.row + (size_t)sl[u] * (D + 1);
+      const ulonglong2* r = src.row + (size_t)sl[u] * (D + 1);
       cnt += r[0].x;
 #pragma unroll
       for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
     }
-    ulonglong2* r = Q.row + (size_t)s * (D + 1);
+    ulonglong2* r = dst.row + (size_t)sl0 * (D + 1);
     r[0] = make_ulonglong2(cnt, 0ull);
 #pragma unroll
     for (int a = 0; a < D; ++a) r[1 + a] = pack(N[a]);
   }
 }
 
-// Q's table back to clean (keys empty, counts zero) once step 0 has read it.
 template <int D>
-__device__ void pencil_release(const LoopArgs& A, uint32_t qn) {
-  const uint32_t tid = item_tid(qn);
+__device__ void phase_pencil_sums(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
+  pencil_sums_into<D>(0, A.qlist, qn, A.tab[2], A.tab[0], maskA);
+}
+
+template <int D>
+__device__ void phase_pencil_sums2(const LoopArgs& A, uint32_t qn2, uint32_t maskQ) {
+  pencil_sums_into<D>(1, A.ptab.list, qn2, A.ptab, A.tab[2], maskQ);
+}
+
+// A pencil table back to clean (keys empty, counts zero) once step 0 has
+// read it.
+template <int D>
+__device__ void pencil_release(const LevelTable& Q, const uint32_t* list, uint32_t n) {
+  const uint32_t tid = item_tid(n);
   const uint32_t nth = gridDim.x * blockDim.x;
-  const LevelTable Q = A.tab[2];
-  for (uint32_t j = tid; j < qn; j += nth) {
-    const uint32_t s = A.qlist[j];
-    Q.key[s] = kEmpty;
-    Q.row[(size_t)s * (D + 1)].x = 0;
+  // four list entries loaded before any store, so their loads overlap
+  for (uint32_t j = tid; j < n; j += 4 * nth) {
+    uint32_t sl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sl[k] = j + k * nth < n ? list[j + k * nth] : kNone;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (sl[k] == kNone) continue;
+      Q.key[sl[k]] = kEmpty;
+      Q.row[(size_t)sl[k] * (D + 1)].x = 0;
+    }
   }
 }
 
@@ -518,27 +554,31 @@ __device__ void pencil_release(const LoopArgs& A, uint32_t qn) {
 // the run, the merge table is cleared instead of used.
 // For t > 0 the same phase links every cell of level t-1 to its cell of level
 // t (the union of resident sets of Eq. 4) and clears level t-1's table.
-// With pen (step 0 only) the sums over the 3^d neighbours are taken as sums
-// over the 3^(d-1) offsets with v_0 = 0 of the pencil table tab[2] (mask
-// `mask`), each entry of which already holds the three cells along axis 0.
-// A neighbour v != 0 is present iff D exceeds the cell's own count.
+// With pen = 1 (step 0 only) the sums over the 3^d neighbours are taken as
+// sums over the 3^(d-1) offsets with v_0 = 0 of the pencil table tab[2]
+// (mask `mask`), each entry of which already holds the three cells along
+// axis 0; with pen = 2 over the 3^(d-2) offsets with v_0 = v_1 = 0 of the
+// second pencil table (nine cells per entry).  A neighbour v != 0 is present
+// iff D exceeds the cell's own count.
 template <int D, int GS, bool BT>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
-                             unsigned& inexact, unsigned& werr, bool pen = false) {
+                             unsigned& inexact, unsigned& werr, int pen = 0) {
   constexpr int U = ProbeBatch<D, GS>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
   const uint32_t group = item_group<GS>(m);
   const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
-  const LevelTable G = A.tab[pen ? 2 : t % 3];
+  const LevelTable G = A.tab[t % 3];
+  const LevelTable P = pen == 2 ? A.ptab : A.tab[pen == 1 ? 2 : t % 3];  // the table probed
   const LevelTable M = A.tab[(t + 1) % 3];
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
-  // probes pbase .. pbase + np - 1 of the offset table (axis 0 the slowest
-  // digit: v_0 = 0 is its middle third)
-  const int np = pen ? g_plan.nprobe / 3 : g_plan.nprobe, pbase = pen ? np : 0;
+  // probes pbase .. pbase + np - 1 of the offset table (axes 0, 1 the slowest
+  // digits: v_0 = 0 is its middle third, v_0 = v_1 = 0 that third's middle)
+  const int np = g_plan.nprobe / (pen == 2 ? 9 : pen == 1 ? 3 : 1);
+  const int pbase = pen == 2 ? 4 * np : pen == 1 ? np : 0;
   // the level's occupancy filter, into shared memory; the filter of level
   // t-1 is cleared for level t+1
   extern __shared__ uint4 s_dyn[];
@@ -591,11 +631,11 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         const uint32_t fb = filter_bit(q[u], lg);
         v[u] = p < np && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
       }
-      table_find_many<U>(G.key, mask, q, v, sl);
+      table_find_many<U>(P.key, mask, q, v, sl);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (sl[u] == kNone) continue;
-        const ulonglong2* r = G.row + (size_t)sl[u] * (D + 1);
+        const ulonglong2* r = P.row + (size_t)sl[u] * (D + 1);
         Dc += (uint32_t)r[0].x;
 #pragma unroll
         for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
@@ -1079,50 +1119,65 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
 // cells q - e_0, q, q + e_0, and their count-weighted mean offset from q's
 // lower face.
 template <int D>
-__device__ void phase_pencil_keys32(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
+__device__ __forceinline__ void pencil_keys_into32(const LoopArgs& A, int axis,
+                                                   const uint32_t* srows, const uint64_t* skey,
+                                                   const uint32_t* via, uint32_t n,
+                                                   uint32_t* drows, uint32_t dmask,
+                                                   uint32_t* dlist, uint32_t* dcount, int lg0) {
   constexpr int W = RowW<D>::value;
-  const uint32_t tid = item_tid(3 * m0);
+  const uint32_t tid = item_tid(3 * n);
   const uint32_t nth = gridDim.x * blockDim.x;
-  uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
-  const Cells c = A.cells[0];
-  const int lg0 = filter_log2(m0);
-  const uint64_t e0 = 1ull << g_plan.off[0];
-  for (uint32_t w = tid; w < 3 * m0; w += nth) {
-    const uint32_t id = w / 3;
-    const uint32_t u = w - 3 * id;  // 0, 1, 2: offsets -1, 0, +1
-    const uint64_t key = c.key[id];
-    const int64_t f0 = (int64_t)(key >> g_plan.off[0]) + (int64_t)u - 1;
-    if (f0 < 1 || f0 > g_plan.span[0]) continue;
-    const uint64_t q = key + (u == 0 ? (uint64_t)0 - e0 : u == 2 ? e0 : 0ull);
+  const uint64_t e = 1ull << g_plan.off[axis];
+  for (uint32_t w = tid; w < 3 * n; w += nth) {
+    const uint32_t i = w / 3;
+    const uint32_t u = w - 3 * i;  // 0, 1, 2: offsets -1, 0, +1
+    const uint64_t key =
+        srows ? *reinterpret_cast<const unsigned long long*>(srows + (size_t)via[i] * W) : skey[i];
+    const int64_t f = key_field(key, axis) + (int64_t)u - 1;
+    if (f < 1 || f > g_plan.span[axis]) continue;
+    const uint64_t q = key + (u == 0 ? (uint64_t)0 - e : u == 2 ? e : 0ull);
     bool won;
-    const uint32_t s = row_insert<W>(qrow, maskQ, q, won, &A.fl->err);
-    if (s != kNone && won) {
-      const uint32_t j = atomicAdd(&A.st[0].qn, 1u);
-      A.qlist[j] = s;
+    const uint32_t sl = row_insert<W>(drows, dmask, q, won, &A.fl->err);
+    if (sl != kNone && won) {
+      dlist[atomicAdd(dcount, 1u)] = sl;
       if (u != 1) filter_set(A.filter[0], q, lg0);
     }
   }
 }
 
 template <int D>
-__device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
+__device__ void phase_pencil_keys32(const LoopArgs& A, uint32_t m0, uint32_t maskQ) {
+  pencil_keys_into32<D>(A, 0, nullptr, A.cells[0].key, nullptr, m0,
+                        reinterpret_cast<uint32_t*>(A.tab[2].row), maskQ, A.qlist, &A.st[0].qn,
+                        filter_log2(m0));
+}
+
+template <int D>
+__device__ void phase_pencil_keys2_32(const LoopArgs& A, uint32_t qn, uint32_t m0, uint32_t maskQ2) {
+  pencil_keys_into32<D>(A, 1, reinterpret_cast<const uint32_t*>(A.tab[2].row), nullptr, A.qlist,
+                        qn, reinterpret_cast<uint32_t*>(A.ptab.row), maskQ2, A.ptab.list,
+                        &A.st[0].qn2, filter_log2(m0));
+}
+
+// The count of the three entries q - e, q, q + e of the source rows and their
+// count-weighted mean offset from q's lower face.
+template <int D>
+__device__ void pencil_sums_into32(int axis, const uint32_t* dlist, uint32_t n, uint32_t* drows,
+                                   const uint32_t* srows, uint32_t smask) {
   constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
-  const uint32_t tid = item_tid(qn);
+  const uint32_t tid = item_tid(n);
   const uint32_t nth = gridDim.x * blockDim.x;
-  const uint32_t* grow = reinterpret_cast<const uint32_t*>(A.tab[0].row);
-  uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
-  const uint64_t e0 = 1ull << g_plan.off[0];
+  const uint64_t e = 1ull << g_plan.off[axis];
   const float h = g_plan.h32;
-  for (uint32_t j = tid; j < qn; j += nth) {
-    const uint32_t s = A.qlist[j];
-    uint32_t* r = qrow + (size_t)s * W;
+  for (uint32_t j = tid; j < n; j += nth) {
+    uint32_t* r = drows + (size_t)dlist[j] * W;
     const uint64_t q = *reinterpret_cast<const unsigned long long*>(r);
-    const int64_t f0 = (int64_t)(q >> g_plan.off[0]);
-    const uint64_t keys[3] = {q - e0, q, q + e0};
-    const bool valid[3] = {f0 >= 2, f0 >= 1 && f0 <= g_plan.span[0], f0 + 1 <= g_plan.span[0]};
+    const int64_t f = key_field(q, axis);
+    const uint64_t keys[3] = {q - e, q, q + e};
+    const bool valid[3] = {f >= 2, f >= 1 && f <= g_plan.span[axis], f + 1 <= g_plan.span[axis]};
     uint32_t sl[3];
     uint4 dat[3][NL];
-    row_find_many<D, 3>(grow, maskA, keys, valid, sl, dat);
+    row_find_many<D, 3>(srows, smask, keys, valid, sl, dat);
     uint32_t cnt = 0;
     KS S[D];
 #pragma unroll
@@ -1133,7 +1188,8 @@ __device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t mas
       cnt += cn;
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        S[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) + (a == 0 ? (float)(u - 1) * h : 0.f)));
+        S[a].add(fc * (__uint_as_float(row_word(dat[u], 3 + a)) +
+                       (a == axis ? (float)((int)u - 1) * h : 0.f)));
     }
     const float fC = (float)cnt;
     r[2] = cnt;
@@ -1146,12 +1202,31 @@ __device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t mas
 }
 
 template <int D>
-__device__ void pencil_release32(const LoopArgs& A, uint32_t qn) {
+__device__ void phase_pencil_sums32(const LoopArgs& A, uint32_t qn, uint32_t maskA) {
+  pencil_sums_into32<D>(0, A.qlist, qn, reinterpret_cast<uint32_t*>(A.tab[2].row),
+                        reinterpret_cast<const uint32_t*>(A.tab[0].row), maskA);
+}
+
+template <int D>
+__device__ void phase_pencil_sums2_32(const LoopArgs& A, uint32_t qn2, uint32_t maskQ) {
+  pencil_sums_into32<D>(1, A.ptab.list, qn2, reinterpret_cast<uint32_t*>(A.ptab.row),
+                        reinterpret_cast<const uint32_t*>(A.tab[2].row), maskQ);
+}
+
+template <int D>
+__device__ void pencil_release32(const LevelTable& Q, const uint32_t* list, uint32_t n) {
   constexpr int W = RowW<D>::value;
-  const uint32_t tid = item_tid(qn);
+  const uint32_t tid = item_tid(n);
   const uint32_t nth = gridDim.x * blockDim.x;
-  uint32_t* qrow = reinterpret_cast<uint32_t*>(A.tab[2].row);
-  for (uint32_t j = tid; j < qn; j += nth) row_release(qrow + (size_t)A.qlist[j] * W);
+  uint32_t* qrow = reinterpret_cast<uint32_t*>(Q.row);
+  for (uint32_t j = tid; j < n; j += 4 * nth) {
+    uint32_t sl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sl[k] = j + k * nth < n ? list[j + k * nth] : kNone;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (sl[k] != kNone) row_release(qrow + (size_t)sl[k] * W);
+  }
 }
 
 // One update step t (float32), as phase_update: Eq. 1-2 over the neighbours
@@ -1165,7 +1240,7 @@ __device__ void pencil_release32(const LoopArgs& A, uint32_t qn) {
 template <int D, int GS, bool BT>
 __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t mask,
                                uint32_t maskM, uint32_t m_prev, uint32_t base_prev,
-                               uint32_t base, bool& any_nb, bool pen = false,
+                               uint32_t base, bool& any_nb, int pen = 0,
                                uint32_t maskQ = 0) {
   constexpr int U = ProbeBatch<D, GS>::value;
   constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
@@ -1178,15 +1253,17 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
   const LevelTable M = A.tab[(t + 1) % 3];
   const uint32_t* grow = reinterpret_cast<const uint32_t*>(G.row);
   // the rows the neighbour sums read: the level's, or the pencil rows
-  const uint32_t* prow = reinterpret_cast<const uint32_t*>(A.tab[pen ? 2 : t % 3].row);
+  const uint32_t* prow = reinterpret_cast<const uint32_t*>(
+      (pen == 2 ? A.ptab : A.tab[pen == 1 ? 2 : t % 3]).row);
   const uint32_t maskP = pen ? maskQ : mask;
   uint32_t* mrow = reinterpret_cast<uint32_t*>(M.row);  // rows with the key inside (RowW)
   float* macc = reinterpret_cast<float*>(M.acc);
   const Cells c = A.cells[t & 1];
   uint32_t* pslot = A.pslot[t & 1];
   const int nprobe = g_plan.nprobe;
-  // probes pbase .. pbase + np - 1 of the offset table (v_0 = 0: the middle third)
-  const int np = pen ? nprobe / 3 : nprobe, pbase = pen ? np : 0;
+  // probes pbase .. pbase + np - 1 of the offset table (as phase_update)
+  const int np = nprobe / (pen == 2 ? 9 : pen == 1 ? 3 : 1);
+  const int pbase = pen == 2 ? 4 * np : pen == 1 ? np : 0;
   const float h = g_plan.h32;
   extern __shared__ uint4 s_dyn[];
   uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
@@ -2220,12 +2297,16 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   if (!grid_sync(A.bar, A.fl)) return;
   clk.lap(kSegLevel0);
 
-  // the pencil form of step 0 (plain runs with enough cells)
-  bool pen = false;
-  uint32_t maskQ = 0, qn = 0;
+  // the pencil form of step 0 (plain runs with enough cells): stage 1 along
+  // axis 0 into tab[2]; from d = 6, where the second pencil table has room
+  // for three times stage 1's positions at load 1/2, stage 2 along axis 1
+  // (measured on GB300: at d = 5 building stage 2 costs more than the 27
+  // probes per cell it saves; at d = 6 it saves 81 of 243)
+  int pen = 0;
+  uint32_t maskQ = 0, qn = 0, maskQ2 = 0, qn2 = 0;
   if constexpr (!BT && D >= 3) {
     if (m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr) {
-      pen = true;
+      pen = 1;
       maskQ = mask_for(3 * m0, A.capAB);
       if (F32)
         phase_pencil_keys32<D>(A, m0, maskQ);
@@ -2233,11 +2314,27 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
         phase_pencil_keys<D>(A, m0, maskQ);
       if (!grid_sync(A.bar, A.fl)) return;
       qn = vst[0].qn;
-      if (F32)
+      if (D >= kPencil2MinD && A.ptab.cap != 0 && 6ull * qn <= (uint64_t)A.ptab.cap) {
+        pen = 2;
+        maskQ2 = mask_for(3 * qn, A.ptab.cap);
+      }
+      // stage 1's sums and stage 2's keys (which need only stage 1's keys)
+      if (F32) {
         phase_pencil_sums32<D>(A, qn, maskA);
-      else
+        if (pen == 2) phase_pencil_keys2_32<D>(A, qn, m0, maskQ2);
+      } else {
         phase_pencil_sums<D>(A, qn, maskA);
+        if (pen == 2) phase_pencil_keys2<D>(A, qn, m0, maskQ2);
+      }
       if (!grid_sync(A.bar, A.fl)) return;
+      if (pen == 2) {
+        qn2 = vst[0].qn2;
+        if (F32)
+          phase_pencil_sums2_32<D>(A, qn2, maskQ);
+        else
+          phase_pencil_sums2<D>(A, qn2, maskQ);
+        if (!grid_sync(A.bar, A.fl)) return;
+      }
       clk.lap(kSegUpdateFirst);
     }
   }
@@ -2279,20 +2376,21 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     // lanes per cell: the fewest (most cells in flight) while the level has
     // more cells than warps, else 32
     constexpr int GSmin = GatherLanes<D>::min;
-    const bool pt = pen && t == 0;
+    const int pt = t == 0 ? pen : 0;
+    const uint32_t maskPt = pt == 2 ? maskQ2 : maskQ;
     if (F32) {
       if (GSmin < 32 && m > (nth >> 5))
         phase_update32<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
-                                     maskQ);
+                                     maskPt);
       else
         phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
-                                  maskQ);
+                                  maskPt);
     } else {
       if (GSmin < 32 && m > (nth >> 5))
-        phase_update<D, GSmin, BT>(A, t, m, pt ? maskQ : mask, maskM, m_prev, base_prev, base,
+        phase_update<D, GSmin, BT>(A, t, m, pt ? maskPt : mask, maskM, m_prev, base_prev, base,
                                    any_nb, inexact, werr, pt);
       else
-        phase_update<D, 32, BT>(A, t, m, pt ? maskQ : mask, maskM, m_prev, base_prev, base,
+        phase_update<D, 32, BT>(A, t, m, pt ? maskPt : mask, maskM, m_prev, base_prev, base,
                                 any_nb, inexact, werr, pt);
     }
     if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
@@ -2301,10 +2399,13 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     // the pencil table is read: back to clean (the next use of tab[2], as
     // step 1's merge table, is a grid barrier away)
     if (pen && t == 0) {
-      if (F32)
-        pencil_release32<D>(A, qn);
-      else
-        pencil_release<D>(A, qn);
+      if (F32) {
+        pencil_release32<D>(A.tab[2], A.qlist, qn);
+        if (pen == 2) pencil_release32<D>(A.ptab, A.ptab.list, qn2);
+      } else {
+        pencil_release<D>(A.tab[2], A.qlist, qn);
+        if (pen == 2) pencil_release<D>(A.ptab, A.ptab.list, qn2);
+      }
     }
     if (!vst[t].has_nb) {
       converged = true;

@@ -37,6 +37,7 @@ struct IterState {
   uint32_t has_nb;  // 1 if some cell of level t has an active neighbour (v != 0)
   uint32_t base;    // first node of level t in the forest of merges
   uint32_t qn;      // level 0 only: positions of the pencil set of step 0
+  uint32_t qn2;     // level 0 only: positions of the second pencil set
 };
 
 // Plan status (DevFlags::plan_status).
