@@ -235,6 +235,48 @@ gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_stream, const
                          gs_dtype dtype, int64_t n, int32_t* labels, double* modes,
                          int64_t modes_cap, int64_t* k_out, gs_fit_info* info);
 
+/* ---------------------------------------------------------------------------
+ * Tracking window step (Sec. 2.3, Algorithm 2).  The tracker of Algorithm 2
+ * keeps a set B of colour cells floor(c / h) (c the d colour channels of a
+ * pixel, h the context's h) and, per frame, finds the pixels of a search
+ * window whose colour cell lies in B:
+ *     R = { pixel x in the window : floor(c(x) / h) in B },
+ * then moves the window to the mean (x, y) position of R, replaces B by the
+ * cells of R's pixels, and adapts the window's size from R's extent.  This
+ * call computes one R: its size, the sum, mean and extent of its pixel
+ * positions, and which cells of B it contains (the next B).  The loop of
+ * Algorithm 2 around it (convergence of the centre, window resizing, frames)
+ * is host logic: see gridshift.py (track).
+ *
+ * The frame is `height` x `width` pixels in row-major order (y outer, x
+ * inner), d = the context's d colour channels per pixel (device, float64 or
+ * float32 as dtype says); pixel (x, y) is point y * width + x.  The window is
+ * the pixel rectangle x0 <= x < x1, y0 <= y < y1, clipped to the frame (an
+ * empty rectangle gives an empty R).  bins is host memory, k x d integer cell
+ * keys floor(c / h) per channel, in any order, duplicates allowed; k may be 0.
+ * floor(c / h) is the floor of the exact quotient, as in gs_fit.
+ *
+ * Results (host): out->count = |R|; out->sum_x, sum_y = exact sums of the
+ * positions of R's pixels; out->mean_x = sum_x / count and mean_y likewise,
+ * each one IEEE division of the exact integers (NaN when count = 0);
+ * out->min_x .. max_y = the bounding box of R's positions (min > max when
+ * R is empty); present (host, k bytes, may be NULL): present[j] = 1 if some
+ * pixel of R lies in cell bins[j], else 0.  The call synchronises the stream.
+ * Returns GS_OK, GS_E_INVALID (null pointers, negative sizes, k < 0, a colour
+ * in the window that is not finite or has |c / h| >= 2^52: then
+ * out->count = -1), GS_E_NOMEM or GS_E_CUDA. */
+typedef struct {
+  int64_t count;
+  int64_t sum_x, sum_y;
+  double mean_x, mean_y;
+  int64_t min_x, max_x, min_y, max_y;
+} gs_track_result;
+
+gs_status gs_track_window(gs_ctx* ctx, const void* frame, gs_dtype dtype, int64_t width,
+                          int64_t height, const int64_t* bins, int64_t k, int64_t x0,
+                          int64_t y0, int64_t x1, int64_t y1, gs_track_result* out,
+                          uint8_t* present);
+
 /* Copies a description of the last error of this context (NUL-terminated,
  * truncated to len bytes) into buf.  Returns GS_OK or GS_E_INVALID. */
 gs_status gs_get_last_error(gs_ctx* ctx, char* buf, size_t len);

@@ -381,3 +381,51 @@ done:
   free(nk); free(parent); free(ck2); free(cc2); free(cs2); free(acc); free(probe);
   return ret;
 }
+
+int gso_track_window(const double *frame, int64_t width, int64_t height, int d, double h,
+                     const int64_t *bins, int64_t k, int64_t x0, int64_t y0, int64_t x1,
+                     int64_t y1, int64_t *out, uint8_t *present) {
+  int64_t count = 0, sx = 0, sy = 0;
+  int64_t mnx = INT64_MAX, mxx = INT64_MIN, mny = INT64_MAX, mxy = INT64_MIN;
+  int64_t key[8];
+  for (int64_t j = 0; j < k; j++) present[j] = 0;
+  if (x0 < 0) x0 = 0;
+  if (y0 < 0) y0 = 0;
+  if (x1 > width) x1 = width;
+  if (y1 > height) y1 = height;
+  for (int64_t y = y0; y < y1; y++) {
+    for (int64_t x = x0; x < x1; x++) {
+      const double *c = frame + (y * width + x) * d;
+      for (int a = 0; a < d; a++) {
+        if (!(fabs(c[a] / h) < 4.0e15)) return 1;
+        key[a] = gso_floor_div(c[a], h);
+      }
+      int in = 0;
+      for (int64_t j = 0; j < k; j++) {
+        int same = 1;
+        for (int a = 0; a < d; a++)
+          if (bins[j * d + a] != key[a]) same = 0;
+        if (same) {
+          present[j] = 1;
+          in = 1;
+        }
+      }
+      if (!in) continue;
+      count++;
+      sx += x;
+      sy += y;
+      if (x < mnx) mnx = x;
+      if (x > mxx) mxx = x;
+      if (y < mny) mny = y;
+      if (y > mxy) mxy = y;
+    }
+  }
+  out[0] = count;
+  out[1] = sx;
+  out[2] = sy;
+  out[3] = mnx;
+  out[4] = mxx;
+  out[5] = mny;
+  out[6] = mxy;
+  return 0;
+}

@@ -52,6 +52,20 @@ double gso_exact_sum(const double *v, const uint32_t *w, int64_t n);
 /* (sum_i v[i]) / D computed exactly and rounded once to nearest-even; D >= 1, D < 2^32. */
 double gso_exact_mean(const double *v, int64_t n, uint64_t D);
 
+/* The window step of GridShift-based tracking (Sec. 2.3, Algorithm 2): over
+ * the pixels x0 <= x < x1, y0 <= y < y1 of a width x height frame (clipped to
+ * it; pixel (x, y) is row y * width + x of the row-major frame of d colour
+ * channels), R = the pixels whose colour cell floor(c / h) (per channel) is
+ * one of the k keys in bins (k x d, any order).  out[0..6] = |R|, sum of x,
+ * sum of y, min x, max x, min y, max y over R (min = INT64_MAX, max =
+ * INT64_MIN when R is empty); present[j] = 1 if some pixel of R lies in cell
+ * bins[j], else 0.  A plain double loop with a linear search of bins.
+ * Returns 0, or 1 when a colour in the window is not finite or has
+ * |c / h| >= 2^52. */
+int gso_track_window(const double *frame, int64_t width, int64_t height, int d, double h,
+                     const int64_t *bins, int64_t k, int64_t x0, int64_t y0, int64_t x1,
+                     int64_t y1, int64_t *out, uint8_t *present);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,12 @@ def lib():
         L.gso_exact_sum.argtypes = [P(ctypes.c_double), P(ctypes.c_uint32), ctypes.c_int64]
         L.gso_exact_mean.restype = ctypes.c_double
         L.gso_exact_mean.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_uint64]
+        L.gso_track_window.restype = ctypes.c_int
+        L.gso_track_window.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_int, ctypes.c_double, P(ctypes.c_int64),
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_int64, P(ctypes.c_int64),
+                                       P(ctypes.c_uint8)]
         _lib = L
     return _lib
 
@@ -121,3 +127,68 @@ def exact_sum(v, w=None) -> float:
 def exact_mean(v, D: int) -> float:
     v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
     return float(lib().gso_exact_mean(_ptr(v, ctypes.c_double), v.size, int(D)))
+
+
+# ---------------------------------------------------------------------------
+# GridShift-based object tracking (Sec. 2.3, Algorithm 2)
+
+def track_window(frame, width: int, height: int, h: float, bins, rect) -> tuple:
+    """R of one search window (gso_track_window): returns (dict with count,
+    sum_x, sum_y, mean_x, mean_y, min_x, max_x, min_y, max_y; present uint8[k]).
+    The mean is the exact integer sum divided by the count, one IEEE division
+    (NaN for an empty R)."""
+    f = np.ascontiguousarray(np.asarray(frame, dtype=np.float64).reshape(int(height) * int(width), -1))
+    d = f.shape[1]
+    b = np.ascontiguousarray(np.asarray(bins, dtype=np.int64).reshape(-1, d))
+    k = b.shape[0]
+    out = np.zeros(7, dtype=np.int64)
+    present = np.zeros(max(k, 1), dtype=np.uint8)
+    st = lib().gso_track_window(_ptr(f, ctypes.c_double), int(width), int(height), d, float(h),
+                                _ptr(b, ctypes.c_int64), k, int(rect[0]), int(rect[1]),
+                                int(rect[2]), int(rect[3]), _ptr(out, ctypes.c_int64),
+                                _ptr(present, ctypes.c_uint8))
+    if st != 0:
+        raise ValueError("a colour in the window has no exact cell")
+    cnt = int(out[0])
+    r = dict(count=cnt, sum_x=int(out[1]), sum_y=int(out[2]),
+             mean_x=float(out[1]) / cnt if cnt else float("nan"),
+             mean_y=float(out[2]) / cnt if cnt else float("nan"),
+             min_x=int(out[3]), max_x=int(out[4]), min_y=int(out[5]), max_y=int(out[6]))
+    return r, present[:k]
+
+
+def track(frames, width: int, height: int, h: float, o, length: float, window_width: float,
+          bins, f: float = 1.0, eta: float = 0.5, max_inner: int = 50) -> list:
+    """Algorithm 2 from an initial centre, window size and reference cells B,
+    over frames[0], frames[1], ...: per frame, the search window W(o, l/f, w/f)
+    (the pixels within l/2 of o_x and w/2 of o_y) is applied until the centre
+    moves by less than eta (at most max_inner times).  An empty R grows l and w
+    by 1.1; otherwise o moves to R's mean position, B becomes the cells R
+    occupies, and l (w) shrinks by 0.99 where R's x (y) extent is below it,
+    else grows by 1.01.  Returns per frame (o, l, w, inner steps, |B|)."""
+    import math
+    o = (float(o[0]), float(o[1]))
+    l, w = float(length), float(window_width)
+    d = np.asarray(frames[0]).reshape(int(height) * int(width), -1).shape[1]
+    B = np.asarray(bins, dtype=np.int64).reshape(-1, d)
+    emitted = []
+    for fr in frames:
+        inner = 0
+        while inner < max_inner:
+            inner += 1
+            lo, wo = l / f, w / f
+            rect = (math.ceil(o[0] - lo / 2), math.ceil(o[1] - wo / 2),
+                    math.floor(o[0] + lo / 2) + 1, math.floor(o[1] + wo / 2) + 1)
+            r, present = track_window(fr, width, height, h, B, rect)
+            if r["count"] == 0:
+                l, w = 1.1 * l, 1.1 * w
+                continue
+            step = math.hypot(r["mean_x"] - o[0], r["mean_y"] - o[1])
+            o = (r["mean_x"], r["mean_y"])
+            B = B[present == 1]
+            l = l * (0.99 if r["max_x"] - r["min_x"] < l else 1.01)
+            w = w * (0.99 if r["max_y"] - r["min_y"] < w else 1.01)
+            if step < eta:
+                break
+        emitted.append((o, l, w, inner, int(B.shape[0])))
+    return emitted

@@ -1,6 +1,7 @@
 // gs_api.cu -- host side of the C ABI declared in include/gridshift.h: argument
 // checks, the context and its growable device workspace.  The order of the
 // steps of one run is in gs_driver.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -421,10 +422,17 @@ struct gs_ctx {
   PhaseTimer tm;
   gs_phase_times last_times{};
   CtxWorkspace ws;
+  // the tracking window step: reference cells, accumulators, cell flags
+  DBuf<int64_t> tbins;
+  DBuf<TrackAcc> tacc;
+  DBuf<uint8_t> tpresent;
 
   void release_device() {
     ws.release();
     tm.release();
+    tbins.release();
+    tacc.release();
+    tpresent.release();
   }
 };
 
@@ -567,6 +575,116 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
       for (int c = 0; c < 2; ++c) ctx->last_times.step_ms[i][c] = kms[kLoopPhases + 2 * i + c];
   }
   return st;
+}
+
+gs_status gs_track_window(gs_ctx* ctx, const void* frame, gs_dtype dtype, int64_t width,
+                          int64_t height, const int64_t* bins, int64_t k, int64_t x0,
+                          int64_t y0, int64_t x1, int64_t y1, gs_track_result* out,
+                          uint8_t* present) {
+  if (!ctx) return GS_E_INVALID;
+  ctx->err.clear();
+  if (!out) return fail(ctx, GS_E_INVALID, "out is NULL");
+  out->count = 0;
+  out->sum_x = out->sum_y = 0;
+  out->mean_x = out->mean_y = std::nan("");
+  out->min_x = out->min_y = INT64_MAX;
+  out->max_x = out->max_y = INT64_MIN;
+  if (width < 0 || height < 0 || k < 0 || width > (1ll << 31) || height > (1ll << 31))
+    return fail(ctx, GS_E_INVALID, "negative size or count");
+  if (k > 0 && !bins) return fail(ctx, GS_E_INVALID, "bins is NULL with k > 0");
+  if (dtype != GS_IN_F64 && dtype != GS_IN_F32) return fail(ctx, GS_E_INVALID, "bad dtype");
+  if (present)
+    for (int64_t j = 0; j < k; ++j) present[j] = 0;
+  // the window, clipped to the frame
+  x0 = x0 < 0 ? 0 : x0;
+  y0 = y0 < 0 ? 0 : y0;
+  x1 = x1 > width ? width : x1;
+  y1 = y1 > height ? height : y1;
+  const int64_t ww = x1 > x0 ? x1 - x0 : 0, wh = y1 > y0 ? y1 - y0 : 0;
+  if (ww == 0 || wh == 0) return GS_OK;
+  if (!frame) return fail(ctx, GS_E_INVALID, "frame is NULL");
+  const int d = ctx->d;
+  // B sorted lexicographically without duplicates; uidx maps bins[j] to it
+  std::vector<int64_t> order((size_t)k);
+  for (int64_t j = 0; j < k; ++j) order[(size_t)j] = j;
+  auto less = [&](int64_t p, int64_t q) {
+    for (int a = 0; a < d; ++a) {
+      const int64_t u = bins[p * d + a], v = bins[q * d + a];
+      if (u != v) return u < v;
+    }
+    return false;
+  };
+  std::sort(order.begin(), order.end(), less);
+  std::vector<int64_t> ukeys;
+  std::vector<int64_t> uidx((size_t)k);
+  ukeys.reserve((size_t)k * d);
+  int64_t nu = 0;
+  for (int64_t r = 0; r < k; ++r) {
+    const int64_t j = order[(size_t)r];
+    if (r == 0 || less(order[(size_t)r - 1], j)) {
+      for (int a = 0; a < d; ++a) ukeys.push_back(bins[j * d + a]);
+      ++nu;
+    }
+    uidx[(size_t)j] = nu - 1;
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(ctx, GS_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorName(ce));
+  if (ctx->device != dev) {
+    ctx->release_device();
+    ctx->device = dev;
+  }
+  const cudaStream_t s = ctx->stream;
+#define TR_CU(call, what)                                                                   \
+  do {                                                                                      \
+    ce = (call);                                                                            \
+    if (ce != cudaSuccess)                                                                  \
+      return fail(ctx, ce == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA,            \
+                  std::string(what) + ": " + cudaGetErrorName(ce));                         \
+  } while (0)
+  TR_CU(ctx->tbins.ensure((size_t)(nu > 0 ? nu : 1) * d), "alloc track bins");
+  TR_CU(ctx->tacc.ensure(1), "alloc track accumulators");
+  TR_CU(ctx->tpresent.ensure((size_t)(nu > 0 ? nu : 1)), "alloc track flags");
+  TrackAcc h_acc;
+  h_acc.count = 0;
+  h_acc.bad = 0;
+  h_acc.sum_x = h_acc.sum_y = 0;
+  h_acc.min_x = h_acc.min_y = INT64_MAX;
+  h_acc.max_x = h_acc.max_y = INT64_MIN;
+  if (nu > 0)
+    TR_CU(cudaMemcpyAsync(ctx->tbins.p, ukeys.data(), sizeof(int64_t) * nu * d,
+                          cudaMemcpyHostToDevice, s), "H2D track bins");
+  TR_CU(cudaMemcpyAsync(ctx->tacc.p, &h_acc, sizeof(TrackAcc), cudaMemcpyHostToDevice, s),
+        "H2D track accumulators");
+  TR_CU(cudaMemsetAsync(ctx->tpresent.p, 0, (size_t)(nu > 0 ? nu : 1), s), "memset track flags");
+  TR_CU(launch_track(frame, dtype == GS_IN_F32, d, width, x0, y0, ww, wh, ctx->h, ctx->tbins.p, nu,
+                     ctx->tacc.p, ctx->tpresent.p, s), "k_track");
+  std::vector<uint8_t> upresent((size_t)(nu > 0 ? nu : 1));
+  TR_CU(cudaMemcpyAsync(&h_acc, ctx->tacc.p, sizeof(TrackAcc), cudaMemcpyDeviceToHost, s),
+        "D2H track accumulators");
+  if (nu > 0)
+    TR_CU(cudaMemcpyAsync(upresent.data(), ctx->tpresent.p, (size_t)nu, cudaMemcpyDeviceToHost, s),
+          "D2H track flags");
+  TR_CU(cudaStreamSynchronize(s), "sync track");
+#undef TR_CU
+  if (h_acc.bad) {
+    out->count = -1;
+    return fail(ctx, GS_E_INVALID, "a colour in the window is not finite or has |c / h| >= 2^52");
+  }
+  out->count = (int64_t)h_acc.count;
+  out->sum_x = h_acc.sum_x;
+  out->sum_y = h_acc.sum_y;
+  if (out->count > 0) {
+    out->mean_x = (double)out->sum_x / (double)out->count;
+    out->mean_y = (double)out->sum_y / (double)out->count;
+  }
+  out->min_x = h_acc.min_x;
+  out->max_x = h_acc.max_x;
+  out->min_y = h_acc.min_y;
+  out->max_y = h_acc.max_y;
+  if (present)
+    for (int64_t j = 0; j < k; ++j) present[j] = upresent[(size_t)uidx[(size_t)j]];
+  return GS_OK;
 }
 
 gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const int64_t* offsets,

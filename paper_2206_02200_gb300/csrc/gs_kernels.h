@@ -100,6 +100,23 @@ struct LoopArgs {
   bool mixed;             // the float32 mixed-precision variant (GS_FP32_MIXED)
 };
 
+// Accumulators of one tracking window step (gs_track_window).
+struct TrackAcc {
+  unsigned long long count;
+  unsigned long long bad;  // colours without an exact cell (non-finite, |c / h| >= 2^52)
+  long long sum_x, sum_y;
+  long long min_x, max_x, min_y, max_y;
+};
+
+// The window step of Algorithm 2 over the pixels x0 <= x < x0 + ww,
+// y0 <= y < y0 + wh of a width-wide frame of d channels: R = the pixels whose
+// colour cell lies in bins (k x d keys, sorted lexicographically, unique);
+// count, sums and extent of R's positions into acc (initialised by the
+// caller), present[j] = 1 for each bin j that R's pixels occupy.
+cudaError_t launch_track(const void* frame, bool f32, int d, int64_t width, int64_t x0,
+                         int64_t y0, int64_t ww, int64_t wh, double h, const int64_t* bins,
+                         int64_t k, TrackAcc* acc, uint8_t* present, cudaStream_t s);
+
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
                          cudaStream_t s);
 // Binning, first pass.  offsets (device, B + 1 entries) give the points of

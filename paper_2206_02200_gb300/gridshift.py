@@ -32,8 +32,8 @@ GS_IN_F32 = 1
 
 #: every symbol the header declares, in declaration order
 EXPORTS = ("gs_create", "gs_set_precision", "gs_set_stream", "gs_fit", "gs_fit_batched",
-           "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_get_last_error",
-           "gs_status_string", "gs_destroy")
+           "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_track_window",
+           "gs_get_last_error", "gs_status_string", "gs_destroy")
 
 #: gs_phase names, in enum order: CUDA-event phases, then the loop kernel's
 #: own device-clock split
@@ -61,6 +61,17 @@ class gs_phase_times(ctypes.Structure):
     def steps(self) -> list:
         """[(update ms, compaction ms)] of the first 16 update steps."""
         return [(float(self.step_ms[i][0]), float(self.step_ms[i][1])) for i in range(16)]
+
+
+class gs_track_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("sum_x", ctypes.c_int64), ("sum_y", ctypes.c_int64),
+                ("mean_x", ctypes.c_double), ("mean_y", ctypes.c_double),
+                ("min_x", ctypes.c_int64), ("max_x", ctypes.c_int64),
+                ("min_y", ctypes.c_int64), ("max_y", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: (float(getattr(self, f)) if t is ctypes.c_double else int(getattr(self, f)))
+                for f, t in self._fields_}
 
 
 class GridShiftError(RuntimeError):
@@ -102,6 +113,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.gs_fit_noalloc.restype = i32
     L.gs_fit_noalloc.argtypes = [i32, ctypes.c_double, i32, vp, vp, i32, i64, vp, vp, i64,
                                  ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
+    L.gs_track_window.restype = i32
+    L.gs_track_window.argtypes = [vp, vp, i32, i64, i64, vp, i64, i64, i64, i64, i64,
+                                  ctypes.POINTER(gs_track_result), vp]
     L.gs_get_last_error.restype = i32
     L.gs_get_last_error.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     L.gs_status_string.restype = ctypes.c_char_p
@@ -140,6 +154,21 @@ def gs_fit(ctx: int, points_ptr: int, dtype: int, n: int, labels_ptr: int, modes
     st = load().gs_fit(ctx, points_ptr or None, int(dtype), int(n), labels_ptr or None,
                        modes_ptr or None, int(modes_cap), ctypes.byref(k), ctypes.byref(info))
     return st, int(k.value), info
+
+
+def gs_track_window(ctx: int, frame_ptr: int, dtype: int, width: int, height: int, bins,
+                    x0: int, y0: int, x1: int, y1: int):
+    """Raw call; bins: host k x d int64 array.  Returns (status, gs_track_result,
+    present uint8[k])."""
+    import numpy as np
+    b = np.ascontiguousarray(np.asarray(bins, dtype=np.int64))
+    k = b.shape[0] if b.ndim == 2 else 0
+    present = np.zeros(max(k, 1), dtype=np.uint8)
+    res = gs_track_result()
+    st = load().gs_track_window(ctx, frame_ptr or None, int(dtype), int(width), int(height),
+                                b.ctypes.data if k else None, int(k), int(x0), int(y0), int(x1),
+                                int(y1), ctypes.byref(res), present.ctypes.data)
+    return st, res, present[:k]
 
 
 def gs_fit_batched(ctx: int, points_ptr: int, dtype: int, offsets, labels_ptr: int,
@@ -319,3 +348,78 @@ def fit(points, h: float, max_iter: int = 50):
     """One-shot GridShift on an n x d CUDA tensor: (labels, modes, info)."""
     with GridShift(points.shape[1], h, max_iter) as g:
         return g.fit(points)
+
+
+# ---------------------------------------------------------------------------
+# GridShift-based object tracking (Sec. 2.3, Algorithm 2).  The window step
+# runs on the GPU (gs_track_window); the loop around it is host logic.
+
+def window_rect(o, length: float, width: float):
+    """Pixel rectangle (x0, y0, x1, y1) of the window W(o, length, width): the
+    pixels with |x - o_x| <= length / 2 and |y - o_y| <= width / 2."""
+    import math
+    return (math.ceil(o[0] - length / 2), math.ceil(o[1] - width / 2),
+            math.floor(o[0] + length / 2) + 1, math.floor(o[1] + width / 2) + 1)
+
+
+class Tracker:
+    """The tracker of Algorithm 2 over frames of `height` x `width` pixels with
+    d colour channels (CUDA tensors of width * height x d, row-major, y outer).
+
+    State: centre o, window size (length along x, width along y) and the
+    reference set B of colour cells floor(c / h) (a k x d int64 array).  Each
+    frame: search windows W(o, length / f, width / f) until the centre moves by
+    less than eta (at most max_inner times); a window with no pixel of B grows
+    the size by 1.1; otherwise the centre moves to the mean position of R, B
+    becomes the cells of R, and the size shrinks by 0.99 where R's extent is
+    below it, else grows by 1.01.
+    """
+
+    def __init__(self, d: int, h: float, width: int, height: int, o, length: float,
+                 window_width: float, bins, f: float = 1.0, eta: float = 0.5,
+                 max_inner: int = 50):
+        import numpy as np
+        self.ctx = GridShift(d, h, 1)
+        self.W, self.H = int(width), int(height)
+        self.o = (float(o[0]), float(o[1]))
+        self.l, self.w = float(length), float(window_width)
+        self.B = np.ascontiguousarray(np.asarray(bins, dtype=np.int64).reshape(-1, d))
+        self.f, self.eta, self.max_inner = float(f), float(eta), int(max_inner)
+
+    def close(self) -> None:
+        self.ctx.close()
+
+    def window_step(self, frame, rect):
+        """One R (gs_track_window) on a CUDA frame tensor: (result dict, present)."""
+        import torch
+        dt = GS_IN_F64 if frame.dtype == torch.float64 else GS_IN_F32
+        if not frame.is_cuda or not frame.is_contiguous():
+            raise ValueError("frame must be a contiguous CUDA tensor")
+        gs_set_stream(self.ctx._ctx, torch.cuda.current_stream(frame.device).cuda_stream)
+        st, res, present = gs_track_window(self.ctx._ctx, frame.data_ptr(), dt, self.W, self.H,
+                                           self.B, *rect)
+        if st != GS_OK:
+            raise GridShiftError(st, gs_get_last_error(self.ctx._ctx))
+        return res.as_dict(), present
+
+    def step(self, frame) -> dict:
+        """Tracks one frame; returns the emitted window and the inner iterations."""
+        import math
+        inner = 0
+        for inner in range(1, self.max_inner + 1):
+            rect = window_rect(self.o, self.l / self.f, self.w / self.f)
+            r, present = self.window_step(frame, rect)
+            if r["count"] == 0:
+                self.l *= 1.1
+                self.w *= 1.1
+                continue
+            o_new = (r["mean_x"], r["mean_y"])
+            self.B = self.B[present.astype(bool)]
+            self.l *= 0.99 if (r["max_x"] - r["min_x"]) < self.l else 1.01
+            self.w *= 0.99 if (r["max_y"] - r["min_y"]) < self.w else 1.01
+            moved = math.hypot(o_new[0] - self.o[0], o_new[1] - self.o[1])
+            self.o = o_new
+            if moved < self.eta:
+                break
+        return {"o": self.o, "length": self.l, "width": self.w, "inner": inner,
+                "bins": int(self.B.shape[0])}

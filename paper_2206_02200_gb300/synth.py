@@ -23,6 +23,7 @@ __all__ = [
     "image_features",
     "gmm_points",
     "image_batch",
+    "moving_object_frames",
     "WORKLOADS",
 ]
 
@@ -86,6 +87,43 @@ def image_features(img: np.ndarray, xy_scale: float | None = None) -> np.ndarray
     x = xx.reshape(-1) * xy_scale
     y = yy.reshape(-1) * xy_scale
     return np.ascontiguousarray(np.concatenate([rgb, x[:, None], y[:, None]], axis=1))
+
+
+def moving_object_frames(H: int, W: int, T: int, seed: int, radius: float = 20.0,
+                         speed: float = 3.0, sigma: float = 6.0) -> tuple:
+    """T frames (T x H x W x 3 float64, uint8 values) of a disc of one colour
+    moving in a straight line over a fixed Voronoi background (8 regions),
+    with fresh i.i.d. N(0, sigma^2) noise per frame, and the disc's centre per
+    frame (T x 2, (x, y)).  Stands in for a tracking sequence.
+
+    The disc starts at a seed-drawn point in the middle of the image and moves
+    ``speed`` pixels per frame in a seed-drawn direction; its colour is drawn
+    at least 80 (max-norm) away from every background colour."""
+    rng = np.random.default_rng(seed)
+    sites = np.stack([rng.uniform(0.0, W, 8), rng.uniform(0.0, H, 8)], axis=1)
+    bg = rng.uniform(0.0, 255.0, size=(8, 3))
+    while True:
+        obj = rng.uniform(0.0, 255.0, size=3)
+        if np.min(np.max(np.abs(bg - obj[None, :]), axis=1)) >= 80.0:
+            break
+    lab = _nearest_site(H, W, sites)
+    base = bg[lab]
+    c0 = np.array([rng.uniform(0.35 * W, 0.65 * W), rng.uniform(0.35 * H, 0.65 * H)])
+    ang = rng.uniform(0.0, 2.0 * np.pi)
+    vel = speed * np.array([np.cos(ang), np.sin(ang)])
+    yy, xx = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64),
+                         indexing="ij")
+    frames = np.empty((T, H, W, 3), dtype=np.float64)
+    centres = np.empty((T, 2), dtype=np.float64)
+    for t in range(T):
+        c = c0 + t * vel
+        centres[t] = c
+        img = base.copy()
+        inside = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 <= radius * radius
+        img[inside] = obj
+        img = img + rng.normal(0.0, sigma, size=img.shape)
+        frames[t] = np.rint(np.clip(img, 0.0, 255.0))
+    return frames, centres
 
 
 def gmm_points(n: int, d: int, components: int, seed: int, lo: float = 0.0, hi: float = 100.0,

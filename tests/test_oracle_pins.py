@@ -17,6 +17,7 @@ Nothing here compares the oracle with itself.  The pins are:
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 from fractions import Fraction as Fr
 
 import numpy as np
@@ -340,3 +341,116 @@ def test_exact_sum_and_mean():
     assert oracle.exact_sum([1e300, 1.0, -1e300]) == 1.0
     assert oracle.exact_sum([2.0 ** 53, 1.0]) == 2.0 ** 53
     assert oracle.exact_sum([2.0 ** 53, 1.0, 2.0 ** -60]) == 2.0 ** 53 + 2
+
+
+# ---------------------------------------------------------------------------
+# GridShift-based tracking (Sec. 2.3, Algorithm 2): the window step R and the
+# tracker loop of the oracle, against exact rational arithmetic and closed
+# forms.
+
+def _cell(c, h):
+    return [math.floor(Fraction(float(v)) / Fraction(float(h))) for v in c]
+
+
+def _window_brute(frame, W, H, h, bins, rect):
+    """R by exact rationals: count, sums, extent, present."""
+    x0, y0 = max(rect[0], 0), max(rect[1], 0)
+    x1, y1 = min(rect[2], W), min(rect[3], H)
+    keys = [tuple(b) for b in np.asarray(bins, dtype=np.int64).tolist()]
+    present = [0] * len(keys)
+    xs, ys = [], []
+    for y in range(y0, y1):
+        for x in range(x0, x1):
+            kc = tuple(_cell(frame[y * W + x], h))
+            hit = False
+            for j, b in enumerate(keys):
+                if b == kc:
+                    present[j] = 1
+                    hit = True
+            if hit:
+                xs.append(x)
+                ys.append(y)
+    return xs, ys, present
+
+
+def test_track_window_hand_example():
+    # 4 x 3 frame, one channel, value of pixel (x, y) = 4 y + x; h = 2, so the
+    # cell of a value v is floor(v / 2).  B = {1, 4}: cell 1 holds values 2, 3
+    # (pixels (2,0), (3,0)), cell 4 holds 8, 9 (pixels (0,2), (1,2)).  R is
+    # those four pixels: sum x = 2+3+0+1 = 6, sum y = 0+0+2+2 = 4, mean
+    # (1.5, 1.0), x extent 0..3, y extent 0..2, both cells present.
+    frame = np.arange(12, dtype=np.float64).reshape(12, 1)
+    r, present = oracle.track_window(frame, 4, 3, 2.0, [[1], [4]], (0, 0, 4, 3))
+    assert (r["count"], r["sum_x"], r["sum_y"]) == (4, 6, 4)
+    assert (r["mean_x"], r["mean_y"]) == (1.5, 1.0)
+    assert (r["min_x"], r["max_x"], r["min_y"], r["max_y"]) == (0, 3, 0, 2)
+    assert present.tolist() == [1, 1]
+    # the window x in [1, 3), y in [0, 3) keeps (2,0) and (1,2) only; cell 6
+    # (values 12, 13) holds no pixel
+    r, present = oracle.track_window(frame, 4, 3, 2.0, [[1], [4], [6]], (1, 0, 3, 3))
+    assert (r["count"], r["sum_x"], r["sum_y"]) == (2, 3, 2)
+    assert present.tolist() == [1, 1, 0]
+
+
+def test_track_window_whole_frame_closed_form():
+    # B = every cell of the frame and the window = the frame: R is every
+    # pixel, whose mean position is the frame's centre ((W-1)/2, (H-1)/2)
+    rng = np.random.default_rng(5)
+    W, H, h = 13, 9, 7.5
+    frame = rng.uniform(-50, 50, size=(W * H, 3))
+    B = np.unique(np.array([_cell(c, h) for c in frame], dtype=np.int64), axis=0)
+    r, present = oracle.track_window(frame, W, H, h, B, (-5, -5, W + 5, H + 5))
+    assert r["count"] == W * H
+    assert (r["mean_x"], r["mean_y"]) == ((W - 1) / 2, (H - 1) / 2)
+    assert (r["min_x"], r["max_x"], r["min_y"], r["max_y"]) == (0, W - 1, 0, H - 1)
+    assert present.all()
+    # an empty B, or a window outside the frame, gives an empty R
+    r, present = oracle.track_window(frame, W, H, h, np.zeros((0, 3), np.int64), (0, 0, W, H))
+    assert r["count"] == 0 and math.isnan(r["mean_x"]) and r["min_x"] > r["max_x"]
+    r, present = oracle.track_window(frame, W, H, h, B, (W, 0, W + 4, H))
+    assert r["count"] == 0 and not present.any()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_track_window_against_exact_rationals(seed):
+    rng = np.random.default_rng(100 + seed)
+    W, H, d = int(rng.integers(5, 14)), int(rng.integers(5, 14)), int(rng.integers(1, 4))
+    h = float(rng.uniform(3, 12))
+    frame = np.rint(rng.uniform(0, 60, size=(W * H, d))) + (rng.random((W * H, d)) < 0.3) * 0.5
+    cells = np.array([_cell(c, h) for c in frame], dtype=np.int64)
+    B = cells[rng.choice(len(cells), size=6)]
+    B = np.concatenate([B, B[:2], [[999] * d]])  # duplicates and an absent cell
+    rect = (int(rng.integers(-3, W)), int(rng.integers(-3, H)), 0, 0)
+    rect = (rect[0], rect[1], rect[0] + int(rng.integers(0, W + 4)), rect[1] + int(rng.integers(0, H + 4)))
+    r, present = oracle.track_window(frame, W, H, h, B, rect)
+    xs, ys, pres = _window_brute(frame, W, H, h, B, rect)
+    assert r["count"] == len(xs) and r["sum_x"] == sum(xs) and r["sum_y"] == sum(ys)
+    if xs:
+        assert r["mean_x"] == sum(xs) / len(xs) and r["mean_y"] == sum(ys) / len(ys)
+        assert (r["min_x"], r["max_x"], r["min_y"], r["max_y"]) == (min(xs), max(xs), min(ys), max(ys))
+    assert present.tolist() == pres
+
+
+def test_tracker_follows_a_moving_object():
+    # Algorithm 2 on a disc moving 3 px per frame: the emitted centre stays
+    # within 2 px of the disc's centre, and the window never loses it
+    H, W, T, h = 96, 128, 8, 16.0
+    rng = np.random.default_rng(11)
+    yy, xx = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64),
+                         indexing="ij")
+    bg = np.where((xx < W / 2)[..., None], [[40.0, 200.0, 90.0]], [[180.0, 60.0, 30.0]])
+    centres = np.array([[50.0 + 3.0 * t, 40.0 + 2.0 * t] for t in range(T)])
+    frames = []
+    for c in centres:
+        img = bg.copy()
+        img[(xx - c[0]) ** 2 + (yy - c[1]) ** 2 <= 144.0] = [120.0, 120.0, 230.0]
+        frames.append(np.rint(np.clip(img + rng.normal(0.0, 5.0, img.shape), 0, 255)))
+    f0 = frames[0].reshape(H * W, 3)
+    yy, xx = np.divmod(np.arange(H * W), W)
+    inside = (xx - centres[0, 0]) ** 2 + (yy - centres[0, 1]) ** 2 <= 12.0 ** 2
+    B = np.unique(np.array([_cell(c, h) for c in f0[inside]], dtype=np.int64), axis=0)
+    out = oracle.track([fr.reshape(H * W, 3) for fr in frames[1:]], W, H, h,
+                       centres[0] + np.array([2.0, -1.0]), 40.0, 40.0, B, f=1.0, eta=0.25)
+    for (o, l, w, inner, nb), c in zip(out, centres[1:]):
+        assert math.hypot(o[0] - c[0], o[1] - c[1]) < 2.0
+        assert nb > 0 and inner >= 1
