@@ -263,8 +263,9 @@ gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_stream, const
  * R is empty); present (host, k bytes, may be NULL): present[j] = 1 if some
  * pixel of R lies in cell bins[j], else 0.  The call synchronises the stream.
  * Returns GS_OK, GS_E_INVALID (null pointers, negative sizes, k < 0, a colour
- * in the window that is not finite or has |c / h| >= 2^52: then
- * out->count = -1), GS_E_NOMEM or GS_E_CUDA. */
+ * in the window that is not finite or has |c| >= 4e15 h, the product rounded
+ * to float64: then out->count = -1), GS_E_KEYRANGE (the keys of bins span
+ * more than 2^22 cells on one channel), GS_E_NOMEM or GS_E_CUDA. */
 typedef struct {
   int64_t count;
   int64_t sum_x, sum_y;

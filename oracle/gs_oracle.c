@@ -397,7 +397,7 @@ int gso_track_window(const double *frame, int64_t width, int64_t height, int d, 
     for (int64_t x = x0; x < x1; x++) {
       const double *c = frame + (y * width + x) * d;
       for (int a = 0; a < d; a++) {
-        if (!(fabs(c[a] / h) < 4.0e15)) return 1;
+        if (!(fabs(c[a]) < 4.0e15 * h)) return 1;
         key[a] = gso_floor_div(c[a], h);
       }
       int in = 0;

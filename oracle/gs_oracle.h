@@ -61,7 +61,7 @@ double gso_exact_mean(const double *v, int64_t n, uint64_t D);
  * INT64_MIN when R is empty); present[j] = 1 if some pixel of R lies in cell
  * bins[j], else 0.  A plain double loop with a linear search of bins.
  * Returns 0, or 1 when a colour in the window is not finite or has
- * |c / h| >= 2^52. */
+ * |c| >= 4e15 h (the product rounded to double). */
 int gso_track_window(const double *frame, int64_t width, int64_t height, int d, double h,
                      const int64_t *bins, int64_t k, int64_t x0, int64_t y0, int64_t x1,
                      int64_t y1, int64_t *out, uint8_t *present);

@@ -10,6 +10,7 @@
 
 #include "../../include/gridshift.h"
 #include "gs_driver.h"
+#include "gs_planner.cuh"
 
 using namespace gs;
 
@@ -422,17 +423,19 @@ struct gs_ctx {
   PhaseTimer tm;
   gs_phase_times last_times{};
   CtxWorkspace ws;
-  // the tracking window step: reference cells, accumulators, cell flags
-  DBuf<int64_t> tbins;
-  DBuf<TrackAcc> tacc;
-  DBuf<uint8_t> tpresent;
+  // the tracking window step: one device block [accumulators | reference
+  // cells | cell flags] and its pinned host staging
+  DBuf<uint4> tbuf;
+  unsigned char* h_track = nullptr;
+  size_t h_track_cap = 0;
 
   void release_device() {
     ws.release();
     tm.release();
-    tbins.release();
-    tacc.release();
-    tpresent.release();
+    tbuf.release();
+    if (h_track) cudaFreeHost(h_track);
+    h_track = nullptr;
+    h_track_cap = 0;
   }
 };
 
@@ -642,46 +645,79 @@ gs_status gs_track_window(gs_ctx* ctx, const void* frame, gs_dtype dtype, int64_
       return fail(ctx, ce == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA,            \
                   std::string(what) + ": " + cudaGetErrorName(ce));                         \
   } while (0)
-  TR_CU(ctx->tbins.ensure((size_t)(nu > 0 ? nu : 1) * d), "alloc track bins");
-  TR_CU(ctx->tacc.ensure(1), "alloc track accumulators");
-  TR_CU(ctx->tpresent.ensure((size_t)(nu > 0 ? nu : 1)), "alloc track flags");
-  TrackAcc h_acc;
-  h_acc.count = 0;
-  h_acc.bad = 0;
-  h_acc.sum_x = h_acc.sum_y = 0;
-  h_acc.min_x = h_acc.min_y = INT64_MAX;
-  h_acc.max_x = h_acc.max_y = INT64_MIN;
-  if (nu > 0)
-    TR_CU(cudaMemcpyAsync(ctx->tbins.p, ukeys.data(), sizeof(int64_t) * nu * d,
-                          cudaMemcpyHostToDevice, s), "H2D track bins");
-  TR_CU(cudaMemcpyAsync(ctx->tacc.p, &h_acc, sizeof(TrackAcc), cudaMemcpyHostToDevice, s),
-        "H2D track accumulators");
-  TR_CU(cudaMemsetAsync(ctx->tpresent.p, 0, (size_t)(nu > 0 ? nu : 1), s), "memset track flags");
-  TR_CU(launch_track(frame, dtype == GS_IN_F32, d, width, x0, y0, ww, wh, ctx->h, ctx->tbins.p, nu,
-                     ctx->tacc.p, ctx->tpresent.p, s), "k_track");
-  std::vector<uint8_t> upresent((size_t)(nu > 0 ? nu : 1));
-  TR_CU(cudaMemcpyAsync(&h_acc, ctx->tacc.p, sizeof(TrackAcc), cudaMemcpyDeviceToHost, s),
-        "D2H track accumulators");
-  if (nu > 0)
-    TR_CU(cudaMemcpyAsync(upresent.data(), ctx->tpresent.p, (size_t)nu, cudaMemcpyDeviceToHost, s),
-          "D2H track flags");
-  TR_CU(cudaStreamSynchronize(s), "sync track");
-#undef TR_CU
-  if (h_acc.bad) {
-    out->count = -1;
-    return fail(ctx, GS_E_INVALID, "a colour in the window is not finite or has |c / h| >= 2^52");
+  // cell decisions: per channel, the exact faces spanning B's keys
+  TrackPlan tp;
+  std::memset(&tp, 0, sizeof(tp));
+  size_t nthr = 0;
+  for (int a = 0; a < d; ++a) {
+    int64_t lo = 0, hi = -1;  // no keys: an empty span (one face)
+    for (int64_t u = 0; u < nu; ++u) {
+      const int64_t v = ukeys[(size_t)u * d + a];
+      if (u == 0 || v < lo) lo = v;
+      if (u == 0 || v > hi) hi = v;
+    }
+    if (hi - lo >= (1ll << 22))
+      return fail(ctx, GS_E_KEYRANGE, "bins span more than 2^22 cells on one channel");
+    tp.lo[a] = lo;
+    tp.span[a] = (int)(hi - lo + 1);
+    tp.toff[a] = (int)nthr;
+    nthr += (size_t)tp.span[a] + 1;
   }
-  out->count = (int64_t)h_acc.count;
-  out->sum_x = h_acc.sum_x;
-  out->sum_y = h_acc.sum_y;
+  const double lim = 4.0e15 * ctx->h;
+  std::memcpy(&tp.lim_bits, &lim, 8);
+  tp.inv_h = (float)(1.0 / ctx->h);
+  // [TrackAcc | nu * d keys | faces | nu flags], 16-byte aligned pieces
+  const size_t off_bins = (sizeof(TrackAcc) + 15) & ~size_t(15);
+  const size_t off_thr = off_bins + sizeof(int64_t) * (size_t)nu * d;
+  const size_t off_flags = off_thr + sizeof(int64_t) * nthr;
+  const size_t bytes = off_flags + (size_t)(nu > 0 ? nu : 1);
+  TR_CU(ctx->tbuf.ensure((bytes + 15) / 16), "alloc track buffers");
+  if (ctx->h_track_cap < bytes) {
+    if (ctx->h_track) cudaFreeHost(ctx->h_track);
+    ctx->h_track = nullptr;
+    ctx->h_track_cap = 0;
+    TR_CU(cudaHostAlloc((void**)&ctx->h_track, bytes, cudaHostAllocDefault), "alloc track staging");
+    ctx->h_track_cap = bytes;
+  }
+  unsigned char* hb = ctx->h_track;
+  unsigned char* db = reinterpret_cast<unsigned char*>(ctx->tbuf.p);
+  TrackAcc* h_acc = reinterpret_cast<TrackAcc*>(hb);
+  h_acc->count = 0;
+  h_acc->bad = 0;
+  h_acc->sum_x = h_acc->sum_y = 0;
+  h_acc->min_x = h_acc->min_y = INT64_MAX;
+  h_acc->max_x = h_acc->max_y = INT64_MIN;
+  if (nu > 0) std::memcpy(hb + off_bins, ukeys.data(), sizeof(int64_t) * (size_t)nu * d);
+  int64_t* hthr = reinterpret_cast<int64_t*>(hb + off_thr);
+  for (int a = 0; a < d; ++a)
+    for (int j = 0; j <= tp.span[a]; ++j)
+      hthr[tp.toff[a] + j] = plan_ord_of(plan_face(tp.lo[a] + j, ctx->h));
+  std::memset(hb + off_flags, 0, (size_t)(nu > 0 ? nu : 1));
+  TR_CU(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s), "H2D track inputs");
+  TR_CU(launch_track(frame, dtype == GS_IN_F32, d, width, x0, y0, ww, wh, tp,
+                     reinterpret_cast<const int64_t*>(db + off_thr),
+                     reinterpret_cast<const int64_t*>(db + off_bins), nu,
+                     reinterpret_cast<TrackAcc*>(db), db + off_flags, s), "k_track");
+  // the accumulators and the flags back (the keys between them come along)
+  TR_CU(cudaMemcpyAsync(hb, db, bytes, cudaMemcpyDeviceToHost, s), "D2H track results");
+  TR_CU(cudaStreamSynchronize(s), "sync track");
+  const uint8_t* upresent = hb + off_flags;
+#undef TR_CU
+  if (h_acc->bad) {
+    out->count = -1;
+    return fail(ctx, GS_E_INVALID, "a colour in the window is not finite or has |c| >= 4e15 h");
+  }
+  out->count = (int64_t)h_acc->count;
+  out->sum_x = h_acc->sum_x;
+  out->sum_y = h_acc->sum_y;
   if (out->count > 0) {
     out->mean_x = (double)out->sum_x / (double)out->count;
     out->mean_y = (double)out->sum_y / (double)out->count;
   }
-  out->min_x = h_acc.min_x;
-  out->max_x = h_acc.max_x;
-  out->min_y = h_acc.min_y;
-  out->max_y = h_acc.max_y;
+  out->min_x = h_acc->min_x;
+  out->max_x = h_acc->max_x;
+  out->min_y = h_acc->min_y;
+  out->max_y = h_acc->max_y;
   if (present)
     for (int64_t j = 0; j < k; ++j) present[j] = upresent[(size_t)uidx[(size_t)j]];
   return GS_OK;

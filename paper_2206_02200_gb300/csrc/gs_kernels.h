@@ -108,14 +108,29 @@ struct TrackAcc {
   long long min_x, max_x, min_y, max_y;
 };
 
+// Cell decisions of the tracking window step: per channel a, B's keys span
+// lo[a] .. lo[a] + span[a] - 1, and the face table at thr + toff[a] holds the
+// order codes of the span[a] + 1 faces (least double >= q h) of
+// q = lo[a] .. lo[a] + span[a]; lim_bits = the bits of 4e15 h (|c| at or
+// above it: no exact cell).
+struct TrackPlan {
+  int64_t lo[kMaxD];
+  int span[kMaxD];
+  int toff[kMaxD];
+  uint64_t lim_bits;
+  float inv_h;
+};
+
 // The window step of Algorithm 2 over the pixels x0 <= x < x0 + ww,
 // y0 <= y < y0 + wh of a width-wide frame of d channels: R = the pixels whose
-// colour cell lies in bins (k x d keys, sorted lexicographically, unique);
-// count, sums and extent of R's positions into acc (initialised by the
-// caller), present[j] = 1 for each bin j that R's pixels occupy.
+// colour cell lies in bins (k >= 1 keys of d channels, sorted
+// lexicographically, unique); count, sums and extent of R's positions into
+// acc (initialised by the caller), present[j] = 1 for each bin j that R's
+// pixels occupy.
 cudaError_t launch_track(const void* frame, bool f32, int d, int64_t width, int64_t x0,
-                         int64_t y0, int64_t ww, int64_t wh, double h, const int64_t* bins,
-                         int64_t k, TrackAcc* acc, uint8_t* present, cudaStream_t s);
+                         int64_t y0, int64_t ww, int64_t wh, const TrackPlan& tp,
+                         const int64_t* thr, const int64_t* bins, int64_t k, TrackAcc* acc,
+                         uint8_t* present, cudaStream_t s);
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
                          cudaStream_t s);

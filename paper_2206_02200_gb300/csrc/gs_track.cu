@@ -3,15 +3,16 @@
 // lies in the reference set B, with the count, the exact position sums and
 // extent of R, and which cells of B occur in R (the next B).
 //
-// One thread per window pixel: the exact cell key of its colour (floor of the
-// exact quotient, as the plan's face tables decide it), a binary search in B
-// sorted lexicographically, then warp and block reductions and one set of
-// global atomics per block.  The work is a single pass over the window's
-// colours (bound by their read); B is small and stays in L1/L2.
+// One thread per window pixel: per channel, the exact cell key of its colour
+// (floor of the exact quotient) decided by integer compares against a table
+// of exact cell faces spanning B's keys on that channel (a colour outside
+// that span cannot be in B), then a binary search in B sorted
+// lexicographically, warp and block reductions and one set of global atomics
+// per block.  No float64 arithmetic: the pass is bound by the read of the
+// window's colours; B and the face table stay in L1/L2.
 #include <cstdint>
 
 #include "gs_common.cuh"
-#include "gs_planner.cuh"
 
 namespace gs {
 
@@ -20,7 +21,8 @@ namespace {
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock)
     k_track(const T* __restrict__ frame, int64_t width, int64_t x0, int64_t y0, int64_t ww,
-            int64_t npix, double h, const int64_t* __restrict__ bins, int64_t k, TrackAcc* acc,
+            int64_t npix, TrackPlan tp, const int64_t* __restrict__ thr,
+            const int64_t* __restrict__ bins, int64_t k, TrackAcc* acc,
             uint8_t* __restrict__ present) {
   __shared__ unsigned long long s_cnt, s_bad;
   __shared__ long long s_sx, s_sy, s_mnx, s_mxx, s_mny, s_mxy;
@@ -39,19 +41,23 @@ __global__ void __launch_bounds__(kBlock)
     const int64_t x = x0 + p % ww, y = y0 + p / ww;
     const T* c = frame + (size_t)(y * width + x) * D;
     int64_t key[D];
-    bool finite = true;
+    bool valid = true, inside = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const double v = (double)__ldg(c + a);
-      // a colour whose quotient by h is not below 2^52 in magnitude (or is
-      // not finite) has no exact integer cell here: counted as invalid
-      finite = finite && fabs(v / h) < 4.0e15;
-      key[a] = finite ? plan_floor_div(v, h) : 0;
+      const uint64_t b = load_bits<T>(c + a);
+      // not finite, or |c| >= lim (4e15 h): no exact cell (counted invalid)
+      valid = valid && (b & 0x7FFFFFFFFFFFFFFFull) < tp.lim_bits;
+      const int64_t v = ord_of_bits(b);
+      const int64_t* t = thr + tp.toff[a];
+      // outside the faces of B's keys on this axis: not in B
+      inside = inside && v >= __ldg(&t[0]) && v < __ldg(&t[tp.span[a]]);
+      key[a] = inside ? tp.lo[a] + key_index(t, tp.span[a], tp.lo[a], tp.inv_h, b) : 0;
     }
-    if (!finite) {
+    if (!valid) {
       ++bad;
       continue;
     }
+    if (!inside) continue;
     // lexicographic binary search for the first bin >= key
     int64_t lo = 0, hi = k;
     while (lo < hi) {
@@ -114,17 +120,20 @@ __global__ void __launch_bounds__(kBlock)
 }  // namespace
 
 cudaError_t launch_track(const void* frame, bool f32, int d, int64_t width, int64_t x0,
-                         int64_t y0, int64_t ww, int64_t wh, double h, const int64_t* bins,
-                         int64_t k, TrackAcc* acc, uint8_t* present, cudaStream_t s) {
+                         int64_t y0, int64_t ww, int64_t wh, const TrackPlan& tp,
+                         const int64_t* thr, const int64_t* bins, int64_t k, TrackAcc* acc,
+                         uint8_t* present, cudaStream_t s) {
   const int64_t npix = ww * wh;
   if (npix <= 0) return cudaSuccess;
   const unsigned g = grid_for(npix, kBlock, 152u * 8u);
   if (f32) {
     GS_DISPATCH_D(d, k_track<D, float><<<g, kBlock, 0, s>>>((const float*)frame, width, x0, y0,
-                                                            ww, npix, h, bins, k, acc, present));
+                                                            ww, npix, tp, thr, bins, k, acc,
+                                                            present));
   } else {
     GS_DISPATCH_D(d, k_track<D, double><<<g, kBlock, 0, s>>>((const double*)frame, width, x0, y0,
-                                                             ww, npix, h, bins, k, acc, present));
+                                                             ww, npix, tp, thr, bins, k, acc,
+                                                             present));
   }
   return cudaGetLastError();
 }
