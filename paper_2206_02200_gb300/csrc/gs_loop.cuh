@@ -1242,7 +1242,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
                                uint32_t maskM, uint32_t m_prev, uint32_t base_prev,
                                uint32_t base, bool& any_nb, int pen = 0,
                                uint32_t maskQ = 0) {
-  constexpr int U = ProbeBatch<D, GS>::value;
+  constexpr int U = ProbeBatch<D, GS>::value > 2 ? 2 : ProbeBatch<D, GS>::value;
   constexpr int W = RowW<D>::value, NL = RowW<D>::loads;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
