@@ -564,7 +564,7 @@ template <int D, int GS, bool BT>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
                              unsigned& inexact, unsigned& werr, int pen = 0) {
-  constexpr int U = ProbeBatch<D, GS>::value;
+  constexpr int U = ProbeBatch<D, GS>::value > 2 ? 2 : ProbeBatch<D, GS>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
