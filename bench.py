@@ -147,6 +147,24 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the job's ranks (a job's time is its slowest
+    rank's); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank
+    processes units_per_rank per step, and the job takes `seconds`."""
+    return units_per_rank * steps * world / seconds / 1e6
+
+
 def load_workload(name: str) -> dict:
     from paper_2206_02200_gb300 import synth
     return synth.WORKLOADS[name]()
@@ -337,12 +355,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     barrier()
     clk = clocks.stop()
     g.set_timing(False)
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = n * args.steps * world / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    value = job_rate(n, args.steps, world, total_ms / 1e3)
 
     # -- agreement of the float32 path with the FP64 path (which the tests
     #    hold bit-identical to the oracle)
@@ -413,11 +427,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         h_modes[:kk].copy_(modes[:kk], non_blocking=True)
         stream.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = n * e2e_steps * world / float(t.item()) / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = job_rate(n, e2e_steps, world, e2e_s)
 
     # -- roofline of the dominant kernel (the loop kernel: one launch per step)
     pk = peaks()
