@@ -331,8 +331,13 @@ struct CtxWorkspace : public Workspace {
       WS_CU(pslot[i].ensure(m), "alloc pslot");
     }
     WS_CU(qlist.ensure((size_t)m * 3), "alloc pencil list");
-    if (d >= kPencil2MinD)
-      WS_CU(ptab.ensure(pow2_at_least(12ull * m, 64), d, (size_t)m * 9, s), "alloc pencil table");
+    // the second pencil table: 12 slots per cell bound, at most 2^24 slots
+    // (2 GB at d = 6); where it is short, step 0 uses one pencil stage
+    if (d >= kPencil2MinD) {
+      uint32_t cp = pow2_at_least(12ull * m, 64);
+      if (cp > (1u << 24)) cp = 1u << 24;
+      WS_CU(ptab.ensure(cp, d, (size_t)m * 9, s), "alloc pencil table");
+    }
     b.ptab = ptab.view();
     WS_CU(forest.ensure((size_t)m * (max_iter + 1)), "alloc forest");
     WS_CU(forest2.ensure((size_t)m * (max_iter + 1)), "alloc forest");
