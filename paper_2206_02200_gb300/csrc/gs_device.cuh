@@ -185,6 +185,31 @@ __device__ __forceinline__ double round_fixed(u128 V, int L, unsigned& inexact) 
   return round_limbs<4>(w, L, neg, false, inexact);
 }
 
+// V (units of 2^L, two's complement) rounded to the nearest value a float64
+// holds (ties to even), still in units of 2^L: the value round_fixed gives,
+// converted back by to_fixed, computed on the integer directly (keep the 53
+// bits from the leading one, or the bits from 2^-1074 up where that is
+// lower, and round on the rest).  Sets err where to_fixed would: a result of
+// 2^126 or more.
+__device__ __forceinline__ u128 round_to_double(u128 V, int L, unsigned& err) {
+  const bool neg = is_neg(V);
+  u128 mag = neg ? (u128)0 - V : V;
+  if (mag == 0) return 0;
+  const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
+  const int P = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  int rp = P - 52;  // the last bit kept
+  if (rp < -1074 - L) rp = -1074 - L;
+  if (rp > 0) {
+    const u128 keep = mag >> rp;
+    const u128 rem = mag - (keep << rp);
+    const u128 half = (u128)1 << (rp - 1);
+    const bool up = rem > half || (rem == half && ((uint64_t)keep & 1u));
+    mag = (keep + (up ? 1u : 0u)) << rp;
+  }
+  if ((uint64_t)(mag >> 64) >> 62) err = 1;
+  return neg ? (u128)0 - mag : mag;
+}
+
 // Round the exact quotient (N * 2^L) / D to float64 (D >= 1).  Long division
 // of N * 2^64 by D in 32-bit digits, from the top; once three digits below
 // the leading nonzero one are known (at least 65 quotient bits), the rest only

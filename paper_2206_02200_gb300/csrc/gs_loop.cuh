@@ -138,9 +138,10 @@ __device__ __forceinline__ ulonglong2 pack(u128 v) {
 // equals; clears the accumulators.
 __device__ __forceinline__ ulonglong2 settle_sum(uint64_t* acc, int L, unsigned& inexact,
                                                  unsigned& werr) {
-  const double v = round_fixed(limbs_value(acc), L, inexact);
+  (void)inexact;
+  const u128 v = round_to_double(limbs_value(acc), L, werr);
   acc[0] = acc[1] = acc[2] = acc[3] = 0;
-  return pack(to_fixed(bits_of(v), L, inexact, werr));
+  return pack(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -1847,8 +1848,7 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
             Sa = Sx[a];
             La = g_plan.L[a];
           }
-        const double v = round_fixed(Sa, La, inexact);
-        S.sum(nxtb)[(size_t)id * D + glane] = pack(to_fixed(bits_of(v), La, inexact, werr));
+        S.sum(nxtb)[(size_t)id * D + glane] = pack(round_to_double(Sa, La, werr));
       }
       if (live) {
         if (glane == 0) {
