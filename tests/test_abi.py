@@ -4,10 +4,12 @@ No compute call is made here (these run without a GPU)."""
 from __future__ import annotations
 
 import ctypes
+import math
 import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2206_02200_gb300 import _native, gridshift
@@ -101,3 +103,35 @@ def test_product_never_imports_the_oracle():
         text = open(path).read()
         assert "import oracle" not in text and "from oracle" not in text, path
         assert "gs_oracle" not in text and "gso_" not in text, path
+
+
+def test_track_window_host_only_checks(lib):
+    # argument checks and empty windows return before any device work
+    ctx = gridshift.gs_create(3, 16.0, 1)
+    try:
+        bins = np.zeros((2, 3), dtype=np.int64)
+        st, res, present = gridshift.gs_track_window(ctx, 0, gridshift.GS_IN_F64, 64, 48, bins,
+                                                     10, 10, 10, 20)  # zero-width window
+        assert st == gridshift.GS_OK and res.count == 0 and present.tolist() == [0, 0]
+        assert math.isnan(res.mean_x) and res.min_x > res.max_x
+        st, res, _ = gridshift.gs_track_window(ctx, 0, gridshift.GS_IN_F64, 64, 48, bins,
+                                               70, 0, 90, 48)  # right of the frame
+        assert st == gridshift.GS_OK and res.count == 0
+        st, _, _ = gridshift.gs_track_window(ctx, 0, gridshift.GS_IN_F64, -1, 48, bins, 0, 0, 1, 1)
+        assert st == gridshift.GS_E_INVALID
+        st, _, _ = gridshift.gs_track_window(ctx, 0, 9, 64, 48, bins, 0, 0, 1, 1)
+        assert st == gridshift.GS_E_INVALID
+        st, _, _ = gridshift.gs_track_window(ctx, 0, gridshift.GS_IN_F64, 64, 48, bins, 0, 0, 8, 8)
+        assert st == gridshift.GS_E_INVALID  # NULL frame with a non-empty window
+        out = gridshift.gs_track_result()
+        assert lib.gs_track_window(ctx, None, 0, 4, 4, None, 1, 0, 0, 4, 4, ctypes.byref(out),
+                                   None) == gridshift.GS_E_INVALID  # bins NULL with k > 0
+    finally:
+        gridshift.gs_destroy(ctx)
+
+
+def test_window_rect():
+    # W(o, l, w): the pixels within l/2 of o_x and w/2 of o_y
+    assert gridshift.window_rect((10.5, 20.0), 5.0, 4.0) == (8, 18, 14, 23)
+    assert gridshift.window_rect((0.0, 0.0), 1.0, 1.0) == (0, 0, 1, 1)
+    assert gridshift.window_rect((3.2, 7.7), 0.2, 0.2) == (4, 8, 4, 8)  # no pixel inside
