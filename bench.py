@@ -55,8 +55,8 @@ def loop_bytes(n: int, d: int, elem: int, cell_steps: int, fp32: bool) -> int:
 # on (the files that define k_range, k_plan, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
-    ("image_1080p_d5", "fp64", "k_loop"): (138.78e6, "0ab741ec451851a0"),
-    ("image_1080p_d5", "fp64", "k_bin"): (92.02e6, "0ab741ec451851a0"),
+    ("image_1080p_d5", "fp64", "k_loop"): (139.71e6, "d236db15bdb005c3"),
+    ("image_1080p_d5", "fp64", "k_bin"): (91.92e6, "d236db15bdb005c3"),
 }
 
 

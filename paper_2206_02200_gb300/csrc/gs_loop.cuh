@@ -2305,7 +2305,9 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   int pen = 0;
   uint32_t maskQ = 0, qn = 0, maskQ2 = 0, qn2 = 0;
   if constexpr (!BT && D >= 3) {
-    if (m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr) {
+    // Q holds at most 3 m0 keys: only where tab[2] keeps them at load <= 3/4
+    if (m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr &&
+        4ull * m0 <= (uint64_t)A.capAB) {
       pen = 1;
       maskQ = mask_for(3 * m0, A.capAB);
       if (F32)

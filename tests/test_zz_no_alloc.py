@@ -100,3 +100,21 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
     assert st == gridshift.GS_E_SCRATCH
     # still usable afterwards
     test_noalloc_matches_gs_fit_twice_in_a_row()
+
+
+@pytest.mark.parametrize("d", [3, 6])
+def test_noalloc_with_nearly_one_cell_per_point(d):
+    # as many cells as points and more than 4096 of them: the static tables
+    # are sized for the points, so the pencil form of the first update (which
+    # needs room for three times the cells) must step aside
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(40 + d)
+    X = rng.uniform(0.0, 60.0 if d == 3 else 6.0, size=(5000, d))
+    ref = _fit_with_ctx(X, 1.0, 8, dev)
+    assert ref[2]["m0"] > 4096
+    pts = torch.from_numpy(X).to(dev)
+    labels = torch.full((X.shape[0],), -1, dtype=torch.int32, device=dev)
+    modes = torch.zeros((8192, d), dtype=torch.float64, device=dev)
+    st, k, info = _fit_noalloc(pts, 1.0, 8, labels, modes, dev)
+    assert st == gridshift.GS_OK, gridshift.gs_status_string(st)
+    _check(ref, (labels.cpu().numpy(), modes.cpu().numpy(), k, info), 1.0)
