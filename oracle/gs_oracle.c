@@ -38,6 +38,21 @@
  *   R6  Clusters are numbered by ascending lexicographic final key, axis 0 most
  *       significant; a mode is the final cell's sum divided by its count.
  *
+ * gso_fit_sequential computes the sequential form of update ii) instead
+ * (Eq. 5, Sec. 2.2; Algorithm 1 writes S'(j) in place inside its loop over the
+ * cells): a cell's neighbourhood sum uses the already updated centroid of every
+ * neighbour that precedes it in the sweep.  Readings:
+ *   R7  The sweep order, which the paper leaves to the hash table, is by
+ *       parity colour: colour(k) = sum_a (k_a mod 2) 2^(d-1-a) (axis 0 the
+ *       most significant bit), colours ascending, then keys ascending.  Two
+ *       distinct cells of one colour differ by an even, non-zero amount on
+ *       some axis, so they are never neighbours and the order inside a colour
+ *       does not change the result.
+ *   R8  A neighbour updated earlier in the sweep contributes its count times
+ *       its new centroid C(q) S'(q) (exact product); any other cell its stored
+ *       sum, as in the parallel form.  Counts do not change during the sweep.
+ *   Everything else (re-key, merge, stop test, labels) is as above.
+ *
  * Exact arithmetic: an accumulator is an array of signed 64-bit "digits", digit
  * k standing for multiples of 2^(32k + XBASE).  Adding m * v (v a double, m a
  * count) splits the exact integer product of m and v's significand into 32-bit
@@ -219,9 +234,17 @@ static int64_t find_cell(const int64_t *ck, int64_t m, int d, const int64_t *key
   return -1;
 }
 
-int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
-            int32_t *labels, double *modes, int64_t cap, int64_t *final_keys,
-            uint64_t *final_cnt, int64_t *m_hist, double *trace, gso_info *info) {
+/* Parity colour of a key (R7): bit d-1-a is k_a mod 2. */
+static int64_t key_colour(const int64_t *k, int d) {
+  int64_t c = 0;
+  for (int a = 0; a < d; a++) c = 2 * c + (k[a] % 2 != 0);
+  return c;
+}
+
+static int fit_impl(const double *X, int64_t n, int d, double h, int max_iter,
+                    int32_t *labels, double *modes, int64_t cap, int64_t *final_keys,
+                    uint64_t *final_cnt, int64_t *m_hist, double *trace, gso_info *info,
+                    int sequential) {
   if (n < 0 || d < 1 || d > 12 || !(h > 0) || !isfinite(h) || max_iter < 0 || !info) return 1;
   if (n > 0 && (!X || !labels)) return 1;
   for (int64_t i = 0; i < n * d; i++)
@@ -249,8 +272,10 @@ int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
   double *cs2 = malloc(sizeof(double) * n * d);
   xacc *acc = malloc(sizeof(xacc) * d);
   int64_t *probe = malloc(sizeof(int64_t) * d);
+  int64_t *sweep = malloc(sizeof(int64_t) * n);     /* order of the update sweep */
+  char *done = malloc((size_t)n);                   /* updated earlier in this sweep */
   if (!K || !ord || !cell_of || !ck || !cc || !cs || !cur || !sp || !nk || !parent || !ck2 ||
-      !cc2 || !cs2 || !acc || !probe) {
+      !cc2 || !cs2 || !acc || !probe || !sweep || !done) {
     ret = 2;
     goto done;
   }
@@ -286,9 +311,22 @@ int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
 
   int t = 0, converged = 0;
   for (;;) {
-    /* ii) neighbourhood-weighted centroid of every cell, from the old state */
+    /* ii) neighbourhood-weighted centroid of every cell: from the old state
+     * (parallel form), or in the sweep order of R7 reading what the sweep has
+     * already updated (sequential form, R8) */
     int any_nb = 0;
-    for (int64_t j = 0; j < m; j++) {
+    int64_t ns = 0;
+    if (sequential) {
+      const int64_t ncol = (int64_t)1 << d;
+      for (int64_t col = 0; col < ncol; col++)
+        for (int64_t j = 0; j < m; j++)
+          if (key_colour(ck + j * d, d) == col) sweep[ns++] = j;
+    } else {
+      for (int64_t j = 0; j < m; j++) sweep[ns++] = j;
+    }
+    memset(done, 0, (size_t)m);
+    for (int64_t s = 0; s < m; s++) {
+      const int64_t j = sweep[s];
       uint64_t D = 0;
       for (int a = 0; a < d; a++) xacc_clear(&acc[a]);
       for (int64_t v = 0; v < nv; v++) {
@@ -303,10 +341,14 @@ int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
         int64_t q = find_cell(ck, m, d, probe);
         if (q < 0) continue;
         D += cc[q];
-        for (int a = 0; a < d; a++) xacc_add(&acc[a], cs[q * d + a], 1u);
+        for (int a = 0; a < d; a++) {
+          if (done[q]) xacc_add(&acc[a], sp[q * d + a], cc[q]);
+          else xacc_add(&acc[a], cs[q * d + a], 1u);
+        }
         if (!centre) any_nb = 1;
       }
       for (int a = 0; a < d; a++) sp[j * d + a] = xacc_div_round(&acc[a], D);
+      if (sequential) done[j] = 1;
     }
     /* v) stop test, before the update is applied */
     if (!any_nb) { converged = 1; break; }
@@ -379,7 +421,22 @@ int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
 done:
   free(K); free(ord); free(cell_of); free(ck); free(cc); free(cs); free(cur); free(sp);
   free(nk); free(parent); free(ck2); free(cc2); free(cs2); free(acc); free(probe);
+  free(sweep); free(done);
   return ret;
+}
+
+int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
+            int32_t *labels, double *modes, int64_t cap, int64_t *final_keys,
+            uint64_t *final_cnt, int64_t *m_hist, double *trace, gso_info *info) {
+  return fit_impl(X, n, d, h, max_iter, labels, modes, cap, final_keys, final_cnt, m_hist,
+                  trace, info, 0);
+}
+
+int gso_fit_sequential(const double *X, int64_t n, int d, double h, int max_iter,
+                       int32_t *labels, double *modes, int64_t cap, int64_t *final_keys,
+                       uint64_t *final_cnt, int64_t *m_hist, double *trace, gso_info *info) {
+  return fit_impl(X, n, d, h, max_iter, labels, modes, cap, final_keys, final_cnt, m_hist,
+                  trace, info, 1);
 }
 
 int gso_track_window(const double *frame, int64_t width, int64_t height, int d, double h,

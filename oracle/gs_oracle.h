@@ -43,6 +43,15 @@ int gso_fit(const double *X, int64_t n, int d, double h, int max_iter,
             int32_t *labels, double *modes, int64_t cap, int64_t *final_keys,
             uint64_t *final_cnt, int64_t *m_hist, double *trace, gso_info *info);
 
+/* The same run with the sequential update of Eq. 5 (Sec. 2.2): the cells are
+ * swept in ascending parity colour (colour bit d-1-a = k_a mod 2), then
+ * ascending key, and each cell's neighbourhood sum takes the new centroid of
+ * every neighbour updated earlier in the sweep, weighted by its count.
+ * Arguments, outputs and return codes as gso_fit. */
+int gso_fit_sequential(const double *X, int64_t n, int d, double h, int max_iter,
+                       int32_t *labels, double *modes, int64_t cap, int64_t *final_keys,
+                       uint64_t *final_cnt, int64_t *m_hist, double *trace, gso_info *info);
+
 /* floor(x / h) of the exact quotient, for finite x and finite h > 0. */
 int64_t gso_floor_div(double x, double h);
 

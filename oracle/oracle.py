@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's CPU
 legs may import this module.  The product library never does.
 
 ``build()`` compiles gs_oracle.c with gcc into oracle/_build/ (plain -O2,
-no FP contraction); ``fit()`` runs one GridShift instance; ``fit_batched()``
-runs several independent instances one after another.
+no FP contraction); ``fit()`` runs one GridShift instance (parallel update of
+Eq. 6, or the sequential one of Eq. 5); ``fit_batched()`` runs several
+independent instances one after another.
 """
 from __future__ import annotations
 
@@ -49,11 +50,12 @@ def lib():
         build()
         L = ctypes.CDLL(_SO)
         P = ctypes.POINTER
-        L.gso_fit.restype = ctypes.c_int
-        L.gso_fit.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_int, ctypes.c_double,
-                              ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int64,
-                              P(ctypes.c_int64), P(ctypes.c_uint64), P(ctypes.c_int64),
-                              P(ctypes.c_double), P(_Info)]
+        for fn in (L.gso_fit, L.gso_fit_sequential):
+            fn.restype = ctypes.c_int
+            fn.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                           ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int64,
+                           P(ctypes.c_int64), P(ctypes.c_uint64), P(ctypes.c_int64),
+                           P(ctypes.c_double), P(_Info)]
         L.gso_floor_div.restype = ctypes.c_int64
         L.gso_floor_div.argtypes = [ctypes.c_double, ctypes.c_double]
         L.gso_exact_sum.restype = ctypes.c_double
@@ -74,12 +76,19 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
 
 
-def fit(points, h: float, max_iter: int = 50, trace: bool = False) -> dict:
+def fit(points, h: float, max_iter: int = 50, trace: bool = False,
+        update: str = "parallel") -> dict:
     """Run the oracle on an n x d array (any real dtype; converted to float64 exactly).
+
+    ``update`` is "parallel" (Eq. 6: every cell reads the state before the
+    update) or "sequential" (Eq. 5: a sweep in ascending parity colour, then
+    key, that reads the neighbours it has already updated).
 
     Returns dict(labels, modes, keys, counts, iterations, converged, m0, k,
     m_hist[, trace]).
     """
+    if update not in ("parallel", "sequential"):
+        raise ValueError("update must be 'parallel' or 'sequential'")
     X = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
     if X.ndim != 2:
         raise ValueError("points must be n x d")
@@ -92,13 +101,14 @@ def fit(points, h: float, max_iter: int = 50, trace: bool = False) -> dict:
     m_hist = np.zeros(max_iter + 1, dtype=np.int64)
     tr = np.zeros((max(max_iter, 1), 2, d), dtype=np.float64) if trace else None
     info = _Info()
-    rc = lib().gso_fit(_ptr(X, ctypes.c_double), n, d, float(h), int(max_iter),
+    fn = lib().gso_fit if update == "parallel" else lib().gso_fit_sequential
+    rc = fn(_ptr(X, ctypes.c_double), n, d, float(h), int(max_iter),
                        _ptr(labels, ctypes.c_int32), _ptr(modes, ctypes.c_double), cap,
                        _ptr(keys, ctypes.c_int64), _ptr(cnt, ctypes.c_uint64),
                        _ptr(m_hist, ctypes.c_int64), _ptr(tr, ctypes.c_double),
                        ctypes.byref(info))
     if rc != 0:
-        raise RuntimeError(f"oracle gso_fit failed with code {rc}")
+        raise RuntimeError(f"oracle {update} fit failed with code {rc}")
     k = int(info.k)
     it = int(info.iterations)
     out = dict(labels=labels, modes=modes[:k].copy(), keys=keys[:k].copy(),

@@ -22,7 +22,7 @@ def load(path: str) -> dict:
             i += 1
             while i < len(lines) and lines[i].split()[0] not in (
                     "labels", "iterations", "converged", "m_hist", "modes", "points", "h",
-                    "max_iter"):
+                    "max_iter", "tol_ulp"):
                 rows.append(lines[i].split())
                 i += 1
             if head == "points":
@@ -32,7 +32,7 @@ def load(path: str) -> dict:
             continue
         if head == "h":
             out["h"] = float(Fraction(rest[0]))
-        elif head in ("max_iter", "iterations", "converged"):
+        elif head in ("max_iter", "iterations", "converged", "tol_ulp"):
             out[head] = int(rest[0])
         elif head in ("labels", "m_hist"):
             out[head] = [int(v) for v in rest]
@@ -41,4 +41,10 @@ def load(path: str) -> dict:
 
 
 def all_cases() -> list:
+    """The hand-worked cases of the parallel update (Eq. 6)."""
     return [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))]
+
+
+def sequential_cases() -> list:
+    """The hand-worked cases of the sequential update (Eq. 5)."""
+    return [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "sequential", "*.txt")))]

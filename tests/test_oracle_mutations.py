@@ -1,8 +1,9 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake in a copy of the oracle's C source (in a
-temporary directory, on the CPU) and runs the pin tests against the copy:
-at least one pin must fail.  The unmodified copy must pass.
+temporary directory, on the CPU) and runs the pin tests of the update form
+it touches (parallel, Eq. 6, or sequential, Eq. 5) against the copy: at
+least one pin must fail.  The unmodified copy must pass.
 """
 from __future__ import annotations
 
@@ -42,6 +43,30 @@ MUTANTS = {
                               "modes[c * d + a] = cs[c * d + a] / (double)(cc[c] + 1);"),
 }
 
+# Mistakes in the sequential update (Sec. 2.2, Eq. 5), caught by its own pins
+SEQ_MUTANTS = {
+    # a neighbour updated earlier in the sweep is read at its new centroid
+    "sequential_reads_old_state": (
+        "if (done[q]) xacc_add(&acc[a], sp[q * d + a], cc[q]);",
+        "if (0 && done[q]) xacc_add(&acc[a], sp[q * d + a], cc[q]);"),
+    # ... weighted by its count
+    "updated_neighbour_unweighted": ("sp[q * d + a], cc[q]);", "sp[q * d + a], 1u);"),
+    # the colour's most significant bit is axis 0
+    "colour_axes_reversed": ("for (int a = 0; a < d; a++) c = 2 * c + (k[a] % 2 != 0);",
+                             "for (int a = d - 1; a >= 0; a--) c = 2 * c + (k[a] % 2 != 0);"),
+    # negative odd keys are odd
+    "negative_parity": ("c = 2 * c + (k[a] % 2 != 0);", "c = 2 * c + (k[a] % 2 == 1);"),
+    # the sweep goes by colour, not by key alone
+    "sweep_in_key_order": ("if (key_colour(ck + j * d, d) == col) sweep[ns++] = j;",
+                           "if (col == 0) sweep[ns++] = j;"),
+    # colours ascending
+    "colours_descending": ("for (int64_t col = 0; col < ncol; col++)",
+                           "for (int64_t col = ncol - 1; col >= 0; col--)"),
+}
+
+PIN_FILES = {"parallel": "tests/test_oracle_pins.py",
+             "sequential": "tests/test_oracle_sequential.py"}
+
 
 def _copy_tree(dst):
     ign = shutil.ignore_patterns("_build", "__pycache__", "*.so")
@@ -49,25 +74,27 @@ def _copy_tree(dst):
     shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(dst, "tests"), ignore=ign)
 
 
-def _run_pins(dst):
+def _run_pins(dst, *files):
     return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                           "tests/test_oracle_pins.py"], cwd=dst, capture_output=True, text=True,
-                          timeout=600)
+                           *files], cwd=dst, capture_output=True, text=True, timeout=600)
 
 
 def test_unmodified_copy_passes(tmp_path):
     _copy_tree(str(tmp_path))
-    r = _run_pins(str(tmp_path))
+    r = _run_pins(str(tmp_path), *PIN_FILES.values())
     assert r.returncode == 0, r.stdout[-2000:]
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_is_caught(tmp_path, name):
-    old, new = MUTANTS[name]
+_ALL = sorted([(n, "parallel") for n in MUTANTS] + [(n, "sequential") for n in SEQ_MUTANTS])
+
+
+@pytest.mark.parametrize("name,form", _ALL, ids=[n for n, _ in _ALL])
+def test_planted_mistake_is_caught(tmp_path, name, form):
+    old, new = (MUTANTS if form == "parallel" else SEQ_MUTANTS)[name]
     _copy_tree(str(tmp_path))
     src = os.path.join(str(tmp_path), "oracle", "gs_oracle.c")
     text = open(src).read()
     assert text.count(old) == 1, f"mutation site for {name} not found once"
     open(src, "w").write(text.replace(old, new))
-    r = _run_pins(str(tmp_path))
+    r = _run_pins(str(tmp_path), PIN_FILES[form])
     assert r.returncode != 0, f"no pin caught the mutant {name}:\n{r.stdout[-1500:]}"
