@@ -78,6 +78,18 @@ typedef enum {
 
 typedef enum { GS_IN_F64 = 0, GS_IN_F32 = 1 } gs_dtype;
 
+typedef enum {
+  GS_UPDATE_PARALLEL = 0,   /* Eq. 6: every cell's new centroid from the state before the
+                               update (Sec. 2.2, the parallel form; the default) */
+  GS_UPDATE_SEQUENTIAL = 1  /* Eq. 5: the cells updated one after another, each reading the
+                               new centroid of every neighbour updated before it (Sec. 2.2;
+                               Algorithm 1 updates in place).  Order: ascending parity colour
+                               sum_a (k_a mod 2) 2^(d-1-a), axis 0 the most significant bit;
+                               cells of one colour are never neighbours, so each colour is one
+                               parallel pass (2^d passes per update).  An updated neighbour
+                               contributes its count times its new centroid, exactly */
+} gs_update;
+
 typedef struct gs_ctx gs_ctx; /* opaque; owns the device workspace */
 
 typedef struct {
@@ -132,13 +144,21 @@ gs_status gs_create(int d, double h, int max_iter, gs_ctx** out);
  * Unknown values return GS_E_INVALID and leave the setting unchanged. */
 gs_status gs_set_precision(gs_ctx* ctx, gs_precision p);
 
+/* Selects the update form of later gs_fit calls (see gs_update; default
+ * GS_UPDATE_PARALLEL).  GS_UPDATE_SEQUENTIAL is available for GS_FP64 runs of
+ * one point set: while it is set, gs_fit with GS_FP32_MIXED and gs_fit_batched
+ * with B > 1 return GS_E_INVALID.  Unknown values return GS_E_INVALID and
+ * leave the setting unchanged. */
+gs_status gs_set_update(gs_ctx* ctx, gs_update u);
+
 /* Sets the CUDA stream (a cudaStream_t passed as void*, e.g.
  * torch.cuda.current_stream().cuda_stream) on which every later call issues
  * its work.  NULL selects the legacy default stream. */
 gs_status gs_set_stream(gs_ctx* ctx, void* cuda_stream);
 
 /* Runs GridShift (Sec. 2.1 steps i-v, Algorithm 1, Eq. 1-4 with the parallel
- * update of Eq. 6) on one point set.
+ * update of Eq. 6, or the sequential one of Eq. 5: gs_set_update) on one
+ * point set.
  *   points     device, n x d row-major, dtype as given
  *   n          number of points, 0 <= n < 2^31
  *   labels     device int32[n]: cluster of every point (output)

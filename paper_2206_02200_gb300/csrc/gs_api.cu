@@ -214,6 +214,7 @@ struct CtxWorkspace : public Workspace {
   DBuf<uint32_t> sval, sval2, shist;
   DBuf<int64_t> offsets;
   DBuf<uint32_t> inst;
+  DBuf<ulonglong2> srow;          // the sequential update's shifted rows
   std::vector<uint64_t> h_inst;   // host copy of the per-instance state (8-byte aligned)
 
   DevFlags* h_flags = nullptr;    // pinned
@@ -387,6 +388,12 @@ struct CtxWorkspace : public Workspace {
     *host = reinterpret_cast<uint32_t*>(h_inst.data());
     return GS_OK;
   }
+  gs_status shift_rows(uint32_t cap, int d, Bufs& b, std::string* err) override {
+    cudaError_t e;
+    WS_CU(srow.ensure((size_t)cap * d), "alloc shifted rows");
+    b.srow = srow.p;
+    return GS_OK;
+  }
 #undef WS_CU
 
   void mark_dirty(bool d) override { dirty = d; }
@@ -402,7 +409,7 @@ struct CtxWorkspace : public Workspace {
     }
     qlist.release(); ptab.release(); forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
-    offsets.release(); inst.release();
+    offsets.release(); inst.release(); srow.release();
     if (h_flags) cudaFreeHost(h_flags);
     if (h_res) cudaFreeHost(h_res);
     if (h_words) cudaFreeHost(h_words);
@@ -421,6 +428,7 @@ struct gs_ctx {
   double h = 0;
   int max_iter = 0;
   gs_precision prec = GS_FP64;
+  gs_update update = GS_UPDATE_PARALLEL;
   cudaStream_t stream = nullptr;
   int device = -1;
   std::string err;
@@ -492,6 +500,14 @@ gs_status gs_set_precision(gs_ctx* ctx, gs_precision p) {
   return GS_OK;
 }
 
+gs_status gs_set_update(gs_ctx* ctx, gs_update u) {
+  if (!ctx) return GS_E_INVALID;
+  if (u != GS_UPDATE_PARALLEL && u != GS_UPDATE_SEQUENTIAL)
+    return fail(ctx, GS_E_INVALID, "unknown update form");
+  ctx->update = u;
+  return GS_OK;
+}
+
 gs_status gs_set_stream(gs_ctx* ctx, void* cuda_stream) {
   if (!ctx) return GS_E_INVALID;
   ctx->stream = (cudaStream_t)cuda_stream;
@@ -532,6 +548,8 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   if (modes_cap < 0 || (modes_cap > 0 && !modes))
     return fail(ctx, GS_E_INVALID, "modes is NULL with modes_cap > 0");
   if (n > 0 && (!points || !labels)) return fail(ctx, GS_E_INVALID, "NULL points or labels");
+  if (ctx->update == GS_UPDATE_SEQUENTIAL && ctx->prec != GS_FP64)
+    return fail(ctx, GS_E_INVALID, "the sequential update runs in GS_FP64 only");
   gs_fit_info inf;
   std::memset(&inf, 0, sizeof(inf));
   *k_out = 0;
@@ -561,6 +579,7 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   a.modes = modes;
   a.modes_cap = modes_cap;
   a.mixed = ctx->prec == GS_FP32_MIXED;
+  a.sequential = ctx->update == GS_UPDATE_SEQUENTIAL;
   double kms[kLoopPhases + 2 * kClockSteps] = {};
   gs_status st = fit_pipeline(a, ctx->ws, ctx->timing ? &ctx->tm : nullptr, k_out, &inf, kms,
                               &ctx->err);
@@ -735,6 +754,8 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   ctx->err.clear();
   if (!offsets || !mode_offsets || !infos) return fail(ctx, GS_E_INVALID, "NULL offsets, mode_offsets or infos");
   if (B < 1 || B > kMaxBatch) return fail(ctx, GS_E_INVALID, "B out of range");
+  if (B > 1 && ctx->update == GS_UPDATE_SEQUENTIAL)
+    return fail(ctx, GS_E_INVALID, "the sequential update runs on one point set only (B = 1)");
   if (offsets[0] != 0) return fail(ctx, GS_E_INVALID, "offsets[0] must be 0");
   for (int i = 0; i < B; ++i)
     if (offsets[i + 1] < offsets[i]) return fail(ctx, GS_E_INVALID, "offsets must not decrease");

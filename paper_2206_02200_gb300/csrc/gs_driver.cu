@@ -85,6 +85,8 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   const int d = a.d;
   const cudaStream_t s = a.stream;
   const int64_t n = a.n;
+  if (a.sequential && (a.mixed || a.B > 1))
+    return fail(err, GS_E_INVALID, "the sequential update runs in GS_FP64 on one point set only");
   Bufs b;
   GS_ST(ws.begin(b, err));
 
@@ -124,7 +126,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   // fit the device-side capacity, neither ran, and the host makes the plan
   // and runs them again.
   ws.mark_dirty(true);
-  const int grid = loop_grid(d, a.mixed);
+  const int grid = a.sequential ? loop_grid_seq(d) : loop_grid(d, a.mixed);
   if (grid <= 0) return fail(err, GS_E_CUDA, "no co-resident grid for the loop kernel");
   LoopArgs L;
   LoopResult* hr = ws.host_result();
@@ -140,6 +142,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
       GS_CU(cudaMemsetAsync(b.st, 0, sizeof(IterState) * (a.max_iter + 2), s), "memset state");
       GS_CU(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), s), "memset barrier");
     }
+    if (a.sequential) GS_ST(ws.shift_rows(b.capAB, d, b, err));
     std::memset(&L, 0, sizeof(L));
     L.P.d = d;  // the loop kernel reads the plan from b.flags
     L.pts = a.points;
@@ -177,13 +180,14 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.rank_max = kRankMax;
     L.B = a.B;
     L.mixed = a.mixed;
+    L.srow = a.sequential ? b.srow : nullptr;
     if (a.B > 1) L.I = inst_views(b.inst, a.B);
     GS_T_BEGIN(GS_PHASE_BIN);
     GS_LAUNCH(launch_bin(a.points, a.f32, n, d, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells,
                          b.slot0, b.flags, b.offsets, a.B, s), "k_bin", 1);
     GS_T_END();
     GS_T_BEGIN(GS_PHASE_LOOP);
-    GS_LAUNCH(launch_loop(L, grid, s), "k_loop", 1);
+    GS_LAUNCH(a.sequential ? launch_loop_seq(L, grid, s) : launch_loop(L, grid, s), "k_loop", 1);
     GS_T_END();
     GS_CU(cudaMemcpyAsync(hr, b.res, sizeof(LoopResult), cudaMemcpyDeviceToHost, s), "D2H result");
     GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");

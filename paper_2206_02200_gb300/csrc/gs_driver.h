@@ -45,6 +45,7 @@ struct Bufs {
   uint32_t* sval = nullptr;
   uint32_t* sval2 = nullptr;
   uint32_t* shist = nullptr;   // radix_hist_words(k)
+  ulonglong2* srow = nullptr;  // sequential update: capAB * d
 };
 
 // Source of the device buffers and host staging of one run.  Each method
@@ -83,6 +84,9 @@ class Workspace {
   virtual void mark_dirty(bool dirty) = 0;
   // The number of initial cells binning found (sizes later binning tables).
   virtual void note_cells(uint32_t m0) = 0;
+  // The sequential update's shifted rows for level tables of `cap` slots
+  // (b.srow, cap * d entries), or an error.
+  virtual gs_status shift_rows(uint32_t cap, int d, Bufs& b, std::string* err) = 0;
 };
 
 // Optional per-phase CUDA-event timing of a run.
@@ -105,6 +109,7 @@ struct FitArgs {
   double* modes;
   int64_t modes_cap;
   bool mixed = false;  // the float32 mixed-precision variant (GS_FP32_MIXED)
+  bool sequential = false;  // the sequential update (Eq. 5; plain FP64 runs only)
   // batched runs (B > 1): host offsets (B + 1), per-instance results (host)
   int B = 1;
   const int64_t* offsets = nullptr;

@@ -98,6 +98,8 @@ struct LoopArgs {
   int B;                  // instances (1: a plain run)
   InstState I;            // per-instance state when B > 1
   bool mixed;             // the float32 mixed-precision variant (GS_FP32_MIXED)
+  ulonglong2* srow;       // sequential update (plain FP64 runs): count x new centroid of
+                          // every slot of the level tables (capAB x d); null: parallel update
 };
 
 // Accumulators of one tracking window step (gs_track_window).
@@ -168,6 +170,11 @@ cudaError_t launch_loop_fp64(const LoopArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_loop_fp32(const LoopArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_modes_tail_fp64(const LoopArgs& a, uint32_t k, int T, cudaStream_t s);
 cudaError_t launch_modes_tail_fp32(const LoopArgs& a, uint32_t k, int T, cudaStream_t s);
+
+// The sequential update's loop kernel (gs_loop64s.cu; GS_FP64 plain runs with
+// a.srow set): its co-resident grid, and its launch.
+int loop_grid_seq(int d);
+cudaError_t launch_loop_seq(const LoopArgs& a, int grid, cudaStream_t s);
 
 // Numbering of the final cells when k > rank_max: labels of the final cells
 // from the sorted order (sorted_vals[p] = cell of rank p), then labels and

@@ -543,6 +543,31 @@ __device__ void pencil_release(const LevelTable& Q, const uint32_t* list, uint32
   }
 }
 
+// Parity colour of a packed key (the sequential update's sweep order):
+// bit D-1-a is k_a mod 2, where the field of axis a holds k_a - kmin_a + 1.
+template <int D>
+__device__ __forceinline__ uint32_t key_colour(uint64_t key) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    c = 2u * c + (uint32_t)((key_field(key, a) - 1 + g_plan.kmin[a]) & 1);
+  return c;
+}
+
+// Whether the neighbour at probe p (offset digits v_a + 1 in base 3, axis
+// D-1 the fastest) of a cell of colour col has a lower colour: its parity
+// differs from the cell's exactly on the axes with v_a != 0.
+template <int D>
+__device__ __forceinline__ bool colour_before(int p, uint32_t col) {
+  uint32_t nz = 0;
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) {
+    nz |= (uint32_t)(p % 3 != 1) << (D - 1 - a);
+    p /= 3;
+  }
+  return (col ^ nz) < col;
+}
+
 // One update step t for every cell of level t (table tab[t % 3]):
 //   ii)  D = sum of the counts and N = sum of the coordinate sums over the
 //        3^d neighbours present (Eq. 1-2, all cells reading level t: Eq. 6),
@@ -561,10 +586,17 @@ __device__ void pencil_release(const LevelTable& Q, const uint32_t* list, uint32
 // axis 0; with pen = 2 over the 3^(d-2) offsets with v_0 = v_1 = 0 of the
 // second pencil table (nine cells per entry).  A neighbour v != 0 is present
 // iff D exceeds the cell's own count.
-template <int D, int GS, bool BT>
+// With SEQ (the sequential update of Eq. 5, plain FP64 runs, pen = 0) the
+// phase is the pass of parity colour col: only the cells of that colour
+// are updated, a neighbour of a lower colour (updated in an earlier pass of
+// this step) contributes its count times its new centroid from A.srow, and
+// each updated cell leaves that product in A.srow at its slot of level t.
+// The filter load and the links of level t-1 happen in pass 0 only.
+template <int D, int GS, bool BT, bool SEQ = false>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
-                             unsigned& inexact, unsigned& werr, int pen = 0) {
+                             unsigned& inexact, unsigned& werr, int pen = 0, int col = 0) {
+  static_assert(!(SEQ && BT), "the sequential update runs on plain runs only");
   constexpr int U = ProbeBatch<D, GS>::value > 2 ? 2 : ProbeBatch<D, GS>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
@@ -585,7 +617,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   extern __shared__ uint4 s_dyn[];
   uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
   const int lg = filter_log2(m);
-  {
+  if (!SEQ || col == 0) {
     const uint4* src = reinterpret_cast<const uint4*>(A.filter[t & 1]);
     uint4* dst = reinterpret_cast<uint4*>(s_filter);
     const uint32_t n4 = (1u << lg) / 128;
@@ -608,6 +640,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   }
   for (uint32_t j = group; j < m; j += ngroups) {
     const uint64_t key = c.key[j];
+    if (SEQ && key_colour<D>(key) != (uint32_t)col) continue;
     const uint32_t cj = c.cnt[j];
     // batched runs: a cell of an instance that has stopped is carried to the
     // next level unchanged (same key, its own exact sum)
@@ -638,8 +671,12 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         if (sl[u] == kNone) continue;
         const ulonglong2* r = P.row + (size_t)sl[u] * (D + 1);
         Dc += (uint32_t)r[0].x;
+        // sequential passes: a neighbour of a lower colour has its new value
+        const ulonglong2* src = r + 1;
+        if (SEQ && col > 0 && colour_before<D>(p0 + u * GS, (uint32_t)col))
+          src = A.srow + (size_t)sl[u] * D;
 #pragma unroll
-        for (int a = 0; a < D; ++a) N[a] += as_u128(r[1 + a]);
+        for (int a = 0; a < D; ++a) N[a] += as_u128(src[a]);
       }
     }
 #pragma unroll
@@ -712,8 +749,10 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
     ms = __shfl_sync(gmask, ms, 0, GS);
     if (glane < D && ms != kNone)
       atomic_add_fixed(M.acc + ((size_t)ms * D + glane) * 4, V * (u128)mult);
+    // sequential passes: what the later colours read for this cell
+    if (SEQ && glane < D) A.srow[(size_t)G.list[j] * D + glane] = pack(V * (u128)mult);
   }
-  if (t > 0) {
+  if (t > 0 && (!SEQ || col == 0)) {
     // level t-1: parent links, then its table is released
     const uint32_t tid = item_tid(m_prev);
     const uint32_t nth = gridDim.x * blockDim.x;
@@ -2233,8 +2272,12 @@ __device__ void run_tail32(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev
   out.cell_iters = cell_iters;
 }
 
-template <int D, bool BT, bool F32>
+// The loop kernel.  SEQ: the sequential update of Eq. 5 (plain FP64 runs;
+// A.srow holds the shifted rows), a separate instantiation so that the
+// parallel kernels carry none of its code.
+template <int D, bool BT, bool F32, bool SEQ = false>
 __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
+  static_assert(!(SEQ && (BT || F32)), "the sequential update runs on plain FP64 runs only");
   unsigned inexact = 0, werr = 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nth = gridDim.x * blockDim.x;
@@ -2304,9 +2347,12 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   // probes per cell it saves; at d = 6 it saves 81 of 243)
   int pen = 0;
   uint32_t maskQ = 0, qn = 0, maskQ2 = 0, qn2 = 0;
+  // the sequential update: colour passes of the generic update at every
+  // level, no pencil form, no one-block tail
+  constexpr bool seq = SEQ;
   if constexpr (!BT && D >= 3) {
     // Q holds at most 3 m0 keys: only where tab[2] keeps them at load <= 3/4
-    if (m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr &&
+    if (!seq && m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr &&
         4ull * m0 <= (uint64_t)A.capAB) {
       pen = 1;
       maskQ = mask_for(3 * m0, A.capAB);
@@ -2348,7 +2394,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   for (;;) {
     if constexpr (!BT) {
       // a small level: block 0 finishes the update steps in shared memory
-      if (m <= kTailEnter) {
+      if (m <= kTailEnter && !seq) {
         if (blockIdx.x == 0) {
           TailOut to;
           if constexpr (F32)
@@ -2387,6 +2433,13 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       else
         phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
                                   maskPt);
+    } else if constexpr (SEQ) {
+      // Eq. 5: the colours one after another, each reading the ones before
+      for (int col = 0; col < (1 << D); ++col) {
+        if (col > 0 && !grid_sync(A.bar, A.fl)) return;
+        phase_update<D, 32, false, true>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb,
+                                         inexact, werr, 0, col);
+      }
     } else {
       if (GSmin < 32 && m > (nth >> 5))
         phase_update<D, GSmin, BT>(A, t, m, pt ? maskPt : mask, maskM, m_prev, base_prev, base,

@@ -172,6 +172,7 @@ struct StaticWorkspace : public Workspace {
   gs_status batch_space(int, Bufs&, uint32_t**, std::string*) override { return GS_E_INVALID; }
   void mark_dirty(bool) override {}
   void note_cells(uint32_t) override {}
+  gs_status shift_rows(uint32_t, int, Bufs&, std::string*) override { return GS_E_INVALID; }
 };
 
 }  // namespace

@@ -30,8 +30,13 @@ GS_FP32_MIXED = 1
 GS_IN_F64 = 0
 GS_IN_F32 = 1
 
+# Update forms (gs_update): Eq. 6 (parallel) and Eq. 5 (sequential)
+GS_UPDATE_PARALLEL = 0
+GS_UPDATE_SEQUENTIAL = 1
+
 #: every symbol the header declares, in declaration order
-EXPORTS = ("gs_create", "gs_set_precision", "gs_set_stream", "gs_fit", "gs_fit_batched",
+EXPORTS = ("gs_create", "gs_set_precision", "gs_set_update", "gs_set_stream", "gs_fit",
+           "gs_fit_batched",
            "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_track_window",
            "gs_get_last_error", "gs_status_string", "gs_destroy")
 
@@ -98,6 +103,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.gs_create.argtypes = [i32, ctypes.c_double, i32, ctypes.POINTER(vp)]
     L.gs_set_precision.restype = i32
     L.gs_set_precision.argtypes = [vp, i32]
+    L.gs_set_update.restype = i32
+    L.gs_set_update.argtypes = [vp, i32]
     L.gs_set_stream.restype = i32
     L.gs_set_stream.argtypes = [vp, vp]
     L.gs_fit.restype = i32
@@ -140,6 +147,10 @@ def gs_create(d: int, h: float, max_iter: int) -> int:
 
 def gs_set_precision(ctx: int, precision: int) -> int:
     return load().gs_set_precision(ctx, int(precision))
+
+
+def gs_set_update(ctx: int, update: int) -> int:
+    return load().gs_set_update(ctx, int(update))
 
 
 def gs_set_stream(ctx: int, stream: int | None) -> int:
@@ -242,14 +253,18 @@ class GridShift:
 
     ``fit(points)`` takes an n x d float64 or float32 CUDA tensor and returns
     (labels int32[n], modes float64[k x d], info dict), all on the points'
-    device, computed on the current torch stream.
+    device, computed on the current torch stream.  ``update`` selects the
+    parallel (Eq. 6, default) or sequential (Eq. 5) update form.
     """
 
-    def __init__(self, d: int, h: float, max_iter: int = 50, precision: int = GS_FP64):
+    def __init__(self, d: int, h: float, max_iter: int = 50, precision: int = GS_FP64,
+                 update: int = GS_UPDATE_PARALLEL):
         import torch  # noqa: F401  (device memory and streams)
         self.d, self.h, self.max_iter = int(d), float(h), int(max_iter)
         self._ctx = gs_create(self.d, self.h, self.max_iter)
         st = gs_set_precision(self._ctx, precision)
+        if st == GS_OK:
+            st = gs_set_update(self._ctx, update)
         if st != GS_OK:
             msg = gs_get_last_error(self._ctx)
             gs_destroy(self._ctx)

@@ -95,6 +95,30 @@ def test_create_destroy_and_host_only_checks(lib):
     lib.gs_destroy(None)  # ignored
 
 
+def test_update_form_host_only_checks(lib):
+    ctx = gridshift.gs_create(2, 1.0, 10)
+    try:
+        assert gridshift.gs_set_update(ctx, 5) == gridshift.GS_E_INVALID
+        assert gridshift.gs_get_last_error(ctx)
+        assert gridshift.gs_set_update(ctx, gridshift.GS_UPDATE_SEQUENTIAL) == gridshift.GS_OK
+        # the sequential form runs in GS_FP64 on one point set: other uses
+        # are refused before any device work
+        assert gridshift.gs_set_precision(ctx, gridshift.GS_FP32_MIXED) == gridshift.GS_OK
+        st, _, _ = gridshift.gs_fit(ctx, 0, gridshift.GS_IN_F64, 0, 0, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        assert gridshift.gs_set_precision(ctx, gridshift.GS_FP64) == gridshift.GS_OK
+        st, k, _ = gridshift.gs_fit(ctx, 0, gridshift.GS_IN_F64, 0, 0, 0, 0)
+        assert st == gridshift.GS_OK and k == 0
+        st, _, _ = gridshift.gs_fit_batched(ctx, 0, gridshift.GS_IN_F64, [0, 0, 0], 0, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        assert gridshift.gs_set_update(ctx, gridshift.GS_UPDATE_PARALLEL) == gridshift.GS_OK
+        st, _, _ = gridshift.gs_fit_batched(ctx, 0, gridshift.GS_IN_F64, [0, 0, 0], 0, 0, 0)
+        assert st == gridshift.GS_OK
+    finally:
+        gridshift.gs_destroy(ctx)
+    assert lib.gs_set_update(None, 0) == gridshift.GS_E_INVALID
+
+
 def test_product_never_imports_the_oracle():
     pkg = os.path.join(ROOT, "paper_2206_02200_gb300")
     for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
