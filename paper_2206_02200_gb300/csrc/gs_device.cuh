@@ -327,10 +327,6 @@ __device__ __forceinline__ uint32_t table_find_from(const uint64_t* keys, uint32
   return kNone;
 }
 
-__device__ __forceinline__ uint32_t table_find(const uint64_t* keys, uint32_t mask, uint64_t key) {
-  return table_find_from(keys, mask, key, home_bucket(key, mask >> 2), 0);
-}
-
 // Lookups of U keys at once: the home buckets of all of them are loaded
 // before any is examined, so the U loads are in flight together.  valid[u]
 // false leaves slot[u] = kNone.

@@ -12,7 +12,9 @@ Nothing here compares the oracle with itself.  The pins are:
   * closed forms: one cell, all cells mutually adjacent, separated clusters;
   * invariants: total count, sum conservation across merges (Eq. 4),
     non-increasing active-cell count (Sec. 2.1), unique sorted keys, pairwise
-    key distance >= 2 at convergence (Theorem 2), label histogram = counts.
+    key distance >= 2 at convergence (Theorem 2), label histogram = counts;
+  * the shrink rate of the centroids on a Gaussian sample (Theorem 3), with
+    the constant derived from the three-cell window.
 """
 from __future__ import annotations
 
@@ -306,6 +308,37 @@ def test_invariants(d, h, seed):
     scale = np.abs(X).max() * n
     for t in range(r["iterations"]):
         assert np.all(np.abs(tr[t, 0] - tr[t, 1]) <= r["m_hist"][t] * scale * 2.0 ** -52)
+
+
+# ---------------------------------------------------------------------------
+# Convergence rate on a Gaussian sample (Theorem 3, a loose check)
+
+
+def _centroid_spread(r):
+    c = r["counts"].astype(np.float64)
+    m = r["modes"]
+    mu = (c[:, None] * m).sum(0) / c.sum()
+    return np.sqrt((c[:, None] * (m - mu) ** 2).sum(0) / c.sum())
+
+
+@pytest.mark.parametrize("s,h,d", [(8.0, 1.0, 1), (5.0, 1.0, 1), (6.0, 2.0, 1), (5.0, 1.0, 2)])
+def test_gaussian_shrink_rate(s, h, d):
+    # Theorem 3: on a Gaussian sample the cell centroids shrink towards the
+    # mean at every update, s' = s / (1 + c h^2 / s^2).  For s >> h the
+    # leading-order constant follows from the update itself: a cell's new
+    # centroid is the mean of the three-cell window around it (variance
+    # (3h)^2 / 12 = 3/4 h^2 about its centre), so it moves by -(3/4) h^2 x / s^2,
+    # while the cell means it starts from already sit -(1/12) h^2 x / s^2 from
+    # the cell centres: c = 3/4 - 1/12 = 2/3 relative to the spread of the cell
+    # means (the theorem prints 2.25 h^2).  A wrong window (a dropped or extra
+    # term, a shifted neighbourhood) moves c far from 2/3.
+    rng = np.random.default_rng(583 + int(10 * s) + d)
+    X = rng.normal(0, s, size=(60000, d))
+    spreads = [_centroid_spread(oracle.fit(X, h, t)) for t in range(4)]
+    c = (spreads[0] / spreads[1] - 1) * spreads[0] ** 2 / h ** 2
+    assert np.all(np.abs(c - 2.0 / 3.0) < 0.03), c
+    for t in range(3):
+        assert np.all(spreads[t + 1] < spreads[t])  # shrinks at every update
 
 
 # ---------------------------------------------------------------------------
