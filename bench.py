@@ -7,7 +7,9 @@ at most 50 updates, the plain FP64 path.  One step = one complete GridShift run
 ``--precision fp32`` runs the float32 mixed-precision path and reports its
 label agreement and mode error against the FP64 path; ``--workload
 batch_64_d3`` runs 64 uneven images in one batched call (and times 64
-sequential plain calls beside it).
+sequential plain calls beside it); ``--update sequential`` runs the
+sequential update of Eq. 5 (float64, one point set) instead of the parallel
+one of Eq. 6.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
 reference arm: a plain single-threaded FP64 program written from the paper).
@@ -75,7 +77,11 @@ def sources_hash() -> str:
     return m.hexdigest()[:16]
 
 
-def traffic(workload: str, precision: str, kernel: str):
+def traffic(workload: str, precision: str, kernel: str, update: str = "parallel"):
+    """DRAM bytes per launch from the committed capture, or None when none was
+    taken for this case or the kernel sources changed since."""
+    if update != "parallel":
+        return None
     t = TRAFFIC.get((workload, precision, kernel))
     return t[0] if t and t[1] == sources_hash() else None
 
@@ -174,7 +180,7 @@ def load_workload(name: str) -> dict:
     return synth.WORKLOADS[name]()
 
 
-def workload_config(w: dict, name: str, precision: str = "fp64") -> dict:
+def workload_config(w: dict, name: str, precision: str = "fp64", update: str = "parallel") -> dict:
     if "parts" in w:
         n, d = sum(len(p) for p in w["parts"]), w["parts"][0].shape[1]
         dt = w["parts"][0].dtype
@@ -182,7 +188,8 @@ def workload_config(w: dict, name: str, precision: str = "fp64") -> dict:
         (n, d), dt = w["points"].shape, w["points"].dtype
     gen = ("GMM points, seeded" if name.startswith("gmm") else "Voronoi image, seeded")
     cfg = {"workload": w["name"], "n": int(n), "d": int(d), "h": w["h"],
-           "max_iter": w["max_iter"], "precision": precision, "input_dtype": str(dt),
+           "max_iter": w["max_iter"], "precision": precision, "update": update,
+           "input_dtype": str(dt),
            "l2": "flushed between timed steps (256 MiB device write)",
            "generator": gen + " (paper_2206_02200_gb300.synth)"}
     if "parts" in w:
@@ -204,7 +211,8 @@ def _oracle_sample(w: dict):
     return out
 
 
-def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8) -> dict:
+def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8,
+                 update: str = "parallel") -> dict:
     """Times the CPU oracle (single-threaded, as it stands) on the same workload."""
     from oracle import oracle
     oracle.build()
@@ -215,7 +223,7 @@ def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8) -> dict:
     while runs < max_runs and (runs == 0 or total < budget_s):
         t0 = time.perf_counter()
         for X in sample:
-            oracle.fit(X, h, it)
+            oracle.fit(X, h, it, update=update)
         total += time.perf_counter() - t0
         runs += 1
     what = "the workload" if "parts" not in w else f"the first {len(sample)} instances"
@@ -234,12 +242,12 @@ def run_reference(args, rank: int, world: int):
     n = sum(len(X) for X in sample)
     for _ in range(args.warmup):
         for X in sample:
-            oracle.fit(X, h, it)
+            oracle.fit(X, h, it, update=args.update)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         for X in sample:
-            oracle.fit(X, h, it)
+            oracle.fit(X, h, it, update=args.update)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n * args.steps / total / 1e6
@@ -248,7 +256,7 @@ def run_reference(args, rank: int, world: int):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, args.workload),
+            "config": workload_config(w, args.workload, update=args.update),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full runs of {what} ({n} points each)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -299,7 +307,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     elem = X.dtype.itemsize
     fp32 = args.precision == "fp32"
     prec = gridshift.GS_FP32_MIXED if fp32 else gridshift.GS_FP64
-    g = gridshift.GridShift(d, w["h"], w["max_iter"], precision=prec)
+    form = (gridshift.GS_UPDATE_SEQUENTIAL if args.update == "sequential"
+            else gridshift.GS_UPDATE_PARALLEL)
+    g = gridshift.GridShift(d, w["h"], w["max_iter"], precision=prec, update=form)
     pts = torch.from_numpy(X).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     modes = torch.empty((max(n // 16, 4096), d), dtype=torch.float64, device=dev)
@@ -450,11 +460,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs)",
                 "frac_of": pk["source"],
                 "algorithmic_bytes_per_launch": lb, "avg_launch_ms": loop_ms,
-                "traffic": traffic(args.workload, args.precision, "k_loop"),
+                "traffic": traffic(args.workload, args.precision, "k_loop", args.update),
                 "second": {"kernel": "k_bin (binning, first pass)", "achieved": bb / (bin_ms / 1e3) / 1e9,
                            "frac": bb / (bin_ms / 1e3) / 1e9 / pk["hbm_gbs"],
                            "algorithmic_bytes_per_launch": bb, "avg_launch_ms": bin_ms,
-                           "traffic": traffic(args.workload, args.precision, "k_bin")}}
+                           "traffic": traffic(args.workload, args.precision, "k_bin",
+                                              args.update)}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -462,7 +473,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
                 "data": "synthetic",
-                "config": workload_config(w, args.workload, args.precision),
+                "config": workload_config(w, args.workload, args.precision, args.update),
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": int(X.nbytes),
                         "d2h_bytes_per_step": int(n * 4 + kk * d * 8)},
@@ -477,7 +488,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if sequential is not None:
             line["sequential"] = sequential
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(w, update=args.update)
         print(json.dumps(line), flush=True)
     g.close()
     return 0
@@ -576,8 +587,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="image_1080p_d5")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--update", choices=["parallel", "sequential"], default="parallel",
+                    help="update form: Eq. 6 (parallel, default) or Eq. 5 (sequential; "
+                         "float64, one point set per call)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.update == "sequential" and (args.precision != "fp64" or
+                                        args.workload.startswith(("batch", "track"))):
+        ap.error("--update sequential runs in fp64 on workloads of one point set")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

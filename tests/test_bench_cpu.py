@@ -1,0 +1,39 @@
+"""bench.py's CPU-side contract: the reference arm (the oracle) on both update
+forms, the argument checks, and the traffic lookup."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench(*args):
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_sequential_line():
+    r = _bench("--impl", "reference", "--workload", "image_321x481_d3", "--steps", "1",
+               "--warmup", "0", "--update", "sequential")
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["update"] == "sequential"
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_sequential_needs_fp64_and_one_point_set():
+    for extra in (["--precision", "fp32"], ["--workload", "batch_64_d3"]):
+        r = _bench("--update", "sequential", *extra)
+        assert r.returncode == 2 and "sequential" in r.stderr
+
+
+def test_traffic_only_for_captured_parallel_kernels():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.traffic("image_1080p_d5", "fp64", "k_loop", "sequential") is None
+    assert bench.traffic("no_such_workload", "fp64", "k_loop") is None
