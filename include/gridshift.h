@@ -239,7 +239,8 @@ gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
  * max_iter = 50, growing with d and max_iter, plus 272 KB of fixed buffers)
  * must fit what the points leave; the cell-face table holds at most 8192
  * entries (over all axes, the number of cells the data spans plus 3).
- * Beyond these the call returns GS_E_SCRATCH; use gs_fit.  GS_FP64 only.
+ * Beyond these the call returns GS_E_SCRATCH; use gs_fit.  GS_FP64 and the
+ * parallel update (GS_UPDATE_PARALLEL) only.
  *
  * Sharing: every call uses the same array, which keeps the previous call's
  * contents; the call clears what must start at zero itself.  Calls are
