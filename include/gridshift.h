@@ -7,7 +7,8 @@
  *   i)   binning every point into the grid cell floor(x / h) and keeping, per
  *        active cell, its resident count and the sum of its residents;
  *   ii)  moving every active cell to the count-weighted mean over its 3^d
- *        neighbouring cells (Eq. 1-2, applied in the parallel form of Eq. 6);
+ *        neighbouring cells (Eq. 1-2, applied in the parallel form of Eq. 6,
+ *        or in the sequential form of Eq. 5: see gs_update);
  *   iii) re-keying each moved cell by floor(centroid / h);
  *   iv)  merging the cells that share a key, adding counts and count-weighted
  *        centroids (Eq. 3-4);
