@@ -166,6 +166,25 @@ def test_brute_force_matches(X, h, max_iter):
     assert np.array_equal(r["modes"], b["modes"])  # bit-exact
 
 
+def test_wide_key_ranges_match_brute_force():
+    # keys far apart on every axis: a packed key of these cells would need
+    # more than 63 bits (d = 4 axes spanning 2^22 cells each); the oracle
+    # keeps one int64 per axis and must still match the brute force
+    rng = np.random.default_rng(63)
+    for d in (3, 4):
+        C = rng.uniform(-2.0e6, 2.0e6, size=(4, d))
+        X = C[rng.integers(0, 4, 50)] + rng.normal(0, 0.9, size=(50, d))
+        X[:5] = np.round(X[:5] * 2) / 2  # some points on cell faces
+        r = oracle.fit(X, 1.0, 50)
+        b = brute_force(X, 1.0, 50)
+        span = r["keys"].max(axis=0) - r["keys"].min(axis=0)
+        assert np.sum(np.ceil(np.log2(span + 3))) > 63
+        assert r["iterations"] == b["iterations"] and r["m_hist"].tolist() == b["m_hist"]
+        assert np.array_equal(r["labels"], b["labels"])
+        assert np.array_equal(r["keys"], b["keys"])
+        assert np.array_equal(r["modes"], b["modes"])
+
+
 def test_brute_force_order_independent():
     # The result does not depend on the order of the points (Eq. 1-4 define
     # sums only); the oracle's exact sums make that hold bit for bit.
