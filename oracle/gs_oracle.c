@@ -324,7 +324,7 @@ static int fit_impl(const double *X, int64_t n, int d, double h, int max_iter,
     } else {
       for (int64_t j = 0; j < m; j++) sweep[ns++] = j;
     }
-    memset(done, 0, (size_t)m);
+    for (int64_t j = 0; j < m; j++) done[j] = 0;
     for (int64_t s = 0; s < m; s++) {
       const int64_t j = sweep[s];
       uint64_t D = 0;
