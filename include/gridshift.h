@@ -98,7 +98,9 @@ typedef struct {
   int32_t converged;   /* 1 if stopped by the criterion of Sec. 2.1 v (no cell has a neighbour) */
   int64_t m0;          /* active cells after binning (i) */
   int64_t k;           /* active cells at exit = number of clusters */
-  int64_t inexact;     /* values truncated by the fixed-point window (0 in normal use) */
+  int64_t inexact;     /* values truncated by the fixed-point window, or centroids too
+                          close to zero for the window to round (below about 2^-136
+                          times n max|x|); 0 in normal use */
   int64_t cell_iters;  /* sum over applied updates of the active cells updated */
   int64_t launches;    /* CUDA kernels the call launched */
   int64_t face_rechecks; /* GS_FP32_MIXED: key decisions redone in float64 near a face */

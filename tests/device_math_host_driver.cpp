@@ -1,0 +1,110 @@
+// Host build of the library's exact-arithmetic helpers
+// (paper_2206_02200_gb300/csrc/gs_device.cuh: float64 <-> 128-bit fixed point,
+// rounding of exact sums and of exact quotients to float64), for
+// tests/test_device_math_host.py.  The CUDA names the header uses get host
+// meanings below; the functions checked here use only the integer ones.
+// Queries on stdin, one answer line each (integers in hex, two 64-bit halves
+// for a 128-bit value, float64 results as their bit patterns):
+//   T bits L        -> to_fixed: hi lo inexact err
+//   R hi lo L       -> round_fixed: bits
+//   Q hi lo L       -> round_to_double: hi lo err
+//   V hi lo D L     -> div_round: bits inexact
+//   W f32bits       -> f32_bits_to_f64_bits: bits
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define __restrict__ __restrict
+
+struct ulonglong2 {
+  unsigned long long x, y;
+};
+
+static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+static inline int __clzll(long long x) { return x ? __builtin_clzll((unsigned long long)x) : 64; }
+static inline int __popc(unsigned x) { return __builtin_popcount(x); }
+static inline unsigned long long __umul64hi(unsigned long long a, unsigned long long b) {
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+}
+static inline double __longlong_as_double(long long v) {
+  double d;
+  std::memcpy(&d, &v, 8);
+  return d;
+}
+static inline long long __double_as_longlong(double d) {
+  long long v;
+  std::memcpy(&v, &d, 8);
+  return v;
+}
+static inline unsigned __float_as_uint(float f) {
+  unsigned u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+static inline float __uint_as_float(unsigned u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+static inline long long __float2ll_rd(float f) { return (long long)std::floor(f); }
+template <class T>
+static inline T __ldg(const T* p) { return *p; }
+template <class T>
+static inline T __ldcg(const T* p) { return *p; }
+// atomics and warp shuffles: declared only (nothing checked here calls them)
+template <class T, class U>
+T atomicAdd(T* p, U v);
+template <class T, class U, class V>
+T atomicCAS(T* p, U c, V v);
+template <class T, class U>
+T atomicOr(T* p, U v);
+template <class T>
+T __shfl_xor_sync(unsigned mask, T v, int lane, int width = 32);
+
+#include "../paper_2206_02200_gb300/csrc/gs_device.cuh"
+
+using gs::u128;
+
+static u128 read128(unsigned long long hi, unsigned long long lo) {
+  return ((u128)hi << 64) | lo;
+}
+
+static unsigned long long bits_of(double d) { return (unsigned long long)__double_as_longlong(d); }
+
+int main() {
+  char op[8];
+  while (std::scanf("%7s", op) == 1) {
+    unsigned long long hi = 0, lo = 0, b = 0;
+    int L = 0;
+    unsigned inexact = 0, err = 0;
+    if (std::strcmp(op, "T") == 0) {
+      if (std::scanf("%llx %d", &b, &L) != 2) return 2;
+      const u128 V = gs::to_fixed(b, L, inexact, err);
+      std::printf("%llx %llx %u %u\n", (unsigned long long)(V >> 64), (unsigned long long)V,
+                  inexact, err);
+    } else if (std::strcmp(op, "R") == 0) {
+      if (std::scanf("%llx %llx %d", &hi, &lo, &L) != 3) return 2;
+      std::printf("%llx\n", bits_of(gs::round_fixed(read128(hi, lo), L, inexact)));
+    } else if (std::strcmp(op, "Q") == 0) {
+      if (std::scanf("%llx %llx %d", &hi, &lo, &L) != 3) return 2;
+      const u128 V = gs::round_to_double(read128(hi, lo), L, err);
+      std::printf("%llx %llx %u\n", (unsigned long long)(V >> 64), (unsigned long long)V, err);
+    } else if (std::strcmp(op, "V") == 0) {
+      unsigned D = 0;
+      if (std::scanf("%llx %llx %u %d", &hi, &lo, &D, &L) != 4 || D == 0) return 2;
+      const double q = gs::div_round(read128(hi, lo), D, L, inexact);
+      std::printf("%llx %u\n", bits_of(q), inexact);
+    } else if (std::strcmp(op, "W") == 0) {
+      unsigned f = 0;
+      if (std::scanf("%x", &f) != 1) return 2;
+      std::printf("%llx\n", (unsigned long long)gs::f32_bits_to_f64_bits(f));
+    } else {
+      return 2;
+    }
+  }
+  return 0;
+}

@@ -1,0 +1,170 @@
+"""The library's exact-arithmetic helpers (csrc/gs_device.cuh), built for the
+host with g++, against Python Fractions.  On the device these form every sum
+and quotient of the GS_FP64 path; here they are checked one by one:
+  * to_fixed: a float64 as a two's-complement integer in units of 2^L
+    (truncated toward zero; inexact / out-of-window flags);
+  * round_fixed: V * 2^L rounded to the nearest float64, ties to even,
+    subnormals included;
+  * round_to_double: the same rounding kept in units of 2^L (equal to
+    to_fixed(round_fixed(V, L), L));
+  * div_round: the exact quotient V * 2^L / D rounded once, ties to even,
+    or the inexact flag where the quotient has too few bits to round (its
+    documented limit);
+  * the exact float32 -> float64 widening of the bit patterns."""
+from __future__ import annotations
+
+import math
+import os
+import random
+import shutil
+import struct
+import subprocess
+from fractions import Fraction as Fr
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+M128 = (1 << 128) - 1
+
+
+@pytest.fixture(scope="module")
+def dm(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("devmath")
+    # the header includes <cuda_runtime.h>; the host build needs none of it
+    (d / "cuda_runtime.h").write_text("")
+    exe = str(d / "device_math_host")
+    b = subprocess.run([gxx, "-std=c++17", "-O2", "-Wno-unknown-pragmas", "-I", str(d),
+                        "-o", exe, os.path.join(ROOT, "tests", "device_math_host_driver.cpp")],
+                       capture_output=True, text=True)
+    assert b.returncode == 0, b.stderr[-3000:]
+
+    def ask(lines):
+        r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True,
+                           text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-1000:]
+        out = r.stdout.strip().splitlines()
+        assert len(out) == len(lines)
+        return out
+    return ask
+
+
+def bits(x: float) -> int:
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def from_bits(b: int) -> float:
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+def split(v: int) -> str:
+    v &= M128
+    return f"{v >> 64:x} {v & ((1 << 64) - 1):x}"
+
+
+def signed(hi: str, lo: str) -> int:
+    v = (int(hi, 16) << 64) | int(lo, 16)
+    return v - (1 << 128) if v >> 127 else v
+
+
+def rn(q: Fr) -> float:
+    return float(q)  # Python rounds a Fraction correctly (ties to even, subnormals)
+
+
+def _values(rng, n):
+    """Signed integers of every width up to 125 bits, and tie patterns."""
+    out = []
+    for _ in range(n):
+        w = rng.randint(1, 125)
+        v = rng.getrandbits(w) | (1 << (w - 1))
+        out.append(v if rng.random() < 0.5 else -v)
+    for w in (54, 60, 80, 120):  # exact ties at the 53-bit boundary, odd and even
+        for last in (0, 1):
+            top = (1 << 52) | rng.getrandbits(51) << 1 | last
+            v = (2 * top + 1) << (w - 54)
+            out += [v, -v]
+    return out
+
+
+LS = [-1100, -1075, -300, -64, -20, 0, 17]
+
+
+def test_to_fixed(dm):
+    rng = random.Random(1)
+    cases = []
+    for _ in range(400):
+        x = rng.uniform(-1, 1) * 2.0 ** rng.randint(-1080, 120)
+        cases.append((x, rng.choice(LS)))
+    cases += [(0.0, 0), (-0.0, 5), (5e-324, -1074), (5e-324, -1000), (2.0 ** 125, 0),
+              (2.0 ** 126, 0), (-(2.0 ** 200), 70)]
+    out = dm([f"T {bits(x):x} {L}" for x, L in cases])
+    for (x, L), line in zip(cases, out):
+        hi, lo, inexact, err = line.split()
+        q = Fr(x) / Fr(2) ** L
+        if abs(q) >= 2 ** 126:
+            assert err == "1", (x, L)
+            continue
+        assert err == "0", (x, L)
+        t = math.trunc(q)  # toward zero
+        assert signed(hi, lo) == t, (x, L)
+        assert inexact == ("1" if q != t else "0"), (x, L)
+
+
+def test_round_fixed_and_round_to_double(dm):
+    rng = random.Random(2)
+    cases = [(v, rng.choice(LS)) for v in _values(rng, 500)]
+    out_r = dm([f"R {split(v)} {L}" for v, L in cases])
+    out_q = dm([f"Q {split(v)} {L}" for v, L in cases])
+    for (v, L), r, q in zip(cases, out_r, out_q):
+        want = rn(Fr(v) * Fr(2) ** L)
+        assert int(r, 16) == bits(want) or (want == 0 and from_bits(int(r, 16)) == 0), (v, L)
+        hi, lo, err = q.split()
+        back = Fr(want) / Fr(2) ** L
+        assert back.denominator == 1
+        assert signed(hi, lo) == back.numerator, (v, L)
+        assert err == ("1" if abs(back) >= 2 ** 126 else "0")
+
+
+def test_div_round(dm):
+    rng = random.Random(3)
+    cases = []
+    for v in _values(rng, 400):
+        D = rng.choice([1, 2, 3, 7, 1 << 31, (1 << 32) - 1, rng.randint(1, (1 << 32) - 1),
+                        rng.randint(1, 1000)])
+        cases.append((v, D, rng.choice(LS)))
+    for _ in range(100):  # quotients that are exact ties
+        D = rng.randint(1, 1 << 20)
+        top = (1 << 52) | rng.getrandbits(52)
+        X = (2 * top + 1) << rng.randint(0, 40)
+        if X * D < 1 << 125:
+            cases.append((X * D * rng.choice([1, -1]), D, rng.choice(LS)))
+    cases += [(-38, 3986530705, 17), (1, (1 << 32) - 1, 0)]  # quotients of few bits
+    out = dm([f"V {split(v)} {D} {L}" for v, D, L in cases])
+    flagged = 0
+    for (v, D, L), line in zip(cases, out):
+        b, inexact = line.split()
+        want = rn(Fr(v) * Fr(2) ** L / D)
+        got = from_bits(int(b, 16))
+        Q, R = divmod(abs(v) << 64, D)  # the 64 fraction bits the division forms
+        if inexact == "1":
+            # the documented limit: the quotient has at most 53 bits there and
+            # a nonzero remainder, so the rounding is unknown and flagged
+            assert Q.bit_length() <= 53 and R != 0, (v, D, L)
+            flagged += 1
+            continue
+        assert got == want and math.copysign(1, got) == math.copysign(1, want) or \
+            (want == 0 and got == 0), (v, D, L, got, want)
+    assert flagged >= 2 and flagged < len(cases) // 10
+
+
+def test_float32_widening(dm):
+    rng = random.Random(4)
+    fs = [0, 0x80000000, 1, 0x807FFFFF, 0x00400000, 0x3F800000, 0x7F7FFFFF, 0xFF7FFFFF]
+    fs += [rng.getrandbits(32) for _ in range(500)]
+    fs = [f for f in fs if (f >> 23) & 0xFF != 0xFF]  # finite inputs only
+    out = dm([f"W {f:x}" for f in fs])
+    for f, line in zip(fs, out):
+        x = struct.unpack("<f", struct.pack("<I", f))[0]  # exact in a Python float
+        assert int(line, 16) == bits(x), hex(f)
