@@ -1,8 +1,10 @@
 // Host build of the library's exact-arithmetic helpers
 // (paper_2206_02200_gb300/csrc/gs_device.cuh: float64 <-> 128-bit fixed point,
 // rounding of exact sums and of exact quotients to float64), for
-// tests/test_device_math_host.py.  The CUDA names the header uses get host
-// meanings below; the functions checked here use only the integer ones.
+// tests/test_device_math_host.py; key_index comes with the face table the
+// planner (gs_planner.cuh) builds.  The CUDA names the headers use get host
+// meanings below (atomics and warp shuffles are declared only: nothing checked
+// here calls them).
 // Queries on stdin, one answer line each (integers in hex, two 64-bit halves
 // for a 128-bit value, float64 results as their bit patterns):
 //   T bits L        -> to_fixed: hi lo inexact err
@@ -10,6 +12,8 @@
 //   Q hi lo L       -> round_to_double: hi lo err
 //   V hi lo D L     -> div_round: bits inexact
 //   W f32bits       -> f32_bits_to_f64_bits: bits
+//   K h kmin span x -> key_index over the face table of cells kmin .. kmin+span-1
+//                      (h and x as C99 hex floats): the cell's index
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -66,6 +70,10 @@ template <class T>
 T __shfl_xor_sync(unsigned mask, T v, int lane, int width = 32);
 
 #include "../paper_2206_02200_gb300/csrc/gs_device.cuh"
+#include "../paper_2206_02200_gb300/csrc/gs_planner.cuh"
+
+#include <cstdlib>
+#include <vector>
 
 using gs::u128;
 
@@ -102,6 +110,16 @@ int main() {
       unsigned f = 0;
       if (std::scanf("%x", &f) != 1) return 2;
       std::printf("%llx\n", (unsigned long long)gs::f32_bits_to_f64_bits(f));
+    } else if (std::strcmp(op, "K") == 0) {
+      char hs[64], xs[64];
+      long long kmin = 0;
+      int span = 0;
+      if (std::scanf("%63s %lld %d %63s", hs, &kmin, &span, xs) != 4 || span < 1) return 2;
+      const double h = std::strtod(hs, nullptr), x = std::strtod(xs, nullptr);
+      std::vector<int64_t> thr((size_t)span + 1);
+      for (int j = 0; j <= span; ++j) thr[(size_t)j] = gs::plan_ord_of(gs::plan_face(kmin + j, h));
+      std::printf("%d\n", gs::key_index(thr.data(), span, (int64_t)kmin, (float)(1.0 / h),
+                                        bits_of(x)));
     } else {
       return 2;
     }

@@ -10,7 +10,9 @@ and quotient of the GS_FP64 path; here they are checked one by one:
   * div_round: the exact quotient V * 2^L / D rounded once, ties to even,
     or the inexact flag where the quotient has too few bits to round (its
     documented limit);
-  * the exact float32 -> float64 widening of the bit patterns."""
+  * the exact float32 -> float64 widening of the bit patterns;
+  * key_index: the cell of a value by a float guess corrected against the
+    exact face table (the device's floor(x / h))."""
 from __future__ import annotations
 
 import math
@@ -168,3 +170,30 @@ def test_float32_widening(dm):
     for f, line in zip(fs, out):
         x = struct.unpack("<f", struct.pack("<I", f))[0]  # exact in a Python float
         assert int(line, 16) == bits(x), hex(f)
+
+
+def test_key_index_is_floor(dm):
+    rng = random.Random(5)
+    cases = []
+    for h in (0.1, 1.0 / 3.0, 12.0, 1e-3, 7.5e5, 0.75, 2.0 ** -20, 16.0):
+        for _ in range(120):
+            span = rng.choice([1, 2, 3, rng.randint(1, 5000)])
+            kmin = rng.randint(-10 ** 6, 10 ** 6)
+            q = kmin + rng.randrange(span)
+            lo = Fr(q) * Fr(h)
+            f = float(lo)
+            if Fr(f) < lo:
+                f = math.nextafter(f, math.inf)  # the face of cell q
+            kind = rng.randrange(3)
+            if kind == 0:
+                x = f
+            elif kind == 1:
+                x = float(lo + Fr(h) * Fr(rng.random()))
+            else:
+                x = math.nextafter(f, -math.inf) if q > kmin else f
+            cases.append((h, kmin, span, x))
+    out = dm([f"K {h.hex()} {kmin} {span} {x.hex()}" for h, kmin, span, x in cases])
+    for (h, kmin, span, x), got in zip(cases, out):
+        want = math.floor(Fr(x) / Fr(h)) - kmin
+        want = min(max(want, 0), span - 1)  # outside the table: clamped
+        assert int(got) == want, (h, kmin, span, x)
