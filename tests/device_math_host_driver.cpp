@@ -2,9 +2,8 @@
 // (paper_2206_02200_gb300/csrc/gs_device.cuh: float64 <-> 128-bit fixed point,
 // rounding of exact sums and of exact quotients to float64), for
 // tests/test_device_math_host.py; key_index comes with the face table the
-// planner (gs_planner.cuh) builds.  The CUDA names the headers use get host
-// meanings below (atomics and warp shuffles are declared only: nothing checked
-// here calls them).
+// planner (gs_planner.cuh) builds; the hash table's insert and lookup run on
+// one thread.  The CUDA names the headers use get host meanings below.
 // Queries on stdin, one answer line each (integers in hex, two 64-bit halves
 // for a 128-bit value, float64 results as their bit patterns):
 //   T bits L        -> to_fixed: hi lo inexact err
@@ -14,6 +13,9 @@
 //   W f32bits       -> f32_bits_to_f64_bits: bits
 //   K h kmin span x -> key_index over the face table of cells kmin .. kmin+span-1
 //                      (h and x as C99 hex floats): the cell's index
+//   H cap n k_1 .. k_n m a_1 .. a_m -> a table of cap slots: per insert of k_i
+//                      "slot won", then per lookup of a_j its slot (or
+//                      ffffffff), then the error word
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -59,13 +61,26 @@ template <class T>
 static inline T __ldg(const T* p) { return *p; }
 template <class T>
 static inline T __ldcg(const T* p) { return *p; }
-// atomics and warp shuffles: declared only (nothing checked here calls them)
+// atomics with their single-thread meaning (the hash table checks run on one
+// thread); warp shuffles are declared only (nothing checked here calls them)
 template <class T, class U>
-T atomicAdd(T* p, U v);
+T atomicAdd(T* p, U v) {
+  const T old = *p;
+  *p = old + (T)v;
+  return old;
+}
 template <class T, class U, class V>
-T atomicCAS(T* p, U c, V v);
+T atomicCAS(T* p, U c, V v) {
+  const T old = *p;
+  if (old == (T)c) *p = (T)v;
+  return old;
+}
 template <class T, class U>
-T atomicOr(T* p, U v);
+T atomicOr(T* p, U v) {
+  const T old = *p;
+  *p = old | (T)v;
+  return old;
+}
 template <class T>
 T __shfl_xor_sync(unsigned mask, T v, int lane, int width = 32);
 
@@ -120,6 +135,34 @@ int main() {
       for (int j = 0; j <= span; ++j) thr[(size_t)j] = gs::plan_ord_of(gs::plan_face(kmin + j, h));
       std::printf("%d\n", gs::key_index(thr.data(), span, (int64_t)kmin, (float)(1.0 / h),
                                         bits_of(x)));
+    } else if (std::strcmp(op, "H") == 0) {
+      unsigned cap = 0;
+      int n = 0, m = 0;
+      if (std::scanf("%u %d", &cap, &n) != 2 || cap < 4 || (cap & (cap - 1)) || n < 0) return 2;
+      // 32-byte aligned key array, all slots empty
+      std::vector<ulonglong2> store((size_t)cap / 2 + 2);
+      uint64_t* keys = reinterpret_cast<uint64_t*>(
+          (reinterpret_cast<uintptr_t>(store.data()) + 31) & ~(uintptr_t)31);
+      for (unsigned i = 0; i < cap; ++i) keys[i] = gs::kEmpty;
+      uint32_t err = 0;
+      for (int i = 0; i < n; ++i) {
+        unsigned long long k = 0;
+        if (std::scanf("%llx", &k) != 1) return 2;
+        bool won = false;
+        const uint32_t sl = gs::table_insert(keys, cap - 1, k, won, &err);
+        std::printf("%x %d ", sl, won ? 1 : 0);
+      }
+      if (std::scanf("%d", &m) != 1 || m < 0) return 2;
+      for (int j = 0; j < m; ++j) {
+        unsigned long long k = 0;
+        if (std::scanf("%llx", &k) != 1) return 2;
+        const uint64_t q[1] = {k};
+        const bool v[1] = {true};
+        uint32_t sl[1];
+        gs::table_find_many<1>(keys, cap - 1, q, v, sl);
+        std::printf("%x ", sl[0]);
+      }
+      std::printf("%u\n", err);
     } else {
       return 2;
     }

@@ -197,3 +197,57 @@ def test_key_index_is_floor(dm):
         want = math.floor(Fr(x) / Fr(h)) - kmin
         want = min(max(want, 0), span - 1)  # outside the table: clamped
         assert int(got) == want, (h, kmin, span, x)
+
+
+def _home(key: int, buckets: int) -> int:
+    b = buckets.bit_length() - 1  # buckets is a power of two
+    return 0 if b == 0 else ((key * 0x9E3779B97F4A7C15) % 2 ** 64) >> (64 - b)
+
+
+def test_hash_table_insert_and_lookup(dm):
+    # one thread: every distinct key gets its own slot within the probe limit
+    # of its home bucket (Fibonacci hashing, four slots a bucket); a repeated
+    # insert returns the same slot without winning; lookups find every stored
+    # key and no absent one; an insert that finds no free slot within the
+    # limit returns no slot and sets kErrTableFull (never at load <= 1/2)
+    rng = random.Random(6)
+    cases = []
+    for cap in (4, 16, 64, 1024, 4096):
+        for load in (0.25, 0.5, 0.9, 1.0, 1.3):
+            n = int(cap * load)
+            keys = [rng.getrandbits(63) for _ in range(n)]
+            keys += rng.sample(keys, min(len(keys), 5))  # repeats
+            absent = [rng.getrandbits(63) | (1 << 62) for _ in range(10)]
+            cases.append((cap, keys, keys[:50] + absent))
+    lines = [f"H {cap} {len(ins)} " + " ".join(f"{k:x}" for k in ins) + f" {len(look)} "
+             + " ".join(f"{k:x}" for k in look) for cap, ins, look in cases]
+    out = dm(lines)
+    for (cap, ins, look), line in zip(cases, out):
+        f = line.split()
+        slots = [int(x, 16) for x in f[0:2 * len(ins):2]]
+        wons = [int(x) for x in f[1:2 * len(ins):2]]
+        found = [int(x, 16) for x in f[2 * len(ins):2 * len(ins) + len(look)]]
+        err = int(f[-1])
+        buckets = cap // 4
+        where = {}
+        failed = False
+        for k, sl, won in zip(ins, slots, wons):
+            if sl == 0xFFFFFFFF:  # no free slot within the probe limit
+                failed = True
+                assert won == 0 and k not in where
+                continue
+            assert sl < cap
+            if k in where:
+                assert sl == where[k] and won == 0
+            else:
+                assert won == 1 and sl not in where.values()
+                where[k] = sl
+                dist = (sl // 4 - _home(k, buckets)) % buckets
+                assert dist < min(buckets, 128)  # within the probe limit
+        assert bool(err & 1) == failed
+        if len(set(ins)) > cap:
+            assert failed
+        if len(set(ins)) <= cap // 2:  # the loads the library uses
+            assert not failed
+        for k, sl in zip(look, found):
+            assert sl == where.get(k, 0xFFFFFFFF), (cap, k)
