@@ -119,6 +119,15 @@ def test_update_form_host_only_checks(lib):
     assert lib.gs_set_update(None, 0) == gridshift.GS_E_INVALID
 
 
+def test_tensor_front_end_rejects_unknown_forms(lib):
+    pytest.importorskip("torch")
+    for kw in ({"update": 9}, {"precision": 4}):
+        with pytest.raises(gridshift.GridShiftError):
+            gridshift.GridShift(3, 1.0, 10, **kw)
+    with gridshift.GridShift(3, 1.0, 10, update=gridshift.GS_UPDATE_SEQUENTIAL) as g:
+        assert g._ctx
+
+
 def test_product_never_imports_the_oracle():
     pkg = os.path.join(ROOT, "paper_2206_02200_gb300")
     for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
