@@ -7,6 +7,8 @@
 //   O x          -> plan_ord_of(x)
 //   L d B s_0 .. s_{d-1} -> plan_finish status, total key bits, then for every
 //                   probe p: its packed-key offset and 2-bit offset vector
+//   P d h n B (lo hi maxabs) x d -> plan_from_range from the key range: status,
+//                   then per axis "kmin span L thr_off", then the face-table length
 // Doubles are read and written as C99 hex floats.
 #define __host__
 #define __device__
@@ -52,6 +54,32 @@ int main() {
           std::printf(" %" PRIu64 ":%u", delta, vp);
         }
         for (int a = 0; a < d; ++a) std::printf(" off%d=%d", a, P.off[a]);
+      }
+      std::printf("\n");
+    } else if (std::strcmp(op, "P") == 0) {
+      int d, B;
+      char hs[64];
+      long long n;
+      if (std::scanf("%d %63s %lld %d", &d, hs, &n, &B) != 4 || d < 1 || d > gs::kMaxD) return 2;
+      gs::DevFlags fl;
+      std::memset(&fl, 0, sizeof(fl));
+      for (int a = 0; a < d; ++a) {
+        char ls[64], us[64], ms[64];
+        if (std::scanf("%63s %63s %63s", ls, us, ms) != 3) return 2;
+        fl.min_ord[a] = gs::plan_ord_of(std::strtod(ls, nullptr));
+        fl.max_ord[a] = gs::plan_ord_of(std::strtod(us, nullptr));
+        const double m = std::strtod(ms, nullptr);
+        std::memcpy(&fl.maxabs[a], &m, 8);
+      }
+      gs::Plan P;
+      gs::PlanSizes z;
+      std::memset(&z, 0, sizeof(z));
+      const uint32_t st = gs::plan_from_range(d, std::strtod(hs, nullptr), n, B, fl, P, z);
+      std::printf("%u", st);
+      if (st == gs::kPlanOK) {
+        for (int a = 0; a < d; ++a)
+          std::printf(" %lld %d %d %d", (long long)P.kmin[a], P.span[a], P.L[a], P.thr_off[a]);
+        std::printf(" %llu", (unsigned long long)z.thr_words);
       }
       std::printf("\n");
     } else {

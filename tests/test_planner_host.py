@@ -7,7 +7,8 @@ decide every cell key of Sec. 2.1 i, so they are checked here on the CPU:
   * plan_ord_of orders doubles as their values (-0 as +0);
   * plan_finish / plan_probe: the packed-key layout (axis 0 most significant,
     each axis span + 1 values wide, the instance field above) and the 3^d
-    neighbour offsets (axis 0 the slowest digit)."""
+    neighbour offsets (axis 0 the slowest digit);
+  * plan_from_range: the whole plan from a key range, and its refusals."""
 from __future__ import annotations
 
 import math
@@ -118,3 +119,62 @@ def test_packed_key_layout_and_probes(planner):
             delta = sum(v[a] << off[a] for a in range(d)) % 2 ** 64
             vpack = sum((v[a] + 1) << (2 * a) for a in range(d))
             assert f[2 + p] == f"{delta}:{vpack}", (d, spans, p)
+
+
+def test_plan_from_key_range(planner):
+    # the whole plan from a key range (k_plan's input): per axis the key box
+    # widened by one cell each side, the fixed-point unit 2^L with
+    # L = e + ceil(log2 n) - 126 (max |x| < 2^e), the face-table offsets; and
+    # the refusals: |x / h| >= 4e15, more than 2^22 cells on an axis, a packed
+    # key wider than 63 bits
+    rng = random.Random(9)
+    cases = []
+    for _ in range(300):
+        d = rng.randint(1, 8)
+        h = rng.choice(HS)
+        n = rng.choice([1, 2, 3, 1000, 1 << 20, (1 << 31) - 1])
+        B = rng.choice([1, 1, 5])
+        axes = []
+        for _ in range(d):
+            kind = rng.random()
+            if kind < 0.05:
+                lo, hi = -5e15 * h, 1.0 * h  # beyond the exact range
+            elif kind < 0.1:
+                lo, hi = 0.0, h * 5e6  # more than 2^22 cells
+            else:
+                c = rng.uniform(-1e5, 1e5) * h
+                w = rng.choice([0.0, rng.uniform(0, 50), rng.uniform(0, 3000)]) * h
+                lo, hi = c, c + w
+            axes.append((lo, hi, max(abs(lo), abs(hi))))
+        cases.append((d, h, n, B, axes))
+    lines = [f"P {d} {h.hex()} {n} {B} " + " ".join(f"{lo.hex()} {hi.hex()} {m.hex()}"
+                                                    for lo, hi, m in axes)
+             for d, h, n, B, axes in cases]
+    out = planner(lines)
+    for (d, h, n, B, axes), line in zip(cases, out):
+        f = [int(t) for t in line.split()]
+        want_status, rows = 0, []
+        for lo, hi, m in axes:
+            if not (abs(lo / h) < 4.0e15 and abs(hi / h) < 4.0e15):
+                want_status = 2
+                break
+            kmin = math.floor(Fr(lo) / Fr(h)) - 1
+            span = math.floor(Fr(hi) / Fr(h)) + 1 - kmin + 1
+            if span > 1 << 22:
+                want_status = 3
+                break
+            e = math.frexp(m)[1] if m > 0 else 0
+            rows.append((kmin, span, e + (n - 1).bit_length() - 126))
+        if want_status == 0:
+            bits = sum((s + 1).bit_length() for _, s, _ in rows)
+            bits += (B - 1).bit_length() if B > 1 else 0
+            if bits > 63:
+                want_status = 4
+        assert f[0] == want_status, (line, axes)
+        if want_status:
+            continue
+        off = 0
+        for a, (kmin, span, L) in enumerate(rows):
+            assert f[1 + 4 * a: 5 + 4 * a] == [kmin, span, L, off], (a, axes[a])
+            off += span + 1
+        assert f[-1] == off
