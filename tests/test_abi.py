@@ -168,3 +168,24 @@ def test_window_rect():
     assert gridshift.window_rect((10.5, 20.0), 5.0, 4.0) == (8, 18, 14, 23)
     assert gridshift.window_rect((0.0, 0.0), 1.0, 1.0) == (0, 0, 1, 1)
     assert gridshift.window_rect((3.2, 7.7), 0.2, 0.2) == (4, 8, 4, 8)  # no pixel inside
+
+
+def test_noalloc_host_only_checks(lib):
+    # argument checks and the per-point limit are decided before any device
+    # call: 8 bytes a point plus 1 MiB must fit the 64 MiB static array
+    F64 = gridshift.GS_IN_F64
+    fake = 1 << 20  # never dereferenced: every case below returns first
+    st, k, info = gridshift.gs_fit_noalloc(3, 1.0, 10, None, 0, F64, 0, 0, 0, 0)
+    assert st == gridshift.GS_OK and k == 0 and info.converged == 1
+    for args in ((0, 1.0, 10), (9, 1.0, 10), (3, 0.0, 10), (3, math.inf, 10), (3, 1.0, -1)):
+        st, _, _ = gridshift.gs_fit_noalloc(*args, None, fake, F64, 10, fake, 0, 0)
+        assert st == gridshift.GS_E_INVALID, args
+    st, _, _ = gridshift.gs_fit_noalloc(3, 1.0, 10, None, fake, 7, 10, fake, 0, 0)
+    assert st == gridshift.GS_E_INVALID  # dtype
+    st, _, _ = gridshift.gs_fit_noalloc(3, 1.0, 10, None, 0, F64, 10, fake, 0, 0)
+    assert st == gridshift.GS_E_INVALID  # NULL points
+    limit = ((64 << 20) - (1 << 20)) // 8  # 8,257,536 points
+    assert limit == 8_257_536
+    st, _, _ = gridshift.gs_fit_noalloc(3, 1.0, 10, None, fake, F64, limit + 1, fake, 0, 0)
+    assert st == gridshift.GS_E_SCRATCH
+
