@@ -48,3 +48,8 @@ def all_cases() -> list:
 def sequential_cases() -> list:
     """The hand-worked cases of the sequential update (Eq. 5)."""
     return [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "sequential", "*.txt")))]
+
+
+def step_limit_cases() -> list:
+    """Hand-worked cases stopped by max_iter (parallel update)."""
+    return [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "step_limit", "*.txt")))]

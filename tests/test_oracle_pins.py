@@ -120,6 +120,12 @@ def test_golden_examples(case):
             assert abs(Fr(float(g)) - w) <= Fr(math.ulp(float(w))), (g, w)
 
 
+@pytest.mark.parametrize("case", golden_io.step_limit_cases(), ids=lambda c: c["name"])
+def test_golden_step_limit(case):
+    test_golden_examples(case)
+    assert not oracle.fit(case["points"], case["h"], case["max_iter"])["converged"]
+
+
 def test_golden_chain_is_not_plain_mean():
     # E2: the converged mode 97/48 differs from the mean of the points (2.0);
     # an implementation that merged everything at once would return 2.0.
