@@ -38,6 +38,8 @@ MUTANTS = {
     # clusters numbered by ascending key
     "descending_labels": ("    if (a[i] < b[i]) return -1;\n    if (a[i] > b[i]) return 1;",
                           "    if (a[i] < b[i]) return 1;\n    if (a[i] > b[i]) return -1;"),
+    # max_iter counts applied updates
+    "step_limit_off_by_one": ("if (t == max_iter) break;", "if (t > max_iter) break;"),
     # the mode divides the sum by the count
     "mode_off_by_one_count": ("modes[c * d + a] = cs[c * d + a] / (double)cc[c];",
                               "modes[c * d + a] = cs[c * d + a] / (double)(cc[c] + 1);"),
