@@ -40,6 +40,10 @@ MUTANTS = {
                           "    if (a[i] < b[i]) return 1;\n    if (a[i] > b[i]) return -1;"),
     # max_iter counts applied updates
     "step_limit_off_by_one": ("if (t == max_iter) break;", "if (t > max_iter) break;"),
+    # tracking window step (Algorithm 2): R's position sums, extent, membership
+    "track_sum_y_of_x": ("      sy += y;", "      sy += x;"),
+    "track_min_x_as_max": ("if (x < mnx) mnx = x;", "if (x > mnx) mnx = x;"),
+    "track_first_bin_always": ("        if (same) {", "        if (same || j == 0) {"),
     # the mode divides the sum by the count
     "mode_off_by_one_count": ("modes[c * d + a] = cs[c * d + a] / (double)cc[c];",
                               "modes[c * d + a] = cs[c * d + a] / (double)(cc[c] + 1);"),
