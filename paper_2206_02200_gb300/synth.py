@@ -23,6 +23,7 @@ __all__ = [
     "image_features",
     "gmm_points",
     "image_batch",
+    "image_batch_item",
     "moving_object_frames",
     "WORKLOADS",
 ]
@@ -152,15 +153,20 @@ def image_batch(count: int, seed0: int, hmin: int = 240, hmax: int = 1080, wmin:
     Image i uses seed ``seed0 + i``: its height, width and region count are
     drawn uniformly (inclusive) from that seed's stream, then the image itself.
     """
-    out = []
-    for i in range(count):
-        rng = np.random.default_rng(seed0 + i)
-        H = int(rng.integers(hmin, hmax + 1))
-        W = int(rng.integers(wmin, wmax + 1))
-        R = int(rng.integers(rmin, rmax + 1))
-        img = voronoi_image(H, W, R, sigma, seed=seed0 + i + 7919 * (i + 1))
-        out.append(image_features(img))
-    return out
+    return [image_batch_item(i, seed0, hmin, hmax, wmin, wmax, rmin, rmax, sigma)
+            for i in range(count)]
+
+
+def image_batch_item(i: int, seed0: int, hmin: int = 240, hmax: int = 1080, wmin: int = 320,
+                     wmax: int = 1920, rmin: int = 8, rmax: int = 60,
+                     sigma: float = 8.0) -> np.ndarray:
+    """Instance i of ``image_batch(count, seed0, ...)`` alone (any count > i)."""
+    rng = np.random.default_rng(seed0 + i)
+    H = int(rng.integers(hmin, hmax + 1))
+    W = int(rng.integers(wmin, wmax + 1))
+    R = int(rng.integers(rmin, rmax + 1))
+    img = voronoi_image(H, W, R, sigma, seed=seed0 + i + 7919 * (i + 1))
+    return image_features(img)
 
 
 def _cfg_image_small():
@@ -189,12 +195,22 @@ def _cfg_batch64():
     return dict(parts=parts, h=16.0, max_iter=50, name="voronoi_batch64_uneven_d3_h16")
 
 
+def _cfg_sweep():
+    # the 321x481 image over a range of bandwidths (the paper's bandwidth
+    # study, Sec. 4.1, gives no values: eight from 8 to 32 here)
+    return dict(points=image_features(voronoi_image(321, 481, 12, 8.0, seed=1)),
+                hs=[8.0, 10.0, 12.0, 14.0, 16.0, 20.0, 24.0, 32.0], h=8.0, max_iter=50,
+                name="voronoi_321x481_d3_sweep8_h8-32")
+
+
 #: name -> zero-argument builder returning dict(points, h, max_iter, name);
-#: batched workloads give dict(parts=[...], h, max_iter, name) instead
+#: batched workloads give dict(parts=[...], h, max_iter, name) instead, and
+#: bandwidth sweeps dict(points, hs=[...], h, max_iter, name)
 WORKLOADS = {
     "image_321x481_d3": _cfg_image_small,
     "image_1080p_d5": _cfg_1080p,
     "image_4k_d5": _cfg_4k,
     "gmm_10M_d6": _cfg_gmm,
     "batch_64_d3": _cfg_batch64,
+    "sweep_321x481_d3": _cfg_sweep,
 }
