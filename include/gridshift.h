@@ -205,6 +205,36 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
                          int B, int32_t* labels, double* modes, int64_t modes_cap,
                          int64_t* mode_offsets, gs_fit_info* infos);
 
+/* Runs GridShift on one point set for B bandwidths h_0 .. h_{B-1} in one
+ * call: instance b is the run gs_fit gives for the same points with h = hs[b]
+ * (Sec. 2.1; the bandwidth study of Sec. 4.1 runs the method over a range of
+ * h on the same data).  The context's d and max_iter apply, its h does not.
+ *   points        device, n x d row-major, dtype as given (shared by all B runs)
+ *   n             points, 0 <= n, B * n < 2^31
+ *   hs            host float64[B]: the bandwidths, each finite and > 0 (repeats allowed)
+ *   B             1 <= B <= 2^20
+ *   labels        device int32[B * n]: labels[b * n + i] = cluster of point i
+ *                 under h = hs[b], numbered 0 .. k_b - 1 within instance b (output)
+ *   modes         device float64[modes_cap x d]: the modes of instance 0, then
+ *                 of instance 1, ... (output)
+ *   modes_cap     rows available in modes
+ *   mode_offsets  host int64[B + 1]: instance b's modes are rows
+ *                 mode_offsets[b] .. mode_offsets[b + 1] - 1 (output)
+ *   infos         host gs_fit_info[B]: per-instance statistics, as gs_fit_batched
+ * All B runs go through one pass of the batched pipeline (one launch of each
+ * kernel): every instance decides its cells with its own h against its own
+ * exact cell faces, and the instances share the packed-key layout.  The
+ * plans are made on the host after the key-range pass (one extra round
+ * trip).  GS_FP64 and GS_UPDATE_PARALLEL only (other settings return
+ * GS_E_INVALID).  If the total number of clusters exceeds modes_cap, returns
+ * GS_E_CAPACITY with labels, mode_offsets and infos filled.  Returns GS_OK,
+ * GS_E_INVALID, GS_E_NOMEM, GS_E_KEYRANGE (the key fields of the smallest h
+ * and the instance index do not fit 63 bits together), GS_E_CAPACITY,
+ * GS_E_CUDA or GS_E_INTERNAL. */
+gs_status gs_fit_sweep(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n,
+                       const double* hs, int B, int32_t* labels, double* modes,
+                       int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos);
+
 /* Turns per-phase device timing of later gs_fit calls on (enable != 0) or
  * off.  When on, each call records CUDA events on its stream around each
  * launch group and reads their elapsed times after its final synchronisation;
@@ -232,9 +262,12 @@ gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
  * process exits.  The call allocates no device or pinned host memory and calls
  * no allocating CUDA routine.
  *
- * Set-up: the first call on a device looks up the device address of the
- * static array (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.
+ * Set-up: every call, the first one on a device included, looks up the
+ * device address of the static array (cudaGetSymbolAddress) in the context
+ * current on the calling thread, so a call after a device reset, or from
+ * another context on the same device, finds the array where it now is.  The
+ * first call on a device also loads the library's kernels there: make it
+ * before any stream capture.
  *
  * Limits: the per-point arrays (cell slot and counting-sort position) take
  * 8 bytes per point and 1 MiB is kept for the rest, so n <= 8,257,536; the

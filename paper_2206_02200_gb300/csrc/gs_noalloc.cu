@@ -16,16 +16,17 @@ namespace {
 
 // The static scratch.  Every GPU that loads this library holds it until the
 // process exits.  Host code must not use the symbol itself as a device
-// address: the address is obtained once per device with cudaGetSymbolAddress.
+// address: every call obtains the address with cudaGetSymbolAddress, with the
+// calling device current.  The address belongs to the context that is current
+// then; it is not kept between calls, because a device reset (or another
+// context made current on the same device) moves the array.
 constexpr size_t kScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
 constexpr size_t kThrMax = 8192;   // face-table entries (sum over axes of span + 1)
 constexpr size_t kProbeMax = 6561; // 3^8 neighbour offsets
 
 std::mutex g_mu;  // serialises calls: they share g_scratch and the host buffers below
-unsigned char* g_dev_ptr[kMaxDevices] = {};
 int64_t g_words[kThrMax + 2 * kProbeMax];
 DevFlags g_hflags;
 LoopResult g_hres;
@@ -173,6 +174,7 @@ struct StaticWorkspace : public Workspace {
   void mark_dirty(bool) override {}
   void note_cells(uint32_t) override {}
   gs_status shift_rows(uint32_t, int, Bufs&, std::string*) override { return GS_E_INVALID; }
+  gs_status sweep_space(int, Bufs&, std::string*) override { return GS_E_INVALID; }
 };
 
 }  // namespace
@@ -200,15 +202,10 @@ extern "C" gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_st
   if ((size_t)n * 2 * sizeof(uint32_t) + (size_t(1) << 20) > kScratchBytes) return GS_E_SCRATCH;
 
   std::lock_guard<std::mutex> lock(g_mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return GS_E_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return GS_E_CUDA;
-  if (!g_dev_ptr[dev]) {
-    // set-up on this device, once: the device address of the static scratch
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return GS_E_CUDA;
-    g_dev_ptr[dev] = static_cast<unsigned char*>(p);
-  }
+  // set-up, on every call: the device address of the static scratch in the
+  // context current on this thread (a lookup; nothing is allocated)
+  void* scratch = nullptr;
+  if (cudaGetSymbolAddress(&scratch, g_scratch) != cudaSuccess || !scratch) return GS_E_CUDA;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   FitArgs a;
   a.d = d;
@@ -221,7 +218,7 @@ extern "C" gs_status gs_fit_noalloc(int d, double h, int max_iter, void* cuda_st
   a.labels = labels;
   a.modes = modes;
   a.modes_cap = modes_cap;
-  StaticWorkspace ws(g_dev_ptr[dev]);
+  StaticWorkspace ws(static_cast<unsigned char*>(scratch));
   gs_status st = fit_pipeline(a, ws, nullptr, k_out, &inf, nullptr, nullptr);
   // no work of this call may still run when the next one reuses the scratch
   if (st != GS_OK) cudaStreamSynchronize(s);

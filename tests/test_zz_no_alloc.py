@@ -12,6 +12,7 @@ from __future__ import annotations
 import numpy as np
 import pytest
 
+from oracle import oracle
 from paper_2206_02200_gb300 import gridshift, synth
 
 pytestmark = pytest.mark.gpu
@@ -67,7 +68,11 @@ def test_noalloc_matches_gs_fit_twice_in_a_row():
         modes = torch.zeros((4096, X.shape[1]), dtype=torch.float64, device=dev)
         st, k, info = _fit_noalloc(pts, h, 50, labels, modes, dev)
         assert st == gridshift.GS_OK, gridshift.gs_status_string(st)
-        _check(ref, (labels.cpu().numpy(), modes.cpu().numpy(), k, info), h)
+        got = (labels.cpu().numpy(), modes.cpu().numpy(), k, info)
+        _check(ref, got, h)
+        # and directly against the oracle, bit for bit
+        o = oracle.fit(X, h, 50)
+        _check((o["labels"], o["modes"], {"k": o["k"], "iterations": o["iterations"]}), got, h)
     # and the first input again, after the second
     X, h = cases[0]
     pts = torch.from_numpy(X).to(dev)
