@@ -32,7 +32,20 @@ if ROOT not in sys.path:
 METRIC = "Mpixels/s end-to-end (1080p/4K, d=3/5), FP32 vs FP64, at stated label agreement"
 UNIT = "Mpixels/s"
 
-# Bytes each unit of work must move through DRAM (algorithmic, not measured):
+# Bytes each unit of work must move (algorithmic, not measured), two counts.
+#
+# The scope count (what the method must touch, counted in 32-byte sectors;
+# the roofline's `achieved`):
+#   per point: its cell slot written by binning and read back, and its label
+#     written (3 x 4 B; the coordinates are binning's, below);
+#   per active cell and update step (the stop test's step included, which
+#     probes too): one 32-byte key sector for each of the 3^d neighbour probes
+#     (Eq. 1), two payload sectors (the cell's own row and one neighbour row),
+#     the new centroid and key written (d x elem + 8 B), and the merge (a
+#     radix sort of 4 passes over 12-byte (key, id) pairs, 48 B, plus a
+#     segmented reduction reading and writing the payload, 2 x (4 + d x elem) B).
+#
+# The DRAM count (what must leave the chip when the level tables stay in L2):
 #   k_bin (binning, first pass): per point, read its d coordinates and write
 #     its cell slot (4 B).
 #   k_loop (everything after): per point, read its d coordinates again for the
@@ -47,8 +60,21 @@ def bin_bytes_per_point(d: int, elem: int) -> int:
 
 
 def loop_bytes(n: int, d: int, elem: int, cell_steps: int, fp32: bool) -> int:
+    """The DRAM count of k_loop per launch."""
     row = (4 if fp32 else 16) * (d + 1)
     return n * (d * elem + 24) + cell_steps * (2 * row + 8)
+
+
+def scope_bytes_per_cell_step(d: int, fp32: bool) -> int:
+    """The scope count per active cell and update step."""
+    e = 4 if fp32 else 8
+    return 3 ** d * 32 + 2 * 32 + (d * e + 8) + 48 + 2 * (4 + d * e)
+
+
+def loop_scope_bytes(n: int, d: int, probe_cell_steps: int, fp32: bool) -> int:
+    """The scope count of k_loop per launch (probe_cell_steps = active cells
+    summed over every update step that probed, the stop test's included)."""
+    return n * 12 + probe_cell_steps * scope_bytes_per_cell_step(d, fp32)
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -194,6 +220,9 @@ def workload_config(w: dict, name: str, precision: str = "fp64", update: str = "
            "generator": gen + " (paper_2206_02200_gb300.synth)"}
     if "parts" in w:
         cfg["instances"] = len(w["parts"])
+    if "hs" in w:
+        cfg["hs"] = list(w["hs"])
+        cfg["instances"] = len(w["hs"])
     return cfg
 
 
@@ -211,79 +240,155 @@ def _oracle_sample(w: dict):
     return out
 
 
+def host_cores() -> int:
+    """Cores this process may run on (the host's, unless restricted)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(paths, hs, it, update, cmd_q, done_q):
+    """One oracle process: loads its copy of the sample, then runs the oracle
+    once over it (for every bandwidth in hs) per command until told to stop."""
+    import numpy as np
+    from oracle import oracle
+    sample = [np.load(p) for p in paths]
+    oracle.lib()
+    done_q.put(("ready", 0.0))
+    while True:
+        c = cmd_q.get()
+        if c is None:
+            return
+        t0 = time.perf_counter()
+        for X in sample:
+            for h in hs:
+                oracle.fit(X, h, it, update=update)
+        done_q.put(("done", time.perf_counter() - t0))
+
+
+class OracleWorkers:
+    """P spawn-method processes, each running the oracle (as it stands,
+    single-threaded) on its own copy of the sample: one step = every process
+    runs the sample once, timed by wall clock from the command to the last
+    completion.  The oracle is not parallelised; the host's cores run P
+    independent copies of it (spawn, so no process inherits a CUDA context)."""
+
+    def __init__(self, sample, hs, it, update="parallel", procs=None):
+        import multiprocessing
+        import tempfile
+
+        import numpy as np
+        from oracle import oracle
+        oracle.build()
+        self.procs = procs or host_cores()
+        self.tmp = tempfile.mkdtemp(prefix="gs_oracle_sample_")
+        paths = []
+        for i, X in enumerate(sample):
+            pth = os.path.join(self.tmp, f"part{i}.npy")
+            np.save(pth, np.ascontiguousarray(X))
+            paths.append(pth)
+        ctx = multiprocessing.get_context("spawn")
+        self.cmd = [ctx.Queue() for _ in range(self.procs)]
+        self.done = ctx.Queue()
+        self.ps = [ctx.Process(target=_oracle_worker, args=(paths, hs, it, update, q, self.done),
+                               daemon=True) for q in self.cmd]
+        for pr in self.ps:
+            pr.start()
+        for _ in self.ps:
+            self.done.get(timeout=600)
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        for q in self.cmd:
+            q.put(1)
+        for _ in self.ps:
+            self.done.get(timeout=3600)
+        return time.perf_counter() - t0
+
+    def close(self):
+        import shutil
+        for q in self.cmd:
+            q.put(None)
+        for pr in self.ps:
+            pr.join(timeout=30)
+            if pr.is_alive():
+                pr.terminate()
+        shutil.rmtree(self.tmp, ignore_errors=True)
+
+
 def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8,
                  update: str = "parallel") -> dict:
-    """Times the CPU oracle (single-threaded, as it stands) on the same workload."""
+    """Times the CPU oracle (as it stands) on the same workload: single-threaded
+    (a bounded number of full runs of the sample), and on all the host's cores
+    as independent copies (two steps of OracleWorkers).  The all-core figure is
+    the line's value; the single-core one is nested."""
     from oracle import oracle
     oracle.build()
     sample = _oracle_sample(w)
-    h, it = w["h"], w["max_iter"]
-    n = sum(len(X) for X in sample)
+    hs, it = w.get("hs", [w["h"]]), w["max_iter"]
+    n = sum(len(X) for X in sample) * len(hs)
     runs, total = 0, 0.0
     while runs < max_runs and (runs == 0 or total < budget_s):
         t0 = time.perf_counter()
         for X in sample:
-            oracle.fit(X, h, it, update=update)
+            for h in hs:
+                oracle.fit(X, h, it, update=update)
         total += time.perf_counter() - t0
         runs += 1
     what = "the workload" if "parts" not in w else f"the first {len(sample)} instances"
-    return {"value": n * runs / total / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full runs of {what} ({n} points each), {total:.1f} s"}
+    single = {"value": n * runs / total / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{runs} full runs of {what} ({n} points each), {total:.1f} s"}
+    ow = OracleWorkers(sample, hs, it, update)
+    try:
+        ts = [ow.step() for _ in range(2)]
+    finally:
+        ow.close()
+    P = ow.procs
+    return {"value": n * P * len(ts) / sum(ts) / 1e6, "unit": UNIT, "cores": P, "kind": "oracle",
+            "nproc": host_cores(),
+            "sample": (f"{len(ts)} steps of {P} independent single-threaded oracle processes, "
+                       f"each running {what} ({n} points) once per step, {sum(ts):.1f} s"),
+            "single_core": single}
 
 
 def run_reference(args, rank: int, world: int):
+    """The reference arm: the oracle as it stands, as P independent
+    single-threaded processes over the host's cores; one step = each process
+    runs the sample once."""
     if rank != 0:
         return 0
     w = load_workload(args.workload)
-    from oracle import oracle
-    oracle.build()
     sample = _oracle_sample(w)
-    h, it = w["h"], w["max_iter"]
-    n = sum(len(X) for X in sample)
-    for _ in range(args.warmup):
-        for X in sample:
-            oracle.fit(X, h, it, update=args.update)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for X in sample:
-            oracle.fit(X, h, it, update=args.update)
-        times.append(time.perf_counter() - t0)
+    hs, it = w.get("hs", [w["h"]]), w["max_iter"]
+    n = sum(len(X) for X in sample) * len(hs)
+    ow = OracleWorkers(sample, hs, it, args.update)
+    try:
+        for _ in range(args.warmup):
+            ow.step()
+        times = [ow.step() for _ in range(args.steps)]
+    finally:
+        ow.close()
+    P = ow.procs
     total = sum(times)
-    value = n * args.steps / total / 1e6
+    value = n * P * args.steps / total / 1e6
     what = "the workload" if "parts" not in w else f"the first {len(sample)} instances"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * total / args.steps,
+            "median_ms_per_step": 1e3 * statistics.median(times) if times else None,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, args.workload, update=args.update),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full runs of {what} ({n} points each)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+                             "nproc": host_cores(),
+                             "sample": (f"{args.steps} steps of {P} independent single-threaded "
+                                        f"oracle processes, each running {what} ({n} points) "
+                                        f"once per step")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-def _agreement(lab, ref_lab, modes, ref_modes, h) -> tuple:
-    """Fraction of points in the best-overlapping reference cluster, and the
-    largest mode distance (units of h) over mutually best cluster pairs."""
-    import numpy as np
-    if lab.size == 0:
-        return 1.0, 0.0
-    pairs, counts = np.unique(np.stack([lab, ref_lab], 1), axis=0, return_counts=True)
-    best, rbest = {}, {}
-    for (a, b), c in zip(pairs.tolist(), counts.tolist()):
-        if c > best.get(a, (None, -1))[1]:
-            best[a] = (b, c)
-        if c > rbest.get(b, (None, -1))[1]:
-            rbest[b] = (a, c)
-    agree = sum(c for _, c in best.values()) / lab.size
-    err = 0.0
-    for a, (b, _) in best.items():
-        if rbest[b][0] == a:
-            err = max(err, float(np.max(np.abs(modes[a] - ref_modes[b]))) / h)
-    return agree, err
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -350,6 +455,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     launches = 0
     cell_iters = 0
     m0_total = 0
+    k_total = 0
     vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     clocks = ClockSampler(vis[local_rank] if local_rank < len(vis) else local_rank)
     barrier()
@@ -362,6 +468,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         launches += infos[0]["launches"]
         cell_iters += sum(x["cell_iters"] for x in infos)
         m0_total += sum(x["m0"] for x in infos)
+        k_total += sum(x["k"] for x in infos)
         if not batched:
             for p, (ms, c) in g.phase_times().items():
                 phase_ms[p] += ms
@@ -369,7 +476,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     barrier()
     clk = clocks.stop()
     g.set_timing(False)
-    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    median_ms = max_over_ranks(statistics.median(step_ms), world, dev)
     value = job_rate(n, args.steps, world, total_ms / 1e3)
 
     # -- agreement of the float32 path with the FP64 path (which the tests
@@ -385,22 +494,28 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         k64, infos64 = call(pts, lab64, md64, g64)
         torch.cuda.synchronize(dev)
         l64, m64 = lab64.cpu().numpy(), md64[:k64].cpu().numpy()
+        from paper_2206_02200_gb300 import agreement as agm
         if batched:
-            agree_n, err = 0.0, 0.0
+            agree_n, err, k32, k64, worst = 0.0, 0.0, 0, 0, 1.0
             mo32 = np.concatenate([[0], np.cumsum([x["k"] for x in infos])])
             mo64 = np.concatenate([[0], np.cumsum([x["k"] for x in infos64])])
             for b in range(len(offsets) - 1):
                 s0, s1 = offsets[b], offsets[b + 1]
-                a_b, e_b = _agreement(lab32[s0:s1], l64[s0:s1], md32[mo32[b]:mo32[b + 1]],
-                                      m64[mo64[b]:mo64[b + 1]], w["h"])
-                agree_n += a_b * (s1 - s0)
-                err = max(err, e_b)
-            agree = agree_n / n
+                ab = agm.agreement(lab32[s0:s1], l64[s0:s1], md32[mo32[b]:mo32[b + 1]],
+                                   m64[mo64[b]:mo64[b + 1]], w["h"])
+                agree_n += ab["labels"] * (s1 - s0)
+                worst = min(worst, ab["labels"])
+                err = max(err, ab["max_mode_error_h"])
+                k32 += ab["k"]
+                k64 += ab["k_ref"]
+            ag = {"labels": agree_n / n, "worst_instance_labels": worst,
+                  "max_mode_error_h": err, "k": k32, "k_ref": k64}
         else:
-            agree, err = _agreement(lab32, l64, md32, m64, w["h"])
-        agreement = {"labels": agree, "max_mode_error_h": err,
-                     "face_rechecks_per_step": sum(x["face_rechecks"] for x in infos),
-                     "against": "FP64 GPU path (bit-identical to the FP64 oracle in the tests)"}
+            ag = agm.agreement(lab32, l64, md32, m64, w["h"])
+            ag.pop("matched", None)
+        agreement = dict(ag, metric="clusters matched one to one, greedily by overlap",
+                         face_rechecks_per_step=sum(x["face_rechecks"] for x in infos),
+                         against="FP64 GPU path (bit-identical to the FP64 oracle in the tests)")
         g64.close()
 
     # -- sequential plain calls beside the batched one
@@ -450,17 +565,28 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if not batched:
         loop_ms = phase_ms["loop"] / max(phase_cnt["loop"], 1)
         cell_steps = (cell_iters + m0_total) // args.steps
+        probe_steps = (cell_iters + k_total) // args.steps
         lb = loop_bytes(n, d, elem, cell_steps, fp32)
-        achieved = lb / (loop_ms / 1e3) / 1e9
+        sb = loop_scope_bytes(n, d, probe_steps, fp32)
+        achieved = sb / (loop_ms / 1e3) / 1e9
         bin_ms = phase_ms["bin"] / max(phase_cnt["bin"], 1)
         bb = n * bin_bytes_per_point(d, elem)
+        tr = traffic(args.workload, args.precision, "k_loop", args.update)
         roof = {"kernel": "k_loop (exact cell sums, update steps ii-v, labels)", "bound": "hbm",
                 "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
                 "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs)",
                 "frac_of": pk["source"],
-                "algorithmic_bytes_per_launch": lb, "avg_launch_ms": loop_ms,
-                "traffic": traffic(args.workload, args.precision, "k_loop", args.update),
+                "algorithmic_bytes_per_launch": sb,
+                "algorithmic_count": ("scope count: 12 B per point; per active cell and "
+                                      "update step 3^d key sectors of 32 B, 2 payload "
+                                      "sectors, centroid and key write, sort-and-reduce "
+                                      "merge"),
+                "avg_launch_ms": loop_ms, "traffic": tr,
+                "dram_count": {"bytes_per_launch": lb,
+                               "achieved": lb / (loop_ms / 1e3) / 1e9,
+                               "frac": lb / (loop_ms / 1e3) / 1e9 / pk["hbm_gbs"]},
+                "traffic_frac": (tr / (loop_ms / 1e3) / 1e9 / pk["hbm_gbs"]) if tr else None,
                 "second": {"kernel": "k_bin (binning, first pass)", "achieved": bb / (bin_ms / 1e3) / 1e9,
                            "frac": bb / (bin_ms / 1e3) / 1e9 / pk["hbm_gbs"],
                            "algorithmic_bytes_per_launch": bb, "avg_launch_ms": bin_ms,
@@ -470,7 +596,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": max(args.warmup, 3),
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "ms_per_step": total_ms / args.steps, "median_ms_per_step": median_ms,
+                "value_at_median": job_rate(n, 1, world, median_ms / 1e3),
+                "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
                 "data": "synthetic",
                 "config": workload_config(w, args.workload, args.precision, args.update),
@@ -579,6 +707,124 @@ def run_track(args) -> int:
     return 0
 
 
+def run_sweep(args) -> int:
+    """A bandwidth sweep: one step = one gs_fit_sweep call over every h of the
+    workload (the same points, B instances in one pass of the batched
+    pipeline); beside it, the same B runs as B separate gs_fit calls.  Units:
+    pixel-bandwidth pairs (B x n per step)."""
+    import numpy as np
+    import torch
+
+    from paper_2206_02200_gb300 import gridshift
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = load_workload(args.workload)
+    X, hs = w["points"], list(w["hs"])
+    n, d = X.shape
+    B = len(hs)
+    pts = torch.from_numpy(X).to(dev)
+    labels = torch.empty((B, n), dtype=torch.int32, device=dev)
+    modes = torch.empty((65536, d), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    g = gridshift.GridShift(d, hs[0], w["max_iter"])
+    gridshift.gs_set_stream(g._ctx, stream.cuda_stream)
+    dt = gridshift.GS_IN_F64 if X.dtype == np.float64 else gridshift.GS_IN_F32
+
+    def sweep_call(p=pts):
+        st, mo, infos = gridshift.gs_fit_sweep(g._ctx, p.data_ptr(), dt, n, hs, labels.data_ptr(),
+                                               modes.data_ptr(), modes.shape[0])
+        if st != gridshift.GS_OK:
+            raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(g._ctx))
+        return mo, [x.as_dict() for x in infos]
+
+    singles = []
+    for h in hs:
+        gg = gridshift.GridShift(d, h, w["max_iter"])
+        gridshift.gs_set_stream(gg._ctx, stream.cuda_stream)
+        singles.append(gg)
+
+    def separate_calls():
+        for b, gg in enumerate(singles):
+            st, k, info = gridshift.gs_fit(gg._ctx, pts.data_ptr(), dt, n, labels[b].data_ptr(),
+                                           modes.data_ptr(), modes.shape[0])
+            if st != gridshift.GS_OK:
+                raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gg._ctx))
+
+    for _ in range(max(args.warmup, 3)):
+        sweep_call()
+        separate_calls()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev, ev_sep = [], []
+    launches = 0
+    cell_iters = 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mo, infos = sweep_call()
+        b.record(stream)
+        ev.append((a, b))
+        launches += infos[0]["launches"]
+        cell_iters += sum(x["cell_iters"] for x in infos)
+        flush.fill_(2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        separate_calls()
+        b.record(stream)
+        ev_sep.append((a, b))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    sep_ms = [a.elapsed_time(b) for a, b in ev_sep]
+    total_ms = sum(step_ms)
+    value = job_rate(n * B, args.steps, 1, total_ms / 1e3)
+    # end to end: the points from pinned host memory, labels and modes back
+    h_pts = torch.from_numpy(X).pin_memory()
+    h_labels = torch.empty((B, n), dtype=torch.int32).pin_memory()
+    h_modes = torch.empty(modes.shape, dtype=torch.float64).pin_memory()
+    d_pts = torch.empty_like(pts)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    kk = 0
+    for _ in range(args.steps):
+        d_pts.copy_(h_pts, non_blocking=True)
+        mo, _ = sweep_call(d_pts)
+        kk = mo[-1]
+        h_labels.copy_(labels, non_blocking=True)
+        h_modes[:kk].copy_(modes[:kk], non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    line = {"metric": "Mpixels/s of a bandwidth sweep (pixel-bandwidth pairs), one call vs "
+                      "separate calls", "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": total_ms / args.steps,
+            "median_ms_per_step": statistics.median(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args.workload),
+            "e2e": {"value": job_rate(n * B, args.steps, 1, e2e_s), "unit": UNIT,
+                    "h2d_bytes_per_step": int(X.nbytes),
+                    "d2h_bytes_per_step": int(B * n * 4 + kk * d * 8)},
+            "gpu_launches": int(launches),
+            "separate_calls": {"what": f"{B} gs_fit calls, one per h",
+                               "ms_per_step": sum(sep_ms) / args.steps,
+                               "value": job_rate(n * B, args.steps, 1, sum(sep_ms) / 1e3),
+                               "unit": UNIT},
+            "k_per_h": [x["k"] for x in infos], "iterations_per_h": [x["iterations"] for x in infos],
+            "active_cell_iterations_per_s": cell_iters / (total_ms / 1e3),
+            "roofline": None, "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    for gg in singles:
+        gg.close()
+    g.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,7 +839,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.update == "sequential" and (args.precision != "fp64" or
-                                        args.workload.startswith(("batch", "track"))):
+                                        args.workload.startswith(("batch", "track", "sweep"))):
         ap.error("--update sequential runs in fp64 on workloads of one point set")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -602,6 +848,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "track_1080p_d3":
         return run_track(args)
+    if args.workload.startswith("sweep"):
+        return run_sweep(args)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -215,6 +215,7 @@ struct CtxWorkspace : public Workspace {
   DBuf<int64_t> offsets;
   DBuf<uint32_t> inst;
   DBuf<ulonglong2> srow;          // the sequential update's shifted rows
+  DBuf<SweepPlan> sweep;          // a bandwidth sweep's per-instance cell decisions
   std::vector<uint64_t> h_inst;   // host copy of the per-instance state (8-byte aligned)
 
   DevFlags* h_flags = nullptr;    // pinned
@@ -394,6 +395,12 @@ struct CtxWorkspace : public Workspace {
     b.srow = srow.p;
     return GS_OK;
   }
+  gs_status sweep_space(int B, Bufs& b, std::string* err) override {
+    cudaError_t e;
+    WS_CU(sweep.ensure((size_t)B), "alloc sweep plans");
+    b.sweep = sweep.p;
+    return GS_OK;
+  }
 #undef WS_CU
 
   void mark_dirty(bool d) override { dirty = d; }
@@ -409,7 +416,7 @@ struct CtxWorkspace : public Workspace {
     }
     qlist.release(); ptab.release(); forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
-    offsets.release(); inst.release(); srow.release();
+    offsets.release(); inst.release(); srow.release(); sweep.release();
     if (h_flags) cudaFreeHost(h_flags);
     if (h_res) cudaFreeHost(h_res);
     if (h_words) cudaFreeHost(h_words);
@@ -802,6 +809,70 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   a.offsets = offsets;
   a.infos = infos;
   a.mode_offsets = mode_offsets;
+  gs_fit_info total;
+  std::memset(&total, 0, sizeof(total));
+  int64_t k = 0;
+  return fit_pipeline(a, ctx->ws, nullptr, &k, &total, nullptr, &ctx->err);
+}
+
+gs_status gs_fit_sweep(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n,
+                       const double* hs, int B, int32_t* labels, double* modes,
+                       int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos) {
+  if (!ctx) return GS_E_INVALID;
+  ctx->err.clear();
+  if (!hs || !mode_offsets || !infos) return fail(ctx, GS_E_INVALID, "NULL hs, mode_offsets or infos");
+  if (B < 1 || B > kMaxBatch) return fail(ctx, GS_E_INVALID, "B out of range");
+  for (int i = 0; i < B; ++i)
+    if (!(hs[i] > 0) || !std::isfinite(hs[i])) return fail(ctx, GS_E_INVALID, "h not finite and > 0");
+  if (n < 0 || n * (int64_t)B >= (1ll << 31)) return fail(ctx, GS_E_INVALID, "B x n out of range");
+  if (dtype != GS_IN_F64 && dtype != GS_IN_F32) return fail(ctx, GS_E_INVALID, "bad dtype");
+  if (modes_cap < 0 || (modes_cap > 0 && !modes))
+    return fail(ctx, GS_E_INVALID, "modes is NULL with modes_cap > 0");
+  if (n > 0 && (!points || !labels)) return fail(ctx, GS_E_INVALID, "NULL points or labels");
+  if (ctx->prec != GS_FP64 || ctx->update != GS_UPDATE_PARALLEL)
+    return fail(ctx, GS_E_INVALID, "a bandwidth sweep runs in GS_FP64 with the parallel update");
+  std::memset(infos, 0, sizeof(gs_fit_info) * (size_t)B);
+  for (int i = 0; i <= B; ++i) mode_offsets[i] = 0;
+  ctx->tm.reset();
+  std::memset(&ctx->last_times, 0, sizeof(ctx->last_times));
+  if (n == 0) {
+    for (int i = 0; i < B; ++i) infos[i].converged = 1;
+    return GS_OK;
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(ctx, GS_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorName(ce));
+  if (ctx->device != dev) {
+    ctx->release_device();
+    ctx->device = dev;
+  }
+  FitArgs a;
+  a.d = ctx->d;
+  a.h = hs[0];
+  a.max_iter = ctx->max_iter;
+  a.stream = ctx->stream;
+  a.points = points;
+  a.f32 = dtype == GS_IN_F32;
+  a.labels = labels;
+  a.modes = modes;
+  a.modes_cap = modes_cap;
+  if (B == 1) {
+    // one bandwidth: the plain run with that h
+    a.n = n;
+    int64_t k = 0;
+    gs_status st = fit_pipeline(a, ctx->ws, nullptr, &k, &infos[0], nullptr, &ctx->err);
+    mode_offsets[1] = k;
+    return st;
+  }
+  std::vector<int64_t> offsets((size_t)B + 1);
+  for (int i = 0; i <= B; ++i) offsets[(size_t)i] = (int64_t)i * n;
+  a.n = n * B;
+  a.B = B;
+  a.offsets = offsets.data();
+  a.infos = infos;
+  a.mode_offsets = mode_offsets;
+  a.sweep_h = hs;
+  a.n0 = (uint32_t)n;
   gs_fit_info total;
   std::memset(&total, 0, sizeof(total));
   int64_t k = 0;

@@ -4,6 +4,7 @@
 // update steps ii-v, the labels and the modes.  Buffers come from a Workspace.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "gs_driver.h"
 #include "gs_planner.cuh"
@@ -75,6 +76,93 @@ gs_status plan_fail(std::string* err, uint32_t st) {
     GS_CU(call, where);                 \
     info->launches += (nk);             \
   } while (0)
+// Bandwidth sweep: the plan of every instance from the key range of the
+// shared points, made on the host (one round trip after k_range).  Each
+// instance decides floor(x / h_b) against its own faces (SweepPlan); the
+// packed-key layout is shared, each axis field as wide as the largest span,
+// so the neighbour offsets are too.  The fixed-point units depend only on the
+// points and on n0 (every sum of an instance has at most n0 terms), so they
+// are shared as well.  Lays out the workspace, uploads the face tables, the
+// offsets and the per-instance plans, and clears the loop kernel's start
+// state (which k_plan clears in other runs).
+static gs_status sweep_prepare(const FitArgs& a, Workspace& ws, Bufs& b, DevFlags* hf,
+                               int nprobe, gs_fit_info* info, std::string* err) {
+  const int d = a.d, B = a.B;
+  const cudaStream_t s = a.stream;
+  GS_LAUNCH(launch_range(a.points, a.f32, (int64_t)a.n0, d, b.flags, s), "k_range", 1);
+  GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
+  GS_CU(cudaStreamSynchronize(s), "sync key range");
+  if (hf->bad) return plan_fail(err, kPlanNonFinite);
+  std::vector<SweepPlan> sp((size_t)B);
+  Plan P;
+  std::memset(&P, 0, sizeof(P));
+  uint64_t thr_words = 0;
+  for (int i = 0; i < B; ++i) {
+    Plan Pi;
+    std::memset(&Pi, 0, sizeof(Pi));
+    for (int ax = 0; ax < d; ++ax) {
+      const uint32_t st = plan_axis(ax, a.sweep_h[i], (int64_t)a.n0, *hf, Pi);
+      if (st != kPlanOK) return plan_fail(err, st);
+    }
+    SweepPlan& S = sp[(size_t)i];
+    std::memset(&S, 0, sizeof(S));
+    for (int ax = 0; ax < d; ++ax) {
+      S.kmin[ax] = Pi.kmin[ax];
+      S.span[ax] = Pi.span[ax];
+      S.thr_off[ax] = (int)thr_words;
+      thr_words += (uint64_t)Pi.span[ax] + 1;
+      if (Pi.span[ax] > P.span[ax]) P.span[ax] = Pi.span[ax];
+      P.L[ax] = Pi.L[ax];
+    }
+    S.inv_h = (float)(1.0 / a.sweep_h[i]);
+    if (thr_words >= (1ull << 31))
+      return fail(err, GS_E_KEYRANGE, "the sweep's face tables exceed 2^31 entries");
+  }
+  PlanSizes z;
+  const uint32_t st = plan_finish(d, a.sweep_h[0], B, P, z);
+  if (st != kPlanOK) return plan_fail(err, st);
+  // instance 0's decisions in the shared plan (the sweep's kernels use sp)
+  for (int ax = 0; ax < d; ++ax) {
+    P.kmin[ax] = sp[0].kmin[ax];
+    P.thr_off[ax] = sp[0].thr_off[ax];
+  }
+  P.inv_h = sp[0].inv_h;
+  z.thr_words = thr_words;
+  GS_ST(ws.prepare(a.n, d, a.max_iter, thr_words, nprobe, (uint64_t)a.n, s, b, err));
+  GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
+  GS_ST(ws.sweep_space(B, b, err));
+  const size_t plan_words = (sizeof(SweepPlan) * (size_t)B + 7) / 8;
+  int64_t* stage = nullptr;
+  GS_ST(ws.host_words(thr_words + 2 * (size_t)nprobe + plan_words, &stage, err));
+  for (int i = 0; i < B; ++i)
+    for (int ax = 0; ax < d; ++ax)
+      for (int j = 0; j <= sp[(size_t)i].span[ax]; ++j)
+        stage[sp[(size_t)i].thr_off[ax] + j] =
+            plan_ord_of(plan_face(sp[(size_t)i].kmin[ax] + j, a.sweep_h[i]));
+  uint64_t* hd = reinterpret_cast<uint64_t*>(stage + thr_words);
+  uint32_t* hv = reinterpret_cast<uint32_t*>(hd + nprobe);
+  for (int p = 0; p < nprobe; ++p) plan_probe(P, p, hd + p, hv + p);
+  int64_t* hp = stage + thr_words + 2 * (size_t)nprobe;
+  std::memcpy(hp, sp.data(), sizeof(SweepPlan) * (size_t)B);
+  GS_CU(cudaMemcpyAsync(b.thr, stage, sizeof(int64_t) * thr_words, cudaMemcpyHostToDevice, s),
+        "H2D thr");
+  GS_CU(cudaMemcpyAsync(b.dtab, hd, sizeof(uint64_t) * 2 * nprobe, cudaMemcpyHostToDevice, s),
+        "H2D dtab");
+  GS_CU(cudaMemcpyAsync(b.sweep, hp, sizeof(SweepPlan) * (size_t)B, cudaMemcpyHostToDevice, s),
+        "H2D sweep plans");
+  GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s), "memset filters");
+  GS_CU(cudaMemsetAsync(b.res, 0, sizeof(LoopResult), s), "memset result");
+  GS_CU(cudaMemsetAsync(b.st, 0, sizeof(IterState) * (a.max_iter + 2), s), "memset state");
+  GS_CU(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), s), "memset barrier");
+  hf->plan = P;
+  hf->plan_sizes = z;
+  hf->plan_status = kPlanOK;
+  hf->err = 0;
+  hf->m0 = 0;
+  GS_CU(cudaMemcpyAsync(b.flags, hf, sizeof(DevFlags), cudaMemcpyHostToDevice, s), "H2D flags");
+  return GS_OK;
+}
+
 #define GS_T_BEGIN(ph) \
   do { if (timer) GS_CU(timer->begin(ph, s), "cudaEventRecord"); } while (0)
 #define GS_T_END() \
@@ -87,6 +175,9 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   const int64_t n = a.n;
   if (a.sequential && (a.mixed || a.B > 1))
     return fail(err, GS_E_INVALID, "the sequential update runs in GS_FP64 on one point set only");
+  if (a.sweep_h && (a.mixed || a.sequential || a.B < 2 || a.n0 == 0 ||
+                    (int64_t)a.n0 * a.B != a.n))
+    return fail(err, GS_E_INVALID, "a bandwidth sweep runs B > 1 instances of n0 points in GS_FP64");
   Bufs b;
   GS_ST(ws.begin(b, err));
 
@@ -103,13 +194,17 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   const size_t thr_cap = ws.plan_thr_cap();
   int nprobe = 1;
   for (int i = 0; i < d; ++i) nprobe *= 3;
-  GS_ST(ws.prepare(n, d, a.max_iter, thr_cap, nprobe, (uint64_t)n, s, b, err));
-  GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
-  GS_T_BEGIN(GS_PHASE_RANGE);
-  GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, s), "k_range", 1);
-  GS_LAUNCH(launch_plan(d, a.h, n, a.B, b.flags, b.thr, thr_cap, b.dtab, b.filter, b.st,
-                        (uint32_t)(a.max_iter + 2), b.bar, b.res, s), "k_plan", 1);
-  GS_T_END();
+  if (a.sweep_h) {
+    GS_ST(sweep_prepare(a, ws, b, hf, nprobe, info, err));
+  } else {
+    GS_ST(ws.prepare(n, d, a.max_iter, thr_cap, nprobe, (uint64_t)n, s, b, err));
+    GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
+    GS_T_BEGIN(GS_PHASE_RANGE);
+    GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, s), "k_range", 1);
+    GS_LAUNCH(launch_plan(d, a.h, n, a.B, b.flags, b.thr, thr_cap, b.dtab, b.filter, b.st,
+                          (uint32_t)(a.max_iter + 2), b.bar, b.res, s), "k_plan", 1);
+    GS_T_END();
+  }
   uint32_t* hinst = nullptr;
   if (a.B > 1) {
     // batched: instance offsets, cleared per-instance state
@@ -181,10 +276,12 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.B = a.B;
     L.mixed = a.mixed;
     L.srow = a.sequential ? b.srow : nullptr;
+    L.sweep = a.sweep_h ? b.sweep : nullptr;
+    L.n0 = a.sweep_h ? a.n0 : 0;
     if (a.B > 1) L.I = inst_views(b.inst, a.B);
     GS_T_BEGIN(GS_PHASE_BIN);
     GS_LAUNCH(launch_bin(a.points, a.f32, n, d, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells,
-                         b.slot0, b.flags, b.offsets, a.B, s), "k_bin", 1);
+                         b.slot0, b.flags, b.offsets, a.B, L.sweep, L.n0, s), "k_bin", 1);
     GS_T_END();
     GS_T_BEGIN(GS_PHASE_LOOP);
     GS_LAUNCH(a.sequential ? launch_loop_seq(L, grid, s) : launch_loop(L, grid, s), "k_loop", 1);

@@ -46,6 +46,7 @@ struct Bufs {
   uint32_t* sval2 = nullptr;
   uint32_t* shist = nullptr;   // radix_hist_words(k)
   ulonglong2* srow = nullptr;  // sequential update: capAB * d
+  SweepPlan* sweep = nullptr;  // bandwidth sweep: B per-instance cell decisions
 };
 
 // Source of the device buffers and host staging of one run.  Each method
@@ -87,6 +88,9 @@ class Workspace {
   // The sequential update's shifted rows for level tables of `cap` slots
   // (b.srow, cap * d entries), or an error.
   virtual gs_status shift_rows(uint32_t cap, int d, Bufs& b, std::string* err) = 0;
+  // A bandwidth sweep's per-instance cell decisions (b.sweep, B entries), or
+  // an error.
+  virtual gs_status sweep_space(int B, Bufs& b, std::string* err) = 0;
 };
 
 // Optional per-phase CUDA-event timing of a run.
@@ -115,6 +119,11 @@ struct FitArgs {
   const int64_t* offsets = nullptr;
   gs_fit_info* infos = nullptr;
   int64_t* mode_offsets = nullptr;
+  // bandwidth sweep (B > 1): the B values of h (host), one instance per h over
+  // the same n0 points (n = B * n0, offsets[b] = b * n0); GS_FP64, parallel
+  // update
+  const double* sweep_h = nullptr;
+  uint32_t n0 = 0;
 };
 
 // 32-bit words of per-instance state of a batched run of B instances: one

@@ -236,7 +236,8 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kBlock, 6)
     k_bin(const T* __restrict__ pts, int64_t n, const int64_t* __restrict__ thr,
           BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
-          DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B) {
+          DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B,
+          const SweepPlan* __restrict__ sweep, uint32_t n0) {
   __shared__ __align__(16) T s_pts[kWarps][32 * D];
   __shared__ Plan s_plan;
   __shared__ uint32_t s_ok;
@@ -253,11 +254,25 @@ __global__ void __launch_bounds__(kBlock, 6)
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = gwarp * 32; base < n; base += nwarps * 32) {
     const int cnt = n - base < 32 ? (int)(n - base) : 32;
-    stage_points<T>(pts + base * D, cnt * D, s_pts[w], vec_ok, lane);
+    if (!sweep) stage_points<T>(pts + base * D, cnt * D, s_pts[w], vec_ok, lane);
     __syncwarp();
     const bool valid = lane < cnt;
     uint64_t key = kEmpty;
-    if (valid) {
+    if (valid && sweep) {
+      // bandwidth sweep: point j of instance b is row j of pts, its cell
+      // decided with b's bandwidth
+      const int64_t i = base + lane;
+      const uint32_t b = (uint32_t)(i / n0);
+      const T* row = pts + (size_t)(i - (int64_t)b * n0) * D;
+      const SweepPlan* S = sweep + b;
+      key = (uint64_t)b << P.inst_off;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int idx = key_index(thr + __ldg(&S->thr_off[a]), __ldg(&S->span[a]),
+                                  __ldg(&S->kmin[a]), __ldg(&S->inv_h), bits_of(__ldg(row + a)));
+        key |= (uint64_t)(idx + 1) << P.off[a];
+      }
+    } else if (valid) {
       key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << P.inst_off : 0ull;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -362,17 +377,19 @@ cudaError_t launch_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t
 
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
-                       DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s) {
+                       DevFlags* fl, const int64_t* offsets, int B, const SweepPlan* sweep,
+                       uint32_t n0, cudaStream_t s) {
   const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * 6u);
   const bool vec_ok = ((uintptr_t)pts & 15u) == 0;
+  if (sweep && n0 == 0) return cudaErrorInvalidValue;
   if (f32) {
     GS_DISPATCH_D(d, k_bin<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, thr, T0,
                                                             mask0, maxcells, slot0, fl, vec_ok,
-                                                            offsets, B));
+                                                            offsets, B, sweep, n0));
   } else {
     GS_DISPATCH_D(d, k_bin<D, double><<<g, kBlock, 0, s>>>((const double*)pts, n, thr, T0,
                                                              mask0, maxcells, slot0, fl, vec_ok,
-                                                             offsets, B));
+                                                             offsets, B, sweep, n0));
   }
   return cudaGetLastError();
 }

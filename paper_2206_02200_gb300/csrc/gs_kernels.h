@@ -100,6 +100,10 @@ struct LoopArgs {
   bool mixed;             // the float32 mixed-precision variant (GS_FP32_MIXED)
   ulonglong2* srow;       // sequential update (plain FP64 runs): count x new centroid of
                           // every slot of the level tables (capAB x d); null: parallel update
+  const SweepPlan* sweep; // bandwidth sweep (batched FP64 runs): per-instance cell decisions
+                          // (B entries); null otherwise
+  uint32_t n0;            // bandwidth sweep: points per instance (instance b's point j is
+                          // row j of pts); 0 otherwise
 };
 
 // Accumulators of one tracking window step (gs_track_window).
@@ -146,9 +150,12 @@ cudaError_t launch_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t
                         uint64_t thr_cap, uint64_t* dtab, uint32_t* filters, IterState* st,
                         uint32_t n_st, GridBar* bar, LoopResult* res, cudaStream_t s);
 // Binning with the plan in fl->plan (nothing runs unless fl->plan_status is 0).
+// A bandwidth sweep (sweep != null) bins B x n0 points: instance b's point j
+// is row j of pts, decided with sweep[b] (n = B x n0).
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
-                       DevFlags* fl, const int64_t* offsets, int B, cudaStream_t s);
+                       DevFlags* fl, const int64_t* offsets, int B, const SweepPlan* sweep,
+                       uint32_t n0, cudaStream_t s);
 
 // Blocks of the cooperative loop kernel for dimension d on the current device
 // (all co-resident, at most kMaxLoopGrid), or a negative value on error;

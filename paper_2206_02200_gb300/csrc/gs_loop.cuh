@@ -330,12 +330,16 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) s[e] = idx[e] != kNone ? A.slot0[idx[e]] : kNone;
+    // the row of each point (a bandwidth sweep's instances share the points)
+    uint32_t src[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) src[e] = A.n0 && idx[e] != kNone ? idx[e] % A.n0 : idx[e];
     uint64_t raw[E][D];
 #pragma unroll
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)idx[e] * D + a) : 0ull;
+        raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)src[e] * D + a) : 0ull;
     // the cells' ids, loaded while the coordinates are in flight
     uint32_t cid[E];
 #pragma unroll
@@ -706,6 +710,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
       u128 Na = 0;
       int off = 0, span = 1, toff = 0;
       int64_t kmin = 0;
+      float inv_h = g_plan.inv_h;
 #pragma unroll
       for (int a = 0; a < D; ++a)
         if (a == glane) {
@@ -716,8 +721,16 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
           toff = g_plan.thr_off[a];
           kmin = g_plan.kmin[a];
         }
+      if (BT && A.sweep) {
+        // bandwidth sweep: the cell decision of this instance's h
+        const SweepPlan* S = A.sweep + inst;
+        span = __ldg(&S->span[glane]);
+        toff = __ldg(&S->thr_off[glane]);
+        kmin = __ldg(&S->kmin[glane]);
+        inv_h = __ldg(&S->inv_h);
+      }
       const double sv = div_round(Na, Dc, La, inexact);
-      const int idx = key_index(A.thr + toff, span, kmin, g_plan.inv_h, bits_of(sv));
+      const int idx = key_index(A.thr + toff, span, kmin, inv_h, bits_of(sv));
       field = (uint64_t)(idx + 1) << off;
       V = to_fixed(bits_of(sv), La, inexact, werr);
     }

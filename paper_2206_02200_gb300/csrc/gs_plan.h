@@ -30,6 +30,20 @@ struct Plan {
   float h32;                // h rounded to float (the float32 variant)
 };
 
+// The cell decisions of one bandwidth of a bandwidth sweep (gs_fit_sweep):
+// B instances share the points and the packed-key layout (each axis field as
+// wide as the largest span over the bandwidths), and differ in h.  Instance b
+// decides floor(x / h_b) along axis a against its own faces, the span[a] + 1
+// entries at thr_off[a] of the call's face table, for the cell indices
+// kmin[a] .. kmin[a] + span[a] (Sec. 2.1 i with its own h).
+struct SweepPlan {
+  int64_t kmin[kMaxD];
+  int span[kMaxD];
+  int thr_off[kMaxD];
+  float inv_h;  // 1/h_b rounded to float: first guess of a cell index only
+  int pad;
+};
+
 // Device-resident state of one level t (the cells before update step t).
 struct IterState {
   uint32_t m;       // active cells at level t

@@ -36,7 +36,7 @@ GS_UPDATE_SEQUENTIAL = 1
 
 #: every symbol the header declares, in declaration order
 EXPORTS = ("gs_create", "gs_set_precision", "gs_set_update", "gs_set_stream", "gs_fit",
-           "gs_fit_batched",
+           "gs_fit_batched", "gs_fit_sweep",
            "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_track_window",
            "gs_get_last_error", "gs_status_string", "gs_destroy")
 
@@ -113,6 +113,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.gs_fit_batched.restype = i32
     L.gs_fit_batched.argtypes = [vp, vp, i32, ctypes.POINTER(i64), i32, vp, vp, i64,
                                  ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
+    L.gs_fit_sweep.restype = i32
+    L.gs_fit_sweep.argtypes = [vp, vp, i32, i64, ctypes.POINTER(ctypes.c_double), i32, vp, vp,
+                               i64, ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
     L.gs_set_timing.restype = i32
     L.gs_set_timing.argtypes = [vp, i32]
     L.gs_get_phase_times.restype = i32
@@ -192,6 +195,19 @@ def gs_fit_batched(ctx: int, points_ptr: int, dtype: int, offsets, labels_ptr: i
     infos = (gs_fit_info * max(B, 1))()
     st = load().gs_fit_batched(ctx, points_ptr or None, int(dtype), off, int(B), labels_ptr or None,
                                modes_ptr or None, int(modes_cap), mo, infos)
+    return st, [int(v) for v in mo], [infos[i] for i in range(B)]
+
+
+def gs_fit_sweep(ctx: int, points_ptr: int, dtype: int, n: int, hs, labels_ptr: int,
+                 modes_ptr: int, modes_cap: int):
+    """Raw call; hs: B host floats.  Returns (status, mode_offsets list of B + 1,
+    list of B gs_fit_info)."""
+    B = len(hs)
+    hv = (ctypes.c_double * max(B, 1))(*[float(v) for v in hs])
+    mo = (ctypes.c_int64 * (B + 1))()
+    infos = (gs_fit_info * max(B, 1))()
+    st = load().gs_fit_sweep(ctx, points_ptr or None, int(dtype), int(n), hv, int(B),
+                             labels_ptr or None, modes_ptr or None, int(modes_cap), mo, infos)
     return st, [int(v) for v in mo], [infos[i] for i in range(B)]
 
 
@@ -310,6 +326,36 @@ class GridShift:
         cap = 0 if modes is None else modes.shape[0]
         return gs_fit(self._ctx, points.data_ptr(), dt, points.shape[0], labels.data_ptr(),
                       0 if modes is None else modes.data_ptr(), cap)
+
+    def fit_sweep(self, points, hs):
+        """GridShift on the same points for every bandwidth in hs (one call).
+        points: n x d CUDA tensor.  Returns (labels int32[B, n] numbered per
+        bandwidth, list of B modes tensors, list of B info dicts)."""
+        import torch
+        if points.dtype == torch.float64:
+            dt = GS_IN_F64
+        elif points.dtype == torch.float32:
+            dt = GS_IN_F32
+        else:
+            raise TypeError("points must be float64 or float32")
+        if not points.is_cuda or not points.is_contiguous() or points.dim() != 2:
+            raise ValueError("points must be a contiguous n x d CUDA tensor")
+        n, B = points.shape[0], len(hs)
+        with torch.cuda.device(points.device):
+            gs_set_stream(self._ctx, torch.cuda.current_stream(points.device).cuda_stream)
+            labels = torch.empty((B, n), dtype=torch.int32, device=points.device)
+            while True:
+                modes = torch.empty((self._modes_cap, self.d), dtype=torch.float64,
+                                    device=points.device)
+                st, mo, infos = gs_fit_sweep(self._ctx, points.data_ptr(), dt, n, hs,
+                                             labels.data_ptr(), modes.data_ptr(), modes.shape[0])
+                if st == GS_E_CAPACITY:
+                    self._modes_cap = max(2 * self._modes_cap, mo[-1])
+                    continue
+                if st != GS_OK:
+                    raise GridShiftError(st, gs_get_last_error(self._ctx))
+                return (labels, [modes[mo[b]:mo[b + 1]] for b in range(len(mo) - 1)],
+                        [i.as_dict() for i in infos])
 
     def fit_batched(self, points, offsets):
         """GridShift on each instance of a concatenated batch.  points: n x d

@@ -189,3 +189,24 @@ def test_noalloc_host_only_checks(lib):
     st, _, _ = gridshift.gs_fit_noalloc(3, 1.0, 10, None, fake, F64, limit + 1, fake, 0, 0)
     assert st == gridshift.GS_E_SCRATCH
 
+
+
+def test_sweep_host_only_checks(lib):
+    F64 = gridshift.GS_IN_F64
+    fake = 1 << 20  # never dereferenced: every case below returns first
+    ctx = gridshift.gs_create(3, 16.0, 10)
+    try:
+        st, mo, infos = gridshift.gs_fit_sweep(ctx, 0, F64, 0, [4.0, 8.0], 0, 0, 0)
+        assert st == gridshift.GS_OK and mo == [0, 0, 0] and [i.converged for i in infos] == [1, 1]
+        for hs in ([], [1.0, 0.0], [math.nan], [-2.0], [math.inf, 1.0]):
+            st, _, _ = gridshift.gs_fit_sweep(ctx, fake, F64, 10, hs, fake, 0, 0)
+            assert st == gridshift.GS_E_INVALID, hs
+        st, _, _ = gridshift.gs_fit_sweep(ctx, fake, F64, 1 << 30, [1.0, 2.0], fake, 0, 0)
+        assert st == gridshift.GS_E_INVALID  # B x n >= 2^31
+        st, _, _ = gridshift.gs_fit_sweep(ctx, 0, F64, 10, [1.0, 2.0], fake, 0, 0)
+        assert st == gridshift.GS_E_INVALID  # NULL points
+        assert gridshift.gs_set_precision(ctx, gridshift.GS_FP32_MIXED) == gridshift.GS_OK
+        st, _, _ = gridshift.gs_fit_sweep(ctx, fake, F64, 10, [1.0, 2.0], fake, 0, 0)
+        assert st == gridshift.GS_E_INVALID and "GS_FP64" in gridshift.gs_get_last_error(ctx)
+    finally:
+        gridshift.gs_destroy(ctx)

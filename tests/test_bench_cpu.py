@@ -37,3 +37,21 @@ def test_traffic_only_for_captured_parallel_kernels():
     import bench
     assert bench.traffic("image_1080p_d5", "fp64", "k_loop", "sequential") is None
     assert bench.traffic("no_such_workload", "fp64", "k_loop") is None
+
+
+def test_scope_count_of_the_loop_kernel():
+    # 1080p d=5 FP64: 3^5 key sectors, 2 payload sectors, the centroid and key
+    # written (48 B) and the merge (48 B of sort passes, 2 x 44 B of payload)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.scope_bytes_per_cell_step(5, False) == 243 * 32 + 64 + 48 + 48 + 88
+    assert bench.scope_bytes_per_cell_step(6, True) == 729 * 32 + 64 + 32 + 48 + 56
+    assert bench.loop_scope_bytes(10, 3, 0, False) == 120
+
+
+def test_reference_arm_uses_every_core():
+    r = _bench("--impl", "reference", "--workload", "image_321x481_d3", "--steps", "1",
+               "--warmup", "0")
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["cpu_baseline"]["cores"] == line["cpu_baseline"]["nproc"] >= 1
