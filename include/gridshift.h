@@ -57,10 +57,12 @@ extern "C" {
 
 typedef enum {
   GS_OK = 0,
-  GS_E_INVALID = 1,  /* bad argument: null pointer, d out of 1..8, h not > 0, NaN/Inf input, ... */
+  GS_E_INVALID = 1,  /* bad argument: null pointer, d out of 1..12, h not > 0, NaN/Inf input, ... */
   GS_E_NOMEM = 2,    /* a device or pinned host allocation failed */
-  GS_E_KEYRANGE = 3, /* the integer cell keys do not fit the 63-bit packed key, or a
-                        coordinate's key range exceeds 2^22 cells */
+  GS_E_KEYRANGE = 3, /* a coordinate divided by h is 4e15 or more; for gs_fit_batched,
+                        gs_fit_sweep and gs_fit_noalloc also: the integer cell keys do not
+                        fit the 63-bit packed key, or an axis spans more than 2^22 cells
+                        (gs_fit runs such keys through its wide-key pipeline instead) */
   GS_E_CAPACITY = 4, /* modes_cap < k: *k_out is set and labels are valid */
   GS_E_CUDA = 5,     /* a CUDA runtime call failed; see gs_get_last_error */
   GS_E_INTERNAL = 6, /* a device-side bound (hash probe limit, table overflow) was hit */
@@ -138,8 +140,8 @@ typedef struct {
 
 /* Creates a context for d-dimensional points, cell side (bandwidth) h and at
  * most max_iter update steps (Sec. 2.1; h is the cell side of step i).
- * 1 <= d <= 8, h finite and > 0, max_iter >= 0.  Allocates no device memory
- * yet.  *out receives the context (NULL on error).  Returns GS_OK,
+ * 1 <= d <= 12, h finite and > 0, max_iter >= 0 (d > 8: gs_fit only, in
+ * GS_FP64 with the parallel update).  Allocates no device memory yet.  *out receives the context (NULL on error).  Returns GS_OK,
  * GS_E_INVALID or GS_E_NOMEM. */
 gs_status gs_create(int d, double h, int max_iter, gs_ctx** out);
 
@@ -171,7 +173,17 @@ gs_status gs_set_stream(gs_ctx* ctx, void* cuda_stream);
  *   k_out      host: number of clusters k (output; required)
  *   info       host: statistics (output; may be NULL)
  * n == 0 returns GS_OK with k = 0.  If k > modes_cap, returns GS_E_CAPACITY
- * with *k_out = k and labels filled; call again with a larger buffer. */
+ * with *k_out = k and labels filled; call again with a larger buffer.
+ *
+ * Cell keys are integer vectors of any size (Sec. 2.1).  The main pipeline
+ * packs a key into 63 bits (d <= 8, at most 2^22 cells per axis); where the
+ * data's keys do not fit (d > 8, an axis spanning more cells, or fields wider
+ * than 63 bits together), a GS_FP64 parallel-update run goes through the
+ * wide-key pipeline instead: one int64 field per axis, cells kept in key
+ * order, neighbours found by binary search, merges by a stable radix sort,
+ * the same exact sums (bit-identical results; slower, with one host
+ * synchronisation per update step).  GS_FP32_MIXED or GS_UPDATE_SEQUENTIAL
+ * runs with such keys return GS_E_KEYRANGE (d <= 8) or GS_E_INVALID (d > 8). */
 gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int32_t* labels,
                  double* modes, int64_t modes_cap, int64_t* k_out, gs_fit_info* info);
 
@@ -275,8 +287,9 @@ gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
  * max_iter = 50, growing with d and max_iter, plus 272 KB of fixed buffers)
  * must fit what the points leave; the cell-face table holds at most 8192
  * entries (over all axes, the number of cells the data spans plus 3).
- * Beyond these the call returns GS_E_SCRATCH; use gs_fit.  GS_FP64 and the
- * parallel update (GS_UPDATE_PARALLEL) only.
+ * Beyond these the call returns GS_E_SCRATCH; use gs_fit.  GS_FP64, the
+ * parallel update (GS_UPDATE_PARALLEL) and keys that fit the 63-bit packed
+ * key (1 <= d <= 8) only.
  *
  * Sharing: every call uses the same array, which keeps the previous call's
  * contents; the call clears what must start at zero itself.  Calls are

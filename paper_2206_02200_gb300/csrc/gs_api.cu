@@ -11,6 +11,7 @@
 #include "../../include/gridshift.h"
 #include "gs_driver.h"
 #include "gs_planner.cuh"
+#include "gs_wide.h"
 
 using namespace gs;
 
@@ -443,6 +444,7 @@ struct gs_ctx {
   PhaseTimer tm;
   gs_phase_times last_times{};
   CtxWorkspace ws;
+  WideWorkspace* wide = nullptr;  // the wide-key pipeline's buffers (made on first use)
   // the tracking window step: one device block [accumulators | reference
   // cells | cell flags] and its pinned host staging
   DBuf<uint4> tbuf;
@@ -451,6 +453,8 @@ struct gs_ctx {
 
   void release_device() {
     ws.release();
+    wide_workspace_free(wide);
+    wide = nullptr;
     tm.release();
     tbuf.release();
     if (h_track) cudaFreeHost(h_track);
@@ -487,7 +491,8 @@ const char* gs_status_string(gs_status s) {
 gs_status gs_create(int d, double h, int max_iter, gs_ctx** out) {
   if (!out) return GS_E_INVALID;
   *out = nullptr;
-  if (d < 1 || d > kMaxD || !(h > 0) || !std::isfinite(h) || max_iter < 0 || max_iter > 100000)
+  if (d < 1 || d > kMaxWideD || !(h > 0) || !std::isfinite(h) || max_iter < 0 ||
+      max_iter > 100000)
     return GS_E_INVALID;
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return GS_E_NOMEM;
@@ -588,8 +593,27 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   a.mixed = ctx->prec == GS_FP32_MIXED;
   a.sequential = ctx->update == GS_UPDATE_SEQUENTIAL;
   double kms[kLoopPhases + 2 * kClockSteps] = {};
-  gs_status st = fit_pipeline(a, ctx->ws, ctx->timing ? &ctx->tm : nullptr, k_out, &inf, kms,
-                              &ctx->err);
+  gs_status st;
+  const bool wide_ok = !a.mixed && !a.sequential;
+  if (ctx->d > kMaxD) {
+    // more axes than the packed key holds: the wide-key pipeline
+    if (!wide_ok)
+      return fail(ctx, GS_E_INVALID, "d > 8 runs in GS_FP64 with the parallel update only");
+    if (!ctx->wide && !(ctx->wide = wide_workspace_new())) return fail(ctx, GS_E_NOMEM, "wide workspace");
+    st = wide_fit(ctx->wide, a, k_out, &inf, &ctx->err);
+  } else {
+    uint32_t plan_st = kPlanOK;
+    a.plan_status_out = &plan_st;
+    st = fit_pipeline(a, ctx->ws, ctx->timing ? &ctx->tm : nullptr, k_out, &inf, kms, &ctx->err);
+    if (st == GS_E_KEYRANGE && wide_ok && (plan_st == kPlanBits || plan_st == kPlanSpan)) {
+      // the keys do not fit the 63-bit packed key: the wide-key pipeline
+      // (its kernels count on top of the refused attempt's)
+      if (!ctx->wide && !(ctx->wide = wide_workspace_new()))
+        return fail(ctx, GS_E_NOMEM, "wide workspace");
+      ctx->err.clear();
+      st = wide_fit(ctx->wide, a, k_out, &inf, &ctx->err);
+    }
+  }
   if (info) *info = inf;
   if (st != GS_OK && st != GS_E_CAPACITY) return st;
   if (ctx->timing) {
@@ -626,6 +650,7 @@ gs_status gs_track_window(gs_ctx* ctx, const void* frame, gs_dtype dtype, int64_
   if (width < 0 || height < 0 || k < 0 || width > (1ll << 31) || height > (1ll << 31))
     return fail(ctx, GS_E_INVALID, "negative size or count");
   if (k > 0 && !bins) return fail(ctx, GS_E_INVALID, "bins is NULL with k > 0");
+  if (ctx->d > kMaxD) return fail(ctx, GS_E_INVALID, "the tracking window step needs d <= 8");
   if (dtype != GS_IN_F64 && dtype != GS_IN_F32) return fail(ctx, GS_E_INVALID, "bad dtype");
   if (present)
     for (int64_t j = 0; j < k; ++j) present[j] = 0;
@@ -761,6 +786,7 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   ctx->err.clear();
   if (!offsets || !mode_offsets || !infos) return fail(ctx, GS_E_INVALID, "NULL offsets, mode_offsets or infos");
   if (B < 1 || B > kMaxBatch) return fail(ctx, GS_E_INVALID, "B out of range");
+  if (B > 1 && ctx->d > kMaxD) return fail(ctx, GS_E_INVALID, "batched runs need d <= 8");
   if (B > 1 && ctx->update == GS_UPDATE_SEQUENTIAL)
     return fail(ctx, GS_E_INVALID, "the sequential update runs on one point set only (B = 1)");
   if (offsets[0] != 0) return fail(ctx, GS_E_INVALID, "offsets[0] must be 0");
@@ -831,6 +857,7 @@ gs_status gs_fit_sweep(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t 
   if (n > 0 && (!points || !labels)) return fail(ctx, GS_E_INVALID, "NULL points or labels");
   if (ctx->prec != GS_FP64 || ctx->update != GS_UPDATE_PARALLEL)
     return fail(ctx, GS_E_INVALID, "a bandwidth sweep runs in GS_FP64 with the parallel update");
+  if (ctx->d > kMaxD) return fail(ctx, GS_E_INVALID, "a bandwidth sweep needs d <= 8");
   std::memset(infos, 0, sizeof(gs_fit_info) * (size_t)B);
   for (int i = 0; i <= B; ++i) mode_offsets[i] = 0;
   ctx->tm.reset();

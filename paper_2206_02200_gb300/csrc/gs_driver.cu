@@ -290,13 +290,19 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
     GS_CU(cudaStreamSynchronize(s), "sync loop");
     if (hf->plan_status != kPlanOK) {
-      if (hf->plan_status != kPlanTable || host_planned) return plan_fail(err, hf->plan_status);
+      if (hf->plan_status != kPlanTable || host_planned) {
+        if (a.plan_status_out) *a.plan_status_out = hf->plan_status;
+        return plan_fail(err, hf->plan_status);
+      }
       // the face table is larger than the device-side capacity: the plan,
       // face table and offsets from the host, then binning and the loop
       Plan P;
       PlanSizes z;
       const uint32_t st = plan_from_range(d, a.h, n, a.B, *hf, P, z);
-      if (st != kPlanOK) return plan_fail(err, st);
+      if (st != kPlanOK) {
+        if (a.plan_status_out) *a.plan_status_out = st;
+        return plan_fail(err, st);
+      }
       const uint64_t m_bound = (uint64_t)n < z.span_prod ? (uint64_t)n : z.span_prod;
       GS_ST(ws.prepare(n, d, a.max_iter, z.thr_words, nprobe, m_bound, s, b, err));
       int64_t* stage = nullptr;

@@ -124,6 +124,9 @@ struct FitArgs {
   // update
   const double* sweep_h = nullptr;
   uint32_t n0 = 0;
+  // where a plan was refused, its status (kPlan*), for callers that have
+  // another way to run (the wide-key pipeline); may be null
+  uint32_t* plan_status_out = nullptr;
 };
 
 // 32-bit words of per-instance state of a batched run of B instances: one

@@ -190,6 +190,13 @@ def _cfg_gmm():
                 name="gmm_10M_d6_h4")
 
 
+def _cfg_gmm_4m():
+    # the same mixture at 4 million points: a profiling case whose tables
+    # exceed L2 while the whole run holds a few GB of device memory
+    return dict(points=gmm_points(4_000_000, 6, 200, seed=5), h=4.0, max_iter=50,
+                name="gmm_4M_d6_h4")
+
+
 def _cfg_batch64():
     parts = image_batch(64, 1000)
     return dict(parts=parts, h=16.0, max_iter=50, name="voronoi_batch64_uneven_d3_h16")
@@ -211,6 +218,7 @@ WORKLOADS = {
     "image_1080p_d5": _cfg_1080p,
     "image_4k_d5": _cfg_4k,
     "gmm_10M_d6": _cfg_gmm,
+    "gmm_4M_d6": _cfg_gmm_4m,
     "batch_64_d3": _cfg_batch64,
     "sweep_321x481_d3": _cfg_sweep,
 }

@@ -54,7 +54,7 @@ def test_status_strings(lib):
         assert gridshift.gs_status_string(code) == name
 
 
-@pytest.mark.parametrize("d,h,max_iter", [(0, 1.0, 5), (9, 1.0, 5), (3, 0.0, 5), (3, -1.0, 5),
+@pytest.mark.parametrize("d,h,max_iter", [(0, 1.0, 5), (13, 1.0, 5), (3, 0.0, 5), (3, -1.0, 5),
                                           (3, float("nan"), 5), (3, float("inf"), 5),
                                           (3, 1.0, -1)])
 def test_create_rejects_bad_arguments(lib, d, h, max_iter):
@@ -208,5 +208,25 @@ def test_sweep_host_only_checks(lib):
         assert gridshift.gs_set_precision(ctx, gridshift.GS_FP32_MIXED) == gridshift.GS_OK
         st, _, _ = gridshift.gs_fit_sweep(ctx, fake, F64, 10, [1.0, 2.0], fake, 0, 0)
         assert st == gridshift.GS_E_INVALID and "GS_FP64" in gridshift.gs_get_last_error(ctx)
+    finally:
+        gridshift.gs_destroy(ctx)
+
+
+def test_wide_dimensions_host_only_checks(lib):
+    # d up to 12 is accepted (the wide-key pipeline); batched runs, sweeps and
+    # the tracking window step keep the packed key (d <= 8) and refuse first
+    F64 = gridshift.GS_IN_F64
+    fake = 1 << 20
+    ctx = gridshift.gs_create(12, 1.0, 10)
+    try:
+        st, k, info = gridshift.gs_fit(ctx, 0, F64, 0, 0, 0, 0)
+        assert st == gridshift.GS_OK and k == 0
+        st, _, _ = gridshift.gs_fit_batched(ctx, fake, F64, [0, 5, 10], fake, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        st, _, _ = gridshift.gs_fit_sweep(ctx, fake, F64, 10, [1.0, 2.0], fake, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        st, _, _ = gridshift.gs_track_window(ctx, fake, F64, 8, 8, np.zeros((1, 12), np.int64),
+                                             0, 0, 4, 4)
+        assert st == gridshift.GS_E_INVALID
     finally:
         gridshift.gs_destroy(ctx)
