@@ -428,7 +428,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     prec = gridshift.GS_FP32_MIXED if fp32 else gridshift.GS_FP64
     form = (gridshift.GS_UPDATE_SEQUENTIAL if args.update == "sequential"
             else gridshift.GS_UPDATE_PARALLEL)
-    g = gridshift.GridShift(d, w["h"], w["max_iter"], precision=prec, update=form)
+    g = gridshift.GridShift(d, w["h"], w["max_iter"], precision=prec, update=form,
+                            tuning="auto" if args.tuning == "auto" else None)
+    g._apply_auto_tuning(n, batched)
     pts = torch.from_numpy(X).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     modes = torch.empty((max(n // 16, 4096), d), dtype=torch.float64, device=dev)
@@ -615,7 +617,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
                 "data": "synthetic",
-                "config": workload_config(w, args.workload, args.precision, args.update),
+                "config": dict(workload_config(w, args.workload, args.precision, args.update),
+                               tuning=g.tuning(), tuning_source=g.tuning_source),
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": int(X.nbytes),
                         "d2h_bytes_per_step": int(n * 4 + kk * d * 8)},
@@ -851,6 +854,9 @@ def main():
                     help="update form: Eq. 6 (parallel, default) or Eq. 5 (sequential; "
                          "float64, one point set per call)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", choices=["auto", "default"], default="auto",
+                    help="launch choices: the autotuner's cached entry for the workload "
+                         "(auto, default) or the library's built-in ones")
     args = ap.parse_args()
     if args.update == "sequential" and (args.precision != "fp64" or
                                         args.workload.startswith(("batch", "track", "sweep"))):

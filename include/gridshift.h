@@ -247,6 +247,38 @@ gs_status gs_fit_sweep(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t 
                        const double* hs, int B, int32_t* labels, double* modes,
                        int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos);
 
+/* Launch choices of the update loop.  They decide which lanes, tables and
+ * phases compute a result, never the result itself (every sum is exact, so
+ * the results are bit-identical under any valid choice).  This is
+ * instrumentation for the autotuner (paper_2206_02200_gb300/autotune.py),
+ * not a step of the paper's method. */
+typedef struct {
+  int32_t few_lanes_x4;  /* a level is updated with few lanes per cell (4 at d <= 3, 8 at
+                            d = 4, 5, 16 at d = 6, 32 above; several cells in flight per
+                            warp) when 4 x its cells exceed few_lanes_x4 x the warps of the
+                            loop kernel's grid, else with 32 lanes per cell; 0 .. 2^20,
+                            default 4 (more cells than warps) */
+  int32_t load_shift;    /* level hash tables sized for load <= 2^-load_shift: 1 or 2
+                            (default 2) */
+  int32_t filter;        /* 1 (default): neighbour probes test the level's occupancy filter
+                            (in shared memory) before the table; 0: every probe reads the
+                            table */
+  int32_t tail_enter;    /* a level of at most this many cells finishes the run in one block
+                            of the loop kernel, pairwise in shared memory; 0 .. 256, default
+                            128 (plain runs) */
+  int32_t pencil_min;    /* the first update takes the pencil form (sums along axis 0 first,
+                            d >= 3) when binning found at least this many cells; >= 0,
+                            default 4096 (plain runs) */
+} gs_tuning;
+
+/* Sets the launch choices of later gs_fit, gs_fit_batched and gs_fit_sweep
+ * calls (t == NULL: the defaults).  Values out of range return GS_E_INVALID
+ * and leave the setting unchanged. */
+gs_status gs_set_tuning(gs_ctx* ctx, const gs_tuning* t);
+
+/* Copies the context's launch choices into *out (host). */
+gs_status gs_get_tuning(gs_ctx* ctx, gs_tuning* out);
+
 /* Turns per-phase device timing of later gs_fit calls on (enable != 0) or
  * off.  When on, each call records CUDA events on its stream around each
  * launch group and reads their elapsed times after its final synchronisation;

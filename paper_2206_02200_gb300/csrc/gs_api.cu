@@ -437,6 +437,7 @@ struct gs_ctx {
   int max_iter = 0;
   gs_precision prec = GS_FP64;
   gs_update update = GS_UPDATE_PARALLEL;
+  Tuning tune = kDefaultTuning;
   cudaStream_t stream = nullptr;
   int device = -1;
   std::string err;
@@ -526,6 +527,34 @@ gs_status gs_set_stream(gs_ctx* ctx, void* cuda_stream) {
   return GS_OK;
 }
 
+gs_status gs_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
+  if (!ctx) return GS_E_INVALID;
+  if (!t) {
+    ctx->tune = kDefaultTuning;
+    return GS_OK;
+  }
+  if (t->few_lanes_x4 < 0 || t->few_lanes_x4 > (1 << 20) || (t->load_shift != 1 && t->load_shift != 2) ||
+      (t->filter != 0 && t->filter != 1) || t->tail_enter < 0 ||
+      t->tail_enter > (int32_t)kTailMaxCells || t->pencil_min < 0)
+    return fail(ctx, GS_E_INVALID, "tuning value out of range");
+  ctx->tune.few_lanes_x4 = (uint32_t)t->few_lanes_x4;
+  ctx->tune.load_shift = (uint32_t)t->load_shift;
+  ctx->tune.filter = (uint32_t)t->filter;
+  ctx->tune.tail_enter = (uint32_t)t->tail_enter;
+  ctx->tune.pencil_min = (uint32_t)t->pencil_min;
+  return GS_OK;
+}
+
+gs_status gs_get_tuning(gs_ctx* ctx, gs_tuning* out) {
+  if (!ctx || !out) return GS_E_INVALID;
+  out->few_lanes_x4 = (int32_t)ctx->tune.few_lanes_x4;
+  out->load_shift = (int32_t)ctx->tune.load_shift;
+  out->filter = (int32_t)ctx->tune.filter;
+  out->tail_enter = (int32_t)ctx->tune.tail_enter;
+  out->pencil_min = (int32_t)ctx->tune.pencil_min;
+  return GS_OK;
+}
+
 gs_status gs_set_timing(gs_ctx* ctx, int enable) {
   if (!ctx) return GS_E_INVALID;
   ctx->timing = enable != 0;
@@ -590,6 +619,7 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   a.labels = labels;
   a.modes = modes;
   a.modes_cap = modes_cap;
+  a.tune = ctx->tune;
   a.mixed = ctx->prec == GS_FP32_MIXED;
   a.sequential = ctx->update == GS_UPDATE_SEQUENTIAL;
   double kms[kLoopPhases + 2 * kClockSteps] = {};
@@ -830,6 +860,7 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   a.labels = labels;
   a.modes = modes;
   a.modes_cap = modes_cap;
+  a.tune = ctx->tune;
   a.mixed = ctx->prec == GS_FP32_MIXED;
   a.B = B;
   a.offsets = offsets;
@@ -883,6 +914,7 @@ gs_status gs_fit_sweep(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t 
   a.labels = labels;
   a.modes = modes;
   a.modes_cap = modes_cap;
+  a.tune = ctx->tune;
   if (B == 1) {
     // one bandwidth: the plain run with that h
     a.n = n;

@@ -277,6 +277,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.mixed = a.mixed;
     L.srow = a.sequential ? b.srow : nullptr;
     L.sweep = a.sweep_h ? b.sweep : nullptr;
+    L.tune = a.tune;
     L.n0 = a.sweep_h ? a.n0 : 0;
     if (a.B > 1) L.I = inst_views(b.inst, a.B);
     GS_T_BEGIN(GS_PHASE_BIN);

@@ -127,6 +127,8 @@ struct FitArgs {
   // where a plan was refused, its status (kPlan*), for callers that have
   // another way to run (the wide-key pipeline); may be null
   uint32_t* plan_status_out = nullptr;
+  // launch choices of the loop kernel (results do not depend on them)
+  Tuning tune = kDefaultTuning;
 };
 
 // 32-bit words of per-instance state of a batched run of B instances: one

@@ -104,6 +104,7 @@ struct LoopArgs {
                           // (B entries); null otherwise
   uint32_t n0;            // bandwidth sweep: points per instance (instance b's point j is
                           // row j of pts); 0 otherwise
+  Tuning tune;            // launch choices (lanes per cell, table load, filter, tail, pencil)
 };
 
 // Accumulators of one tracking window step (gs_track_window).

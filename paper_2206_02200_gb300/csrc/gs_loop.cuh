@@ -165,6 +165,14 @@ __device__ __forceinline__ void filter_set(uint32_t* f, uint64_t key, int lg) {
   atomicOr(&f[b >> 5], 1u << (b & 31));
 }
 
+// Capacity mask of a level table that receives at most m distinct keys, at
+// load <= 2^-shift where cap_max allows.
+__device__ __forceinline__ uint32_t level_mask(uint32_t m, uint32_t cap_max, uint32_t shift) {
+  uint64_t c = 64;
+  while (c < ((uint64_t)m << shift) && c < cap_max) c <<= 1;
+  return (uint32_t)c - 1u;
+}
+
 // Lanes given to one cell in the update: a power of two, at least d and at
 // least GatherLanes<D>::min.  Few lanes per cell put several cells in flight
 // per warp, which hides the latency of their dependent table loads when a
@@ -427,9 +435,9 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
 // probes.  Q lives in tab[2] (free during step 0) with its slots listed in
 // qlist, and its keys join the level-0 occupancy filter.
 
-// Minimum level-0 cells for the pencil form (below it the two extra grid
-// barriers cost more than the probes they save).
-constexpr uint32_t kPencilMin = 4096;
+// The least level-0 cells for the pencil form is Tuning::pencil_min (by
+// default 4096: below it the two extra grid barriers cost more than the
+// probes they save).
 
 // Field of axis a of a packed key (plain runs: nothing above axis 0).
 __device__ __forceinline__ int64_t key_field(uint64_t key, int a) {
@@ -667,7 +675,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
         const int p = p0 + u * GS;
         q[u] = key + (p < np ? __ldg(&A.dtab[pbase + p]) : 0ull);
         const uint32_t fb = filter_bit(q[u], lg);
-        v[u] = p < np && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
+        v[u] = p < np && (!A.tune.filter || ((s_filter[fb >> 5] >> (fb & 31)) & 1u));
       }
       table_find_many<U>(P.key, mask, q, v, sl);
 #pragma unroll
@@ -1362,7 +1370,7 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
         const int p = p0 + u * GS;
         q[u] = key + (p < np ? __ldg(&A.dtab[pbase + p]) : 0ull);
         const uint32_t fb = filter_bit(q[u], lg);
-        v[u] = p < np && ((s_filter[fb >> 5] >> (fb & 31)) & 1u);
+        v[u] = p < np && (!A.tune.filter || ((s_filter[fb >> 5] >> (fb & 31)) & 1u));
       }
       row_find_many<D, U>(prow, maskP, q, v, sl, dat);
 #pragma unroll
@@ -1600,7 +1608,7 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
 
 // ---------------------------------------------------------------------------
 // The tail of the update loop in one block (plain runs).  Once a
-// level has at most kTailEnter cells, block 0 copies it into shared memory
+// level has at most Tuning::tail_enter cells, block 0 copies it into shared memory
 // and runs the remaining update steps alone, with block barriers, while the
 // other blocks wait at one grid barrier.  With so few cells, neighbours are
 // found by comparing every pair of cells (|k_i - k_j| <= 1 on every axis is
@@ -1613,12 +1621,12 @@ __device__ __forceinline__ void mode_and_release32(const LevelTable& G, const Pl
 // load per step) instead of pointer jumping (one grid barrier per round).
 constexpr int kWalkMax = 16;
 
-// Largest level handed to the one-block tail.  A tail step makes m^2 pair
-// tests on one SM; measured on GB300 (d = 3 and 5), it beats a multi-block
-// step (grid barriers, dependent L2 loads) up to about 110 cells and loses
-// from about 150 (14 against 20 us at 107 cells, 31 against 21 us at 149).
-constexpr uint32_t kTailEnter = 128;
-constexpr int kTailMax = 256;  // cells the tail's shared memory holds
+// Largest level handed to the one-block tail: Tuning::tail_enter.  A tail
+// step makes m^2 pair tests on one SM; measured on GB300 (d = 3 and 5), it
+// beats a multi-block step (grid barriers, dependent L2 loads) up to about
+// 110 cells and loses from about 150 (14 against 20 us at 107 cells, 31
+// against 21 us at 149): 128 by default.
+constexpr int kTailMax = (int)kTailMaxCells;  // cells the tail's shared memory holds
 constexpr int kTailLanes = 8;  // lanes comparing one cell against the level
 
 constexpr size_t tail_bytes(int d, int mx) {
@@ -1662,7 +1670,7 @@ struct TailMem {
                                        (size_t)which * Mx * 2);
   }
 };
-static_assert(kTailEnter <= (uint32_t)kTailMax &&
+static_assert(kDefaultTuning.tail_enter <= kTailMaxCells &&
                   tail_bytes(kMaxD, kTailMax) <= (size_t)kFilterWords * 4,
               "the tail's shared memory must fit in the filter's");
 
@@ -1923,7 +1931,7 @@ __device__ void run_tail(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev,
   {
     const LevelTable G = A.tab[t % 3];
     const Cells c = A.cells[t & 1];
-    const uint32_t maskT = mask_for(m, A.capAB);
+    const uint32_t maskT = level_mask(m, A.capAB, A.tune.load_shift);
     for (uint32_t i = tid; i < m; i += nth) {
       bool won;
       const uint64_t k = S.key(cur)[i];
@@ -2257,7 +2265,7 @@ __device__ void run_tail32(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev
     const LevelTable G = A.tab[t % 3];
     uint32_t* grow = reinterpret_cast<uint32_t*>(G.row);
     const Cells c = A.cells[t & 1];
-    const uint32_t maskT = mask_for(m, A.capAB);
+    const uint32_t maskT = level_mask(m, A.capAB, A.tune.load_shift);
     for (uint32_t i = tid; i < m; i += nth) {
       bool won;
       const uint64_t k = S.key(cur)[i];
@@ -2334,7 +2342,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   clk.lap(kSegSums);
 
   // level 0
-  const uint32_t maskA = mask_for(m0, A.capAB);
+  const uint32_t maskA = level_mask(m0, A.capAB, A.tune.load_shift);
   if (tid == 0) {
     A.st[0].m = m0;
     A.st[0].mask = maskA;
@@ -2365,7 +2373,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   constexpr bool seq = SEQ;
   if constexpr (!BT && D >= 3) {
     // Q holds at most 3 m0 keys: only where tab[2] keeps them at load <= 3/4
-    if (!seq && m0 > kTailEnter && m0 >= kPencilMin && A.qlist != nullptr &&
+    if (!seq && m0 > A.tune.tail_enter && m0 >= A.tune.pencil_min && A.qlist != nullptr &&
         4ull * m0 <= (uint64_t)A.capAB) {
       pen = 1;
       maskQ = mask_for(3 * m0, A.capAB);
@@ -2407,7 +2415,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   for (;;) {
     if constexpr (!BT) {
       // a small level: block 0 finishes the update steps in shared memory
-      if (m <= kTailEnter && !seq) {
+      if (m <= A.tune.tail_enter && !seq) {
         if (blockIdx.x == 0) {
           TailOut to;
           if constexpr (F32)
@@ -2433,14 +2441,15 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
       }
     }
     bool any_nb = false;
-    const uint32_t maskM = mask_for(m, A.capAB);
+    const uint32_t maskM = level_mask(m, A.capAB, A.tune.load_shift);
     // lanes per cell: the fewest (most cells in flight) while the level has
     // more cells than warps, else 32
     constexpr int GSmin = GatherLanes<D>::min;
+    const bool few_lanes = 4ull * m > (uint64_t)A.tune.few_lanes_x4 * (nth >> 5);
     const int pt = t == 0 ? pen : 0;
     const uint32_t maskPt = pt == 2 ? maskQ2 : maskQ;
     if (F32) {
-      if (GSmin < 32 && m > (nth >> 5))
+      if (GSmin < 32 && few_lanes)
         phase_update32<D, GSmin, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
                                      maskPt);
       else
@@ -2454,7 +2463,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
                                          inexact, werr, 0, col);
       }
     } else {
-      if (GSmin < 32 && m > (nth >> 5))
+      if (GSmin < 32 && few_lanes)
         phase_update<D, GSmin, BT>(A, t, m, pt ? maskPt : mask, maskM, m_prev, base_prev, base,
                                    any_nb, inexact, werr, pt);
       else

@@ -44,6 +44,21 @@ struct SweepPlan {
   int pad;
 };
 
+// Launch choices of the loop kernel that do not change its results (only
+// which lanes, tables and phases compute them); chosen per workload by the
+// autotuner (gs_set_tuning), else the defaults below.
+struct Tuning {
+  uint32_t few_lanes_x4;  // a level is updated with GatherLanes<D>::min lanes per cell when
+                          // 4 x its cells exceed few_lanes_x4 x the grid's warps, else 32
+  uint32_t load_shift;    // level tables sized for load <= 2^-load_shift (1 or 2)
+  uint32_t filter;        // 1: neighbour probes pass the level's occupancy filter first
+  uint32_t tail_enter;    // levels of at most this many cells finish in one block (<= 256)
+  uint32_t pencil_min;    // least initial cells for the pencil form of the first update
+};
+
+constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u};
+constexpr uint32_t kTailMaxCells = 256;  // the one-block tail's shared memory holds this many
+
 // Device-resident state of one level t (the cells before update step t).
 struct IterState {
   uint32_t m;       // active cells at level t

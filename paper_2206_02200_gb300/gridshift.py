@@ -36,7 +36,7 @@ GS_UPDATE_SEQUENTIAL = 1
 
 #: every symbol the header declares, in declaration order
 EXPORTS = ("gs_create", "gs_set_precision", "gs_set_update", "gs_set_stream", "gs_fit",
-           "gs_fit_batched", "gs_fit_sweep",
+           "gs_fit_batched", "gs_fit_sweep", "gs_set_tuning", "gs_get_tuning",
            "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_track_window",
            "gs_get_last_error", "gs_status_string", "gs_destroy")
 
@@ -66,6 +66,20 @@ class gs_phase_times(ctypes.Structure):
     def steps(self) -> list:
         """[(update ms, compaction ms)] of the first 16 update steps."""
         return [(float(self.step_ms[i][0]), float(self.step_ms[i][1])) for i in range(16)]
+
+
+class gs_tuning(ctypes.Structure):
+    _fields_ = [("few_lanes_x4", ctypes.c_int32), ("load_shift", ctypes.c_int32),
+                ("filter", ctypes.c_int32), ("tail_enter", ctypes.c_int32),
+                ("pencil_min", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+#: the library's built-in launch choices (gs_set_tuning with NULL)
+DEFAULT_TUNING = {"few_lanes_x4": 4, "load_shift": 2, "filter": 1, "tail_enter": 128,
+                  "pencil_min": 4096}
 
 
 class gs_track_result(ctypes.Structure):
@@ -116,6 +130,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.gs_fit_sweep.restype = i32
     L.gs_fit_sweep.argtypes = [vp, vp, i32, i64, ctypes.POINTER(ctypes.c_double), i32, vp, vp,
                                i64, ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
+    L.gs_set_tuning.restype = i32
+    L.gs_set_tuning.argtypes = [vp, ctypes.POINTER(gs_tuning)]
+    L.gs_get_tuning.restype = i32
+    L.gs_get_tuning.argtypes = [vp, ctypes.POINTER(gs_tuning)]
     L.gs_set_timing.restype = i32
     L.gs_set_timing.argtypes = [vp, i32]
     L.gs_get_phase_times.restype = i32
@@ -211,6 +229,23 @@ def gs_fit_sweep(ctx: int, points_ptr: int, dtype: int, n: int, hs, labels_ptr: 
     return st, [int(v) for v in mo], [infos[i] for i in range(B)]
 
 
+def gs_set_tuning(ctx: int, tuning: dict | None) -> int:
+    """Raw call; tuning: dict of gs_tuning fields (missing ones take the
+    defaults), or None for the built-in choices."""
+    if tuning is None:
+        return load().gs_set_tuning(ctx, None)
+    t = gs_tuning(**{k: int(v) for k, v in dict(DEFAULT_TUNING, **tuning).items()})
+    return load().gs_set_tuning(ctx, ctypes.byref(t))
+
+
+def gs_get_tuning(ctx: int) -> dict:
+    t = gs_tuning()
+    st = load().gs_get_tuning(ctx, ctypes.byref(t))
+    if st != GS_OK:
+        raise GridShiftError(st, "gs_get_tuning")
+    return t.as_dict()
+
+
 def gs_set_timing(ctx: int, enable: bool) -> int:
     return load().gs_set_timing(ctx, 1 if enable else 0)
 
@@ -274,19 +309,42 @@ class GridShift:
     """
 
     def __init__(self, d: int, h: float, max_iter: int = 50, precision: int = GS_FP64,
-                 update: int = GS_UPDATE_PARALLEL):
+                 update: int = GS_UPDATE_PARALLEL, tuning=None):
         import torch  # noqa: F401  (device memory and streams)
         self.d, self.h, self.max_iter = int(d), float(h), int(max_iter)
+        self.precision = int(precision)
         self._ctx = gs_create(self.d, self.h, self.max_iter)
         st = gs_set_precision(self._ctx, precision)
         if st == GS_OK:
             st = gs_set_update(self._ctx, update)
+        if st == GS_OK and isinstance(tuning, dict):
+            st = gs_set_tuning(self._ctx, tuning)
         if st != GS_OK:
             msg = gs_get_last_error(self._ctx)
             gs_destroy(self._ctx)
             self._ctx = None
             raise GridShiftError(st, msg)
         self._modes_cap = 1024
+        # "auto": the autotuner's cached choice for each call's size (see
+        # autotune.py), looked up per point count
+        self._auto = tuning == "auto"
+        self._auto_n = None
+        self.tuning_source = "given" if isinstance(tuning, dict) else "built-in"
+
+    def _apply_auto_tuning(self, n: int, batched: bool = False) -> None:
+        if not self._auto or self._auto_n == (n, batched):
+            return
+        from . import autotune
+        entry = autotune.lookup(self.d, self.precision, n, batched)
+        st = gs_set_tuning(self._ctx, entry["tuning"] if entry else None)
+        if st != GS_OK:
+            raise GridShiftError(st, gs_get_last_error(self._ctx))
+        self.tuning_source = entry["key"] if entry else "built-in (no cache entry)"
+        self._auto_n = (n, batched)
+
+    def tuning(self) -> dict:
+        """The launch choices the context uses now."""
+        return gs_get_tuning(self._ctx)
 
     def close(self) -> None:
         if getattr(self, "_ctx", None):
@@ -323,6 +381,7 @@ class GridShift:
             raise ValueError(f"points have d={points.shape[1]}, context has d={self.d}")
         stream = torch.cuda.current_stream(points.device).cuda_stream
         gs_set_stream(self._ctx, stream)
+        self._apply_auto_tuning(points.shape[0])
         cap = 0 if modes is None else modes.shape[0]
         return gs_fit(self._ctx, points.data_ptr(), dt, points.shape[0], labels.data_ptr(),
                       0 if modes is None else modes.data_ptr(), cap)
@@ -371,6 +430,7 @@ class GridShift:
         if not points.is_cuda or not points.is_contiguous() or points.dim() != 2:
             raise ValueError("points must be a contiguous n x d CUDA tensor")
         n = points.shape[0]
+        self._apply_auto_tuning(n, batched=True)
         with torch.cuda.device(points.device):
             gs_set_stream(self._ctx, torch.cuda.current_stream(points.device).cuda_stream)
             labels = torch.empty(n, dtype=torch.int32, device=points.device)

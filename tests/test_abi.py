@@ -230,3 +230,43 @@ def test_wide_dimensions_host_only_checks(lib):
         assert st == gridshift.GS_E_INVALID
     finally:
         gridshift.gs_destroy(ctx)
+
+
+def test_tuning_host_only_checks(lib, tmp_path):
+    ctx = gridshift.gs_create(5, 12.0, 50)
+    try:
+        assert gridshift.gs_get_tuning(ctx) == gridshift.DEFAULT_TUNING
+        t = {"few_lanes_x4": 16, "load_shift": 1, "filter": 0, "tail_enter": 256,
+             "pencil_min": 0}
+        assert gridshift.gs_set_tuning(ctx, t) == gridshift.GS_OK
+        assert gridshift.gs_get_tuning(ctx) == t
+        for bad in ({"load_shift": 3}, {"load_shift": 0}, {"filter": 2}, {"tail_enter": 257},
+                    {"tail_enter": -1}, {"few_lanes_x4": -1}, {"pencil_min": -5}):
+            assert gridshift.gs_set_tuning(ctx, bad) == gridshift.GS_E_INVALID, bad
+            assert gridshift.gs_get_tuning(ctx) == t  # unchanged
+        assert gridshift.gs_set_tuning(ctx, None) == gridshift.GS_OK
+        assert gridshift.gs_get_tuning(ctx) == gridshift.DEFAULT_TUNING
+    finally:
+        gridshift.gs_destroy(ctx)
+
+
+def test_autotune_cache_lookup(tmp_path):
+    import json
+    from paper_2206_02200_gb300 import autotune
+    F64, F32 = gridshift.GS_FP64, gridshift.GS_FP32_MIXED
+    assert autotune.key_for(5, F64, 2_073_600, False) == "d5_fp64_one_n2^21"
+    assert autotune.key_for(3, F32, 47_465_008, True) == "d3_fp32_batch_n2^26"
+    cache = {"d5_fp64_one_n2^21": {"tuning": {"filter": 0}},
+             "d5_fp64_one_n2^23": {"tuning": {"filter": 1}},
+             "d3_fp32_batch_n2^26": {"tuning": {"load_shift": 1}}}
+    path = tmp_path / "tuning.json"
+    path.write_text(json.dumps(cache))
+    e = autotune.lookup(5, F64, 2_073_600, False, path=str(path))
+    assert e["key"] == "d5_fp64_one_n2^21" and e["tuning"] == {"filter": 0}
+    assert autotune.lookup(5, F64, 1 << 23, False, path=str(path))["tuning"] == {"filter": 1}
+    assert autotune.lookup(5, F64, 1 << 19, False, path=str(path))["key"] == "d5_fp64_one_n2^21"
+    assert autotune.lookup(5, F64, 1 << 26, False, path=str(path)) is None  # too far
+    assert autotune.lookup(5, F32, 2_073_600, False, path=str(path)) is None
+    assert autotune.lookup(3, F32, 40_000_000, True, path=str(path))["tuning"] == {"load_shift": 1}
+    for k, v in gridshift.DEFAULT_TUNING.items():
+        assert v in autotune.CANDIDATES[k]
