@@ -275,10 +275,22 @@ def check_ctx_reuse(g):
 
 
 def test_key_range_error():
+    # 10^15 cells along the axis: more than the packed key's 2^22, so gs_fit
+    # takes the wide-key pipeline and still equals the oracle
     X = np.array([[0.0], [1e12]])
-    with pytest.raises(gridshift.GridShiftError) as e:
-        _gpu_fit(X, 1e-3)
-    assert e.value.status == gridshift.GS_E_KEYRANGE
+    check_parity(X, 1e-3)
+    # a batched run keeps the packed key and refuses
+    with gridshift.GridShift(1, 1e-3, 50) as g:
+        with pytest.raises(gridshift.GridShiftError) as e:
+            g.fit_batched(torch.from_numpy(np.concatenate([X, X])).cuda(), [0, 2, 4])
+        assert e.value.status == gridshift.GS_E_KEYRANGE
+    # |x / h| of 4e15 or more has no exact integer cell on either pipeline
+    for Y in (np.array([[0.0], [1e13]]), np.zeros((3, 10))):
+        Y = Y.copy()
+        Y[-1, 0] = 1e13
+        with pytest.raises(gridshift.GridShiftError) as e:
+            _gpu_fit(Y, 1e-3)
+        assert e.value.status == gridshift.GS_E_KEYRANGE
 
 
 @pytest.mark.parametrize("d,width", [(1, 200_000.0), (2, 40_000.0)])
