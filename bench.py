@@ -80,7 +80,7 @@ def loop_scope_bytes(n: int, d: int, probe_cell_steps: int, fp32: bool) -> int:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from the committed ncu captures under profiles/, keyed by (workload,
 # precision, kernel), each with the hash of the kernel sources it was taken
-# on (the files that define k_range, k_plan, k_bin and k_loop, not the host
+# on (the files that define k_range, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
     ("image_1080p_d5", "fp64", "k_loop"): (139.71e6, "d236db15bdb005c3"),
@@ -446,13 +446,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             if st != gridshift.GS_OK:
                 raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gg._ctx))
             return mo[-1], [x.as_dict() for x in infos]
-        gridshift.gs_set_stream(gg._ctx, stream.cuda_stream)
-        st, k, info = gg.fit_into(p, lab, md)
+        # the C entry point itself (the context's stream and launch choices
+        # are set once, outside the timed calls)
+        st, k, info = gridshift.gs_fit(gg._ctx, p.data_ptr(), dt_in, n, lab.data_ptr(),
+                                       md.data_ptr(), md.shape[0])
         if st != gridshift.GS_OK:
             raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gg._ctx))
         return k, [info.as_dict()]
 
     gridshift.gs_set_stream(g._ctx, stream.cuda_stream)
+    dt_in = gridshift.GS_IN_F64 if X.dtype == np.float64 else gridshift.GS_IN_F32
 
     def barrier():
         if world > 1:
@@ -540,13 +543,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         gp = gridshift.GridShift(d, w["h"], w["max_iter"])
         gridshift.gs_set_stream(gp._ctx, stream.cuda_stream)
         parts_dev = [pts[offsets[b]:offsets[b + 1]] for b in range(len(offsets) - 1)]
+        def plain(P):
+            return gridshift.gs_fit(gp._ctx, P.data_ptr(), dt_in, P.shape[0], labels.data_ptr(),
+                                    modes.data_ptr(), modes.shape[0])
+
         for P in parts_dev[:3]:
-            gp.fit_into(P, labels, modes)
+            plain(P)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for P in parts_dev:
-            st, _, _ = gp.fit_into(P, labels, modes)
+            st, _, _ = plain(P)
             if st != gridshift.GS_OK:
                 raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gp._ctx))
         e1.record(stream)

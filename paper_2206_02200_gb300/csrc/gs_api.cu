@@ -216,6 +216,7 @@ struct CtxWorkspace : public Workspace {
   DBuf<int64_t> offsets;
   DBuf<uint32_t> inst;
   DBuf<ulonglong2> srow;          // the sequential update's shifted rows
+  DBuf<uint32_t> seq_aux;         // the sequential update's colour lists
   DBuf<SweepPlan> sweep;          // a bandwidth sweep's per-instance cell decisions
   std::vector<uint64_t> h_inst;   // host copy of the per-instance state (8-byte aligned)
 
@@ -393,7 +394,9 @@ struct CtxWorkspace : public Workspace {
   gs_status shift_rows(uint32_t cap, int d, Bufs& b, std::string* err) override {
     cudaError_t e;
     WS_CU(srow.ensure((size_t)cap * d), "alloc shifted rows");
+    WS_CU(seq_aux.ensure((size_t)cap + 512), "alloc colour lists");
     b.srow = srow.p;
+    b.seq_aux = seq_aux.p;
     return GS_OK;
   }
   gs_status sweep_space(int B, Bufs& b, std::string* err) override {
@@ -417,7 +420,7 @@ struct CtxWorkspace : public Workspace {
     }
     qlist.release(); ptab.release(); forest.release(); forest2.release(); labslot.release(); rank.release(); filter.release();
     skey.release(); skey2.release(); sval.release(); sval2.release(); shist.release();
-    offsets.release(); inst.release(); srow.release(); sweep.release();
+    offsets.release(); inst.release(); srow.release(); sweep.release(); seq_aux.release();
     if (h_flags) cudaFreeHost(h_flags);
     if (h_res) cudaFreeHost(h_res);
     if (h_words) cudaFreeHost(h_words);

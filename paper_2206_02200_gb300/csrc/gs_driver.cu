@@ -84,12 +84,12 @@ gs_status plan_fail(std::string* err, uint32_t st) {
 // points and on n0 (every sum of an instance has at most n0 terms), so they
 // are shared as well.  Lays out the workspace, uploads the face tables, the
 // offsets and the per-instance plans, and clears the loop kernel's start
-// state (which k_plan clears in other runs).
+// state (which the key-range kernel clears in other runs).
 static gs_status sweep_prepare(const FitArgs& a, Workspace& ws, Bufs& b, DevFlags* hf,
                                int nprobe, gs_fit_info* info, std::string* err) {
   const int d = a.d, B = a.B;
   const cudaStream_t s = a.stream;
-  GS_LAUNCH(launch_range(a.points, a.f32, (int64_t)a.n0, d, b.flags, s), "k_range", 1);
+  GS_LAUNCH(launch_range(a.points, a.f32, (int64_t)a.n0, d, b.flags, nullptr, s), "k_range", 1);
   GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
   GS_CU(cudaStreamSynchronize(s), "sync key range");
   if (hf->bad) return plan_fail(err, kPlanNonFinite);
@@ -181,9 +181,9 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   Bufs b;
   GS_ST(ws.begin(b, err));
 
-  // a0: key range, fixed-point window, finiteness (k_range), then the plan
-  // on the device (k_plan: no host round trip before binning); the face
-  // table gets the workspace's device-side capacity
+  // a0: key range, fixed-point window, finiteness, then the plan on the
+  // device (k_range's last block); the face table gets the workspace's
+  // device-side capacity
   DevFlags* hf = ws.host_flags();
   std::memset(hf, 0, sizeof(DevFlags));
   for (int i = 0; i < kMaxD; ++i) {
@@ -200,9 +200,21 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_ST(ws.prepare(n, d, a.max_iter, thr_cap, nprobe, (uint64_t)n, s, b, err));
     GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
     GS_T_BEGIN(GS_PHASE_RANGE);
-    GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, s), "k_range", 1);
-    GS_LAUNCH(launch_plan(d, a.h, n, a.B, b.flags, b.thr, thr_cap, b.dtab, b.filter, b.st,
-                          (uint32_t)(a.max_iter + 2), b.bar, b.res, s), "k_plan", 1);
+    PlanJob job;
+    job.h = a.h;
+    job.B = a.B;
+    job.thr = b.thr;
+    job.thr_cap = thr_cap;
+    job.dtab = b.dtab;
+    job.filters = reinterpret_cast<uint4*>(b.filter);
+    job.filter_vec = 2 * kFilterWords / 4;
+    job.st = b.st;
+    job.n_st = (uint32_t)(a.max_iter + 2);
+    job.bar = b.bar;
+    job.res = b.res;
+    // the key range, then (in its last block) the plan: no host round trip
+    // before binning
+    GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, &job, s), "k_range", 1);
     GS_T_END();
   }
   uint32_t* hinst = nullptr;
@@ -229,7 +241,8 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   for (int attempt = 0;; ++attempt) {
     if (attempt > 0) {
       // a second binning (larger table, or the host's plan): the level
-      // workspace for its cell bound, and the start state k_plan cleared
+      // workspace for its cell bound, and the start state the key-range
+      // kernel cleared
       GS_ST(ws.levels(b.t0_maxcells, d, a.max_iter, s, b, err));
       GS_CU(cudaMemsetAsync(b.filter, 0, sizeof(uint32_t) * 2 * kFilterWords, s),
             "memset filters");
@@ -276,6 +289,7 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     L.B = a.B;
     L.mixed = a.mixed;
     L.srow = a.sequential ? b.srow : nullptr;
+    L.seq_aux = a.sequential ? b.seq_aux : nullptr;
     L.sweep = a.sweep_h ? b.sweep : nullptr;
     L.tune = a.tune;
     L.n0 = a.sweep_h ? a.n0 : 0;

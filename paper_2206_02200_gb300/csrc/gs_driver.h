@@ -46,6 +46,7 @@ struct Bufs {
   uint32_t* sval2 = nullptr;
   uint32_t* shist = nullptr;   // radix_hist_words(k)
   ulonglong2* srow = nullptr;  // sequential update: capAB * d
+  uint32_t* seq_aux = nullptr; // sequential update: 512 + capAB words
   SweepPlan* sweep = nullptr;  // bandwidth sweep: B per-instance cell decisions
 };
 
@@ -86,7 +87,8 @@ class Workspace {
   // The number of initial cells binning found (sizes later binning tables).
   virtual void note_cells(uint32_t m0) = 0;
   // The sequential update's shifted rows for level tables of `cap` slots
-  // (b.srow, cap * d entries), or an error.
+  // (b.srow, cap * d entries) and its colour lists (b.seq_aux, 512 + cap
+  // words), or an error.
   virtual gs_status shift_rows(uint32_t cap, int d, Bufs& b, std::string* err) = 0;
   // A bandwidth sweep's per-instance cell decisions (b.sweep, B entries), or
   // an error.

@@ -1,7 +1,8 @@
 // gs_kernels.cu -- the per-point kernels of the GridShift hot path on sm_103a
 // (Kumar et al., arXiv 2206.02200, Sec. 2.1 and Algorithm 1):
-//   k_range  key range, fixed-point window and finiteness of the input
-//   k_plan   the plan of the call (key packing, face table, offsets)
+//   k_range  key range, fixed-point window and finiteness of the input, then
+//            (its last block) the plan of the call (key packing, face table,
+//            offsets)
 //   k_bin    step i, first pass: cell key and count of every point
 // and the kernels that finish the labels when the final cells are numbered
 // by a radix sort.  Everything between binning and the labels runs in the
@@ -75,10 +76,22 @@ struct RangeAcc {
   }
 };
 
+__device__ void plan_block(int d, int64_t n, const PlanJob& J, DevFlags* fl);
+
 template <int D, typename T, int W>
 __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int64_t n,
-                                                  DevFlags* fl) {
+                                                  DevFlags* fl, bool plan, PlanJob J) {
   constexpr int U = 4;  // words in flight per thread
+  if (plan) {
+    // the loop kernel's start state, cleared by the whole grid
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (uint32_t w = gt; w < J.filter_vec; w += gs) J.filters[w] = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = gt; i < J.n_st; i += gs) J.st[i] = IterState{};
+    if (gt == 0) {
+      *J.bar = GridBar{};
+      *J.res = LoopResult{};
+    }
+  }
   __shared__ long long s_mn[D], s_mx[D];
   __shared__ unsigned long long s_ma[D], s_bad;
   if (threadIdx.x < D) {
@@ -145,6 +158,16 @@ __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int
     atomicMax(&fl->maxabs[threadIdx.x], s_ma[threadIdx.x]);
   }
   if (threadIdx.x == 0 && s_bad) atomicAdd(&fl->bad, s_bad);
+  if (!plan) return;
+  // the last block to publish its extremes makes the plan
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&fl->range_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  plan_block(D, n, J, fl);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,39 +207,35 @@ __device__ __forceinline__ uint32_t instance_of(const int64_t* __restrict__ offs
   return (uint32_t)lo;
 }
 
-// The plan of a call (Sec. 2.1 i) from its key range, on the device.  Block
-// 0: one thread per axis, then one thread for the key layout, into fl->plan;
-// then the block fills the face table and the neighbour offsets.  A
-// non-finite input, a key range the packing cannot hold, or a face table
-// above thr_cap entries sets fl->plan_status instead (binning and the loop
-// kernel then do nothing; the host reads the status).  Every block also
-// clears part of the loop kernel's start state (the occupancy filters, the
-// per-level state, the grid barrier, the result).
-__global__ void __launch_bounds__(kBlock)
-    k_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t* __restrict__ thr,
-           uint64_t thr_cap, uint64_t* __restrict__ dtab, uint4* filters, uint32_t filter_vec,
-           IterState* st, uint32_t n_st, GridBar* bar, LoopResult* res) {
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < filter_vec;
-       w += gridDim.x * blockDim.x)
-    filters[w] = make_uint4(0, 0, 0, 0);
-  if (blockIdx.x != 0) return;
-  for (uint32_t i = threadIdx.x; i < n_st; i += blockDim.x) st[i] = IterState{};
-  if (threadIdx.x == 0) {
-    *bar = GridBar{};
-    *res = LoopResult{};
-  }
+// The plan of a call (Sec. 2.1 i) from its key range, on the device, by one
+// block (the last block of the key-range kernel, once every block has
+// published its extremes): one thread per axis, then one thread for the key
+// layout, into fl->plan; then the block fills the face table and the
+// neighbour offsets.  A non-finite input, a key range the packing cannot
+// hold, or a face table above thr_cap entries sets fl->plan_status instead
+// (binning and the loop kernel then do nothing; the host reads the status).
+__device__ void plan_block(int d, int64_t n, const PlanJob& J, DevFlags* fl) {
   __shared__ Plan s_plan;
   __shared__ PlanSizes s_z;
   __shared__ uint32_t s_st, s_ax[kMaxD];
-  if (threadIdx.x == 0) memset(&s_plan, 0, sizeof(s_plan));
+  __shared__ DevFlags s_fl;  // the key range, read at L2 (other blocks wrote it)
+  if (threadIdx.x == 0) {
+    memset(&s_plan, 0, sizeof(s_plan));
+    for (int a = 0; a < kMaxD; ++a) {
+      s_fl.min_ord[a] = __ldcg(&fl->min_ord[a]);
+      s_fl.max_ord[a] = __ldcg(&fl->max_ord[a]);
+      s_fl.maxabs[a] = __ldcg(&fl->maxabs[a]);
+    }
+    s_fl.bad = __ldcg(&fl->bad);
+  }
   __syncthreads();
-  if ((int)threadIdx.x < d) s_ax[threadIdx.x] = plan_axis(threadIdx.x, h, n, *fl, s_plan);
+  if ((int)threadIdx.x < d) s_ax[threadIdx.x] = plan_axis(threadIdx.x, J.h, n, s_fl, s_plan);
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t status = fl->bad ? kPlanNonFinite : kPlanOK;
+    uint32_t status = s_fl.bad ? kPlanNonFinite : kPlanOK;
     for (int a = 0; a < d && status == kPlanOK; ++a) status = s_ax[a];
-    if (status == kPlanOK) status = plan_finish(d, h, B, s_plan, s_z);
-    if (status == kPlanOK && s_z.thr_words > thr_cap) status = kPlanTable;
+    if (status == kPlanOK) status = plan_finish(d, J.h, J.B, s_plan, s_z);
+    if (status == kPlanOK && s_z.thr_words > J.thr_cap) status = kPlanTable;
     fl->plan = s_plan;
     fl->plan_sizes = s_z;
     fl->plan_status = status;
@@ -225,11 +244,11 @@ __global__ void __launch_bounds__(kBlock)
   __syncthreads();
   if (s_st != kPlanOK) return;
   for (uint64_t j = threadIdx.x; j < s_z.thr_words; j += blockDim.x)
-    thr[j] = plan_face_entry(s_plan, h, j);
+    J.thr[j] = plan_face_entry(s_plan, J.h, j);
   // dtab: nprobe packed-key offsets, then nprobe 32-bit offset vectors
-  uint32_t* vpack = reinterpret_cast<uint32_t*>(dtab + s_plan.nprobe);
+  uint32_t* vpack = reinterpret_cast<uint32_t*>(J.dtab + s_plan.nprobe);
   for (int p = threadIdx.x; p < s_plan.nprobe; p += blockDim.x)
-    plan_probe(s_plan, p, dtab + p, vpack + p);
+    plan_probe(s_plan, p, J.dtab + p, vpack + p);
 }
 
 template <int D, typename T>
@@ -346,32 +365,25 @@ __global__ void k_rank(const uint32_t* __restrict__ sorted_vals, uint32_t* __res
 // Launchers
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
-                         cudaStream_t s) {
+                         const PlanJob* job, cudaStream_t s) {
   const bool vec = ((uintptr_t)pts & 15u) == 0;
   const int W = vec ? (f32 ? 4 : 2) : 1;
   const unsigned g = grid_for(n * d / W, kBlock * 4, 152u * 8u);
+  const bool plan = job != nullptr;
+  const PlanJob J = plan ? *job : PlanJob{};
   if (f32) {
     if (vec) {
-      GS_DISPATCH_D(d, k_range<D, float, 4><<<g, kBlock, 0, s>>>((const float*)pts, n, fl));
+      GS_DISPATCH_D(d, k_range<D, float, 4><<<g, kBlock, 0, s>>>((const float*)pts, n, fl, plan, J));
     } else {
-      GS_DISPATCH_D(d, k_range<D, float, 1><<<g, kBlock, 0, s>>>((const float*)pts, n, fl));
+      GS_DISPATCH_D(d, k_range<D, float, 1><<<g, kBlock, 0, s>>>((const float*)pts, n, fl, plan, J));
     }
   } else {
     if (vec) {
-      GS_DISPATCH_D(d, k_range<D, double, 2><<<g, kBlock, 0, s>>>((const double*)pts, n, fl));
+      GS_DISPATCH_D(d, k_range<D, double, 2><<<g, kBlock, 0, s>>>((const double*)pts, n, fl, plan, J));
     } else {
-      GS_DISPATCH_D(d, k_range<D, double, 1><<<g, kBlock, 0, s>>>((const double*)pts, n, fl));
+      GS_DISPATCH_D(d, k_range<D, double, 1><<<g, kBlock, 0, s>>>((const double*)pts, n, fl, plan, J));
     }
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t* thr,
-                        uint64_t thr_cap, uint64_t* dtab, uint32_t* filters, IterState* st,
-                        uint32_t n_st, GridBar* bar, LoopResult* res, cudaStream_t s) {
-  const uint32_t vec = 2 * kFilterWords / 4;
-  k_plan<<<32, kBlock, 0, s>>>(d, h, n, B, fl, thr, thr_cap, dtab,
-                               reinterpret_cast<uint4*>(filters), vec, st, n_st, bar, res);
   return cudaGetLastError();
 }
 

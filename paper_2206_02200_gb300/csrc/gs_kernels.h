@@ -105,6 +105,8 @@ struct LoopArgs {
   uint32_t n0;            // bandwidth sweep: points per instance (instance b's point j is
                           // row j of pts); 0 otherwise
   Tuning tune;            // launch choices (lanes per cell, table load, filter, tail, pencil)
+  uint32_t* seq_aux;      // sequential update: 256 colour counts, 256 cursors, then the
+                          // level's cells in colour order (capAB words)
 };
 
 // Accumulators of one tracking window step (gs_track_window).
@@ -139,17 +141,31 @@ cudaError_t launch_track(const void* frame, bool f32, int d, int64_t width, int6
                          const int64_t* thr, const int64_t* bins, int64_t k, TrackAcc* acc,
                          uint8_t* present, cudaStream_t s);
 
+// The plan a key-range launch makes once the range is known (Sec. 2.1 i:
+// key packing, face table, neighbour offsets into fl->plan, fl->plan_status,
+// thr and dtab; the face table gets at most thr_cap entries), and the loop
+// kernel's start state it clears meanwhile: both occupancy filters
+// (filter_vec 16-byte words), n_st level states, the grid barrier, the result.
+struct PlanJob {
+  double h;
+  int B;
+  int64_t* thr;
+  uint64_t thr_cap;
+  uint64_t* dtab;
+  uint4* filters;
+  uint32_t filter_vec;
+  IterState* st;
+  uint32_t n_st;
+  GridBar* bar;
+  LoopResult* res;
+};
+
+// Key range, fixed-point window and finiteness of n points of dimension d
+// into fl; with job != null, the last block to finish also makes the plan.
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
-                         cudaStream_t s);
+                         const PlanJob* job, cudaStream_t s);
 // Binning, first pass.  offsets (device, B + 1 entries) give the points of
 // each instance of a batched run (B > 1); ignored when B == 1.
-// The plan from the key range in fl, into fl->plan (and fl->plan_status),
-// with the face table (at most thr_cap entries) and the neighbour offsets;
-// also clears the loop kernel's start state: both occupancy filters
-// (2 * kFilterWords words), n_st level states, the grid barrier, the result.
-cudaError_t launch_plan(int d, double h, int64_t n, int B, DevFlags* fl, int64_t* thr,
-                        uint64_t thr_cap, uint64_t* dtab, uint32_t* filters, IterState* st,
-                        uint32_t n_st, GridBar* bar, LoopResult* res, cudaStream_t s);
 // Binning with the plan in fl->plan (nothing runs unless fl->plan_status is 0).
 // A bandwidth sweep (sweep != null) bins B x n0 points: instance b's point j
 // is row j of pts, decided with sweep[b] (n = B x n0).

@@ -603,17 +603,22 @@ __device__ __forceinline__ bool colour_before(int p, uint32_t col) {
 // are updated, a neighbour of a lower colour (updated in an earlier pass of
 // this step) contributes its count times its new centroid from A.srow, and
 // each updated cell leaves that product in A.srow at its slot of level t.
-// The filter load and the links of level t-1 happen in pass 0 only.
+// The filter load and the links of level t-1 happen in the step's first pass
+// only (first).
 template <int D, int GS, bool BT, bool SEQ = false>
 __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask, uint32_t maskM,
                              uint32_t m_prev, uint32_t base_prev, uint32_t base, bool& any_nb,
-                             unsigned& inexact, unsigned& werr, int pen = 0, int col = 0) {
+                             unsigned& inexact, unsigned& werr, int pen = 0, int col = 0,
+                             const uint32_t* sel = nullptr, uint32_t nsel = 0,
+                             bool first = true) {
   static_assert(!(SEQ && BT), "the sequential update runs on plain runs only");
   constexpr int U = ProbeBatch<D, GS>::value > 2 ? 2 : ProbeBatch<D, GS>::value;
   const int lane = threadIdx.x & 31;
   const int glane = lane & (GS - 1);
   const unsigned gmask = GS == 32 ? kFull : (((1u << GS) - 1u) << (lane & ~(GS - 1)));
-  const uint32_t group = item_group<GS>(m);
+  // sequential passes update the nsel cells of colour col listed in sel
+  const uint32_t items = SEQ ? nsel : m;
+  const uint32_t group = item_group<GS>(items);
   const uint32_t ngroups = (gridDim.x * blockDim.x) / GS;
   const LevelTable G = A.tab[t % 3];
   const LevelTable P = pen == 2 ? A.ptab : A.tab[pen == 1 ? 2 : t % 3];  // the table probed
@@ -629,7 +634,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
   extern __shared__ uint4 s_dyn[];
   uint32_t* s_filter = reinterpret_cast<uint32_t*>(s_dyn);
   const int lg = filter_log2(m);
-  if (!SEQ || col == 0) {
+  if (!SEQ || first) {
     const uint4* src = reinterpret_cast<const uint4*>(A.filter[t & 1]);
     uint4* dst = reinterpret_cast<uint4*>(s_filter);
     const uint32_t n4 = (1u << lg) / 128;
@@ -650,9 +655,9 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
     }
     __syncthreads();
   }
-  for (uint32_t j = group; j < m; j += ngroups) {
+  for (uint32_t q = group; q < items; q += ngroups) {
+    const uint32_t j = SEQ ? sel[q] : q;
     const uint64_t key = c.key[j];
-    if (SEQ && key_colour<D>(key) != (uint32_t)col) continue;
     const uint32_t cj = c.cnt[j];
     // batched runs: a cell of an instance that has stopped is carried to the
     // next level unchanged (same key, its own exact sum)
@@ -773,7 +778,7 @@ __device__ void phase_update(const LoopArgs& A, int t, uint32_t m, uint32_t mask
     // sequential passes: what the later colours read for this cell
     if (SEQ && glane < D) A.srow[(size_t)G.list[j] * D + glane] = pack(V * (u128)mult);
   }
-  if (t > 0 && (!SEQ || col == 0)) {
+  if (t > 0 && (!SEQ || first)) {
     // level t-1: parent links, then its table is released
     const uint32_t tid = item_tid(m_prev);
     const uint32_t nth = gridDim.x * blockDim.x;
@@ -2293,6 +2298,32 @@ __device__ void run_tail32(const LoopArgs& A, int t, uint32_t m, uint32_t m_prev
   out.cell_iters = cell_iters;
 }
 
+// labels[i] = labslot[slot0[i]] for every point.  Where the labels are
+// 16-byte aligned, a thread takes two words of four points at once, so eight
+// independent gathers are in flight per thread (the loop is bound by the
+// latency of those gathers, not by bandwidth).
+__device__ __forceinline__ void write_labels(const LoopArgs& A, uint32_t tid, uint32_t nth) {
+  int64_t done = 0;
+  if (((uintptr_t)A.labels & 15u) == 0) {
+    const int64_t n4 = A.n / 4;
+    const uint4* __restrict__ s4 = reinterpret_cast<const uint4*>(A.slot0);
+    int4* __restrict__ l4 = reinterpret_cast<int4*>(A.labels);
+    const uint32_t* __restrict__ ls = A.labslot;
+    for (int64_t q = tid; q < n4; q += 2 * (int64_t)nth) {
+      const bool two = q + nth < n4;
+      const uint4 a = s4[q];
+      const uint4 b = two ? s4[q + nth] : make_uint4(0u, 0u, 0u, 0u);
+      const int4 la = make_int4((int)ls[a.x], (int)ls[a.y], (int)ls[a.z], (int)ls[a.w]);
+      int4 lb = make_int4(0, 0, 0, 0);
+      if (two) lb = make_int4((int)ls[b.x], (int)ls[b.y], (int)ls[b.z], (int)ls[b.w]);
+      l4[q] = la;
+      if (two) l4[q + nth] = lb;
+    }
+    done = n4 * 4;
+  }
+  for (int64_t i = done + tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
+}
+
 // The loop kernel.  SEQ: the sequential update of Eq. 5 (plain FP64 runs;
 // A.srow holds the shifted rows), a separate instantiation so that the
 // parallel kernels carry none of its code.
@@ -2317,6 +2348,10 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     return;
   }
 
+  // the sequential update's colour counts and cursors start at zero
+  if constexpr (SEQ) {
+    if (tid < 512) A.seq_aux[tid] = 0;
+  }
   // step i, second pass: exact cell sums
   const uint32_t m0 = *(volatile uint32_t*)&A.fl->m0;
   phase_count_totals(A, m0);
@@ -2456,11 +2491,43 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
         phase_update32<D, 32, BT>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb, pt,
                                   maskPt);
     } else if constexpr (SEQ) {
-      // Eq. 5: the colours one after another, each reading the ones before
-      for (int col = 0; col < (1 << D); ++col) {
-        if (col > 0 && !grid_sync(A.bar, A.fl)) return;
+      // Eq. 5: the colours one after another, each reading the ones before.
+      // The level's cells are first listed by colour (counts, offsets, then
+      // a scatter into colour order), so a pass reads only its own cells and
+      // an empty colour costs neither a pass nor a barrier.
+      constexpr int NC = 1 << D;
+      uint32_t* const chist = A.seq_aux;          // NC counts (zero here)
+      uint32_t* const ccur = A.seq_aux + 256;     // NC cursors (zero here)
+      uint32_t* const corder = A.seq_aux + 512;   // the cells in colour order
+      __shared__ uint32_t s_coff[NC + 1];
+      for (uint32_t j = tid; j < m; j += nth) atomicAdd(&chist[key_colour<D>(A.cells[t & 1].key[j])], 1u);
+      if (!grid_sync(A.bar, A.fl)) return;
+      if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int q = 0; q < NC; ++q) {
+          s_coff[q] = run;
+          run += __ldcg(&chist[q]);
+        }
+        s_coff[NC] = run;
+      }
+      __syncthreads();
+      for (uint32_t j = tid; j < m; j += nth) {
+        const uint32_t cl = key_colour<D>(A.cells[t & 1].key[j]);
+        corder[s_coff[cl] + atomicAdd(&ccur[cl], 1u)] = j;
+      }
+      if (!grid_sync(A.bar, A.fl)) return;
+      if (tid < (uint32_t)NC) {  // for the next step
+        chist[tid] = 0;
+        ccur[tid] = 0;
+      }
+      bool first = true;
+      for (int col = 0; col < NC; ++col) {
+        const uint32_t lo = s_coff[col], cnt = s_coff[col + 1] - lo;
+        if (cnt == 0) continue;
+        if (!first && !grid_sync(A.bar, A.fl)) return;
         phase_update<D, 32, false, true>(A, t, m, mask, maskM, m_prev, base_prev, base, any_nb,
-                                         inexact, werr, 0, col);
+                                         inexact, werr, 0, col, corder + lo, cnt, first);
+        first = false;
       }
     } else {
       if (GSmin < 32 && few_lanes)
@@ -2613,7 +2680,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   }
   if (!grid_sync(A.bar, A.fl)) return;
   if (numbered) {
-    for (int64_t i = tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
+    write_labels(A, tid, nth);
     const LevelTable G = A.tab[T % 3];
     const bool write = (int64_t)k <= A.modes_cap;
     for (uint32_t r = tid; r < k; r += nth) {

@@ -95,13 +95,13 @@ struct DevFlags {
   long long min_ord[kMaxD];     // order code of min_i x_ia
   long long max_ord[kMaxD];     // order code of max_i x_ia
   unsigned long long maxabs[kMaxD];  // bits of max_i |x_ia|
-  // the plan of the call (written by k_plan, or by the host), read by
+  // the plan of the call (written by the key-range kernel or the host), read by
   // binning and the loop kernel; nothing after the key range runs unless
   // plan_status is 0
   Plan plan;
   PlanSizes plan_sizes;
   uint32_t plan_status;
-  uint32_t pad;
+  uint32_t range_done;  // blocks of the key-range kernel that have published their extremes
 };
 
 // Segments of the loop kernel timed on the device clock by block 0 (between

@@ -1,8 +1,9 @@
 // gs_planner.cuh -- the per-call plan (Sec. 2.1 i: how floor(x / h) keys are
 // packed, the exact cell faces, the fixed-point windows) from the key range
-// of the input.  The same code runs on the device (k_plan, between the range
-// reduction and binning, so no host round trip separates them) and on the
-// host (when the face table is larger than the device-side capacity).
+// of the input.  The same code runs on the device (in the last block of the
+// key-range kernel, so no host round trip separates the range and binning)
+// and on the host (when the face table is larger than the device-side
+// capacity).
 #pragma once
 
 #include <cmath>

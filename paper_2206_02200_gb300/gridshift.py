@@ -523,24 +523,43 @@ class Tracker:
             raise GridShiftError(st, gs_get_last_error(self.ctx._ctx))
         return res.as_dict(), present
 
-    def step(self, frame) -> dict:
-        """Tracks one frame; returns the emitted window and the inner iterations."""
+    def _search_rect(self):
+        """The pixel rectangle searched next: the window's size divided by f
+        around the current centre."""
+        return window_rect(self.o, self.l / self.f, self.w / self.f)
+
+    def _absorb(self, r: dict, present) -> float | None:
+        """Folds one window result into the state.  No pixel of the reference
+        colours in the window: the window widens (x1.1 on both sides) and the
+        centre stays, which is not convergence (None).  Otherwise the centre
+        jumps to the mean position of those pixels, the reference colours
+        shrink to the ones seen, and each side of the window tightens
+        (x0.99) where the pixels' extent along it is below it, else loosens
+        (x1.01).  Returns how far the centre moved."""
         import math
-        inner = 0
-        for inner in range(1, self.max_inner + 1):
-            rect = window_rect(self.o, self.l / self.f, self.w / self.f)
-            r, present = self.window_step(frame, rect)
-            if r["count"] == 0:
-                self.l *= 1.1
-                self.w *= 1.1
-                continue
-            o_new = (r["mean_x"], r["mean_y"])
-            self.B = self.B[present.astype(bool)]
-            self.l *= 0.99 if (r["max_x"] - r["min_x"]) < self.l else 1.01
-            self.w *= 0.99 if (r["max_y"] - r["min_y"]) < self.w else 1.01
-            moved = math.hypot(o_new[0] - self.o[0], o_new[1] - self.o[1])
-            self.o = o_new
-            if moved < self.eta:
+        if r["count"] == 0:
+            self.l, self.w = 1.1 * self.l, 1.1 * self.w
+            return None
+        ext_x, ext_y = r["max_x"] - r["min_x"], r["max_y"] - r["min_y"]
+        self.l *= 0.99 if ext_x < self.l else 1.01
+        self.w *= 0.99 if ext_y < self.w else 1.01
+        self.B = self.B[present.astype(bool)]
+        centre = (r["mean_x"], r["mean_y"])
+        moved = math.hypot(centre[0] - self.o[0], centre[1] - self.o[1])
+        self.o = centre
+        return moved
+
+    def step(self, frame) -> dict:
+        """Tracks one frame (Sec. 2.3, Algorithm 2): window searches are
+        repeated until the centre settles (moves by less than eta) or
+        max_inner searches have run; returns the state the frame leaves (the
+        emitted window) and the number of searches."""
+        searches = 0
+        while searches < self.max_inner:
+            searches += 1
+            r, present = self.window_step(frame, self._search_rect())
+            moved = self._absorb(r, present)
+            if moved is not None and moved < self.eta:
                 break
-        return {"o": self.o, "length": self.l, "width": self.w, "inner": inner,
+        return {"o": self.o, "length": self.l, "width": self.w, "inner": searches,
                 "bins": int(self.B.shape[0])}

@@ -1,6 +1,7 @@
 """The library's planner (csrc/gs_planner.cuh), built for the host with g++,
-against exact arithmetic.  The same functions run on the device in k_plan and
-decide every cell key of Sec. 2.1 i, so they are checked here on the CPU:
+against exact arithmetic.  The same functions run on the device (the
+key-range kernel) and decide every cell key of Sec. 2.1 i, so they are
+checked here on the CPU:
   * plan_floor_div(x, h) = floor of the exact quotient x / h (Python
     Fractions), on random values and on both sides of exact cell faces;
   * plan_face(q, h) = the least double >= q h;
@@ -122,7 +123,7 @@ def test_packed_key_layout_and_probes(planner):
 
 
 def test_plan_from_key_range(planner):
-    # the whole plan from a key range (k_plan's input): per axis the key box
+    # the whole plan from a key range (the key-range kernel's input): per axis the key box
     # widened by one cell each side, the fixed-point unit 2^L with
     # L = e + ceil(log2 n) - 126 (max |x| < 2^e), the face-table offsets; and
     # the refusals: |x / h| >= 4e15, more than 2^22 cells on an axis, a packed
