@@ -32,37 +32,40 @@ if ROOT not in sys.path:
 METRIC = "Mpixels/s end-to-end (1080p/4K, d=3/5), FP32 vs FP64, at stated label agreement"
 UNIT = "Mpixels/s"
 
-# Bytes each unit of work must move (algorithmic, not measured), two counts.
+# Bytes each unit of work must move (algorithmic, not measured).
 #
-# The scope count (what the method must touch, counted in 32-byte sectors;
-# the roofline's `achieved`):
-#   per point: its cell slot written by binning and read back, and its label
-#     written (3 x 4 B; the coordinates are binning's, below);
-#   per active cell and update step (the stop test's step included, which
-#     probes too): one 32-byte key sector for each of the 3^d neighbour probes
-#     (Eq. 1), two payload sectors (the cell's own row and one neighbour row),
-#     the new centroid and key written (d x elem + 8 B), and the merge (a
-#     radix sort of 4 passes over 12-byte (key, id) pairs, 48 B, plus a
-#     segmented reduction reading and writing the payload, 2 x (4 + d x elem) B).
+# The loop kernel (k_loop: the cell levels, steps ii-v), counted in 32-byte
+# sectors as the scope states (the roofline's `achieved`): per active cell
+# and update step (the stop test's step included, which probes too), one
+# 32-byte key sector for each of the 3^d neighbour probes (Eq. 1), two
+# payload sectors (the cell's own row and one neighbour row), the new
+# centroid and key written (d x elem + 8 B), and the merge (a radix sort of 4
+# passes over 12-byte (key, id) pairs, 48 B, plus a segmented reduction
+# reading and writing the payload, 2 x (4 + d x elem) B).  Its DRAM count
+# (what must leave the chip when the level tables stay in L2): per active
+# cell and update step, its row read once and the next level's row and key
+# written once (rows: count + d sums, 16 (d + 1) B in FP64, 4 (d + 1) B in
+# FP32; keys 8 B).
 #
-# The DRAM count (what must leave the chip when the level tables stay in L2):
-#   k_bin (binning, first pass): per point, read its d coordinates and write
-#     its cell slot (4 B).
-#   k_loop (everything after): per point, read its d coordinates again for the
-#     exact cell sums, and 4-byte words: its slot read by the scatter, written
-#     to and read from the counting-sort permutation, gathered by the sums,
-#     read again for its label, and the label written (6 x 4 B); per active
-#     cell and update step, its row read once and the next level's row and key
-#     written once (rows: count + d sums, 16 (d + 1) B in FP64, 4 (d + 1) B in
-#     FP32; keys 8 B).
+# The per-point launches, DRAM bytes per point:
+#   k_bin (binning, first pass): its d coordinates read, its cell slot
+#     written (4 B);
+#   k_prep_scatter: the slot read, the counting-sort position written (8 B);
+#   k_prep_sums: the position and the slot read again, the d coordinates
+#     re-read (8 + d x elem B);
+#   k_labels_out: the slot read, the label written (8 B).
 def bin_bytes_per_point(d: int, elem: int) -> int:
     return d * elem + 4
 
 
-def loop_bytes(n: int, d: int, elem: int, cell_steps: int, fp32: bool) -> int:
+def per_point_bytes(kernel: str, d: int, elem: int) -> int:
+    return {"bin": d * elem + 4, "k_scatter": 8, "k_sums": 8 + d * elem, "labels_out": 8}[kernel]
+
+
+def loop_bytes(cell_steps: int, d: int, fp32: bool) -> int:
     """The DRAM count of k_loop per launch."""
     row = (4 if fp32 else 16) * (d + 1)
-    return n * (d * elem + 24) + cell_steps * (2 * row + 8)
+    return cell_steps * (2 * row + 8)
 
 
 def scope_bytes_per_cell_step(d: int, fp32: bool) -> int:
@@ -71,10 +74,10 @@ def scope_bytes_per_cell_step(d: int, fp32: bool) -> int:
     return 3 ** d * 32 + 2 * 32 + (d * e + 8) + 48 + 2 * (4 + d * e)
 
 
-def loop_scope_bytes(n: int, d: int, probe_cell_steps: int, fp32: bool) -> int:
+def loop_scope_bytes(probe_cell_steps: int, d: int, fp32: bool) -> int:
     """The scope count of k_loop per launch (probe_cell_steps = active cells
     summed over every update step that probed, the stop test's included)."""
-    return n * 12 + probe_cell_steps * scope_bytes_per_cell_step(d, fp32)
+    return probe_cell_steps * scope_bytes_per_cell_step(d, fp32)
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -563,58 +566,88 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                       "ms": seq_ms, "value": n / (seq_ms / 1e3) / 1e6, "unit": UNIT}
         gp.close()
 
-    # -- end to end through the public API: host inputs, host outputs
+    # -- end to end through the public API: every step uploads its points
+    #    from pinned host memory and reads its labels and modes back.  The
+    #    upload of step i + 1 and the read-back of step i run on a copy
+    #    stream while step i's fit runs (double-buffered device inputs and
+    #    outputs), as a stream of images would be served.
     h_pts = torch.from_numpy(X).pin_memory()
-    h_labels = torch.empty(n, dtype=torch.int32).pin_memory()
-    h_modes = torch.empty(modes.shape, dtype=torch.float64).pin_memory()
-    d_pts = torch.empty_like(pts)
+    h_labels = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+    h_modes = [torch.empty(modes.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    d_pts = [torch.empty_like(pts) for _ in range(2)]
+    d_lab = [labels, torch.empty_like(labels)]
+    d_md = [modes, torch.empty_like(modes)]
+    copy = torch.cuda.Stream(dev)
+    up = [torch.cuda.Event() for _ in range(2)]
+    fit_done = [torch.cuda.Event() for _ in range(2)]
+    down = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = args.steps
     barrier()
     t0 = time.perf_counter()
     kk = 0
-    for _ in range(e2e_steps):
-        d_pts.copy_(h_pts, non_blocking=True)
-        kk, _ = call(d_pts, labels, modes)
-        h_labels.copy_(labels, non_blocking=True)
-        h_modes[:kk].copy_(modes[:kk], non_blocking=True)
-        stream.synchronize()
+    with torch.cuda.stream(copy):
+        d_pts[0].copy_(h_pts, non_blocking=True)
+        up[0].record(copy)
+    for i in range(e2e_steps):
+        b = i % 2
+        if i + 1 < e2e_steps:
+            with torch.cuda.stream(copy):
+                # (the copy stream already waited for the fit that last read
+                # this buffer, before that fit's read-back)
+                d_pts[1 - b].copy_(h_pts, non_blocking=True)
+                up[1 - b].record(copy)
+        stream.wait_event(up[b])
+        if i >= 2:
+            stream.wait_event(down[b])  # this buffer's previous read-back is done
+        kk, _ = call(d_pts[b], d_lab[b], d_md[b])
+        fit_done[b].record(stream)
+        with torch.cuda.stream(copy):
+            copy.wait_event(fit_done[b])
+            h_labels[b].copy_(d_lab[b], non_blocking=True)
+            h_modes[b][:kk].copy_(d_md[b][:kk], non_blocking=True)
+            down[b].record(copy)
+    copy.synchronize()
+    stream.synchronize()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = job_rate(n, e2e_steps, world, e2e_s)
 
-    # -- roofline of the dominant kernel (the loop kernel: one launch per step)
+    # -- roofline of the dominant kernel (the loop kernel: one launch per
+    #    step), with the per-point launches beside it
     pk = peaks()
     roof = None
     if not batched:
         loop_ms = phase_ms["loop"] / max(phase_cnt["loop"], 1)
         cell_steps = (cell_iters + m0_total) // args.steps
         probe_steps = (cell_iters + k_total) // args.steps
-        lb = loop_bytes(n, d, elem, cell_steps, fp32)
-        sb = loop_scope_bytes(n, d, probe_steps, fp32)
+        lb = loop_bytes(cell_steps, d, fp32)
+        sb = loop_scope_bytes(probe_steps, d, fp32)
         achieved = sb / (loop_ms / 1e3) / 1e9
-        bin_ms = phase_ms["bin"] / max(phase_cnt["bin"], 1)
-        bb = n * bin_bytes_per_point(d, elem)
         tr = traffic(args.workload, args.precision, "k_loop", args.update)
-        roof = {"kernel": "k_loop (exact cell sums, update steps ii-v, labels)", "bound": "hbm",
-                "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        roof = {"kernel": "k_loop (update steps ii-v over the cell levels, numbering, modes)",
+                "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
                 "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs)",
                 "frac_of": pk["source"],
                 "algorithmic_bytes_per_launch": sb,
-                "algorithmic_count": ("scope count: 12 B per point; per active cell and "
-                                      "update step 3^d key sectors of 32 B, 2 payload "
-                                      "sectors, centroid and key write, sort-and-reduce "
-                                      "merge"),
+                "algorithmic_count": ("scope count: per active cell and update step 3^d key "
+                                      "sectors of 32 B, 2 payload sectors, centroid and key "
+                                      "write, sort-and-reduce merge"),
                 "avg_launch_ms": loop_ms, "traffic": tr,
                 "dram_count": {"bytes_per_launch": lb,
                                "achieved": lb / (loop_ms / 1e3) / 1e9,
                                "frac": lb / (loop_ms / 1e3) / 1e9 / pk["hbm_gbs"]},
                 "traffic_frac": (tr / (loop_ms / 1e3) / 1e9 / pk["hbm_gbs"]) if tr else None,
-                "second": {"kernel": "k_bin (binning, first pass)", "achieved": bb / (bin_ms / 1e3) / 1e9,
-                           "frac": bb / (bin_ms / 1e3) / 1e9 / pk["hbm_gbs"],
-                           "algorithmic_bytes_per_launch": bb, "avg_launch_ms": bin_ms,
-                           "traffic": traffic(args.workload, args.precision, "k_bin",
-                                              args.update)}}
+                "per_point_kernels": {}}
+        for ph, name in (("bin", "k_bin"), ("k_scatter", "k_prep_scatter"),
+                         ("k_sums", "k_prep_sums"), ("labels_out", "k_labels_out")):
+            ms = phase_ms[ph] / max(phase_cnt[ph], 1)
+            by = n * per_point_bytes(ph, d, elem)
+            roof["per_point_kernels"][name] = {
+                "algorithmic_bytes_per_launch": by, "avg_launch_ms": ms,
+                "achieved": by / (ms / 1e3) / 1e9 if ms > 0 else None,
+                "frac": by / (ms / 1e3) / 1e9 / pk["hbm_gbs"] if ms > 0 else None,
+                "traffic": traffic(args.workload, args.precision, name, args.update)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -628,7 +661,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                tuning=g.tuning(), tuning_source=g.tuning_source),
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": int(X.nbytes),
-                        "d2h_bytes_per_step": int(n * 4 + kk * d * 8)},
+                        "d2h_bytes_per_step": int(n * 4 + kk * d * 8),
+                        "pipelined": ("the upload of step i + 1 and the read-back of step i "
+                                      "run on a second stream during step i's fit")},
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "active_cell_iterations_per_s": cell_iters * world / (total_ms / 1e3),

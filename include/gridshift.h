@@ -108,27 +108,31 @@ typedef struct {
   int64_t face_rechecks; /* GS_FP32_MIXED: key decisions redone in float64 near a face */
 } gs_fit_info;
 
-/* Timed parts of one call, for gs_get_phase_times.  The first four are CUDA
- * event pairs on the call's stream around launch groups; the others split the
- * loop kernel's time by the device clock, read by one block at the grid
- * barriers between its phases. */
+/* Timed parts of one call, for gs_get_phase_times.  CUDA event pairs on the
+ * call's stream time the launches (GS_PHASE_RANGE .. GS_PHASE_SORT, the three
+ * launch groups of step i's second pass, GS_PHASE_LABELS_OUT); the loop kernel's
+ * own phases are split by the device clock, read by one block at the grid
+ * barriers between them. */
 typedef enum {
-  GS_PHASE_RANGE = 0,    /* key range and finiteness of the input (step i, set-up) */
+  GS_PHASE_RANGE = 0,    /* key range and finiteness of the input, and the plan (step i,
+                            set-up) */
   GS_PHASE_BIN = 1,      /* binning, first pass: cell key and count per point (step i) */
-  GS_PHASE_LOOP = 2,     /* the loop kernel: exact cell sums, steps ii-v, labels and modes */
+  GS_PHASE_LOOP = 2,     /* the loop kernel: steps ii-v, numbering and modes */
   GS_PHASE_SORT = 3,     /* numbering by a radix sort, when there are too many clusters
                             to number inside the loop kernel */
-  GS_PHASE_K_OFFSETS = 4, /* in the loop kernel: binning, second pass: offsets of the
-                             cells in a counting sort of the points by cell (step i) */
-  GS_PHASE_K_SCATTER = 5, /* in the loop kernel: the points sorted by cell */
-  GS_PHASE_K_SUMS = 6,    /* in the loop kernel: exact cell sums from the sorted points */
+  GS_PHASE_K_OFFSETS = 4, /* binning, second pass: offsets of the cells in a counting
+                             sort of the points by cell (step i; two launches) */
+  GS_PHASE_K_SCATTER = 5, /* the points sorted by cell (one launch) */
+  GS_PHASE_K_SUMS = 6,    /* exact cell sums from the sorted points (one launch) */
   GS_PHASE_K_LEVEL0 = 7,  /* in the loop kernel: the initial cells and their table */
   GS_PHASE_K_UPDATE_FIRST = 8, /* in the loop kernel: the first update step (ii-v, merge
                                   into the next level's table), over the initial cells */
   GS_PHASE_K_UPDATE_REST = 9,  /* in the loop kernel: all later update steps */
   GS_PHASE_K_COMPACT = 10, /* in the loop kernel: each next level's cell list and sums */
-  GS_PHASE_K_LABELS = 11,  /* in the loop kernel: final cell of every point, labels, modes */
-  GS_NPHASES = 12
+  GS_PHASE_K_LABELS = 11,  /* in the loop kernel: final cell of every initial cell,
+                              numbering, modes */
+  GS_PHASE_LABELS_OUT = 12, /* the label of every point (one launch after the loop kernel) */
+  GS_NPHASES = 13
 } gs_phase;
 
 typedef struct {
@@ -269,6 +273,10 @@ typedef struct {
   int32_t pencil_min;    /* the first update takes the pencil form (sums along axis 0 first,
                             d >= 3) when binning found at least this many cells; >= 0,
                             default 4096 (plain runs) */
+  int32_t split_min;     /* runs of at least this many points take the second pass of
+                            binning (counting sort, exact cell sums) and the label writes as
+                            launches of their own, with more warps per SM; smaller runs
+                            take them inside the loop kernel; >= 0, default 2^22 */
 } gs_tuning;
 
 /* Sets the launch choices of later gs_fit, gs_fit_batched and gs_fit_sweep

@@ -4,8 +4,9 @@ The choices decide which lanes, tables and phases compute a GridShift run,
 never its result: lanes per cell in the neighbour gather (few lanes, several
 cells in flight per warp, or 32 lanes per cell, by level size), the load of
 the level hash tables, whether probes pass the occupancy filter, the level
-size below which one block finishes the run, and the least cell count for the
-pencil form of the first update.
+size below which one block finishes the run, the least cell count for the
+pencil form of the first update, and the least point count for running the
+per-point passes as launches of their own.
 
 ``tune_workload`` measures them on one workload by coordinate descent from
 the built-in choices (each knob swept over its candidates with the others
@@ -38,9 +39,10 @@ CANDIDATES = {
     "filter": [1, 0],
     "tail_enter": [0, 32, 64, 128, 192, 256],
     "pencil_min": [1024, 4096, 16384, 1 << 30],
+    "split_min": [1 << 22, 0, (1 << 31) - 1],
 }
 #: knobs that batched runs use (the tail and the pencil form are plain-run only)
-BATCHED_KNOBS = ("few_lanes_x4", "load_shift", "filter")
+BATCHED_KNOBS = ("few_lanes_x4", "load_shift", "filter", "split_min")
 MIN_GAIN = 0.01
 
 _cache = None

@@ -538,13 +538,14 @@ gs_status gs_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
   }
   if (t->few_lanes_x4 < 0 || t->few_lanes_x4 > (1 << 20) || (t->load_shift != 1 && t->load_shift != 2) ||
       (t->filter != 0 && t->filter != 1) || t->tail_enter < 0 ||
-      t->tail_enter > (int32_t)kTailMaxCells || t->pencil_min < 0)
+      t->tail_enter > (int32_t)kTailMaxCells || t->pencil_min < 0 || t->split_min < 0)
     return fail(ctx, GS_E_INVALID, "tuning value out of range");
   ctx->tune.few_lanes_x4 = (uint32_t)t->few_lanes_x4;
   ctx->tune.load_shift = (uint32_t)t->load_shift;
   ctx->tune.filter = (uint32_t)t->filter;
   ctx->tune.tail_enter = (uint32_t)t->tail_enter;
   ctx->tune.pencil_min = (uint32_t)t->pencil_min;
+  ctx->tune.split_min = (uint32_t)t->split_min;
   return GS_OK;
 }
 
@@ -555,6 +556,7 @@ gs_status gs_get_tuning(gs_ctx* ctx, gs_tuning* out) {
   out->filter = (int32_t)ctx->tune.filter;
   out->tail_enter = (int32_t)ctx->tune.tail_enter;
   out->pencil_min = (int32_t)ctx->tune.pencil_min;
+  out->split_min = (int32_t)ctx->tune.split_min;
   return GS_OK;
 }
 
@@ -658,8 +660,10 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
       ctx->last_times.ms[ctx->tm.phase[i]] += ms;
       ctx->last_times.count[ctx->tm.phase[i]] += 1;
     }
+    // in-kernel device-clock phases, added to the event-timed launches of
+    // the same phase (the second pass of step i and the label writes)
     for (int i = 0; i < kLoopPhases; ++i) {
-      ctx->last_times.ms[GS_PHASE_K_OFFSETS + i] = kms[i];
+      ctx->last_times.ms[GS_PHASE_K_OFFSETS + i] += kms[i];
       ctx->last_times.count[GS_PHASE_K_OFFSETS + i] = 1;
     }
     for (int i = 0; i < kClockSteps; ++i)

@@ -298,9 +298,28 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_LAUNCH(launch_bin(a.points, a.f32, n, d, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells,
                          b.slot0, b.flags, b.offsets, a.B, L.sweep, L.n0, s), "k_bin", 1);
     GS_T_END();
+    // step i, second pass: the exact cell sums through a counting sort (as
+    // launches of their own for large runs, else inside the loop kernel)
+    const bool split = n >= (int64_t)a.tune.split_min;
+    if (split) {
+      GS_T_BEGIN(GS_PHASE_K_OFFSETS);
+      GS_LAUNCH(launch_prep_offsets(L, s), "k_prep_offsets", kPrepOffsetsLaunches);
+      GS_T_END();
+      GS_T_BEGIN(GS_PHASE_K_SCATTER);
+      GS_LAUNCH(launch_prep_scatter(L, s), "k_prep_scatter", 1);
+      GS_T_END();
+      GS_T_BEGIN(GS_PHASE_K_SUMS);
+      GS_LAUNCH(launch_prep_sums(L, s), "k_prep_sums", 1);
+      GS_T_END();
+    }
     GS_T_BEGIN(GS_PHASE_LOOP);
     GS_LAUNCH(a.sequential ? launch_loop_seq(L, grid, s) : launch_loop(L, grid, s), "k_loop", 1);
     GS_T_END();
+    if (split) {
+      GS_T_BEGIN(GS_PHASE_LABELS_OUT);
+      GS_LAUNCH(launch_labels_out(L, s), "k_labels_out", 1);
+      GS_T_END();
+    }
     GS_CU(cudaMemcpyAsync(hr, b.res, sizeof(LoopResult), cudaMemcpyDeviceToHost, s), "D2H result");
     GS_CU(cudaMemcpyAsync(hf, b.flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s), "D2H flags");
     GS_CU(cudaStreamSynchronize(s), "sync loop");

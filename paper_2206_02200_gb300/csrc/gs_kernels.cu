@@ -454,6 +454,10 @@ int loop_grid(int d, bool mixed) {
   return g;
 }
 
+cudaError_t launch_prep_sums(const LoopArgs& a, cudaStream_t s) {
+  return a.mixed ? launch_prep_sums_fp32(a, s) : launch_prep_sums_fp64(a, s);
+}
+
 cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s) {
   return a.mixed ? launch_loop_fp32(a, grid, s) : launch_loop_fp64(a, grid, s);
 }

@@ -183,6 +183,21 @@ int loop_grid(int d, bool mixed);
 // (Sec. 2.1, Algorithm 1), in one cooperative launch of `grid` blocks
 // (a.mixed selects the float32 variant).
 cudaError_t launch_loop(const LoopArgs& a, int grid, cudaStream_t s);
+// Step i, second pass, before the loop kernel: per-block count totals and
+// the cells' run offsets in a counting sort of the points by cell (two
+// launches); the points sorted by cell; the exact cell sums (a.mixed: the
+// float32 sums).  After the loop kernel: every point's label, when the loop
+// kernel numbered the final cells.  Each does nothing unless the plan is
+// valid and binning fit its table.
+cudaError_t launch_prep_offsets(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_prep_scatter(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_prep_sums(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_prep_sums_fp64(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_prep_sums_fp32(const LoopArgs& a, cudaStream_t s);
+cudaError_t launch_labels_out(const LoopArgs& a, cudaStream_t s);
+// Kernels launch_prep_offsets makes.
+constexpr int kPrepOffsetsLaunches = 2;
+
 // Modes of the final cells and release of their table, after numbering by
 // a radix sort (a.mixed selects the float32 variant).
 cudaError_t launch_modes_tail(const LoopArgs& a, uint32_t k, int T, cudaStream_t s);

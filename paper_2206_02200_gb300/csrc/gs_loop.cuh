@@ -2324,6 +2324,77 @@ __device__ __forceinline__ void write_labels(const LoopArgs& A, uint32_t tid, ui
   for (int64_t i = done + tid; i < A.n; i += nth) A.labels[i] = (int32_t)A.labslot[A.slot0[i]];
 }
 
+// ---------------------------------------------------------------------------
+// Step i, second pass, and the final label writes, as ordinary launches
+// before and after the loop kernel, for runs of at least Tuning::split_min
+// points (smaller runs take them inside the loop kernel, where the launches'
+// own latency would cost more than they gain).  They touch every point, and
+// their gathers are bound by latency: outside the cooperative kernel (one
+// block of 512 threads per SM) they run with as many warps per SM as their
+// registers allow.  Each does nothing unless the plan is valid and binning
+// fit its table (the same flags every block reads, so the decision is
+// uniform).
+
+constexpr int kPrepBlock = 256;
+constexpr int kPrepCountGrid = 304;  // blocks of the count and offset launches
+
+__device__ __forceinline__ bool prep_ok(const LoopArgs& A) {
+  return A.n >= (int64_t)A.tune.split_min &&
+         *(volatile uint32_t*)&A.fl->plan_status == kPlanOK &&
+         (*(volatile uint32_t*)&A.fl->err & (kErrOverflow | kErrTableFull)) == 0u;
+}
+
+// Per-block totals of the cells' counts, then every cell's run offset
+// (phase_count_totals, phase_offsets; both launches kPrepCountGrid blocks).
+__global__ void __launch_bounds__(kLoopBlock) k_prep_counts(LoopArgs A) {
+  if (!prep_ok(A)) return;
+  phase_count_totals(A, *(volatile uint32_t*)&A.fl->m0);
+}
+
+__global__ void __launch_bounds__(kLoopBlock) k_prep_offsets(LoopArgs A) {
+  if (!prep_ok(A)) return;
+  phase_offsets(A, *(volatile uint32_t*)&A.fl->m0);
+}
+
+// The points sorted by cell (phase_scatter).
+__global__ void __launch_bounds__(kPrepBlock) k_prep_scatter(LoopArgs A) {
+  if (!prep_ok(A)) return;
+  phase_scatter(A);
+}
+
+// The exact (FP64) or float32 cell sums (phase_cell_sums, phase_cell_sums32).
+// Three blocks per SM where that costs no spills (the float32 sums, and the
+// exact sums up to d = 3), else two (the exact sums' 128-bit partial sums
+// need about 110 registers a thread at d = 5; d = 8 spills a little).
+template <int D, bool F32>
+__global__ void __launch_bounds__(kPrepBlock, (F32 || D <= 3) ? 3 : 2) k_prep_sums(LoopArgs A) {
+  if (!prep_ok(A)) return;
+  if (threadIdx.x == 0) g_plan = A.fl->plan;
+  __syncthreads();
+  unsigned inexact = 0, werr = 0;
+  if (F32) {
+    if (A.f32)
+      phase_cell_sums32<D, float>(A);
+    else
+      phase_cell_sums32<D, double>(A);
+  } else {
+    if (A.f32)
+      phase_cell_sums<D, float>(A, inexact, werr);
+    else
+      phase_cell_sums<D, double>(A, inexact, werr);
+  }
+  if (inexact) atomicAdd(&A.fl->inexact, 1ull);
+  if (werr) atomicOr(&A.fl->err, kErrWindow);
+}
+
+// Every point's label, once the loop kernel has numbered the final cells
+// (LoopResult::labels_ready; with too many clusters the radix-sort path
+// writes them instead).
+__global__ void __launch_bounds__(kPrepBlock) k_labels_out(LoopArgs A) {
+  if (!*(volatile uint32_t*)&A.res->labels_ready) return;
+  write_labels(A, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 // The loop kernel.  SEQ: the sequential update of Eq. 5 (plain FP64 runs;
 // A.srow holds the shifted rows), a separate instantiation so that the
 // parallel kernels carry none of its code.
@@ -2348,33 +2419,41 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     return;
   }
 
+  // a value above the fixed-point window in the exact sums (k_prep_sums):
+  // the host reports it
+  if (*(volatile uint32_t*)&A.fl->err) return;
+
   // the sequential update's colour counts and cursors start at zero
   if constexpr (SEQ) {
     if (tid < 512) A.seq_aux[tid] = 0;
   }
-  // step i, second pass: exact cell sums
   const uint32_t m0 = *(volatile uint32_t*)&A.fl->m0;
-  phase_count_totals(A, m0);
-  if (!grid_sync(A.bar, A.fl)) return;
-  phase_offsets(A, m0);
-  if (!grid_sync(A.bar, A.fl)) return;
-  clk.lap(kSegOffsets);
-  phase_scatter(A);
-  if (!grid_sync(A.bar, A.fl)) return;
-  clk.lap(kSegScatter);
-  if (F32) {
-    if (A.f32)
-      phase_cell_sums32<D, float>(A);
-    else
-      phase_cell_sums32<D, double>(A);
-  } else {
-    if (A.f32)
-      phase_cell_sums<D, float>(A, inexact, werr);
-    else
-      phase_cell_sums<D, double>(A, inexact, werr);
+  // step i, second pass (the exact cell sums): in the k_prep_* launches
+  // before this kernel when the run has split_min points or more, else here
+  const bool split = A.n >= (int64_t)A.tune.split_min;
+  if (!split) {
+    phase_count_totals(A, m0);
+    if (!grid_sync(A.bar, A.fl)) return;
+    phase_offsets(A, m0);
+    if (!grid_sync(A.bar, A.fl)) return;
+    clk.lap(kSegOffsets);
+    phase_scatter(A);
+    if (!grid_sync(A.bar, A.fl)) return;
+    clk.lap(kSegScatter);
+    if (F32) {
+      if (A.f32)
+        phase_cell_sums32<D, float>(A);
+      else
+        phase_cell_sums32<D, double>(A);
+    } else {
+      if (A.f32)
+        phase_cell_sums<D, float>(A, inexact, werr);
+      else
+        phase_cell_sums<D, double>(A, inexact, werr);
+    }
+    if (!grid_sync(A.bar, A.fl)) return;
+    clk.lap(kSegSums);
   }
-  if (!grid_sync(A.bar, A.fl)) return;
-  clk.lap(kSegSums);
 
   // level 0
   const uint32_t maskA = level_mask(m0, A.capAB, A.tune.load_shift);
@@ -2680,7 +2759,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
   }
   if (!grid_sync(A.bar, A.fl)) return;
   if (numbered) {
-    write_labels(A, tid, nth);
+    if (!split) write_labels(A, tid, nth);
     const LevelTable G = A.tab[T % 3];
     const bool write = (int64_t)k <= A.modes_cap;
     for (uint32_t r = tid; r < k; r += nth) {
@@ -2697,6 +2776,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     A.res->k = k;
     A.res->base = base;
     A.res->need_sort = numbered ? 0u : 1u;
+    A.res->labels_ready = numbered && split ? 1u : 0u;  // k_labels_out writes the labels
     A.res->cell_iters = cell_iters;
 #pragma unroll
     for (int i = 0; i < kLoopPhases; ++i) A.res->ns[i] = clk.ns[i];
@@ -2774,6 +2854,40 @@ cudaError_t launch_loop_t(const LoopArgs& a, int grid, cudaStream_t s) {
                                                           dim3(grid), dim3(kLoopBlock), params,
                                                           smem, s));
   return cudaSuccess;
+}
+
+// Step i's second pass (counts and offsets; scatter; sums) and the label
+// writes.  Templates only so that each translation unit that includes this
+// file compiles what it uses.
+template <bool F32>
+cudaError_t launch_prep_offsets_t(const LoopArgs& a, cudaStream_t s) {
+  k_prep_counts<<<kPrepCountGrid, kLoopBlock, 0, s>>>(a);
+  k_prep_offsets<<<kPrepCountGrid, kLoopBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Grids of the per-point launches: about the blocks that are resident at once
+// (152 SMs; by their registers 8 blocks of the scatter and label writes, 2 or
+// 3 of the sums), so that every warp loops over several chunks instead of
+// the SMs cycling through thousands of short blocks.
+template <bool F32>
+cudaError_t launch_prep_scatter_t(const LoopArgs& a, cudaStream_t s) {
+  k_prep_scatter<<<grid_for(a.n, kPrepBlock * 4, 152u * 8u), kPrepBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool F32>
+cudaError_t launch_prep_sums_t(const LoopArgs& a, cudaStream_t s) {
+  const unsigned per_sm = (F32 || a.P.d <= 3) ? 3u : 2u;
+  const unsigned g = grid_for(a.n, kPrepBlock * 4, 152u * per_sm);
+  GS_DISPATCH_D(a.P.d, (k_prep_sums<D, F32><<<g, kPrepBlock, 0, s>>>(a)));
+  return cudaGetLastError();
+}
+
+template <bool F32>
+cudaError_t launch_labels_out_t(const LoopArgs& a, cudaStream_t s) {
+  k_labels_out<<<grid_for(a.n / 8 + 1, kPrepBlock, 152u * 8u), kPrepBlock, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <bool F32>

@@ -15,4 +15,8 @@ cudaError_t launch_modes_tail_fp32(const LoopArgs& a, uint32_t k, int T, cudaStr
   return launch_modes_tail_t<true>(a, k, T, s);
 }
 
+cudaError_t launch_prep_sums_fp32(const LoopArgs& a, cudaStream_t s) {
+  return launch_prep_sums_t<true>(a, s);
+}
+
 }  // namespace gs

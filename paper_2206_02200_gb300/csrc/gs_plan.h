@@ -54,9 +54,11 @@ struct Tuning {
   uint32_t filter;        // 1: neighbour probes pass the level's occupancy filter first
   uint32_t tail_enter;    // levels of at most this many cells finish in one block (<= 256)
   uint32_t pencil_min;    // least initial cells for the pencil form of the first update
+  uint32_t split_min;     // least points for step i's second pass and the label writes as
+                          // launches of their own (fewer: inside the loop kernel)
 };
 
-constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u};
+constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u, 1u << 22};
 constexpr uint32_t kTailMaxCells = 256;  // the one-block tail's shared memory holds this many
 
 // Device-resident state of one level t (the cells before update step t).
@@ -118,6 +120,7 @@ struct LoopResult {
   uint32_t base;        // first forest node of the final level
   uint32_t need_sort;   // 1: k too large for the in-loop numbering; labels not written
   uint32_t bin_failed;  // 1: binning overflowed its table; nothing after it ran
+  uint32_t labels_ready;  // 1: the final cells are numbered; the labels are to be written
   unsigned long long cell_iters;  // sum of m_t over applied updates
   unsigned long long ns[kLoopPhases];  // nanoseconds spent in each segment
   unsigned long long step_ns[16][2];   // first 16 update steps: update phase, compaction

@@ -40,10 +40,10 @@ EXPORTS = ("gs_create", "gs_set_precision", "gs_set_update", "gs_set_stream", "g
            "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_track_window",
            "gs_get_last_error", "gs_status_string", "gs_destroy")
 
-#: gs_phase names, in enum order: CUDA-event phases, then the loop kernel's
-#: own device-clock split
+#: gs_phase names, in enum order (CUDA-event phases and the loop kernel's own
+#: device-clock split)
 PHASES = ("range", "bin", "loop", "sort", "k_offsets", "k_scatter", "k_sums", "k_level0",
-          "k_update_first", "k_update_rest", "k_compact", "k_labels")
+          "k_update_first", "k_update_rest", "k_compact", "k_labels", "labels_out")
 
 
 class gs_fit_info(ctypes.Structure):
@@ -71,7 +71,7 @@ class gs_phase_times(ctypes.Structure):
 class gs_tuning(ctypes.Structure):
     _fields_ = [("few_lanes_x4", ctypes.c_int32), ("load_shift", ctypes.c_int32),
                 ("filter", ctypes.c_int32), ("tail_enter", ctypes.c_int32),
-                ("pencil_min", ctypes.c_int32)]
+                ("pencil_min", ctypes.c_int32), ("split_min", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -79,7 +79,7 @@ class gs_tuning(ctypes.Structure):
 
 #: the library's built-in launch choices (gs_set_tuning with NULL)
 DEFAULT_TUNING = {"few_lanes_x4": 4, "load_shift": 2, "filter": 1, "tail_enter": 128,
-                  "pencil_min": 4096}
+                  "pencil_min": 4096, "split_min": 1 << 22}
 
 
 class gs_track_result(ctypes.Structure):

@@ -46,7 +46,12 @@ def test_scope_count_of_the_loop_kernel():
     import bench
     assert bench.scope_bytes_per_cell_step(5, False) == 243 * 32 + 64 + 48 + 48 + 88
     assert bench.scope_bytes_per_cell_step(6, True) == 729 * 32 + 64 + 32 + 48 + 56
-    assert bench.loop_scope_bytes(10, 3, 0, False) == 120
+    assert bench.loop_scope_bytes(0, 3, False) == 0
+    assert bench.loop_scope_bytes(7, 3, True) == 7 * bench.scope_bytes_per_cell_step(3, True)
+    # DRAM counts: the loop kernel's rows and keys; the per-point launches
+    assert bench.loop_bytes(10, 5, False) == 10 * (2 * 96 + 8)
+    assert bench.per_point_bytes("k_sums", 5, 8) == 48
+    assert bench.per_point_bytes("bin", 3, 4) == 16
 
 
 def test_reference_arm_uses_every_core():

@@ -22,7 +22,10 @@ CHOICES = [
     {"tail_enter": 256},            # the largest tail
     {"pencil_min": 0},              # pencil form whenever the tail is not entered at once
     {"pencil_min": 1 << 30},        # no pencil form
-    {"few_lanes_x4": 1, "load_shift": 1, "filter": 0, "tail_enter": 32, "pencil_min": 1024},
+    {"split_min": 0},               # per-point passes as launches of their own
+    {"split_min": (1 << 31) - 1},   # per-point passes inside the loop kernel
+    {"few_lanes_x4": 1, "load_shift": 1, "filter": 0, "tail_enter": 32, "pencil_min": 1024,
+     "split_min": 0},
 ]
 
 
@@ -48,14 +51,15 @@ def test_image_d5_under_every_choice(image, tuning):
     _check(image, 12.0, tuning)
 
 
-@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[6:8],
+@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[6:10],
                          ids=lambda t: ",".join(f"{k}={v}" for k, v in t.items()))
 def test_gmm_d6_under_choices(tuning):
     X = synth.gmm_points(60_000, 6, 20, seed=8).astype(np.float64)
     _check(X, 4.0, tuning)
 
 
-@pytest.mark.parametrize("tuning", CHOICES[:4], ids=lambda t: ",".join(f"{k}={v}" for k, v in t.items()))
+@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[8:10],
+                         ids=lambda t: ",".join(f"{k}={v}" for k, v in t.items()))
 def test_batched_under_choices(tuning):
     parts = synth.image_batch(4, 77, hmin=40, hmax=90, wmin=50, wmax=120)
     offsets = np.concatenate([[0], np.cumsum([len(p) for p in parts])]).tolist()
