@@ -86,8 +86,8 @@ def loop_scope_bytes(probe_cell_steps: int, d: int, fp32: bool) -> int:
 # on (the files that define k_range, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
-    ("image_1080p_d5", "fp64", "k_loop"): (139.71e6, "d236db15bdb005c3"),
-    ("image_1080p_d5", "fp64", "k_bin"): (91.92e6, "d236db15bdb005c3"),
+    ("image_1080p_d5", "fp64", "k_loop"): (138.89e6, "ec0d2c1af0736880"),
+    ("image_1080p_d5", "fp64", "k_bin"): (89.20e6, "ec0d2c1af0736880"),
 }
 
 
@@ -434,6 +434,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     g = gridshift.GridShift(d, w["h"], w["max_iter"], precision=prec, update=form,
                             tuning="auto" if args.tuning == "auto" else None)
     g._apply_auto_tuning(n, batched)
+    if args.tune:
+        t = g.tuning()
+        for kv in args.tune:
+            k, v = kv.split("=", 1)
+            t[k] = int(v, 0)
+        if gridshift.gs_set_tuning(g._ctx, t) != gridshift.GS_OK:
+            raise SystemExit(f"bad --tune {args.tune}")
+        g.tuning_source += " + " + ",".join(args.tune)
     pts = torch.from_numpy(X).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     modes = torch.empty((max(n // 16, 4096), d), dtype=torch.float64, device=dev)
@@ -622,6 +630,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         probe_steps = (cell_iters + k_total) // args.steps
         lb = loop_bytes(cell_steps, d, fp32)
         sb = loop_scope_bytes(probe_steps, d, fp32)
+        # below split_min points the per-point passes run inside k_loop:
+        # their bytes are k_loop's
+        split = n >= g.tuning()["split_min"]
+        inner = () if split else ("k_scatter", "k_sums", "labels_out")
+        pp = n * sum(per_point_bytes(ph, d, elem) for ph in inner)
+        lb += pp
+        sb += pp
         achieved = sb / (loop_ms / 1e3) / 1e9
         tr = traffic(args.workload, args.precision, "k_loop", args.update)
         roof = {"kernel": "k_loop (update steps ii-v over the cell levels, numbering, modes)",
@@ -632,15 +647,19 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "algorithmic_bytes_per_launch": sb,
                 "algorithmic_count": ("scope count: per active cell and update step 3^d key "
                                       "sectors of 32 B, 2 payload sectors, centroid and key "
-                                      "write, sort-and-reduce merge"),
+                                      "write, sort-and-reduce merge"
+                                      + ("" if split else "; plus the per-point passes it runs "
+                                         "(scatter 8 B, sums 8 + d x elem B, labels 8 B per "
+                                         "point)")),
                 "avg_launch_ms": loop_ms, "traffic": tr,
                 "dram_count": {"bytes_per_launch": lb,
                                "achieved": lb / (loop_ms / 1e3) / 1e9,
                                "frac": lb / (loop_ms / 1e3) / 1e9 / pk["hbm_gbs"]},
                 "traffic_frac": (tr / (loop_ms / 1e3) / 1e9 / pk["hbm_gbs"]) if tr else None,
                 "per_point_kernels": {}}
-        for ph, name in (("bin", "k_bin"), ("k_scatter", "k_prep_scatter"),
-                         ("k_sums", "k_prep_sums"), ("labels_out", "k_labels_out")):
+        for ph, name in (("bin", "k_bin"),) + ((("k_scatter", "k_prep_scatter"),
+                                                ("k_sums", "k_prep_sums"),
+                                                ("labels_out", "k_labels_out")) if split else ()):
             ms = phase_ms[ph] / max(phase_cnt[ph], 1)
             by = n * per_point_bytes(ph, d, elem)
             roof["per_point_kernels"][name] = {
@@ -899,6 +918,8 @@ def main():
     ap.add_argument("--tuning", choices=["auto", "default"], default="auto",
                     help="launch choices: the autotuner's cached entry for the workload "
                          "(auto, default) or the library's built-in ones")
+    ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
+                    help="override one launch choice (gs_tuning field) after the above")
     args = ap.parse_args()
     if args.update == "sequential" and (args.precision != "fp64" or
                                         args.workload.startswith(("batch", "track", "sweep"))):
