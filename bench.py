@@ -92,7 +92,9 @@ TRAFFIC = {
 
 
 KERNEL_SOURCES = ("gs_common.cuh", "gs_device.cuh", "gs_kernels.cu", "gs_kernels.h",
-                  "gs_loop.cuh", "gs_loop32.cu", "gs_loop64.cu", "gs_plan.h", "gs_planner.cuh")
+                  "gs_loop.cuh", "gs_loop_base.cuh", "gs_loop_fp64.cuh", "gs_loop_fp32.cuh",
+                  "gs_loop_tail.cuh", "gs_loop_kernel.cuh", "gs_loop32.cu", "gs_loop64.cu",
+                  "gs_plan.h", "gs_planner.cuh")
 
 
 def sources_hash() -> str:
