@@ -86,8 +86,23 @@ def loop_scope_bytes(probe_cell_steps: int, d: int, fp32: bool) -> int:
 # on (the files that define k_range, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
-    ("image_1080p_d5", "fp64", "k_loop"): (138.89e6, "ec0d2c1af0736880"),
-    ("image_1080p_d5", "fp64", "k_bin"): (89.20e6, "ec0d2c1af0736880"),
+    ("image_1080p_d5", "fp64", "k_loop"): (138.13e6, "f73bd0d3821ab3d0"),
+    ("image_1080p_d5", "fp64", "k_bin"): (89.03e6, "f73bd0d3821ab3d0"),
+    # the 4M-point mixture with the per-point passes as launches of their own
+    # (--tune split_min=0)
+    ("gmm_4M_d6", "fp64", "k_loop"): (1427.94e6, "f73bd0d3821ab3d0"),
+    ("gmm_4M_d6", "fp64", "k_bin"): (110.16e6, "f73bd0d3821ab3d0"),
+    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.02e6, "f73bd0d3821ab3d0"),
+    ("gmm_4M_d6", "fp64", "k_prep_sums"): (366.48e6, "f73bd0d3821ab3d0"),
+    ("gmm_4M_d6", "fp32", "k_loop"): (870.83e6, "f73bd0d3821ab3d0"),
+    # the 10M-point mixture: the 4M-point captures scaled by the units one
+    # launch processes (points for the per-point kernels, x 2.5; active
+    # cell-updates for k_loop, 285,298 against 205,764, x 1.3865)
+    ("gmm_10M_d6", "fp64", "k_loop"): (1979.8e6, "f73bd0d3821ab3d0"),
+    ("gmm_10M_d6", "fp64", "k_bin"): (275.4e6, "f73bd0d3821ab3d0"),
+    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.05e6, "f73bd0d3821ab3d0"),
+    ("gmm_10M_d6", "fp64", "k_prep_sums"): (916.2e6, "f73bd0d3821ab3d0"),
+    ("gmm_10M_d6", "fp32", "k_loop"): (1207.4e6, "f73bd0d3821ab3d0"),
 }
 
 
