@@ -277,6 +277,9 @@ typedef struct {
                             binning (counting sort, exact cell sums) and the label writes as
                             launches of their own, with more warps per SM; smaller runs
                             take them inside the loop kernel; >= 0, default 2^22 */
+  int32_t bin_list;      /* 1 (default): binning lists the new cells of each warp 32 at a
+                            time, one add on the (single) cell count for each 32, with five
+                            blocks per SM; 0: one add per new cell, six blocks per SM */
 } gs_tuning;
 
 /* Sets the launch choices of later gs_fit, gs_fit_batched and gs_fit_sweep

@@ -5,8 +5,8 @@ never its result: lanes per cell in the neighbour gather (few lanes, several
 cells in flight per warp, or 32 lanes per cell, by level size), the load of
 the level hash tables, whether probes pass the occupancy filter, the level
 size below which one block finishes the run, the least cell count for the
-pencil form of the first update, and the least point count for running the
-per-point passes as launches of their own.
+pencil form of the first update, the least point count for running the
+per-point passes as launches of their own, and how binning lists new cells.
 
 ``tune_workload`` measures them on one workload by coordinate descent from
 the built-in choices (each knob swept over its candidates with the others
@@ -40,9 +40,10 @@ CANDIDATES = {
     "tail_enter": [0, 32, 64, 128, 192, 256],
     "pencil_min": [1024, 4096, 16384, 1 << 30],
     "split_min": [1 << 22, 0, (1 << 31) - 1],
+    "bin_list": [1, 0],
 }
 #: knobs that batched runs use (the tail and the pencil form are plain-run only)
-BATCHED_KNOBS = ("few_lanes_x4", "load_shift", "filter", "split_min")
+BATCHED_KNOBS = ("few_lanes_x4", "load_shift", "filter", "split_min", "bin_list")
 MIN_GAIN = 0.01
 
 _cache = None

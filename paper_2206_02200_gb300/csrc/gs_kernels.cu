@@ -251,13 +251,17 @@ __device__ void plan_block(int d, int64_t n, const PlanJob& J, DevFlags* fl) {
     plan_probe(s_plan, p, J.dtab + p, vpack + p);
 }
 
-template <int D, typename T>
-__global__ void __launch_bounds__(kBlock, 6)
+// LISTED: new cells are listed per warp, 32 at a time (five blocks per SM:
+// the warp's list costs registers); else each new cell takes one add on the
+// cell count (six blocks per SM).  Tuning::bin_list chooses.
+template <int D, typename T, bool LISTED>
+__global__ void __launch_bounds__(kBlock, LISTED ? 5 : 6)
     k_bin(const T* __restrict__ pts, int64_t n, const int64_t* __restrict__ thr,
           BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
           DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B,
           const SweepPlan* __restrict__ sweep, uint32_t n0) {
   __shared__ __align__(16) T s_pts[kWarps][32 * D];
+  __shared__ uint32_t s_new[kWarps][32];  // a warp's new cells not yet listed
   __shared__ Plan s_plan;
   __shared__ uint32_t s_ok;
   // the plan, into shared memory (nothing runs unless it is valid)
@@ -271,6 +275,23 @@ __global__ void __launch_bounds__(kBlock, 6)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // LISTED: new cells are listed per warp, 32 at a time.  The cell count is
+  // one address for the whole grid, where atomics from different warps
+  // serialise (about 0.7 ns each on GB300): one add per new cell costs 0.2 ms
+  // on a 4K image's 268k cells.
+  uint32_t pend = 0;  // entries of s_new[w] (warp-uniform)
+  auto list_cells = [&](uint32_t& cnt) {
+    __syncwarp();
+    uint32_t b0 = 0;
+    if (lane == 0) b0 = atomicAdd(&fl->m0, cnt);
+    b0 = __shfl_sync(kFull, b0, 0);
+    if ((uint32_t)lane < cnt) {
+      const uint32_t id = b0 + lane;
+      if (id < maxcells) T0.list[id] = s_new[w][lane]; else atomicOr(&fl->err, kErrOverflow);
+    }
+    __syncwarp();
+    cnt = 0;
+  };
   for (int64_t base = gwarp * 32; base < n; base += nwarps * 32) {
     const int cnt = n - base < 32 ? (int)(n - base) : 32;
     if (!sweep) stage_points<T>(pts + base * D, cnt * D, s_pts[w], vec_ok, lane);
@@ -304,21 +325,29 @@ __global__ void __launch_bounds__(kBlock, 6)
     const unsigned peers = __match_any_sync(kFull, key);
     const int leader = __ffs(peers) - 1;
     uint32_t s = kNone;
+    bool won = false;
     if (valid && lane == leader) {
-      bool won;
       s = table_insert(T0.key, mask0, key, won, &fl->err);
       if (s != kNone) {
-        if (won) {
+        if (!LISTED && won) {
           const uint32_t id = atomicAdd(&fl->m0, 1u);
           if (id < maxcells) T0.list[id] = s; else atomicOr(&fl->err, kErrOverflow);
         }
         atomicAdd(&T0.cnt[s], (uint32_t)__popc(peers));
       }
+      won = won && s != kNone;
+    }
+    if constexpr (LISTED) {
+      const unsigned wm = __ballot_sync(kFull, won);
+      if (pend + __popc(wm) > 32) list_cells(pend);
+      if (won) s_new[w][pend + __popc(wm & ((1u << lane) - 1u))] = s;
+      pend += __popc(wm);
     }
     s = __shfl_sync(kFull, s, leader);
     if (valid) slot0[base + lane] = s;
     __syncwarp();
   }
+  if (LISTED && pend) list_cells(pend);
 }
 
 // Labels and modes when the final cells were too many to number inside
@@ -390,19 +419,20 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, const int64_t* offsets, int B, const SweepPlan* sweep,
-                       uint32_t n0, cudaStream_t s) {
-  const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * 6u);
+                       uint32_t n0, bool listed, cudaStream_t s) {
+  const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * (listed ? 5u : 6u));
   const bool vec_ok = ((uintptr_t)pts & 15u) == 0;
   if (sweep && n0 == 0) return cudaErrorInvalidValue;
+#define GS_BIN(T, LST)                                                                         \
+  GS_DISPATCH_D(d, (k_bin<D, T, LST><<<g, kBlock, 0, s>>>((const T*)pts, n, thr, T0, mask0,     \
+                                                          maxcells, slot0, fl, vec_ok, offsets, \
+                                                          B, sweep, n0)))
   if (f32) {
-    GS_DISPATCH_D(d, k_bin<D, float><<<g, kBlock, 0, s>>>((const float*)pts, n, thr, T0,
-                                                            mask0, maxcells, slot0, fl, vec_ok,
-                                                            offsets, B, sweep, n0));
+    if (listed) { GS_BIN(float, true); } else { GS_BIN(float, false); }
   } else {
-    GS_DISPATCH_D(d, k_bin<D, double><<<g, kBlock, 0, s>>>((const double*)pts, n, thr, T0,
-                                                             mask0, maxcells, slot0, fl, vec_ok,
-                                                             offsets, B, sweep, n0));
+    if (listed) { GS_BIN(double, true); } else { GS_BIN(double, false); }
   }
+#undef GS_BIN
   return cudaGetLastError();
 }
 

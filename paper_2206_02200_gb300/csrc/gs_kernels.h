@@ -168,11 +168,12 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
 // each instance of a batched run (B > 1); ignored when B == 1.
 // Binning with the plan in fl->plan (nothing runs unless fl->plan_status is 0).
 // A bandwidth sweep (sweep != null) bins B x n0 points: instance b's point j
-// is row j of pts, decided with sweep[b] (n = B x n0).
+// is row j of pts, decided with sweep[b] (n = B x n0).  listed: new cells
+// are listed per warp, 32 at a time (Tuning::bin_list).
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, const int64_t* offsets, int B, const SweepPlan* sweep,
-                       uint32_t n0, cudaStream_t s);
+                       uint32_t n0, bool listed, cudaStream_t s);
 
 // Blocks of the cooperative loop kernel for dimension d on the current device
 // (all co-resident, at most kMaxLoopGrid), or a negative value on error;

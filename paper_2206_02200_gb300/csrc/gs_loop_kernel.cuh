@@ -326,7 +326,9 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
         phase_update<D, 32, BT>(A, t, m, pt ? maskPt : mask, maskM, m_prev, base_prev, base,
                                 any_nb, inexact, werr, pt);
     }
-    if (__any_sync(kFull, any_nb) && (threadIdx.x & 31) == 0) atomicOr(&A.st[t].has_nb, 1u);
+    // one flag add per block (atomics on one address from different warps
+    // serialise; 152 instead of up to 2432 per step)
+    if (__syncthreads_or(any_nb ? 1 : 0) && threadIdx.x == 0) atomicOr(&A.st[t].has_nb, 1u);
     if (!grid_sync(A.bar, A.fl)) return;
     clk.lap_step(t == 0 ? kSegUpdateFirst : kSegUpdateRest, t, A.res);
     // the pencil table is read: back to clean (the next use of tab[2], as

@@ -56,9 +56,11 @@ struct Tuning {
   uint32_t pencil_min;    // least initial cells for the pencil form of the first update
   uint32_t split_min;     // least points for step i's second pass and the label writes as
                           // launches of their own (fewer: inside the loop kernel)
+  uint32_t bin_list;      // 1: binning lists new cells per warp, 32 at a time (one add on
+                          // the cell count for each 32); 0: one add per new cell
 };
 
-constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u, 1u << 22};
+constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u, 1u << 22, 1u};
 constexpr uint32_t kTailMaxCells = 256;  // the one-block tail's shared memory holds this many
 
 // Device-resident state of one level t (the cells before update step t).

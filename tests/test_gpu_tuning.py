@@ -22,6 +22,7 @@ CHOICES = [
     {"tail_enter": 256},            # the largest tail
     {"pencil_min": 0},              # pencil form whenever the tail is not entered at once
     {"pencil_min": 1 << 30},        # no pencil form
+    {"bin_list": 0},                # binning: one add per new cell
     {"split_min": 0},               # per-point passes as launches of their own
     {"split_min": (1 << 31) - 1},   # per-point passes inside the loop kernel
     {"few_lanes_x4": 1, "load_shift": 1, "filter": 0, "tail_enter": 32, "pencil_min": 1024,
@@ -51,14 +52,14 @@ def test_image_d5_under_every_choice(image, tuning):
     _check(image, 12.0, tuning)
 
 
-@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[6:10],
+@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[6:11],
                          ids=lambda t: ",".join(f"{k}={v}" for k, v in t.items()))
 def test_gmm_d6_under_choices(tuning):
     X = synth.gmm_points(60_000, 6, 20, seed=8).astype(np.float64)
     _check(X, 4.0, tuning)
 
 
-@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[8:10],
+@pytest.mark.parametrize("tuning", CHOICES[:4] + CHOICES[8:11],
                          ids=lambda t: ",".join(f"{k}={v}" for k, v in t.items()))
 def test_batched_under_choices(tuning):
     parts = synth.image_batch(4, 77, hmin=40, hmax=90, wmin=50, wmax=120)
