@@ -280,6 +280,15 @@ typedef struct {
   int32_t bin_list;      /* 1 (default): binning lists the new cells of each warp 32 at a
                             time, one add on the (single) cell count for each 32, with five
                             blocks per SM; 0: one add per new cell, six blocks per SM */
+  int32_t bin_sums;      /* 0 (default): a second pass sorts the points by cell (counting
+                            sort) and forms the exact cell sums of Sec. 2.1 i over the
+                            sorted runs; 1: binning forms them as it reads the points: the
+                            points of a warp that share a cell are summed in registers and
+                            added to the cell's sum with one set of atomic adds.  1 pays
+                            where a warp's 32 consecutive points share few cells (measured
+                            on GB300: 10% on a 321x481 image at h = 16); with about 30
+                            points per cell (1080p and 4K images at d = 5, the d = 6
+                            mixture) its adds cost 4 to 8 times the second pass */
 } gs_tuning;
 
 /* Sets the launch choices of later gs_fit, gs_fit_batched and gs_fit_sweep
@@ -326,7 +335,7 @@ gs_status gs_get_phase_times(gs_ctx* ctx, gs_phase_times* out);
  *
  * Limits: the per-point arrays (cell slot and counting-sort position) take
  * 8 bytes per point and 1 MiB is kept for the rest, so n <= 8,257,536; the
- * cell workspace (about 2.1 KB per initial active cell at d = 4 and
+ * cell workspace (about 2.2 KB per initial active cell at d = 4 and
  * max_iter = 50, growing with d and max_iter, plus 272 KB of fixed buffers)
  * must fit what the points leave; the cell-face table holds at most 8192
  * entries (over all axes, the number of cells the data spans plus 3).

@@ -41,9 +41,10 @@ CANDIDATES = {
     "pencil_min": [1024, 4096, 16384, 1 << 30],
     "split_min": [1 << 22, 0, (1 << 31) - 1],
     "bin_list": [1, 0],
+    "bin_sums": [0, 1],
 }
 #: knobs that batched runs use (the tail and the pencil form are plain-run only)
-BATCHED_KNOBS = ("few_lanes_x4", "load_shift", "filter", "split_min", "bin_list")
+BATCHED_KNOBS = ("few_lanes_x4", "load_shift", "filter", "split_min", "bin_list", "bin_sums")
 MIN_GAIN = 0.01
 
 _cache = None

@@ -63,7 +63,7 @@ struct BinTableBuf {
       if ((e = cnt.ensure(c)) != cudaSuccess) return e;
       if ((e = off.ensure(c)) != cudaSuccess) return e;
       if ((e = id.ensure(c)) != cudaSuccess) return e;
-      if ((e = acc.ensure((size_t)(c / 2) * dd * 4)) != cudaSuccess) return e;
+      if ((e = acc.ensure((size_t)c * dd * 4)) != cudaSuccess) return e;
       if ((e = list.ensure(c / 2)) != cudaSuccess) return e;
       cap = c;
       d = dd;
@@ -539,7 +539,7 @@ gs_status gs_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
   if (t->few_lanes_x4 < 0 || t->few_lanes_x4 > (1 << 20) || (t->load_shift != 1 && t->load_shift != 2) ||
       (t->filter != 0 && t->filter != 1) || t->tail_enter < 0 ||
       t->tail_enter > (int32_t)kTailMaxCells || t->pencil_min < 0 || t->split_min < 0 ||
-      (t->bin_list != 0 && t->bin_list != 1))
+      (t->bin_list != 0 && t->bin_list != 1) || (t->bin_sums != 0 && t->bin_sums != 1))
     return fail(ctx, GS_E_INVALID, "tuning value out of range");
   ctx->tune.few_lanes_x4 = (uint32_t)t->few_lanes_x4;
   ctx->tune.load_shift = (uint32_t)t->load_shift;
@@ -548,6 +548,7 @@ gs_status gs_set_tuning(gs_ctx* ctx, const gs_tuning* t) {
   ctx->tune.pencil_min = (uint32_t)t->pencil_min;
   ctx->tune.split_min = (uint32_t)t->split_min;
   ctx->tune.bin_list = (uint32_t)t->bin_list;
+  ctx->tune.bin_sums = (uint32_t)t->bin_sums;
   return GS_OK;
 }
 
@@ -560,6 +561,7 @@ gs_status gs_get_tuning(gs_ctx* ctx, gs_tuning* out) {
   out->pencil_min = (int32_t)ctx->tune.pencil_min;
   out->split_min = (int32_t)ctx->tune.split_min;
   out->bin_list = (int32_t)ctx->tune.bin_list;
+  out->bin_sums = (int32_t)ctx->tune.bin_sums;
   return GS_OK;
 }
 

@@ -297,12 +297,13 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     GS_T_BEGIN(GS_PHASE_BIN);
     GS_LAUNCH(launch_bin(a.points, a.f32, n, d, b.thr, b.t0, b.t0.cap - 1, b.t0_maxcells,
                          b.slot0, b.flags, b.offsets, a.B, L.sweep, L.n0,
-                         a.tune.bin_list != 0, s), "k_bin", 1);
+                         a.tune.bin_list != 0, a.tune.bin_sums != 0, s), "k_bin", 1);
     GS_T_END();
-    // step i, second pass: the exact cell sums through a counting sort (as
-    // launches of their own for large runs, else inside the loop kernel)
+    // step i, second pass (unless binning formed the sums): the exact cell
+    // sums through a counting sort (as launches of their own for large runs,
+    // else inside the loop kernel)
     const bool split = n >= (int64_t)a.tune.split_min;
-    if (split) {
+    if (split && !a.tune.bin_sums) {
       GS_T_BEGIN(GS_PHASE_K_OFFSETS);
       GS_LAUNCH(launch_prep_offsets(L, s), "k_prep_offsets", kPrepOffsetsLaunches);
       GS_T_END();

@@ -24,9 +24,30 @@ namespace {
 // thread t reads the words t, t + S, t + 2S, ... with S a multiple of D, so
 // the j-th value of every word a thread reads has the same coordinate
 // (t*W + j) mod D, and consecutive threads read consecutive words
-// (coalesced).  Four words per thread are in flight at once.  Per-coordinate
-// extremes are reduced in shared memory and published with one global atomic
+// (coalesced).  Four words per thread are in flight at once.  Extremes are
+// kept in the input's own bit width (order codes of float32 values widen to
+// those of float64 at the end: the widening is exact and keeps the order),
+// combined per block without atomics and published with one global atomic
 // per block and coordinate.
+template <typename T>
+struct Bits;  // the unsigned and signed integers of T's width
+template <>
+struct Bits<double> {
+  using U = uint64_t;
+  using S = int64_t;
+  static constexpr int kExpShift = 52;
+  static constexpr U kExpMask = 0x7FF;
+  static __device__ __forceinline__ uint64_t widen(U b) { return b; }
+};
+template <>
+struct Bits<float> {
+  using U = uint32_t;
+  using S = int32_t;
+  static constexpr int kExpShift = 23;
+  static constexpr U kExpMask = 0xFF;
+  static __device__ __forceinline__ uint64_t widen(U b) { return f32_bits_to_f64_bits(b); }
+};
+
 template <int W, typename T>
 struct Word;
 template <>
@@ -37,8 +58,8 @@ struct Word<1, double> {
 };
 template <>
 struct Word<1, float> {
-  static __device__ __forceinline__ void load(const float* p, uint64_t (&b)[1]) {
-    b[0] = f32_bits_to_f64_bits(__float_as_uint(__ldg(p)));
+  static __device__ __forceinline__ void load(const float* p, uint32_t (&b)[1]) {
+    b[0] = __float_as_uint(__ldg(p));
   }
 };
 template <>
@@ -51,37 +72,76 @@ struct Word<2, double> {
 };
 template <>
 struct Word<4, float> {
-  static __device__ __forceinline__ void load(const float* p, uint64_t (&b)[4]) {
+  static __device__ __forceinline__ void load(const float* p, uint32_t (&b)[4]) {
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    b[0] = f32_bits_to_f64_bits(v.x);
-    b[1] = f32_bits_to_f64_bits(v.y);
-    b[2] = f32_bits_to_f64_bits(v.z);
-    b[3] = f32_bits_to_f64_bits(v.w);
+    b[0] = v.x;
+    b[1] = v.y;
+    b[2] = v.z;
+    b[3] = v.w;
   }
 };
 
+// Extremes of one coordinate: order codes (signed integers in the order of
+// the values, -0 as +0) of the least and greatest value, and the largest
+// magnitude's bits.  Non-finite values are counted, not compared.
+template <typename T>
 struct RangeAcc {
-  int64_t mn = INT64_MAX, mx = INT64_MIN;
-  uint64_t ma = 0;
-  __device__ __forceinline__ void add(uint64_t b, unsigned long long& bad) {
-    if (((b >> 52) & 0x7FF) == 0x7FF) {
+  using U = typename Bits<T>::U;
+  using S = typename Bits<T>::S;
+  static constexpr int kBits = 8 * (int)sizeof(U);
+  static constexpr U kSign = (U)1 << (kBits - 1);
+  S mn = (S)(kSign - 1), mx = (S)kSign;
+  U ma = 0;
+  __device__ __forceinline__ void add(U b, unsigned long long& bad) {
+    if (((b >> Bits<T>::kExpShift) & Bits<T>::kExpMask) == Bits<T>::kExpMask) {
       ++bad;
       return;
     }
-    const int64_t o = ord_of_bits(b);
+    const S o = ord(b);
     mn = o < mn ? o : mn;
     mx = o > mx ? o : mx;
-    const uint64_t ab = b & 0x7FFFFFFFFFFFFFFFull;
+    const U ab = b & (kSign - 1);
     ma = ab > ma ? ab : ma;
   }
+  static __device__ __forceinline__ S ord(U b) {
+    if (b == kSign) b = 0;
+    const S s = (S)b;
+    return s ^ ((s >> (kBits - 1)) & (S)(kSign - 1));
+  }
+  static __device__ __forceinline__ U bits(S o) { return (U)(o ^ ((o >> (kBits - 1)) & (S)(kSign - 1))); }
+  __device__ __forceinline__ bool empty() const { return mn == (S)(kSign - 1); }
+  __device__ __forceinline__ void merge(const RangeAcc& r) {
+    mn = r.mn < mn ? r.mn : mn;
+    mx = r.mx > mx ? r.mx : mx;
+    ma = r.ma > ma ? r.ma : ma;
+  }
+  __device__ __forceinline__ RangeAcc shfl_down(int o) const {
+    RangeAcc r;
+    r.mn = (S)__shfl_down_sync(kFull, (U)mn, o);
+    r.mx = (S)__shfl_down_sync(kFull, (U)mx, o);
+    r.ma = __shfl_down_sync(kFull, ma, o);
+    return r;
+  }
+  // the float64 order codes and magnitude bits (non-empty accumulators)
+  __device__ __forceinline__ int64_t mn64() const { return ord_of_bits(Bits<T>::widen(bits(mn))); }
+  __device__ __forceinline__ int64_t mx64() const { return ord_of_bits(Bits<T>::widen(bits(mx))); }
+  __device__ __forceinline__ uint64_t ma64() const { return Bits<T>::widen(ma); }
 };
+
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+// Blocks of the key-range kernel per SM (its launch bound; the grid is at
+// most this many per SM, one wave).
+constexpr unsigned kRangeBlocksPerSM = 4;
 
 __device__ void plan_block(int d, int64_t n, const PlanJob& J, DevFlags* fl);
 
 template <int D, typename T, int W>
-__global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int64_t n,
-                                                  DevFlags* fl, bool plan, PlanJob J) {
-  constexpr int U = 4;  // words in flight per thread
+__global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
+    k_range(const T* __restrict__ pts, int64_t n, DevFlags* fl, bool plan, PlanJob J) {
+  using Acc = RangeAcc<T>;
+  using U = typename Bits<T>::U;
+  constexpr int kInFlight = 4;  // words in flight per thread
   if (plan) {
     // the loop kernel's start state, cleared by the whole grid
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
@@ -92,6 +152,15 @@ __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int
       *J.res = LoopResult{};
     }
   }
+  // Lane l's word slot j holds axis ((t0 + l) W + j) mod D: lanes P apart
+  // (P = D / gcd(D, W)) hold the same axes, so a warp first combines its
+  // lanes with shuffles P, 2P, 4P, ... apart, leaving P W = lcm(D, W) partial
+  // extremes in its first P lanes; one thread per axis then combines the
+  // warps' partials.  (Per-thread atomics on the D shared words serialise
+  // every thread of the block on a few addresses.)
+  constexpr int P = D / gcd_c(D, W);
+  constexpr int PW = P * W;
+  __shared__ Acc s_part[kWarps][PW];
   __shared__ long long s_mn[D], s_mx[D];
   __shared__ unsigned long long s_ma[D], s_bad;
   if (threadIdx.x < D) {
@@ -106,47 +175,69 @@ __global__ void __launch_bounds__(kBlock) k_range(const T* __restrict__ pts, int
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t S = nthreads - nthreads % D;  // stride in words, a multiple of D
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  RangeAcc acc[W];
+  Acc acc[W];
   unsigned long long bad = 0;
   if (t < S) {
     int64_t q = t;
-    for (; q + (U - 1) * S < words; q += U * S) {
-      uint64_t b[U][W];
+    for (; q + (kInFlight - 1) * S < words; q += kInFlight * S) {
+      U b[kInFlight][W];
 #pragma unroll
-      for (int u = 0; u < U; ++u) Word<W, T>::load(pts + (q + u * S) * W, b[u]);
+      for (int u = 0; u < kInFlight; ++u) Word<W, T>::load(pts + (q + u * S) * W, b[u]);
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int u = 0; u < kInFlight; ++u)
 #pragma unroll
         for (int j = 0; j < W; ++j) acc[j].add(b[u][j], bad);
     }
     for (; q < words; q += S) {
-      uint64_t b[W];
+      U b[W];
       Word<W, T>::load(pts + q * W, b);
 #pragma unroll
       for (int j = 0; j < W; ++j) acc[j].add(b[j], bad);
     }
+  }
+  // threads at or past S hold empty accumulators, which combine as no-ops
+  {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const int a = (int)((t * W + j) % D);
-      if (acc[j].mn != INT64_MAX) {
-        atomicMin(&s_mn[a], (long long)acc[j].mn);
-        atomicMax(&s_mx[a], (long long)acc[j].mx);
-        atomicMax(&s_ma[a], (unsigned long long)acc[j].ma);
-      }
+    for (int o = P; o < 32; o <<= 1)
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc[j].merge(acc[j].shfl_down(o));
+    if (lane < P) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) s_part[w][lane * W + j] = acc[j];
     }
   }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    // warp w's partial e = l W + j belongs to thread t0 + 32 w + l, slot j:
+    // axis (base_w + e) mod D with base_w = (t0 + 32 w) W mod D, so axis a
+    // has the partials e = (a - base_w) mod D, then every D-th
+    const int a = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
+    Acc r;
+    for (int w = 0; w < kWarps; ++w) {
+      const int base_w = (int)(((t0 + 32 * w) * W) % D);
+      for (int e = (a - base_w + D) % D; e < PW; e += D) r.merge(s_part[w][e]);
+    }
+    if (!r.empty()) {
+      s_mn[a] = r.mn64();
+      s_mx[a] = r.mx64();
+      s_ma[a] = r.ma64();
+    }
+  }
+  __syncthreads();
   if (t == 0) {
     // values after the last whole word
     for (int64_t e = words * W; e < total; ++e) {
-      uint64_t b[1];
+      U b[1];
       Word<1, T>::load(pts + e, b);
-      RangeAcc r;
+      Acc r;
       r.add(b[0], bad);
       const int a = (int)(e % D);
-      if (r.mn != INT64_MAX) {
-        atomicMin(&s_mn[a], (long long)r.mn);
-        atomicMax(&s_mx[a], (long long)r.mx);
-        atomicMax(&s_ma[a], (unsigned long long)r.ma);
+      if (!r.empty()) {
+        atomicMin(&s_mn[a], (long long)r.mn64());
+        atomicMax(&s_mx[a], (long long)r.mx64());
+        atomicMax(&s_ma[a], (unsigned long long)r.ma64());
       }
     }
   }
@@ -194,6 +285,36 @@ __device__ __forceinline__ void stage_points(const T* __restrict__ src, int coun
     done = (int)((size_t)nvec * 16 / sizeof(T));
   }
   for (int e = done + lane; e < count; e += 32) dst[e] = __ldg(&src[e]);
+}
+
+// The same copy as cp.async 16-byte pieces (global -> shared without a
+// register round trip), for the next chunk while the warp works on this one:
+// the whole 16-byte pieces of the run, in the calling lane's share.  The rest
+// of a run whose size is not a multiple of 16 bytes is copied by
+// stage_points_rest once the pieces are waited for.
+template <typename T>
+__device__ __forceinline__ void stage_points_async(const T* __restrict__ src, int count,
+                                                   T* __restrict__ dst, int lane) {
+  const int nvec = (int)((size_t)count * sizeof(T) / 16);
+  const char* s = reinterpret_cast<const char*>(src);
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  for (int v = lane; v < nvec; v += 32)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * v),
+                 "l"(s + 16 * (size_t)v)
+                 : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void stage_points_rest(const T* __restrict__ src, int count,
+                                                  T* __restrict__ dst, int lane) {
+  const int done = (int)((size_t)count * sizeof(T) / 16 * 16 / sizeof(T));
+  for (int e = done + lane; e < count; e += 32) dst[e] = __ldg(&src[e]);
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// waits until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void cp_async_wait_one() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
 // Instance of point i in a batched run: the b with offsets[b] <= i < offsets[b + 1].
@@ -251,16 +372,31 @@ __device__ void plan_block(int d, int64_t n, const PlanJob& J, DevFlags* fl) {
     plan_probe(s_plan, p, J.dtab + p, vpack + p);
 }
 
-// LISTED: new cells are listed per warp, 32 at a time (five blocks per SM:
-// the warp's list costs registers); else each new cell takes one add on the
-// cell count (six blocks per SM).  Tuning::bin_list chooses.
-template <int D, typename T, bool LISTED>
-__global__ void __launch_bounds__(kBlock, LISTED ? 5 : 6)
+// LISTED: new cells are listed per warp, 32 at a time (the warp's list costs
+// registers); else each new cell takes one add on the cell count.
+// Tuning::bin_list chooses.
+//
+// SUMS: binning also forms the exact cell sums of Sec. 2.1 i (else a counting
+// sort does, after it).  A coordinate's fixed-point value (units of 2^L_a,
+// 128-bit two's complement) is cut into six 24-bit pieces; the lanes that
+// share a cell add each piece with one warp reduction over their match mask
+// (32 pieces of 24 bits fit 29 bits), and the group's first lane adds the
+// reassembled sum (mod 2^128) into the cell's limb accumulators, which are
+// indexed by the cell's table slot.  Exact integer sums make the grouping and
+// the order of the adds irrelevant.  Tuning::bin_sums chooses.
+constexpr unsigned bin_blocks_per_sm(bool listed, bool sums) {
+  return sums ? 4u : (listed ? 5u : 6u);
+}
+
+template <int D, typename T, bool LISTED, bool SUMS>
+__global__ void __launch_bounds__(kBlock, bin_blocks_per_sm(LISTED, SUMS))
     k_bin(const T* __restrict__ pts, int64_t n, const int64_t* __restrict__ thr,
           BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* __restrict__ slot0,
           DevFlags* fl, bool vec_ok, const int64_t* __restrict__ offsets, int B,
           const SweepPlan* __restrict__ sweep, uint32_t n0) {
-  __shared__ __align__(16) T s_pts[kWarps][32 * D];
+  // a warp's chunk of 32 points, double-buffered: with a 16-byte aligned
+  // array the next chunk is copied (cp.async) while this one is worked on
+  __shared__ __align__(16) T s_pts[kWarps][2][32 * D];
   __shared__ uint32_t s_new[kWarps][32];  // a warp's new cells not yet listed
   __shared__ Plan s_plan;
   __shared__ uint32_t s_ok;
@@ -275,6 +411,7 @@ __global__ void __launch_bounds__(kBlock, LISTED ? 5 : 6)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned inexact = 0, werr = 0;  // SUMS: values outside the fixed-point window
   // LISTED: new cells are listed per warp, 32 at a time.  The cell count is
   // one address for the whole grid, where atomics from different warps
   // serialise (about 0.7 ns each on GB300): one add per new cell costs 0.2 ms
@@ -292,18 +429,38 @@ __global__ void __launch_bounds__(kBlock, LISTED ? 5 : 6)
     __syncwarp();
     cnt = 0;
   };
-  for (int64_t base = gwarp * 32; base < n; base += nwarps * 32) {
+  const bool pipe = !sweep && vec_ok;
+  const int64_t step = nwarps * 32;
+  if (pipe && gwarp * 32 < n) {
+    const int64_t b0 = gwarp * 32;
+    stage_points_async<T>(pts + b0 * D, (n - b0 < 32 ? (int)(n - b0) : 32) * D, s_pts[w][0], lane);
+    cp_async_commit();
+  }
+  int par = 0;
+  for (int64_t base = gwarp * 32; base < n; base += step, par ^= 1) {
     const int cnt = n - base < 32 ? (int)(n - base) : 32;
-    if (!sweep) stage_points<T>(pts + base * D, cnt * D, s_pts[w], vec_ok, lane);
+    T* const cur = s_pts[w][par];
+    if (pipe) {
+      const int64_t nb = base + step;
+      if (nb < n)
+        stage_points_async<T>(pts + nb * D, (n - nb < 32 ? (int)(n - nb) : 32) * D,
+                              s_pts[w][par ^ 1], lane);
+      cp_async_commit();
+      cp_async_wait_one();  // this chunk's pieces have landed
+      stage_points_rest<T>(pts + base * D, cnt * D, cur, lane);
+    } else if (!sweep) {
+      stage_points<T>(pts + base * D, cnt * D, cur, vec_ok, lane);
+    }
     __syncwarp();
     const bool valid = lane < cnt;
     uint64_t key = kEmpty;
+    const T* row = nullptr;  // a sweep's point row
     if (valid && sweep) {
       // bandwidth sweep: point j of instance b is row j of pts, its cell
       // decided with b's bandwidth
       const int64_t i = base + lane;
       const uint32_t b = (uint32_t)(i / n0);
-      const T* row = pts + (size_t)(i - (int64_t)b * n0) * D;
+      row = pts + (size_t)(i - (int64_t)b * n0) * D;
       const SweepPlan* S = sweep + b;
       key = (uint64_t)b << P.inst_off;
 #pragma unroll
@@ -316,7 +473,7 @@ __global__ void __launch_bounds__(kBlock, LISTED ? 5 : 6)
       key = B > 1 ? (uint64_t)instance_of(offsets, B, base + lane) << P.inst_off : 0ull;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const uint64_t b = bits_of(s_pts[w][lane * D + a]);
+        const uint64_t b = bits_of(cur[lane * D + a]);
         const int idx = key_index(thr + P.thr_off[a], P.span[a], P.kmin[a], P.inv_h, b);
         key |= (uint64_t)(idx + 1) << P.off[a];
       }
@@ -345,9 +502,28 @@ __global__ void __launch_bounds__(kBlock, LISTED ? 5 : 6)
     }
     s = __shfl_sync(kFull, s, leader);
     if (valid) slot0[base + lane] = s;
+    if constexpr (SUMS) {
+#pragma unroll 1
+      for (int a = 0; a < D; ++a) {
+        uint64_t bits = 0;
+        if (valid) bits = sweep ? bits_of(__ldg(row + a)) : bits_of(cur[lane * D + a]);
+        const u128 V = valid ? to_fixed(bits, P.L[a], inexact, werr) : (u128)0;
+        u128 G = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const uint32_t piece = (uint32_t)(V >> (24 * j)) & 0xFFFFFFu;
+          if (__any_sync(kFull, piece != 0u)) G += (u128)__reduce_add_sync(peers, piece) << (24 * j);
+        }
+        if (lane == leader && s != kNone) atomic_add_fixed(T0.acc + ((size_t)s * D + a) * 4, G);
+      }
+    }
     __syncwarp();
   }
   if (LISTED && pend) list_cells(pend);
+  if constexpr (SUMS) {
+    if (inexact) atomicAdd(&fl->inexact, 1ull);
+    if (werr) atomicOr(&fl->err, kErrWindow);
+  }
 }
 
 // Labels and modes when the final cells were too many to number inside
@@ -397,7 +573,7 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
                          const PlanJob* job, cudaStream_t s) {
   const bool vec = ((uintptr_t)pts & 15u) == 0;
   const int W = vec ? (f32 ? 4 : 2) : 1;
-  const unsigned g = grid_for(n * d / W, kBlock * 4, 152u * 8u);
+  const unsigned g = grid_for(n * d / W, kBlock * 4, 152u * kRangeBlocksPerSM);
   const bool plan = job != nullptr;
   const PlanJob J = plan ? *job : PlanJob{};
   if (f32) {
@@ -419,19 +595,26 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, const int64_t* offsets, int B, const SweepPlan* sweep,
-                       uint32_t n0, bool listed, cudaStream_t s) {
-  const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * (listed ? 5u : 6u));
+                       uint32_t n0, bool listed, bool sums, cudaStream_t s) {
+  const unsigned g = grid_for((n + 31) / 32 * 32, kBlock, 152u * bin_blocks_per_sm(listed, sums));
   const bool vec_ok = ((uintptr_t)pts & 15u) == 0;
   if (sweep && n0 == 0) return cudaErrorInvalidValue;
-#define GS_BIN(T, LST)                                                                         \
-  GS_DISPATCH_D(d, (k_bin<D, T, LST><<<g, kBlock, 0, s>>>((const T*)pts, n, thr, T0, mask0,     \
-                                                          maxcells, slot0, fl, vec_ok, offsets, \
-                                                          B, sweep, n0)))
-  if (f32) {
-    if (listed) { GS_BIN(float, true); } else { GS_BIN(float, false); }
-  } else {
-    if (listed) { GS_BIN(double, true); } else { GS_BIN(double, false); }
+#define GS_BIN(T, LST, SUM)                                                                    \
+  GS_DISPATCH_D(d, (k_bin<D, T, LST, SUM><<<g, kBlock, 0, s>>>((const T*)pts, n, thr, T0, mask0, \
+                                                               maxcells, slot0, fl, vec_ok,      \
+                                                               offsets, B, sweep, n0)))
+#define GS_BIN_T(T)                                              \
+  if (sums) {                                                    \
+    if (listed) { GS_BIN(T, true, true); } else { GS_BIN(T, false, true); }   \
+  } else {                                                       \
+    if (listed) { GS_BIN(T, true, false); } else { GS_BIN(T, false, false); } \
   }
+  if (f32) {
+    GS_BIN_T(float)
+  } else {
+    GS_BIN_T(double)
+  }
+#undef GS_BIN_T
 #undef GS_BIN
   return cudaGetLastError();
 }

@@ -20,7 +20,8 @@ struct BinTable {
   uint32_t* cnt;
   uint32_t* off;
   uint32_t* id;
-  uint64_t* acc;   // maxcells x d x 4
+  uint64_t* acc;   // cap x d x 4, by slot: the exact sums' limb accumulators (float32
+                   // variant with a counting sort: cap x d float sums of offsets)
   uint32_t* list;  // maxcells
   uint32_t cap;    // power of two
 };
@@ -169,11 +170,13 @@ cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* 
 // Binning with the plan in fl->plan (nothing runs unless fl->plan_status is 0).
 // A bandwidth sweep (sweep != null) bins B x n0 points: instance b's point j
 // is row j of pts, decided with sweep[b] (n = B x n0).  listed: new cells
-// are listed per warp, 32 at a time (Tuning::bin_list).
+// are listed per warp, 32 at a time (Tuning::bin_list).  sums: the exact cell
+// sums are added into T0.acc as well (Tuning::bin_sums; a value outside the
+// fixed-point window sets kErrWindow).
 cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_t* thr,
                        BinTable T0, uint32_t mask0, uint32_t maxcells, uint32_t* slot0,
                        DevFlags* fl, const int64_t* offsets, int B, const SweepPlan* sweep,
-                       uint32_t n0, bool listed, cudaStream_t s);
+                       uint32_t n0, bool listed, bool sums, cudaStream_t s);
 
 // Blocks of the cooperative loop kernel for dimension d on the current device
 // (all co-resident, at most kMaxLoopGrid), or a negative value on error;

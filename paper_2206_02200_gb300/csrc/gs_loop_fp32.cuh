@@ -225,15 +225,11 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
 #pragma unroll
       for (int a = 0; a < D; ++a)
         x[e][a] = idx[e] != kNone ? (float)__ldg(pts + (size_t)idx[e] * D + a) : 0.f;
-    // the cells' ids and keys, loaded while the coordinates are in flight
-    uint32_t cid[E];
+    // the cells' keys, loaded while the coordinates are in flight
     uint64_t ckey[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      cid[e] = s[e] != kNone ? A.T0.id[s[e]] : 0u;
-      ckey[e] = s[e] != kNone ? A.T0.key[s[e]] : 0ull;
-    }
-    uint32_t cur = kNone, curid = 0;
+    for (int e = 0; e < E; ++e) ckey[e] = s[e] != kNone ? A.T0.key[s[e]] : 0ull;
+    uint32_t cur = kNone;
     float org[D];
     FF V[D];
 #pragma unroll
@@ -241,10 +237,9 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
       if (s[e] != cur) {
         if (cur != kNone) {
 #pragma unroll
-          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)curid * D + a], V[a].value());
+          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
         }
         cur = s[e];
-        curid = cid[e];
         if (cur != kNone) {
 #pragma unroll
           for (int a = 0; a < D; ++a) org[a] = (float)face_of(g_plan, A.thr, ckey[e], a);
@@ -276,13 +271,15 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
     }
     if (head && cur != kNone) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)curid * D + a], V[a].value());
+      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
     }
   }
 }
 
-// Level 0 (float32): mean offsets of the initial cells; resets the binning
-// table's slots.
+// Level 0 (float32): mean offsets of the initial cells from their lower faces;
+// resets the binning table's slots.  The sums are the float sums of offsets
+// of phase_cell_sums32, or, where binning formed them (Tuning::bin_sums), the
+// exact coordinate sums, rounded once to float64 before the mean is taken.
 template <int D>
 __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) {
   const uint32_t tid = item_tid(m0);
@@ -303,10 +300,22 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
     if (sa != kNone) {
       uint32_t* r = row + (size_t)sa * W;
       r[2] = cnt;
+      if (A.tune.bin_sums) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        r[3 + a] = __float_as_uint(tacc[(size_t)id * D + a] / (float)cnt);
-        tacc[(size_t)id * D + a] = 0.f;
+        for (int a = 0; a < D; ++a) {
+          uint64_t* acc = T0.acc + ((size_t)s * D + a) * 4;
+          unsigned inx = 0;
+          const double sum = round_fixed(limbs_value(acc), g_plan.L[a], inx);
+          acc[0] = acc[1] = acc[2] = acc[3] = 0;
+          const double org = (double)(float)face_of(g_plan, A.thr, key, a);
+          r[3 + a] = __float_as_uint((float)(sum / (double)cnt - org));
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          r[3 + a] = __float_as_uint(tacc[(size_t)s * D + a] / (float)cnt);
+          tacc[(size_t)s * D + a] = 0.f;
+        }
       }
       G.id[sa] = id;
       G.list[id] = sa;

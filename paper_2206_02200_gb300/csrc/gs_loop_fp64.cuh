@@ -125,12 +125,11 @@ __device__ void phase_scatter(const LoopArgs& A) {
 // segment adds the segment's sum.
 constexpr int kSumRun = 4;
 
-// Adds V into the sum accumulators of the cell of id `id` (they are indexed
-// by the cell's id, so the initial cells' sums are dense).
+// Adds V into the sum accumulators of the cell in binning-table slot s.
 template <int D>
-__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t id, const u128 (&V)[D]) {
+__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t s, const u128 (&V)[D]) {
 #pragma unroll
-  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)id * D + a) * 4, V[a]);
+  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)s * D + a) * 4, V[a]);
 }
 
 template <int D, typename T>
@@ -165,21 +164,16 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
 #pragma unroll
       for (int a = 0; a < D; ++a)
         raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)src[e] * D + a) : 0ull;
-    // the cells' ids, loaded while the coordinates are in flight
-    uint32_t cid[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) cid[e] = s[e] != kNone ? A.T0.id[s[e]] : 0u;
     // runs within the lane
-    uint32_t cur = s[0], curid = cid[0];
+    uint32_t cur = s[0];
     u128 V[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], g_plan.L[a], inexact, werr);
 #pragma unroll
     for (int e = 1; e < E; ++e) {
       if (s[e] != cur) {
-        if (cur != kNone) add_cell_sum<D>(A, curid, V);
+        if (cur != kNone) add_cell_sum<D>(A, cur, V);
         cur = s[e];
-        curid = cid[e];
 #pragma unroll
         for (int a = 0; a < D; ++a) V[a] = 0;
       }
@@ -203,7 +197,7 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
         }
       }
     }
-    if (head && cur != kNone) add_cell_sum<D>(A, curid, V);
+    if (head && cur != kNone) add_cell_sum<D>(A, cur, V);
   }
 }
 
@@ -229,7 +223,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
       r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        r[1 + a] = settle_sum(T0.acc + ((size_t)id * D + a) * 4, g_plan.L[a], inexact, werr);
+        r[1 + a] = settle_sum(T0.acc + ((size_t)s * D + a) * 4, g_plan.L[a], inexact, werr);
       G.id[sa] = id;
       G.list[id] = sa;
     }

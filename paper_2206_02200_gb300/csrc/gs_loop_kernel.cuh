@@ -49,7 +49,7 @@ constexpr int kPrepBlock = 256;
 constexpr int kPrepCountGrid = 304;  // blocks of the count and offset launches
 
 __device__ __forceinline__ bool prep_ok(const LoopArgs& A) {
-  return A.n >= (int64_t)A.tune.split_min &&
+  return A.n >= (int64_t)A.tune.split_min && A.tune.bin_sums == 0u &&
          *(volatile uint32_t*)&A.fl->plan_status == kPlanOK &&
          (*(volatile uint32_t*)&A.fl->err & (kErrOverflow | kErrTableFull)) == 0u;
 }
@@ -138,10 +138,11 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(LoopArgs A) {
     if (tid < 512) A.seq_aux[tid] = 0;
   }
   const uint32_t m0 = *(volatile uint32_t*)&A.fl->m0;
-  // step i, second pass (the exact cell sums): in the k_prep_* launches
-  // before this kernel when the run has split_min points or more, else here
+  // step i, second pass (the exact cell sums), unless binning formed them: in
+  // the k_prep_* launches before this kernel when the run has split_min
+  // points or more, else here
   const bool split = A.n >= (int64_t)A.tune.split_min;
-  if (!split) {
+  if (!split && !A.tune.bin_sums) {
     phase_count_totals(A, m0);
     if (!grid_sync(A.bar, A.fl)) return;
     phase_offsets(A, m0);

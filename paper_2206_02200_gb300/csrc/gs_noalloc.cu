@@ -49,7 +49,7 @@ BinTable carve_bin_table(Carve& c, uint32_t cap, uint32_t lmax, int d) {
   t.cnt = c.take<uint32_t>(cap);
   t.off = c.take<uint32_t>(cap);
   t.id = c.take<uint32_t>(cap);
-  t.acc = c.take<uint64_t>((size_t)lmax * d * 4);
+  t.acc = c.take<uint64_t>((size_t)cap * d * 4);
   t.list = c.take<uint32_t>(lmax);
   t.cap = cap;
   return t;
@@ -106,10 +106,10 @@ size_t layout(unsigned char* base, int64_t n, int d, int max_iter, uint32_t M, s
   return c.used;
 }
 
-cudaError_t clear_bin_table(const BinTable& t, uint32_t lmax, int d, cudaStream_t s) {
+cudaError_t clear_bin_table(const BinTable& t, int d, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(t.key, 0xFF, sizeof(uint64_t) * t.cap, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t.cnt, 0, sizeof(uint32_t) * t.cap, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(t.acc, 0, sizeof(uint64_t) * lmax * d * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t.acc, 0, sizeof(uint64_t) * t.cap * d * 4, s);
   return e;
 }
 
@@ -154,7 +154,7 @@ struct StaticWorkspace : public Workspace {
     layout(base, n, d, max_iter, M, thr_words, nprobe, &laid);
     // the scratch keeps the previous call's contents: clear what must start
     // empty or zero
-    if (clear_bin_table(laid.t0, laid.t0_maxcells, d, s) != cudaSuccess) return GS_E_CUDA;
+    if (clear_bin_table(laid.t0, d, s) != cudaSuccess) return GS_E_CUDA;
     for (int i = 0; i < 3; ++i)
       if (clear_level_table(laid.tab[i], d, s) != cudaSuccess) return GS_E_CUDA;
     b = laid;

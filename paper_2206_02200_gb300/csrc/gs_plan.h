@@ -58,9 +58,12 @@ struct Tuning {
                           // launches of their own (fewer: inside the loop kernel)
   uint32_t bin_list;      // 1: binning lists new cells per warp, 32 at a time (one add on
                           // the cell count for each 32); 0: one add per new cell
+  uint32_t bin_sums;      // 1: binning forms the exact cell sums as it reads the points (one
+                          // set of limb adds per distinct cell of a warp); 0: a counting
+                          // sort of the points by cell, then sums over the sorted runs
 };
 
-constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u, 1u << 22, 1u};
+constexpr Tuning kDefaultTuning = {4u, 2u, 1u, 128u, 4096u, 1u << 22, 1u, 0u};
 constexpr uint32_t kTailMaxCells = 256;  // the one-block tail's shared memory holds this many
 
 // Device-resident state of one level t (the cells before update step t).

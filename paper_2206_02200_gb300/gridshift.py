@@ -72,7 +72,7 @@ class gs_tuning(ctypes.Structure):
     _fields_ = [("few_lanes_x4", ctypes.c_int32), ("load_shift", ctypes.c_int32),
                 ("filter", ctypes.c_int32), ("tail_enter", ctypes.c_int32),
                 ("pencil_min", ctypes.c_int32), ("split_min", ctypes.c_int32),
-                ("bin_list", ctypes.c_int32)]
+                ("bin_list", ctypes.c_int32), ("bin_sums", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -80,7 +80,7 @@ class gs_tuning(ctypes.Structure):
 
 #: the library's built-in launch choices (gs_set_tuning with NULL)
 DEFAULT_TUNING = {"few_lanes_x4": 4, "load_shift": 2, "filter": 1, "tail_enter": 128,
-                  "pencil_min": 4096, "split_min": 1 << 22, "bin_list": 1}
+                  "pencil_min": 4096, "split_min": 1 << 22, "bin_list": 1, "bin_sums": 0}
 
 
 class gs_track_result(ctypes.Structure):

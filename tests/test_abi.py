@@ -237,12 +237,12 @@ def test_tuning_host_only_checks(lib, tmp_path):
     try:
         assert gridshift.gs_get_tuning(ctx) == gridshift.DEFAULT_TUNING
         t = {"few_lanes_x4": 16, "load_shift": 1, "filter": 0, "tail_enter": 256,
-             "pencil_min": 0, "split_min": 5, "bin_list": 0}
+             "pencil_min": 0, "split_min": 5, "bin_list": 0, "bin_sums": 1}
         assert gridshift.gs_set_tuning(ctx, t) == gridshift.GS_OK
         assert gridshift.gs_get_tuning(ctx) == t
         for bad in ({"load_shift": 3}, {"load_shift": 0}, {"filter": 2}, {"tail_enter": 257},
                     {"tail_enter": -1}, {"few_lanes_x4": -1}, {"pencil_min": -5},
-                    {"split_min": -1}, {"bin_list": 2}):
+                    {"split_min": -1}, {"bin_list": 2}, {"bin_sums": 2}, {"bin_sums": -1}):
             assert gridshift.gs_set_tuning(ctx, bad) == gridshift.GS_E_INVALID, bad
             assert gridshift.gs_get_tuning(ctx) == t  # unchanged
         assert gridshift.gs_set_tuning(ctx, None) == gridshift.GS_OK

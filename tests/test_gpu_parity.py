@@ -267,6 +267,48 @@ def test_nonfinite_input_is_rejected():
     g.close()
 
 
+def test_nonfinite_float32_input_is_rejected():
+    # float32 input: the key range reads the values in their own width
+    g = gridshift.GridShift(3, 1.0, 10)
+    for bad in (np.nan, np.inf, -np.inf):
+        X = np.zeros((1001, 3), dtype=np.float32)
+        X[500, 2] = bad
+        with pytest.raises(gridshift.GridShiftError) as e:
+            g.fit(torch.from_numpy(X).cuda())
+        assert e.value.status == gridshift.GS_E_INVALID
+    g.close()
+
+
+@pytest.mark.parametrize("as_f32", [False, True], ids=["f64", "f32"])
+@pytest.mark.parametrize("aligned", [True, False], ids=["aligned", "unaligned"])
+def test_key_range_signs_zeros_and_tiny_values(as_f32, aligned):
+    # signed zeros, negative and positive values, and float32 subnormals: the
+    # per-axis extremes (order codes, largest magnitude) set the packing and
+    # the fixed-point window; an unaligned array takes the one-value-per-load
+    # reads of the key range and binning
+    rng = np.random.default_rng(71)
+    n, d = 4099, 3
+    X = rng.normal(0.0, 3.0, size=(n, d))
+    X[::7, 0] = 0.0
+    X[1::7, 0] = -0.0
+    X[2::5, 1] = -X[2::5, 1]
+    X[:, 2] = rng.uniform(-1e-36, 1e-36, size=n)  # cells 0 and -1, a fine fixed-point unit
+    X[::3, 2] = rng.uniform(-1e-38, 1e-38, size=len(X[::3, 2]))  # float32 subnormals
+    X[::13, 2] = -0.0
+    if as_f32:
+        X = X.astype(np.float32).astype(np.float64)
+    ref = oracle.fit(X, 1.5, 50)
+    buf = torch.zeros(n * d + 1, dtype=torch.float32 if as_f32 else torch.float64, device="cuda")
+    off = 0 if aligned else 1
+    pts = buf[off:off + n * d].view(n, d)
+    pts.copy_(torch.from_numpy(X.astype(np.float32) if as_f32 else X))
+    labels, modes, info = gridshift.fit(pts, 1.5, 50)
+    torch.cuda.synchronize()
+    assert info["k"] == ref["k"] and info["iterations"] == ref["iterations"]
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    np.testing.assert_array_equal(modes.cpu().numpy().view(np.int64), ref["modes"].view(np.int64))
+
+
 def check_ctx_reuse(g):
     X = np.random.default_rng(1).normal(0, 5, size=(3000, 2))
     labels, modes, info = g.fit(torch.from_numpy(X).cuda())
