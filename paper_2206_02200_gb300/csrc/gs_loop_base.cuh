@@ -119,15 +119,34 @@ __device__ __forceinline__ ulonglong2 pack(u128 v) {
   return make_ulonglong2((uint64_t)v, (uint64_t)(v >> 64));
 }
 
-// The cell sum of one axis as the float64 value of Sec. 2.1 (the exact sum in
-// the limb accumulators rounded once), held as the fixed-point integer it
-// equals; clears the accumulators.
-__device__ __forceinline__ ulonglong2 settle_sum(uint64_t* acc, int L, unsigned& inexact,
-                                                 unsigned& werr) {
-  (void)inexact;
-  const u128 v = round_to_double(limbs_value(acc), L, werr);
-  acc[0] = acc[1] = acc[2] = acc[3] = 0;
-  return pack(v);
+// The cell sums of all D axes as the float64 values of Sec. 2.1 (each exact
+// sum in its four limb accumulators rounded once), held as the fixed-point
+// integers they equal, into out[0 .. D-1]; clears the accumulators.  Every
+// limb is loaded (from L2) before anything is stored: stores between the
+// loads would make each axis wait for the one before.
+template <int D>
+__device__ __forceinline__ void settle_sums(uint64_t* acc, ulonglong2* out, const int* L,
+                                            unsigned& werr) {
+  ulonglong2 l[D][2];
+  const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(acc);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    l[a][0] = __ldcg(a2 + 2 * a);
+    l[a][1] = __ldcg(a2 + 2 * a + 1);
+  }
+  u128 v[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const uint64_t limbs[4] = {l[a][0].x, l[a][0].y, l[a][1].x, l[a][1].y};
+    v[a] = round_to_double(limbs_value(limbs), L[a], werr);
+  }
+  ulonglong2* z = reinterpret_cast<ulonglong2*>(acc);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    out[a] = pack(v[a]);
+    z[2 * a] = make_ulonglong2(0ull, 0ull);
+    z[2 * a + 1] = make_ulonglong2(0ull, 0ull);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -311,9 +311,13 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
           r[3 + a] = __float_as_uint((float)(sum / (double)cnt - org));
         }
       } else {
+        // all the sums are loaded before any store
+        float sum[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) sum[a] = __ldcg(tacc + (size_t)s * D + a);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          r[3 + a] = __float_as_uint(tacc[(size_t)s * D + a] / (float)cnt);
+          r[3 + a] = __float_as_uint(sum[a] / (float)cnt);
           tacc[(size_t)s * D + a] = 0.f;
         }
       }
@@ -716,9 +720,13 @@ __device__ void phase_compact32(const LoopArgs& A, int t, uint32_t m1) {
       }
     }
     if (!restored) {
+      // all the sums are loaded before any store
+      float sum[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) sum[a] = __ldcg(macc + (size_t)s * D + a);
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        r[3 + a] = __float_as_uint(macc[(size_t)s * D + a] / (float)cnt);
+        r[3 + a] = __float_as_uint(sum[a] / (float)cnt);
         macc[(size_t)s * D + a] = 0.f;
       }
     }

@@ -221,9 +221,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
     if (sa != kNone) {
       ulonglong2* r = G.row + (size_t)sa * (D + 1);
       r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        r[1 + a] = settle_sum(T0.acc + ((size_t)s * D + a) * 4, g_plan.L[a], inexact, werr);
+      settle_sums<D>(T0.acc + (size_t)s * D * 4, r + 1, g_plan.L, werr);
       G.id[sa] = id;
       G.list[id] = sa;
     }
@@ -639,13 +637,10 @@ __device__ void phase_compact(const LoopArgs& A, int t, uint32_t m1, unsigned& i
         restored = true;
       }
     }
-    if (!restored) {
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        r[1 + a] = settle_sum(M.acc + ((size_t)s * D + a) * 4, g_plan.L[a], inexact, werr);
-    }
+    const uint32_t cnt = (uint32_t)__ldcg(&r[0].x);
+    if (!restored) settle_sums<D>(M.acc + (size_t)s * D * 4, r + 1, g_plan.L, werr);
     nx.key[id] = key;
-    nx.cnt[id] = (uint32_t)r[0].x;
+    nx.cnt[id] = cnt;
     M.id[s] = id;
     filter_set(f, key, lg);
   }
