@@ -591,51 +591,115 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                       "ms": seq_ms, "value": n / (seq_ms / 1e3) / 1e6, "unit": UNIT}
         gp.close()
 
-    # -- end to end through the public API: every step uploads its points
+    # -- end to end through the public API: every step uploads its input
     #    from pinned host memory and reads its labels and modes back.  The
     #    upload of step i + 1 and the read-back of step i run on a copy
     #    stream while step i's fit runs (double-buffered device inputs and
-    #    outputs), as a stream of images would be served.
-    h_pts = torch.from_numpy(X).pin_memory()
-    h_labels = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
-    h_modes = [torch.empty(modes.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
-    d_pts = [torch.empty_like(pts) for _ in range(2)]
-    d_lab = [labels, torch.empty_like(labels)]
-    d_md = [modes, torch.empty_like(modes)]
-    copy = torch.cuda.Stream(dev)
-    up = [torch.cuda.Event() for _ in range(2)]
-    fit_done = [torch.cuda.Event() for _ in range(2)]
-    down = [torch.cuda.Event() for _ in range(2)]
-    e2e_steps = args.steps
-    barrier()
-    t0 = time.perf_counter()
-    kk = 0
-    with torch.cuda.stream(copy):
-        d_pts[0].copy_(h_pts, non_blocking=True)
-        up[0].record(copy)
-    for i in range(e2e_steps):
-        b = i % 2
-        if i + 1 < e2e_steps:
-            with torch.cuda.stream(copy):
-                # (the copy stream already waited for the fit that last read
-                # this buffer, before that fit's read-back)
-                d_pts[1 - b].copy_(h_pts, non_blocking=True)
-                up[1 - b].record(copy)
-        stream.wait_event(up[b])
-        if i >= 2:
-            stream.wait_event(down[b])  # this buffer's previous read-back is done
-        kk, _ = call(d_pts[b], d_lab[b], d_md[b])
-        fit_done[b].record(stream)
+    #    outputs), as a stream of images would be served.  Image workloads
+    #    upload the uint8 image and call the image entry point (the features
+    #    are built on the device); the float64 feature upload through gs_fit
+    #    is reported beside it.
+    def run_e2e(h_in, call_in):
+        h_labels = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+        h_modes = [torch.empty(modes.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+        d_in = [torch.empty(h_in.shape, dtype=h_in.dtype, device=dev) for _ in range(2)]
+        d_lab = [labels, torch.empty_like(labels)]
+        d_md = [modes, torch.empty_like(modes)]
+        copy = torch.cuda.Stream(dev)
+        up = [torch.cuda.Event() for _ in range(2)]
+        fit_done = [torch.cuda.Event() for _ in range(2)]
+        down = [torch.cuda.Event() for _ in range(2)]
+        steps = args.steps
+        kk = 0
+        call_in(d_in[0].copy_(h_in), d_lab[0], d_md[0])  # warm-up of this path
+        barrier()
+        t0 = time.perf_counter()
         with torch.cuda.stream(copy):
-            copy.wait_event(fit_done[b])
-            h_labels[b].copy_(d_lab[b], non_blocking=True)
-            h_modes[b][:kk].copy_(d_md[b][:kk], non_blocking=True)
-            down[b].record(copy)
-    copy.synchronize()
-    stream.synchronize()
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e_value = job_rate(n, e2e_steps, world, e2e_s)
+            d_in[0].copy_(h_in, non_blocking=True)
+            up[0].record(copy)
+        for i in range(steps):
+            b = i % 2
+            if i + 1 < steps:
+                with torch.cuda.stream(copy):
+                    # (the copy stream already waited for the fit that last
+                    # read this buffer, before that fit's read-back)
+                    d_in[1 - b].copy_(h_in, non_blocking=True)
+                    up[1 - b].record(copy)
+            stream.wait_event(up[b])
+            if i >= 2:
+                stream.wait_event(down[b])  # this buffer's previous read-back is done
+            kk, _ = call_in(d_in[b], d_lab[b], d_md[b])
+            fit_done[b].record(stream)
+            with torch.cuda.stream(copy):
+                copy.wait_event(fit_done[b])
+                h_labels[b].copy_(d_lab[b], non_blocking=True)
+                h_modes[b][:kk].copy_(d_md[b][:kk], non_blocking=True)
+                down[b].record(copy)
+        copy.synchronize()
+        stream.synchronize()
+        barrier()
+        secs = max_over_ranks(time.perf_counter() - t0, world, dev)
+        return job_rate(n, steps, world, secs), int(h_in.numel() * h_in.element_size()), kk
+
+    e2e_value, e2e_h2d, kk = run_e2e(torch.from_numpy(X).pin_memory(), call)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d,
+           "d2h_bytes_per_step": int(n * 4 + kk * d * 8),
+           "input": "float64 features (n x d), gs_fit",
+           "pipelined": ("the upload of step i + 1 and the read-back of step i "
+                         "run on a second stream during step i's fit")}
+    img = w.get("image")
+    imgs = w.get("images")
+    if img is not None or imgs is not None:
+        if batched:
+            pix = np.ascontiguousarray(np.concatenate([im.reshape(-1, im.shape[2]) for im in imgs], 0))
+            h_img = torch.from_numpy(pix).pin_memory()
+
+            def call_img(p, lab, md, gg=g):
+                st, mo, infos = gridshift.gs_fit_image_batched(gg._ctx, p.data_ptr(), pix.shape[1],
+                                                               offsets, lab.data_ptr(), md.data_ptr(),
+                                                               md.shape[0])
+                if st != gridshift.GS_OK:
+                    raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(gg._ctx))
+                return mo[-1], [x.as_dict() for x in infos]
+            what = "uint8 images (n x 3), features built on the device, gs_fit_image_batched"
+            how = e2e["pipelined"]
+            v_img, h2d_img, kk = run_e2e(h_img, call_img)
+        else:
+            # the library's host-buffer call on a stream of `steps` images: it
+            # uploads each image, fits it and reads labels and modes back,
+            # the copies overlapping the fits inside the call
+            h_img = torch.from_numpy(np.ascontiguousarray(img)).pin_memory()
+            H, W, C = img.shape
+            h_lab = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+            h_md = [torch.empty(modes.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+            cap = modes.shape[0]
+
+            def stream_call(count):
+                st, ks, _ = gridshift.gs_fit_images_host(
+                    g._ctx, [h_img.data_ptr()] * count, H, W, C, w["xy_scale"],
+                    [h_lab[i % 2].data_ptr() for i in range(count)],
+                    [h_md[i % 2].data_ptr() for i in range(count)], cap)
+                if st != gridshift.GS_OK:
+                    raise gridshift.GridShiftError(st, gridshift.gs_get_last_error(g._ctx))
+                return ks
+
+            stream_call(2)  # warm-up of this path
+            barrier()
+            t0 = time.perf_counter()
+            ks = stream_call(args.steps)
+            barrier()
+            secs = max_over_ranks(time.perf_counter() - t0, world, dev)
+            v_img, h2d_img, kk = job_rate(n, args.steps, world, secs), int(img.nbytes), ks[-1]
+            what = (f"uint8 image ({H} x {W} x {C}) in page-locked host memory, one "
+                    f"gs_fit_images_host call for the {args.steps} steps (features built on the "
+                    "device; labels and modes read back into host memory)")
+            how = ("inside the call: the upload of image i + 1 and the read-back of image i run "
+                   "on a second stream while the neighbouring image is fitted")
+        e2e = {"value": v_img, "unit": UNIT, "h2d_bytes_per_step": h2d_img,
+               "d2h_bytes_per_step": int(n * 4 + kk * d * 8), "input": what,
+               "pipelined": how,
+               "features_path": {"value": e2e_value, "h2d_bytes_per_step": e2e_h2d,
+                                 "input": e2e["input"]}}
 
     # -- roofline of the dominant kernel (the loop kernel: one launch per
     #    step), with the per-point launches beside it
@@ -695,11 +759,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "data": "synthetic",
                 "config": dict(workload_config(w, args.workload, args.precision, args.update),
                                tuning=g.tuning(), tuning_source=g.tuning_source),
-                "e2e": {"value": e2e_value, "unit": UNIT,
-                        "h2d_bytes_per_step": int(X.nbytes),
-                        "d2h_bytes_per_step": int(n * 4 + kk * d * 8),
-                        "pipelined": ("the upload of step i + 1 and the read-back of step i "
-                                      "run on a second stream during step i's fit")},
+                "e2e": e2e,
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "active_cell_iterations_per_s": cell_iters * world / (total_ms / 1e3),

@@ -221,6 +221,74 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
                          int B, int32_t* labels, double* modes, int64_t modes_cap,
                          int64_t* mode_offsets, gs_fit_info* infos);
 
+/* Runs GridShift on the pixels of an image, the input of the paper's image
+ * segmentation (Sec. 4.2: each pixel's (r, g, b) values, or (r, g, b, x, y)
+ * with its position).  Pixel p = y * width + x is the point
+ *   (c_0, .., c_{channels-1}, x * xy_scale, y * xy_scale)   if xy_scale > 0
+ *   (c_0, .., c_{channels-1})                               if xy_scale == 0
+ * with every value in float64 (the channel bytes exactly, the positions
+ * rounded once by the product).  The features are built on the device, in the
+ * context's workspace, and fitted as gs_fit fits them: the result is the one
+ * gs_fit gives for that float64 feature matrix (bit for bit in GS_FP64).
+ * Only the image itself need be uploaded: one byte per channel and pixel
+ * instead of eight bytes per feature.
+ *   pixels     device uint8[height x width x channels], row-major: row y,
+ *              column x, then the channels
+ *   height, width  >= 0, height * width < 2^31
+ *   channels   1 .. 8
+ *   xy_scale   0 (no position features) or finite and > 0
+ *   labels, modes, modes_cap, k_out, info: as gs_fit (labels in pixel order;
+ *              info->launches counts the feature build as well)
+ * The context's d must be channels + 2 (xy_scale > 0) or channels.  Returns
+ * what gs_fit returns, or GS_E_INVALID for the arguments above. */
+gs_status gs_fit_image(gs_ctx* ctx, const uint8_t* pixels, int64_t height, int64_t width,
+                       int channels, double xy_scale, int32_t* labels, double* modes,
+                       int64_t modes_cap, int64_t* k_out, gs_fit_info* info);
+
+/* gs_fit_image on a stream of `count` images of one size held in HOST
+ * memory, with host outputs: a video's frames, or images served one after
+ * another.  For every image i the call uploads images[i], runs gs_fit_image
+ * on it, and reads its labels and modes back into labels[i] and modes[i].
+ * The upload of image i + 1 runs on a second stream while image i is
+ * fitted, and the read-back of image i while image i + 1 is fitted, so the
+ * copies overlap the fits (page-locked host buffers, e.g. from
+ * cudaMallocHost, let them run asynchronously; other host memory works, with
+ * the copies serialised).  The results are those of `count` separate gs_fit_image calls.
+ *   count      >= 0 images
+ *   images     host: count pointers, each to uint8[height x width x channels]
+ *   height, width, channels, xy_scale: as gs_fit_image, the same for all
+ *   labels     host: count pointers, each to int32[height x width] (output)
+ *   modes      host: count pointers, each to float64[modes_cap x d] (output;
+ *              may be NULL when modes_cap == 0)
+ *   k_out      host int64[count]: clusters of every image (output; required)
+ *   infos      host gs_fit_info[count] (output; may be NULL)
+ * The device buffers (two of each: image, labels, modes) and the second
+ * stream belong to the context and are kept for later calls.  The call
+ * returns after every copy has finished.  On GS_E_CAPACITY for an image
+ * (more clusters than modes_cap) the others are still fitted and the call
+ * returns GS_E_CAPACITY with every k_out filled; any other error stops the
+ * call.  Returns what gs_fit_image returns, GS_E_NOMEM, or GS_E_INVALID for
+ * the arguments above. */
+gs_status gs_fit_images_host(gs_ctx* ctx, int count, const uint8_t* const* images, int64_t height,
+                             int64_t width, int channels, double xy_scale, int32_t* const* labels,
+                             double* const* modes, int64_t modes_cap, int64_t* k_out,
+                             gs_fit_info* infos);
+
+/* gs_fit_batched on the pixels of B images (the channel values only: d =
+ * channels, as in the (r, g, b) inputs of Sec. 4.2), built on the device as
+ * gs_fit_image builds them.
+ *   pixels     device uint8[n x channels]: the images' pixels concatenated
+ *   channels   1 .. 8, equal to the context's d
+ *   offsets    host int64[B + 1]: image b owns pixels offsets[b] ..
+ *              offsets[b + 1] - 1 (as gs_fit_batched)
+ *   B, labels, modes, modes_cap, mode_offsets, infos: as gs_fit_batched
+ *              (every infos[b].launches counts the feature build as well)
+ * Returns what gs_fit_batched returns, or GS_E_INVALID for the arguments
+ * above. */
+gs_status gs_fit_image_batched(gs_ctx* ctx, const uint8_t* pixels, int channels,
+                               const int64_t* offsets, int B, int32_t* labels, double* modes,
+                               int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos);
+
 /* Runs GridShift on one point set for B bandwidths h_0 .. h_{B-1} in one
  * call: instance b is the run gs_fit gives for the same points with h = hs[b]
  * (Sec. 2.1; the bandwidth study of Sec. 4.1 runs the method over a range of

@@ -454,8 +454,33 @@ struct gs_ctx {
   DBuf<uint4> tbuf;
   unsigned char* h_track = nullptr;
   size_t h_track_cap = 0;
+  DBuf<double> feat;  // gs_fit_image: the pixels' float64 features
+  // gs_fit_images_host: double-buffered device copies of an image, its
+  // labels and modes, the copy stream and its events
+  DBuf<uint8_t> himg[2];
+  DBuf<int32_t> hlab[2];
+  DBuf<double> hmodes[2];
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t up_ev[2] = {nullptr, nullptr}, done_ev[2] = {nullptr, nullptr},
+              down_ev[2] = {nullptr, nullptr};
+
+  void release_stream() {
+    for (int i = 0; i < 2; ++i) {
+      for (cudaEvent_t* e : {&up_ev[i], &done_ev[i], &down_ev[i]}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+      }
+      himg[i].release();
+      hlab[i].release();
+      hmodes[i].release();
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
+  }
 
   void release_device() {
+    release_stream();
+    feat.release();
     ws.release();
     wide_workspace_free(wide);
     wide = nullptr;
@@ -674,6 +699,188 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
     for (int i = 0; i < kClockSteps; ++i)
       for (int c = 0; c < 2; ++c) ctx->last_times.step_ms[i][c] = kms[kLoopPhases + 2 * i + c];
   }
+  return st;
+}
+
+// The device the context last ran on: a change releases its buffers.
+static gs_status bind_device(gs_ctx* ctx) {
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(ctx, GS_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorName(ce));
+  if (ctx->device != dev) {
+    ctx->release_device();
+    ctx->device = dev;
+  }
+  return GS_OK;
+}
+
+// The float64 features of n pixels (channels C, positions if xy) into the
+// context's feature buffer, on its stream.
+static gs_status image_features(gs_ctx* ctx, const uint8_t* pixels, int64_t n, int64_t width,
+                                int C, bool xy, double s) {
+  gs_status st = bind_device(ctx);
+  if (st != GS_OK) return st;
+  const int d = C + (xy ? 2 : 0);
+  cudaError_t ce = ctx->feat.ensure((size_t)n * d);
+  if (ce != cudaSuccess)
+    return fail(ctx, ce == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA,
+                std::string("image features: ") + cudaGetErrorName(ce));
+  ce = launch_image_features(pixels, n, width, C, xy, s, ctx->feat.p, ctx->stream);
+  if (ce != cudaSuccess)
+    return fail(ctx, GS_E_CUDA, std::string("k_image_features: ") + cudaGetErrorName(ce));
+  return GS_OK;
+}
+
+gs_status gs_fit_image(gs_ctx* ctx, const uint8_t* pixels, int64_t height, int64_t width,
+                       int channels, double xy_scale, int32_t* labels, double* modes,
+                       int64_t modes_cap, int64_t* k_out, gs_fit_info* info) {
+  if (!ctx) return GS_E_INVALID;
+  ctx->err.clear();
+  if (!k_out) return fail(ctx, GS_E_INVALID, "k_out is NULL");
+  *k_out = 0;
+  if (height < 0 || width < 0 || height >= (1ll << 31) || width >= (1ll << 31) ||
+      height * width >= (1ll << 31))
+    return fail(ctx, GS_E_INVALID, "image size out of range");
+  if (channels < 1 || channels > 8) return fail(ctx, GS_E_INVALID, "channels out of range");
+  if (!(xy_scale >= 0) || !std::isfinite(xy_scale))
+    return fail(ctx, GS_E_INVALID, "xy_scale must be 0 or finite and > 0");
+  const bool xy = xy_scale > 0;
+  if (channels + (xy ? 2 : 0) != ctx->d)
+    return fail(ctx, GS_E_INVALID, "the context's d is not channels (+ 2 with positions)");
+  const int64_t n = height * width;
+  if (n > 0 && (!pixels || !labels)) return fail(ctx, GS_E_INVALID, "NULL pixels or labels");
+  if (modes_cap < 0 || (modes_cap > 0 && !modes))
+    return fail(ctx, GS_E_INVALID, "modes is NULL with modes_cap > 0");
+  if (n > 0) {
+    gs_status st = image_features(ctx, pixels, n, width, channels, xy, xy_scale);
+    if (st != GS_OK) return st;
+  }
+  gs_status st = gs_fit(ctx, ctx->feat.p, GS_IN_F64, n, labels, modes, modes_cap, k_out, info);
+  if (info && n > 0) info->launches += 1;
+  return st;
+}
+
+gs_status gs_fit_images_host(gs_ctx* ctx, int count, const uint8_t* const* images, int64_t height,
+                             int64_t width, int channels, double xy_scale, int32_t* const* labels,
+                             double* const* modes, int64_t modes_cap, int64_t* k_out,
+                             gs_fit_info* infos) {
+  if (!ctx) return GS_E_INVALID;
+  ctx->err.clear();
+  if (count < 0) return fail(ctx, GS_E_INVALID, "count < 0");
+  if (count == 0) return GS_OK;
+  if (!k_out || !images || !labels) return fail(ctx, GS_E_INVALID, "NULL images, labels or k_out");
+  if (height < 0 || width < 0 || height >= (1ll << 31) || width >= (1ll << 31) ||
+      height * width >= (1ll << 31))
+    return fail(ctx, GS_E_INVALID, "image size out of range");
+  if (channels < 1 || channels > 8) return fail(ctx, GS_E_INVALID, "channels out of range");
+  if (!(xy_scale >= 0) || !std::isfinite(xy_scale))
+    return fail(ctx, GS_E_INVALID, "xy_scale must be 0 or finite and > 0");
+  const int d = channels + (xy_scale > 0 ? 2 : 0);
+  if (d != ctx->d)
+    return fail(ctx, GS_E_INVALID, "the context's d is not channels (+ 2 with positions)");
+  if (modes_cap < 0 || (modes_cap > 0 && !modes))
+    return fail(ctx, GS_E_INVALID, "modes is NULL with modes_cap > 0");
+  const int64_t n = height * width;
+  for (int i = 0; i < count; ++i) {
+    k_out[i] = 0;
+    if (n > 0 && (!images[i] || !labels[i])) return fail(ctx, GS_E_INVALID, "NULL image or labels");
+    if (modes_cap > 0 && !modes[i]) return fail(ctx, GS_E_INVALID, "NULL modes with modes_cap > 0");
+  }
+  if (infos) std::memset(infos, 0, sizeof(gs_fit_info) * (size_t)count);
+  if (n == 0) {
+    for (int i = 0; i < count; ++i)
+      if (infos) infos[i].converged = 1;
+    return GS_OK;
+  }
+  gs_status st = bind_device(ctx);
+  if (st != GS_OK) return st;
+  const size_t img_bytes = (size_t)n * channels;
+  cudaError_t ce = cudaSuccess;
+  if (!ctx->copy_stream) ce = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
+    for (cudaEvent_t* e : {&ctx->up_ev[b], &ctx->done_ev[b], &ctx->down_ev[b]})
+      if (ce == cudaSuccess && !*e) ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = ctx->himg[b].ensure(img_bytes);
+    if (ce == cudaSuccess) ce = ctx->hlab[b].ensure((size_t)n);
+    if (ce == cudaSuccess && modes_cap > 0) ce = ctx->hmodes[b].ensure((size_t)modes_cap * d);
+  }
+  if (ce != cudaSuccess)
+    return fail(ctx, ce == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA,
+                std::string("image stream buffers: ") + cudaGetErrorName(ce));
+  const cudaStream_t cs = ctx->copy_stream, fs = ctx->stream;
+#define GS_IMG_CU(call, what)                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      cudaStreamSynchronize(cs);                                                           \
+      return fail(ctx, GS_E_CUDA, std::string(what) + ": " + cudaGetErrorName(e_));        \
+    }                                                                                      \
+  } while (0)
+  GS_IMG_CU(cudaMemcpyAsync(ctx->himg[0].p, images[0], img_bytes, cudaMemcpyHostToDevice, cs),
+            "H2D image");
+  GS_IMG_CU(cudaEventRecord(ctx->up_ev[0], cs), "cudaEventRecord");
+  gs_status result = GS_OK;
+  for (int i = 0; i < count; ++i) {
+    const int b = i & 1;
+    // the next image's upload (the fit that last read that buffer is done:
+    // every fit returns after its stream has finished)
+    if (i + 1 < count) {
+      GS_IMG_CU(cudaMemcpyAsync(ctx->himg[b ^ 1].p, images[i + 1], img_bytes,
+                                cudaMemcpyHostToDevice, cs), "H2D image");
+      GS_IMG_CU(cudaEventRecord(ctx->up_ev[b ^ 1], cs), "cudaEventRecord");
+    }
+    GS_IMG_CU(cudaStreamWaitEvent(fs, ctx->up_ev[b], 0), "cudaStreamWaitEvent");
+    // this buffer's labels and modes have been read back (image i - 2)
+    if (i >= 2) GS_IMG_CU(cudaStreamWaitEvent(fs, ctx->down_ev[b], 0), "cudaStreamWaitEvent");
+    gs_fit_info inf;
+    st = gs_fit_image(ctx, ctx->himg[b].p, height, width, channels, xy_scale, ctx->hlab[b].p,
+                      modes_cap > 0 ? ctx->hmodes[b].p : nullptr, modes_cap, &k_out[i], &inf);
+    if (infos) infos[i] = inf;
+    if (st != GS_OK && st != GS_E_CAPACITY) {
+      cudaStreamSynchronize(cs);
+      return st;
+    }
+    if (st == GS_E_CAPACITY) result = st;
+    // the read-back of image i, on the copy stream after its fit
+    GS_IMG_CU(cudaEventRecord(ctx->done_ev[b], fs), "cudaEventRecord");
+    GS_IMG_CU(cudaStreamWaitEvent(cs, ctx->done_ev[b], 0), "cudaStreamWaitEvent");
+    GS_IMG_CU(cudaMemcpyAsync(labels[i], ctx->hlab[b].p, sizeof(int32_t) * (size_t)n,
+                              cudaMemcpyDeviceToHost, cs), "D2H labels");
+    const int64_t rows = k_out[i] < modes_cap ? k_out[i] : modes_cap;
+    if (st == GS_OK && rows > 0)
+      GS_IMG_CU(cudaMemcpyAsync(modes[i], ctx->hmodes[b].p, sizeof(double) * (size_t)(rows * d),
+                                cudaMemcpyDeviceToHost, cs), "D2H modes");
+    GS_IMG_CU(cudaEventRecord(ctx->down_ev[b], cs), "cudaEventRecord");
+  }
+#undef GS_IMG_CU
+  ce = cudaStreamSynchronize(cs);
+  if (ce != cudaSuccess) return fail(ctx, GS_E_CUDA, std::string("copy stream: ") + cudaGetErrorName(ce));
+  return result;
+}
+
+gs_status gs_fit_image_batched(gs_ctx* ctx, const uint8_t* pixels, int channels,
+                               const int64_t* offsets, int B, int32_t* labels, double* modes,
+                               int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos) {
+  if (!ctx) return GS_E_INVALID;
+  ctx->err.clear();
+  if (channels < 1 || channels > 8) return fail(ctx, GS_E_INVALID, "channels out of range");
+  if (channels != ctx->d) return fail(ctx, GS_E_INVALID, "the context's d is not channels");
+  if (!offsets || !mode_offsets || !infos) return fail(ctx, GS_E_INVALID, "NULL offsets, mode_offsets or infos");
+  if (B < 1 || B > kMaxBatch) return fail(ctx, GS_E_INVALID, "B out of range");
+  if (offsets[0] != 0) return fail(ctx, GS_E_INVALID, "offsets[0] must be 0");
+  for (int i = 0; i < B; ++i)
+    if (offsets[i + 1] < offsets[i]) return fail(ctx, GS_E_INVALID, "offsets must not decrease");
+  const int64_t n = offsets[B];
+  if (n >= (1ll << 31)) return fail(ctx, GS_E_INVALID, "n out of range");
+  if (n > 0 && (!pixels || !labels)) return fail(ctx, GS_E_INVALID, "NULL pixels or labels");
+  if (n > 0) {
+    gs_status st = image_features(ctx, pixels, n, 1, channels, false, 0.0);
+    if (st != GS_OK) return st;
+  }
+  gs_status st = gs_fit_batched(ctx, ctx->feat.p, GS_IN_F64, offsets, B, labels, modes, modes_cap,
+                                mode_offsets, infos);
+  if (n > 0)
+    for (int b = 0; b < B; ++b) infos[b].launches += 1;
   return st;
 }
 

@@ -130,6 +130,39 @@ struct RangeAcc {
 
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 
+// 16 bytes global -> shared without a register round trip (cp.async), one
+// commit group per call site; wait_group<N>: at most N groups still in flight.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The values of one 16-byte word.
+template <typename T>
+struct Unpack;
+template <>
+struct Unpack<double> {
+  static __device__ __forceinline__ void get(const uint4 v, uint64_t (&b)[2]) {
+    b[0] = (uint64_t)v.x | ((uint64_t)v.y << 32);
+    b[1] = (uint64_t)v.z | ((uint64_t)v.w << 32);
+  }
+};
+template <>
+struct Unpack<float> {
+  static __device__ __forceinline__ void get(const uint4 v, uint32_t (&b)[4]) {
+    b[0] = v.x;
+    b[1] = v.y;
+    b[2] = v.z;
+    b[3] = v.w;
+  }
+};
+
 // Blocks of the key-range kernel per SM (its launch bound; the grid is at
 // most this many per SM, one wave).
 constexpr unsigned kRangeBlocksPerSM = 4;
@@ -141,7 +174,13 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
     k_range(const T* __restrict__ pts, int64_t n, DevFlags* fl, bool plan, PlanJob J) {
   using Acc = RangeAcc<T>;
   using U = typename Bits<T>::U;
-  constexpr int kInFlight = 4;  // words in flight per thread
+  constexpr int kInFlight = 4;  // words in flight per thread (unaligned arrays)
+  // 16-byte words (an aligned array): each thread keeps kDepth words in
+  // flight through its own column of a shared ring (cp.async), so the bytes
+  // in flight cost no registers
+  constexpr bool kStaged = W * sizeof(T) == 16;
+  constexpr int kDepth = 8;
+  __shared__ __align__(16) uint4 s_ring[kStaged ? kDepth : 1][kBlock];
   if (plan) {
     // the loop kernel's start state, cleared by the whole grid
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
@@ -177,7 +216,32 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Acc acc[W];
   unsigned long long bad = 0;
-  if (t < S) {
+  if constexpr (kStaged) {
+    if (t < S) {
+      const unsigned ring = (unsigned)__cvta_generic_to_shared(&s_ring[0][threadIdx.x]);
+      constexpr unsigned kSlot = 16u * kBlock;  // bytes between a thread's slots
+#pragma unroll
+      for (int p = 0; p < kDepth; ++p) {
+        const int64_t qp = t + p * S;
+        if (qp < words) cp_async16(ring + p * kSlot, pts + qp * W);
+        cp_async_commit();
+      }
+      int slot = 0;
+      for (int64_t q = t; q < words; q += S) {
+        cp_async_wait<kDepth - 1>();  // word q has landed in its slot
+        U b[W];
+        Unpack<T>::get(s_ring[slot][threadIdx.x], b);
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc[j].add(b[j], bad);
+        // the slot is read (into registers): its next word
+        const int64_t qn = q + kDepth * S;
+        if (qn < words) cp_async16(ring + slot * kSlot, pts + qn * W);
+        cp_async_commit();
+        slot = slot + 1 == kDepth ? 0 : slot + 1;
+      }
+      cp_async_wait<0>();
+    }
+  } else if (t < S) {
     int64_t q = t;
     for (; q + (kInFlight - 1) * S < words; q += kInFlight * S) {
       U b[kInFlight][W];
@@ -298,23 +362,13 @@ __device__ __forceinline__ void stage_points_async(const T* __restrict__ src, in
   const int nvec = (int)((size_t)count * sizeof(T) / 16);
   const char* s = reinterpret_cast<const char*>(src);
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  for (int v = lane; v < nvec; v += 32)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * v),
-                 "l"(s + 16 * (size_t)v)
-                 : "memory");
+  for (int v = lane; v < nvec; v += 32) cp_async16(d + 16u * v, s + 16 * (size_t)v);
 }
 template <typename T>
 __device__ __forceinline__ void stage_points_rest(const T* __restrict__ src, int count,
                                                   T* __restrict__ dst, int lane) {
   const int done = (int)((size_t)count * sizeof(T) / 16 * 16 / sizeof(T));
   for (int e = done + lane; e < count; e += 32) dst[e] = __ldg(&src[e]);
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-// waits until at most one committed group of this thread is still in flight
-__device__ __forceinline__ void cp_async_wait_one() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
 // Instance of point i in a batched run: the b with offsets[b] <= i < offsets[b + 1].
@@ -446,7 +500,7 @@ __global__ void __launch_bounds__(kBlock, bin_blocks_per_sm(LISTED, SUMS))
         stage_points_async<T>(pts + nb * D, (n - nb < 32 ? (int)(n - nb) : 32) * D,
                               s_pts[w][par ^ 1], lane);
       cp_async_commit();
-      cp_async_wait_one();  // this chunk's pieces have landed
+      cp_async_wait<1>();  // this chunk's pieces have landed
       stage_points_rest<T>(pts + base * D, cnt * D, cur, lane);
     } else if (!sweep) {
       stage_points<T>(pts + base * D, cnt * D, cur, vec_ok, lane);
@@ -523,6 +577,40 @@ __global__ void __launch_bounds__(kBlock, bin_blocks_per_sm(LISTED, SUMS))
   if constexpr (SUMS) {
     if (inexact) atomicAdd(&fl->inexact, 1ull);
     if (werr) atomicOr(&fl->err, kErrWindow);
+  }
+}
+
+// Pixel features of an image (the (r, g, b) or (r, g, b, x, y) inputs of the
+// segmentation experiment, Sec. 4.2): pixel p of a row-major image of width
+// w is the point (c_0 .. c_{C-1}[, x s, y s]), x = p mod w, y = p div w.  A
+// block builds kImgPix pixels' rows in shared memory (one thread per pixel)
+// and writes them out as one contiguous run (consecutive threads write
+// consecutive values).
+constexpr int kImgPix = kBlock;
+constexpr int kImgMaxD = 10;
+
+__global__ void __launch_bounds__(kBlock) k_image_features(const uint8_t* __restrict__ px,
+                                                            int64_t n, int64_t width, int C,
+                                                            int xy, double s,
+                                                            double* __restrict__ out) {
+  __shared__ double s_rows[kImgPix * kImgMaxD];
+  const int d = C + 2 * xy;
+  for (int64_t p0 = (int64_t)blockIdx.x * kImgPix; p0 < n; p0 += (int64_t)gridDim.x * kImgPix) {
+    const int cnt = n - p0 < kImgPix ? (int)(n - p0) : kImgPix;
+    const int i = threadIdx.x;
+    if (i < cnt) {
+      const int64_t p = p0 + i;
+      double* r = s_rows + i * d;
+      for (int c = 0; c < C; ++c) r[c] = (double)__ldg(px + p * C + c);
+      if (xy) {  // p and width are below 2^31
+        const uint32_t y = (uint32_t)p / (uint32_t)width;
+        r[C] = (double)((uint32_t)p - y * (uint32_t)width) * s;
+        r[C + 1] = (double)y * s;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * d; e += blockDim.x) out[p0 * d + e] = s_rows[e];
+    __syncthreads();
   }
 }
 
@@ -616,6 +704,15 @@ cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_
   }
 #undef GS_BIN_T
 #undef GS_BIN
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_features(const uint8_t* px, int64_t n, int64_t width, int C, bool xy,
+                                  double s, double* out, cudaStream_t st) {
+  if (C < 1 || C + (xy ? 2 : 0) > kImgMaxD || (xy && width < 1)) return cudaErrorInvalidValue;
+  if (n == 0) return cudaSuccess;
+  const unsigned g = grid_for(n, kImgPix, 152u * 8u);
+  k_image_features<<<g, kBlock, 0, st>>>(px, n, width, C, xy ? 1 : 0, s, out);
   return cudaGetLastError();
 }
 

@@ -222,6 +222,11 @@ cudaError_t launch_loop_seq(const LoopArgs& a, int grid, cudaStream_t s);
 // Numbering of the final cells when k > rank_max: labels of the final cells
 // from the sorted order (sorted_vals[p] = cell of rank p), then labels and
 // modes.  forest holds the final cell of every initial cell.
+// Pixel features of a row-major image (n pixels, width columns, C uint8
+// channels) into out (n x (C + 2 xy) float64): the channel values, then, if
+// xy, the column and row times s.  C + 2 xy <= 10.
+cudaError_t launch_image_features(const uint8_t* px, int64_t n, int64_t width, int C, bool xy,
+                                  double s, double* out, cudaStream_t st);
 cudaError_t launch_iota_keys(Cells c, uint64_t* keys, uint32_t* vals, uint32_t k,
                              cudaStream_t s);
 cudaError_t launch_rank(const uint32_t* sorted_vals, uint32_t* rank, uint32_t k, cudaStream_t s);

@@ -36,7 +36,9 @@ GS_UPDATE_SEQUENTIAL = 1
 
 #: every symbol the header declares, in declaration order
 EXPORTS = ("gs_create", "gs_set_precision", "gs_set_update", "gs_set_stream", "gs_fit",
-           "gs_fit_batched", "gs_fit_sweep", "gs_set_tuning", "gs_get_tuning",
+           "gs_fit_batched", "gs_fit_image", "gs_fit_images_host", "gs_fit_image_batched",
+           "gs_fit_sweep",
+           "gs_set_tuning", "gs_get_tuning",
            "gs_set_timing", "gs_get_phase_times", "gs_fit_noalloc", "gs_track_window",
            "gs_get_last_error", "gs_status_string", "gs_destroy")
 
@@ -128,6 +130,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.gs_fit_batched.restype = i32
     L.gs_fit_batched.argtypes = [vp, vp, i32, ctypes.POINTER(i64), i32, vp, vp, i64,
                                  ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
+    L.gs_fit_image.restype = i32
+    L.gs_fit_image.argtypes = [vp, vp, i64, i64, i32, ctypes.c_double, vp, vp, i64,
+                               ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
+    L.gs_fit_images_host.restype = i32
+    L.gs_fit_images_host.argtypes = [vp, i32, ctypes.POINTER(vp), i64, i64, i32, ctypes.c_double,
+                                     ctypes.POINTER(vp), ctypes.POINTER(vp), i64,
+                                     ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
+    L.gs_fit_image_batched.restype = i32
+    L.gs_fit_image_batched.argtypes = [vp, vp, i32, ctypes.POINTER(i64), i32, vp, vp, i64,
+                                       ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
     L.gs_fit_sweep.restype = i32
     L.gs_fit_sweep.argtypes = [vp, vp, i32, i64, ctypes.POINTER(ctypes.c_double), i32, vp, vp,
                                i64, ctypes.POINTER(i64), ctypes.POINTER(gs_fit_info)]
@@ -187,6 +199,48 @@ def gs_fit(ctx: int, points_ptr: int, dtype: int, n: int, labels_ptr: int, modes
     st = load().gs_fit(ctx, points_ptr or None, int(dtype), int(n), labels_ptr or None,
                        modes_ptr or None, int(modes_cap), ctypes.byref(k), ctypes.byref(info))
     return st, int(k.value), info
+
+
+def gs_fit_image(ctx: int, pixels_ptr: int, height: int, width: int, channels: int,
+                 xy_scale: float, labels_ptr: int, modes_ptr: int, modes_cap: int):
+    """Raw call; returns (status, k, gs_fit_info)."""
+    k = ctypes.c_int64(0)
+    info = gs_fit_info()
+    st = load().gs_fit_image(ctx, pixels_ptr or None, int(height), int(width), int(channels),
+                             float(xy_scale), labels_ptr or None, modes_ptr or None,
+                             int(modes_cap), ctypes.byref(k), ctypes.byref(info))
+    return st, int(k.value), info
+
+
+def gs_fit_images_host(ctx: int, image_ptrs, height: int, width: int, channels: int,
+                       xy_scale: float, label_ptrs, mode_ptrs, modes_cap: int):
+    """Raw call on host buffers (lists of addresses, one per image; page-locked
+    memory lets the copies overlap the fits).  Returns (status, k list,
+    list of gs_fit_info)."""
+    count = len(image_ptrs)
+    arr = ctypes.c_void_p * max(count, 1)
+    imgs = arr(*[int(p) for p in image_ptrs])
+    labs = arr(*[int(p) for p in label_ptrs])
+    mds = arr(*[int(p) if p else None for p in mode_ptrs]) if mode_ptrs else None
+    ks = (ctypes.c_int64 * max(count, 1))()
+    infos = (gs_fit_info * max(count, 1))()
+    st = load().gs_fit_images_host(ctx, int(count), imgs, int(height), int(width), int(channels),
+                                   float(xy_scale), labs, mds, int(modes_cap), ks, infos)
+    return st, list(ks)[:count], list(infos)[:count]
+
+
+def gs_fit_image_batched(ctx: int, pixels_ptr: int, channels: int, offsets, labels_ptr: int,
+                         modes_ptr: int, modes_cap: int):
+    """Raw call; offsets: B + 1 pixel offsets.  Returns (status, mode_offsets list,
+    list of gs_fit_info)."""
+    B = len(offsets) - 1
+    off = (ctypes.c_int64 * (B + 1))(*[int(o) for o in offsets])
+    mo = (ctypes.c_int64 * (B + 1))()
+    infos = (gs_fit_info * max(B, 1))()
+    st = load().gs_fit_image_batched(ctx, pixels_ptr or None, int(channels), off, int(B),
+                                     labels_ptr or None, modes_ptr or None, int(modes_cap),
+                                     mo, infos)
+    return st, list(mo), list(infos)[:B]
 
 
 def gs_track_window(ctx: int, frame_ptr: int, dtype: int, width: int, height: int, bins,
@@ -441,6 +495,63 @@ class GridShift:
                 st, mo, infos = gs_fit_batched(self._ctx, points.data_ptr(), dt, offsets,
                                                labels.data_ptr(), modes.data_ptr(),
                                                modes.shape[0])
+                if st == GS_E_CAPACITY:
+                    self._modes_cap = max(2 * self._modes_cap, mo[-1])
+                    continue
+                if st != GS_OK:
+                    raise GridShiftError(st, gs_get_last_error(self._ctx))
+                return (labels, [modes[mo[b]:mo[b + 1]] for b in range(len(mo) - 1)],
+                        [i.as_dict() for i in infos])
+
+    def fit_image(self, image, xy_scale: float = 0.0):
+        """GridShift on the pixels of an image (Sec. 4.2): image is a height x
+        width x channels uint8 CUDA tensor; each pixel is the point of its
+        channel values, followed by (x, y) * xy_scale when xy_scale > 0.  The
+        features are built on the device.  Returns (labels int32[height *
+        width] in pixel order, modes, info)."""
+        import torch
+        if image.dtype != torch.uint8 or not image.is_cuda or not image.is_contiguous() \
+                or image.dim() != 3:
+            raise ValueError("image must be a contiguous height x width x channels uint8 "
+                             "CUDA tensor")
+        H, W, C = image.shape
+        n = H * W
+        with torch.cuda.device(image.device):
+            gs_set_stream(self._ctx, torch.cuda.current_stream(image.device).cuda_stream)
+            self._apply_auto_tuning(n)
+            labels = torch.empty(n, dtype=torch.int32, device=image.device)
+            while True:
+                modes = torch.empty((self._modes_cap, self.d), dtype=torch.float64,
+                                    device=image.device)
+                st, k, info = gs_fit_image(self._ctx, image.data_ptr(), H, W, C, xy_scale,
+                                           labels.data_ptr(), modes.data_ptr(), modes.shape[0])
+                if st == GS_E_CAPACITY:
+                    self._modes_cap = max(2 * self._modes_cap, k)
+                    continue
+                if st != GS_OK:
+                    raise GridShiftError(st, gs_get_last_error(self._ctx))
+                return labels, modes[:k], info.as_dict()
+
+    def fit_image_batched(self, pixels, offsets):
+        """GridShift on the pixels of several images (channel values only):
+        pixels is an n x channels uint8 CUDA tensor of the images' pixels
+        concatenated, offsets B + 1 pixel offsets.  Returns (labels int32[n]
+        numbered per image, list of B modes tensors, list of B info dicts)."""
+        import torch
+        if pixels.dtype != torch.uint8 or not pixels.is_cuda or not pixels.is_contiguous() \
+                or pixels.dim() != 2:
+            raise ValueError("pixels must be a contiguous n x channels uint8 CUDA tensor")
+        n, C = pixels.shape
+        self._apply_auto_tuning(n, batched=True)
+        with torch.cuda.device(pixels.device):
+            gs_set_stream(self._ctx, torch.cuda.current_stream(pixels.device).cuda_stream)
+            labels = torch.empty(n, dtype=torch.int32, device=pixels.device)
+            while True:
+                modes = torch.empty((self._modes_cap, self.d), dtype=torch.float64,
+                                    device=pixels.device)
+                st, mo, infos = gs_fit_image_batched(self._ctx, pixels.data_ptr(), C, offsets,
+                                                     labels.data_ptr(), modes.data_ptr(),
+                                                     modes.shape[0])
                 if st == GS_E_CAPACITY:
                     self._modes_cap = max(2 * self._modes_cap, mo[-1])
                     continue

@@ -161,28 +161,39 @@ def image_batch_item(i: int, seed0: int, hmin: int = 240, hmax: int = 1080, wmin
                      wmax: int = 1920, rmin: int = 8, rmax: int = 60,
                      sigma: float = 8.0) -> np.ndarray:
     """Instance i of ``image_batch(count, seed0, ...)`` alone (any count > i)."""
+    return image_features(image_batch_image(i, seed0, hmin, hmax, wmin, wmax, rmin, rmax, sigma))
+
+
+def image_batch_image(i: int, seed0: int, hmin: int = 240, hmax: int = 1080, wmin: int = 320,
+                      wmax: int = 1920, rmin: int = 8, rmax: int = 60,
+                      sigma: float = 8.0) -> np.ndarray:
+    """The uint8 image behind ``image_batch_item(i, seed0, ...)``."""
     rng = np.random.default_rng(seed0 + i)
     H = int(rng.integers(hmin, hmax + 1))
     W = int(rng.integers(wmin, wmax + 1))
     R = int(rng.integers(rmin, rmax + 1))
-    img = voronoi_image(H, W, R, sigma, seed=seed0 + i + 7919 * (i + 1))
-    return image_features(img)
+    return voronoi_image(H, W, R, sigma, seed=seed0 + i + 7919 * (i + 1))
+
+
+def _image_cfg(img, xy_scale, **kw):
+    # the features, and the image they are built from (the image entry points)
+    return dict(points=image_features(img, xy_scale=xy_scale), image=img,
+                xy_scale=0.0 if xy_scale is None else xy_scale, **kw)
 
 
 def _cfg_image_small():
-    return dict(points=image_features(voronoi_image(321, 481, 12, 8.0, seed=1)), h=16.0,
-                max_iter=50, name="voronoi_321x481_d3_h16")
+    return _image_cfg(voronoi_image(321, 481, 12, 8.0, seed=1), None, h=16.0, max_iter=50,
+                      name="voronoi_321x481_d3_h16")
 
 
 def _cfg_1080p():
-    return dict(points=image_features(voronoi_image(1080, 1920, 40, 10.0, seed=2), xy_scale=0.1),
-                h=12.0, max_iter=50, name="voronoi_1920x1080_d5_h12")
+    return _image_cfg(voronoi_image(1080, 1920, 40, 10.0, seed=2), 0.1, h=12.0, max_iter=50,
+                      name="voronoi_1920x1080_d5_h12")
 
 
 def _cfg_4k():
-    return dict(points=image_features(voronoi_image(2160, 3840, 120, 10.0, seed=3, gradient=0.02),
-                                      xy_scale=0.1),
-                h=10.0, max_iter=50, name="voronoi_gradient_3840x2160_d5_h10")
+    return _image_cfg(voronoi_image(2160, 3840, 120, 10.0, seed=3, gradient=0.02), 0.1, h=10.0,
+                      max_iter=50, name="voronoi_gradient_3840x2160_d5_h10")
 
 
 def _cfg_gmm():
@@ -198,8 +209,9 @@ def _cfg_gmm_4m():
 
 
 def _cfg_batch64():
-    parts = image_batch(64, 1000)
-    return dict(parts=parts, h=16.0, max_iter=50, name="voronoi_batch64_uneven_d3_h16")
+    images = [image_batch_image(i, 1000) for i in range(64)]
+    return dict(parts=[image_features(im) for im in images], images=images, h=16.0, max_iter=50,
+                name="voronoi_batch64_uneven_d3_h16")
 
 
 def _cfg_sweep():
@@ -212,7 +224,8 @@ def _cfg_sweep():
 
 #: name -> zero-argument builder returning dict(points, h, max_iter, name);
 #: batched workloads give dict(parts=[...], h, max_iter, name) instead, and
-#: bandwidth sweeps dict(points, hs=[...], h, max_iter, name)
+#: bandwidth sweeps dict(points, hs=[...], h, max_iter, name); image
+#: workloads add the uint8 image and xy_scale (batches: the list of images)
 WORKLOADS = {
     "image_321x481_d3": _cfg_image_small,
     "image_1080p_d5": _cfg_1080p,

@@ -232,6 +232,51 @@ def test_wide_dimensions_host_only_checks(lib):
         gridshift.gs_destroy(ctx)
 
 
+def test_image_entry_points_host_only_checks(lib):
+    # argument checks of gs_fit_image / gs_fit_image_batched, made before any
+    # device work
+    ctx = gridshift.gs_create(5, 12.0, 50)
+    try:
+        # an empty image returns at once
+        st, k, info = gridshift.gs_fit_image(ctx, 0, 0, 7, 3, 0.5, 0, 0, 0)
+        assert st == gridshift.GS_OK and k == 0 and info.converged == 1
+        for args in ((1, 1, 3, 0.0),      # d = 3 against the context's 5
+                     (1, 1, 5, 0.5),      # d = 7
+                     (-1, 4, 3, 0.5),     # negative height
+                     (4, -1, 3, 0.5),     # negative width
+                     (1 << 16, 1 << 16, 3, 0.5),  # 2^32 pixels
+                     (1, 1, 0, 0.5), (1, 1, 9, 0.5),  # channels
+                     (1, 1, 3, -1.0), (1, 1, 3, float("nan")), (1, 1, 3, float("inf"))):
+            H, W, C, s = args
+            st, _, _ = gridshift.gs_fit_image(ctx, 0, H, W, C, s, 0, 0, 0)
+            assert st == gridshift.GS_E_INVALID, args
+        # pixels but no output
+        st, _, _ = gridshift.gs_fit_image(ctx, 1, 2, 2, 3, 0.5, 0, 0, 0)
+        assert st == gridshift.GS_E_INVALID
+        # the host-buffer stream of images: no image is no work; bad
+        # arguments are rejected before any device work
+        assert gridshift.gs_fit_images_host(ctx, [], 4, 4, 3, 0.5, [], [], 0)[0] == gridshift.GS_OK
+        for args in (([1], 4, 4, 3, 0.0, [1]),      # d = 3 against 5
+                     ([0], 4, 4, 3, 0.5, [1]),      # NULL image
+                     ([1], 4, 4, 3, 0.5, [0]),      # NULL labels
+                     ([1], -4, 4, 3, 0.5, [1]),     # negative height
+                     ([1], 4, 4, 9, 0.5, [1])):     # channels
+            imgs, H, W, C, sc, labs = args
+            st, _, _ = gridshift.gs_fit_images_host(ctx, imgs, H, W, C, sc, labs, [], 0)
+            assert st == gridshift.GS_E_INVALID, args
+    finally:
+        gridshift.gs_destroy(ctx)
+    ctx = gridshift.gs_create(3, 12.0, 50)
+    try:
+        st, mo, infos = gridshift.gs_fit_image_batched(ctx, 0, 3, [0, 0, 0], 0, 0, 0)
+        assert st == gridshift.GS_OK and mo == [0, 0, 0]
+        for C, offsets in ((4, [0, 5]), (3, [1, 5]), (3, [0, 5, 4]), (0, [0, 5])):
+            st, _, _ = gridshift.gs_fit_image_batched(ctx, 1, C, offsets, 1, 0, 0)
+            assert st == gridshift.GS_E_INVALID, (C, offsets)
+    finally:
+        gridshift.gs_destroy(ctx)
+
+
 def test_tuning_host_only_checks(lib, tmp_path):
     ctx = gridshift.gs_create(5, 12.0, 50)
     try:
