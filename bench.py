@@ -86,23 +86,23 @@ def loop_scope_bytes(probe_cell_steps: int, d: int, fp32: bool) -> int:
 # on (the files that define k_range, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
-    ("image_1080p_d5", "fp64", "k_loop"): (138.13e6, "f73bd0d3821ab3d0"),
-    ("image_1080p_d5", "fp64", "k_bin"): (89.03e6, "f73bd0d3821ab3d0"),
+    ("image_1080p_d5", "fp64", "k_loop"): (154.02e6, "792682f2d6c4bd7c"),
+    ("image_1080p_d5", "fp64", "k_bin"): (88.70e6, "792682f2d6c4bd7c"),
     # the 4M-point mixture with the per-point passes as launches of their own
     # (--tune split_min=0)
-    ("gmm_4M_d6", "fp64", "k_loop"): (1427.94e6, "f73bd0d3821ab3d0"),
-    ("gmm_4M_d6", "fp64", "k_bin"): (110.16e6, "f73bd0d3821ab3d0"),
-    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.02e6, "f73bd0d3821ab3d0"),
-    ("gmm_4M_d6", "fp64", "k_prep_sums"): (366.48e6, "f73bd0d3821ab3d0"),
-    ("gmm_4M_d6", "fp32", "k_loop"): (870.83e6, "f73bd0d3821ab3d0"),
+    ("gmm_4M_d6", "fp64", "k_loop"): (1472.85e6, "792682f2d6c4bd7c"),
+    ("gmm_4M_d6", "fp64", "k_bin"): (109.54e6, "792682f2d6c4bd7c"),
+    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.16e6, "792682f2d6c4bd7c"),
+    ("gmm_4M_d6", "fp64", "k_prep_sums"): (378.15e6, "792682f2d6c4bd7c"),
+    ("gmm_4M_d6", "fp32", "k_loop"): (892.36e6, "792682f2d6c4bd7c"),
     # the 10M-point mixture: the 4M-point captures scaled by the units one
     # launch processes (points for the per-point kernels, x 2.5; active
     # cell-updates for k_loop, 285,298 against 205,764, x 1.3865)
-    ("gmm_10M_d6", "fp64", "k_loop"): (1979.8e6, "f73bd0d3821ab3d0"),
-    ("gmm_10M_d6", "fp64", "k_bin"): (275.4e6, "f73bd0d3821ab3d0"),
-    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.05e6, "f73bd0d3821ab3d0"),
-    ("gmm_10M_d6", "fp64", "k_prep_sums"): (916.2e6, "f73bd0d3821ab3d0"),
-    ("gmm_10M_d6", "fp32", "k_loop"): (1207.4e6, "f73bd0d3821ab3d0"),
+    ("gmm_10M_d6", "fp64", "k_loop"): (2042.2e6, "792682f2d6c4bd7c"),
+    ("gmm_10M_d6", "fp64", "k_bin"): (273.9e6, "792682f2d6c4bd7c"),
+    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.4e6, "792682f2d6c4bd7c"),
+    ("gmm_10M_d6", "fp64", "k_prep_sums"): (945.4e6, "792682f2d6c4bd7c"),
+    ("gmm_10M_d6", "fp32", "k_loop"): (1237.3e6, "792682f2d6c4bd7c"),
 }
 
 

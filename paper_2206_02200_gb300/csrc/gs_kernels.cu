@@ -81,51 +81,54 @@ struct Word<4, float> {
   }
 };
 
-// Extremes of one coordinate: order codes (signed integers in the order of
-// the values, -0 as +0) of the least and greatest value, and the largest
-// magnitude's bits.  Non-finite values are counted, not compared.
+// Extremes of one coordinate as order codes: signed integers whose order is
+// the order of the values (code = bits with the magnitude bits flipped when
+// the sign bit is set; -0 sits just below +0).  Per value only the code and
+// one min/max pair: a non-finite value shows up as an extreme (+inf and
+// positive NaNs above every finite code, -inf and negative NaNs below), and
+// the largest magnitude is that of the least or the greatest value.
 template <typename T>
 struct RangeAcc {
   using U = typename Bits<T>::U;
   using S = typename Bits<T>::S;
   static constexpr int kBits = 8 * (int)sizeof(U);
   static constexpr U kSign = (U)1 << (kBits - 1);
+  static constexpr U kInfBits = Bits<T>::kExpMask << Bits<T>::kExpShift;  // +inf
   S mn = (S)(kSign - 1), mx = (S)kSign;
-  U ma = 0;
-  __device__ __forceinline__ void add(U b, unsigned long long& bad) {
-    if (((b >> Bits<T>::kExpShift) & Bits<T>::kExpMask) == Bits<T>::kExpMask) {
-      ++bad;
-      return;
-    }
+  __device__ __forceinline__ void add(U b) {
     const S o = ord(b);
     mn = o < mn ? o : mn;
     mx = o > mx ? o : mx;
-    const U ab = b & (kSign - 1);
-    ma = ab > ma ? ab : ma;
   }
   static __device__ __forceinline__ S ord(U b) {
-    if (b == kSign) b = 0;
     const S s = (S)b;
-    return s ^ ((s >> (kBits - 1)) & (S)(kSign - 1));
+    return s ^ (S)((U)(s >> (kBits - 1)) >> 1);
   }
-  static __device__ __forceinline__ U bits(S o) { return (U)(o ^ ((o >> (kBits - 1)) & (S)(kSign - 1))); }
-  __device__ __forceinline__ bool empty() const { return mn == (S)(kSign - 1); }
+  static __device__ __forceinline__ U bits(S o) { return (U)(o ^ (S)((U)(o >> (kBits - 1)) >> 1)); }
+  __device__ __forceinline__ bool empty() const { return mn > mx; }
+  // some value was +-inf or NaN (non-empty accumulators)
+  __device__ __forceinline__ bool nonfinite() const {
+    return mx >= ord(kInfBits) || mn <= ord(kInfBits | kSign);
+  }
   __device__ __forceinline__ void merge(const RangeAcc& r) {
     mn = r.mn < mn ? r.mn : mn;
     mx = r.mx > mx ? r.mx : mx;
-    ma = r.ma > ma ? r.ma : ma;
   }
   __device__ __forceinline__ RangeAcc shfl_down(int o) const {
     RangeAcc r;
     r.mn = (S)__shfl_down_sync(kFull, (U)mn, o);
     r.mx = (S)__shfl_down_sync(kFull, (U)mx, o);
-    r.ma = __shfl_down_sync(kFull, ma, o);
     return r;
   }
-  // the float64 order codes and magnitude bits (non-empty accumulators)
+  // float64 order codes (-0 taken as +0) and the largest magnitude's bits
+  // (finite, non-empty accumulators)
   __device__ __forceinline__ int64_t mn64() const { return ord_of_bits(Bits<T>::widen(bits(mn))); }
   __device__ __forceinline__ int64_t mx64() const { return ord_of_bits(Bits<T>::widen(bits(mx))); }
-  __device__ __forceinline__ uint64_t ma64() const { return Bits<T>::widen(ma); }
+  __device__ __forceinline__ uint64_t ma64() const {
+    const uint64_t a = Bits<T>::widen(bits(mn)) & 0x7FFFFFFFFFFFFFFFull;
+    const uint64_t c = Bits<T>::widen(bits(mx)) & 0x7FFFFFFFFFFFFFFFull;
+    return a > c ? a : c;
+  }
 };
 
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
@@ -215,7 +218,6 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
   const int64_t S = nthreads - nthreads % D;  // stride in words, a multiple of D
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Acc acc[W];
-  unsigned long long bad = 0;
   if constexpr (kStaged) {
     if (t < S) {
       const unsigned ring = (unsigned)__cvta_generic_to_shared(&s_ring[0][threadIdx.x]);
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
         U b[W];
         Unpack<T>::get(s_ring[slot][threadIdx.x], b);
 #pragma unroll
-        for (int j = 0; j < W; ++j) acc[j].add(b[j], bad);
+        for (int j = 0; j < W; ++j) acc[j].add(b[j]);
         // the slot is read (into registers): its next word
         const int64_t qn = q + kDepth * S;
         if (qn < words) cp_async16(ring + slot * kSlot, pts + qn * W);
@@ -250,13 +252,13 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
 #pragma unroll
       for (int u = 0; u < kInFlight; ++u)
 #pragma unroll
-        for (int j = 0; j < W; ++j) acc[j].add(b[u][j], bad);
+        for (int j = 0; j < W; ++j) acc[j].add(b[u][j]);
     }
     for (; q < words; q += S) {
       U b[W];
       Word<W, T>::load(pts + q * W, b);
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j].add(b[j], bad);
+      for (int j = 0; j < W; ++j) acc[j].add(b[j]);
     }
   }
   // threads at or past S hold empty accumulators, which combine as no-ops
@@ -284,9 +286,13 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
       for (int e = (a - base_w + D) % D; e < PW; e += D) r.merge(s_part[w][e]);
     }
     if (!r.empty()) {
-      s_mn[a] = r.mn64();
-      s_mx[a] = r.mx64();
-      s_ma[a] = r.ma64();
+      if (r.nonfinite()) {
+        atomicAdd(&s_bad, 1ull);
+      } else {
+        s_mn[a] = r.mn64();
+        s_mx[a] = r.mx64();
+        s_ma[a] = r.ma64();
+      }
     }
   }
   __syncthreads();
@@ -296,16 +302,17 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
       U b[1];
       Word<1, T>::load(pts + e, b);
       Acc r;
-      r.add(b[0], bad);
+      r.add(b[0]);
       const int a = (int)(e % D);
-      if (!r.empty()) {
+      if (r.nonfinite()) {
+        atomicAdd(&s_bad, 1ull);
+      } else {
         atomicMin(&s_mn[a], (long long)r.mn64());
         atomicMax(&s_mx[a], (long long)r.mx64());
         atomicMax(&s_ma[a], (unsigned long long)r.ma64());
       }
     }
   }
-  if (bad) atomicAdd(&s_bad, bad);
   __syncthreads();
   if (threadIdx.x < D && s_mn[threadIdx.x] != INT64_MAX) {
     atomicMin(&fl->min_ord[threadIdx.x], s_mn[threadIdx.x]);

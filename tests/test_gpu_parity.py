@@ -256,9 +256,15 @@ def test_identical_points_and_exact_faces():
 
 def test_nonfinite_input_is_rejected():
     g = gridshift.GridShift(2, 1.0, 10)
-    for bad in (np.nan, np.inf, -np.inf):
+    for bad in (np.nan, -np.nan, np.inf, -np.inf):
         X = np.zeros((100, 2))
         X[37, 1] = bad
+        with pytest.raises(gridshift.GridShiftError) as e:
+            g.fit(torch.from_numpy(X).cuda())
+        assert e.value.status == gridshift.GS_E_INVALID
+    # every value non-finite (a NaN whose bits are all ones, both signs)
+    for bits in (0x7FFFFFFFFFFFFFFF, 0xFFFFFFFFFFFFFFFF):
+        X = np.full((64, 2), bits, dtype=np.uint64).view(np.float64)
         with pytest.raises(gridshift.GridShiftError) as e:
             g.fit(torch.from_numpy(X).cuda())
         assert e.value.status == gridshift.GS_E_INVALID
@@ -270,9 +276,14 @@ def test_nonfinite_input_is_rejected():
 def test_nonfinite_float32_input_is_rejected():
     # float32 input: the key range reads the values in their own width
     g = gridshift.GridShift(3, 1.0, 10)
-    for bad in (np.nan, np.inf, -np.inf):
+    for bad in (np.nan, -np.nan, np.inf, -np.inf):
         X = np.zeros((1001, 3), dtype=np.float32)
         X[500, 2] = bad
+        with pytest.raises(gridshift.GridShiftError) as e:
+            g.fit(torch.from_numpy(X).cuda())
+        assert e.value.status == gridshift.GS_E_INVALID
+    for bits in (0x7FFFFFFF, 0xFFFFFFFF):
+        X = np.full((33, 3), bits, dtype=np.uint32).view(np.float32)
         with pytest.raises(gridshift.GridShiftError) as e:
             g.fit(torch.from_numpy(X).cuda())
         assert e.value.status == gridshift.GS_E_INVALID
