@@ -86,23 +86,23 @@ def loop_scope_bytes(probe_cell_steps: int, d: int, fp32: bool) -> int:
 # on (the files that define k_range, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
-    ("image_1080p_d5", "fp64", "k_loop"): (154.02e6, "792682f2d6c4bd7c"),
-    ("image_1080p_d5", "fp64", "k_bin"): (88.70e6, "792682f2d6c4bd7c"),
+    ("image_1080p_d5", "fp64", "k_loop"): (149.26e6, "500f52af1b15d0b8"),
+    ("image_1080p_d5", "fp64", "k_bin"): (89.35e6, "500f52af1b15d0b8"),
     # the 4M-point mixture with the per-point passes as launches of their own
     # (--tune split_min=0)
-    ("gmm_4M_d6", "fp64", "k_loop"): (1472.85e6, "792682f2d6c4bd7c"),
-    ("gmm_4M_d6", "fp64", "k_bin"): (109.54e6, "792682f2d6c4bd7c"),
-    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.16e6, "792682f2d6c4bd7c"),
-    ("gmm_4M_d6", "fp64", "k_prep_sums"): (378.15e6, "792682f2d6c4bd7c"),
-    ("gmm_4M_d6", "fp32", "k_loop"): (892.36e6, "792682f2d6c4bd7c"),
+    ("gmm_4M_d6", "fp64", "k_loop"): (1470.79e6, "500f52af1b15d0b8"),
+    ("gmm_4M_d6", "fp64", "k_bin"): (109.54e6, "500f52af1b15d0b8"),
+    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.14e6, "500f52af1b15d0b8"),
+    ("gmm_4M_d6", "fp64", "k_prep_sums"): (382.56e6, "500f52af1b15d0b8"),
+    ("gmm_4M_d6", "fp32", "k_loop"): (882.84e6, "500f52af1b15d0b8"),
     # the 10M-point mixture: the 4M-point captures scaled by the units one
     # launch processes (points for the per-point kernels, x 2.5; active
     # cell-updates for k_loop, 285,298 against 205,764, x 1.3865)
-    ("gmm_10M_d6", "fp64", "k_loop"): (2042.2e6, "792682f2d6c4bd7c"),
-    ("gmm_10M_d6", "fp64", "k_bin"): (273.9e6, "792682f2d6c4bd7c"),
-    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.4e6, "792682f2d6c4bd7c"),
-    ("gmm_10M_d6", "fp64", "k_prep_sums"): (945.4e6, "792682f2d6c4bd7c"),
-    ("gmm_10M_d6", "fp32", "k_loop"): (1237.3e6, "792682f2d6c4bd7c"),
+    ("gmm_10M_d6", "fp64", "k_loop"): (2039.3e6, "500f52af1b15d0b8"),
+    ("gmm_10M_d6", "fp64", "k_bin"): (273.8e6, "500f52af1b15d0b8"),
+    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.4e6, "500f52af1b15d0b8"),
+    ("gmm_10M_d6", "fp64", "k_prep_sums"): (956.4e6, "500f52af1b15d0b8"),
+    ("gmm_10M_d6", "fp32", "k_loop"): (1224.1e6, "500f52af1b15d0b8"),
 }
 
 
@@ -413,7 +413,8 @@ def run_reference(args, rank: int, world: int):
             "median_ms_per_step": 1e3 * statistics.median(times) if times else None,
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, args.workload, update=args.update),
+            "config": {k: v for k, v in workload_config(w, args.workload, update=args.update).items()
+                       if k != "l2"},  # host cores: no device cache to flush
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
                              "nproc": host_cores(),
                              "sample": (f"{args.steps} steps of {P} independent single-threaded "

@@ -20,8 +20,9 @@ struct BinTable {
   uint32_t* cnt;
   uint32_t* off;
   uint32_t* id;
-  uint64_t* acc;   // cap x d x 4, by slot: the exact sums' limb accumulators (float32
-                   // variant with a counting sort: cap x d float sums of offsets)
+  uint64_t* acc;   // cap x d x 4: the exact sums' limb accumulators, by cell id (the
+                   // counting sort) or by slot (sums formed in binning); float32
+                   // variant with a counting sort: d float sums of offsets per id
   uint32_t* list;  // maxcells
   uint32_t cap;    // power of two
 };

@@ -225,11 +225,16 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
 #pragma unroll
       for (int a = 0; a < D; ++a)
         x[e][a] = idx[e] != kNone ? (float)__ldg(pts + (size_t)idx[e] * D + a) : 0.f;
-    // the cells' keys, loaded while the coordinates are in flight
+    // the cells' ids (the sums are indexed by them, as in phase_cell_sums)
+    // and keys, loaded while the coordinates are in flight
+    uint32_t cid[E];
     uint64_t ckey[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) ckey[e] = s[e] != kNone ? A.T0.key[s[e]] : 0ull;
-    uint32_t cur = kNone;
+    for (int e = 0; e < E; ++e) {
+      cid[e] = s[e] != kNone ? A.T0.id[s[e]] : 0u;
+      ckey[e] = s[e] != kNone ? A.T0.key[s[e]] : 0ull;
+    }
+    uint32_t cur = kNone, curid = 0;
     float org[D];
     FF V[D];
 #pragma unroll
@@ -237,9 +242,10 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
       if (s[e] != cur) {
         if (cur != kNone) {
 #pragma unroll
-          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
+          for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)curid * D + a], V[a].value());
         }
         cur = s[e];
+        curid = cid[e];
         if (cur != kNone) {
 #pragma unroll
           for (int a = 0; a < D; ++a) org[a] = (float)face_of(g_plan, A.thr, ckey[e], a);
@@ -271,7 +277,7 @@ __device__ void phase_cell_sums32(const LoopArgs& A) {
     }
     if (head && cur != kNone) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)cur * D + a], V[a].value());
+      for (int a = 0; a < D; ++a) atomicAdd(&tacc[(size_t)curid * D + a], V[a].value());
     }
   }
 }
@@ -314,11 +320,11 @@ __device__ void phase_level0_32(const LoopArgs& A, uint32_t m0, uint32_t maskA) 
         // all the sums are loaded before any store
         float sum[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) sum[a] = __ldcg(tacc + (size_t)s * D + a);
+        for (int a = 0; a < D; ++a) sum[a] = __ldcg(tacc + (size_t)id * D + a);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           r[3 + a] = __float_as_uint(sum[a] / (float)cnt);
-          tacc[(size_t)s * D + a] = 0.f;
+          tacc[(size_t)id * D + a] = 0.f;
         }
       }
       G.id[sa] = id;
@@ -596,6 +602,11 @@ __device__ void phase_update32(const LoopArgs& A, int t, uint32_t m, uint32_t ma
       for (int a = 0; a < D; ++a) org[a] = (double)(float)face_of(g_plan, A.thr, key, a);
       for (int p = glane; p < nprobe; p += GS) {
         const uint64_t qk = key + __ldg(&A.dtab[p]);
+        // the level's occupancy filter (a superset of its keys, also in the
+        // pencil form of step 0) skips the absent neighbours on chip, as in
+        // the main probe loop
+        const uint32_t fb = filter_bit(qk, lg);
+        if (A.tune.filter && !((s_filter[fb >> 5] >> (fb & 31)) & 1u)) continue;
         const uint32_t sl = row_find<D>(grow, mask, qk);
         if (sl == kNone) continue;
         const uint32_t* r = grow + (size_t)sl * W;

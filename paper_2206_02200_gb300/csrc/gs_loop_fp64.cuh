@@ -125,11 +125,14 @@ __device__ void phase_scatter(const LoopArgs& A) {
 // segment adds the segment's sum.
 constexpr int kSumRun = 4;
 
-// Adds V into the sum accumulators of the cell in binning-table slot s.
+// Adds V into the sum accumulators of the cell of id `id` (the counting
+// sort's sums are indexed by the cell's id, its rank in the sorted order, so
+// consecutive runs add to consecutive accumulators; sums formed in binning
+// are indexed by the table slot).
 template <int D>
-__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t s, const u128 (&V)[D]) {
+__device__ __forceinline__ void add_cell_sum(const LoopArgs& A, uint32_t id, const u128 (&V)[D]) {
 #pragma unroll
-  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)s * D + a) * 4, V[a]);
+  for (int a = 0; a < D; ++a) atomic_add_fixed(A.T0.acc + ((size_t)id * D + a) * 4, V[a]);
 }
 
 template <int D, typename T>
@@ -164,16 +167,21 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
 #pragma unroll
       for (int a = 0; a < D; ++a)
         raw[e][a] = idx[e] != kNone ? load_bits<T>(pts + (size_t)src[e] * D + a) : 0ull;
+    // the cells' ids, loaded while the coordinates are in flight
+    uint32_t cid[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) cid[e] = s[e] != kNone ? A.T0.id[s[e]] : 0u;
     // runs within the lane
-    uint32_t cur = s[0];
+    uint32_t cur = s[0], curid = cid[0];
     u128 V[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) V[a] = to_fixed(raw[0][a], g_plan.L[a], inexact, werr);
 #pragma unroll
     for (int e = 1; e < E; ++e) {
       if (s[e] != cur) {
-        if (cur != kNone) add_cell_sum<D>(A, cur, V);
+        if (cur != kNone) add_cell_sum<D>(A, curid, V);
         cur = s[e];
+        curid = cid[e];
 #pragma unroll
         for (int a = 0; a < D; ++a) V[a] = 0;
       }
@@ -197,7 +205,7 @@ __device__ void phase_cell_sums(const LoopArgs& A, unsigned& inexact, unsigned& 
         }
       }
     }
-    if (head && cur != kNone) add_cell_sum<D>(A, cur, V);
+    if (head && cur != kNone) add_cell_sum<D>(A, curid, V);
   }
 }
 
@@ -221,7 +229,7 @@ __device__ void phase_level0(const LoopArgs& A, uint32_t m0, uint32_t maskA, uns
     if (sa != kNone) {
       ulonglong2* r = G.row + (size_t)sa * (D + 1);
       r[0] = make_ulonglong2((uint64_t)cnt, 0ull);
-      settle_sums<D>(T0.acc + (size_t)s * D * 4, r + 1, g_plan.L, werr);
+      settle_sums<D>(T0.acc + (size_t)(A.tune.bin_sums ? s : id) * D * 4, r + 1, g_plan.L, werr);
       G.id[sa] = id;
       G.list[id] = sa;
     }
