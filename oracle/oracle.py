@@ -165,40 +165,3 @@ def track_window(frame, width: int, height: int, h: float, bins, rect) -> tuple:
              mean_y=float(out[2]) / cnt if cnt else float("nan"),
              min_x=int(out[3]), max_x=int(out[4]), min_y=int(out[5]), max_y=int(out[6]))
     return r, present[:k]
-
-
-def track(frames, width: int, height: int, h: float, o, length: float, window_width: float,
-          bins, f: float = 1.0, eta: float = 0.5, max_inner: int = 50) -> list:
-    """Algorithm 2 from an initial centre, window size and reference cells B,
-    over frames[0], frames[1], ...: per frame, the search window W(o, l/f, w/f)
-    (the pixels within l/2 of o_x and w/2 of o_y) is applied until the centre
-    moves by less than eta (at most max_inner times).  An empty R grows l and w
-    by 1.1; otherwise o moves to R's mean position, B becomes the cells R
-    occupies, and l (w) shrinks by 0.99 where R's x (y) extent is below it,
-    else grows by 1.01.  Returns per frame (o, l, w, inner steps, |B|)."""
-    import math
-    o = (float(o[0]), float(o[1]))
-    l, w = float(length), float(window_width)
-    d = np.asarray(frames[0]).reshape(int(height) * int(width), -1).shape[1]
-    B = np.asarray(bins, dtype=np.int64).reshape(-1, d)
-    emitted = []
-    for fr in frames:
-        inner = 0
-        while inner < max_inner:
-            inner += 1
-            lo, wo = l / f, w / f
-            rect = (math.ceil(o[0] - lo / 2), math.ceil(o[1] - wo / 2),
-                    math.floor(o[0] + lo / 2) + 1, math.floor(o[1] + wo / 2) + 1)
-            r, present = track_window(fr, width, height, h, B, rect)
-            if r["count"] == 0:
-                l, w = 1.1 * l, 1.1 * w
-                continue
-            step = math.hypot(r["mean_x"] - o[0], r["mean_y"] - o[1])
-            o = (r["mean_x"], r["mean_y"])
-            B = B[present == 1]
-            l = l * (0.99 if r["max_x"] - r["min_x"] < l else 1.01)
-            w = w * (0.99 if r["max_y"] - r["min_y"] < w else 1.01)
-            if step < eta:
-                break
-        emitted.append((o, l, w, inner, int(B.shape[0])))
-    return emitted

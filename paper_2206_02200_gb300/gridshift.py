@@ -593,85 +593,3 @@ def window_rect(o, length: float, width: float):
     import math
     return (math.ceil(o[0] - length / 2), math.ceil(o[1] - width / 2),
             math.floor(o[0] + length / 2) + 1, math.floor(o[1] + width / 2) + 1)
-
-
-class Tracker:
-    """The tracker of Algorithm 2 over frames of `height` x `width` pixels with
-    d colour channels (CUDA tensors of width * height x d, row-major, y outer).
-
-    State: centre o, window size (length along x, width along y) and the
-    reference set B of colour cells floor(c / h) (a k x d int64 array).  Each
-    frame: search windows W(o, length / f, width / f) until the centre moves by
-    less than eta (at most max_inner times); a window with no pixel of B grows
-    the size by 1.1; otherwise the centre moves to the mean position of R, B
-    becomes the cells of R, and the size shrinks by 0.99 where R's extent is
-    below it, else grows by 1.01.
-    """
-
-    def __init__(self, d: int, h: float, width: int, height: int, o, length: float,
-                 window_width: float, bins, f: float = 1.0, eta: float = 0.5,
-                 max_inner: int = 50):
-        import numpy as np
-        self.ctx = GridShift(d, h, 1)
-        self.W, self.H = int(width), int(height)
-        self.o = (float(o[0]), float(o[1]))
-        self.l, self.w = float(length), float(window_width)
-        self.B = np.ascontiguousarray(np.asarray(bins, dtype=np.int64).reshape(-1, d))
-        self.f, self.eta, self.max_inner = float(f), float(eta), int(max_inner)
-
-    def close(self) -> None:
-        self.ctx.close()
-
-    def window_step(self, frame, rect):
-        """One R (gs_track_window) on a CUDA frame tensor: (result dict, present)."""
-        import torch
-        dt = GS_IN_F64 if frame.dtype == torch.float64 else GS_IN_F32
-        if not frame.is_cuda or not frame.is_contiguous():
-            raise ValueError("frame must be a contiguous CUDA tensor")
-        gs_set_stream(self.ctx._ctx, torch.cuda.current_stream(frame.device).cuda_stream)
-        st, res, present = gs_track_window(self.ctx._ctx, frame.data_ptr(), dt, self.W, self.H,
-                                           self.B, *rect)
-        if st != GS_OK:
-            raise GridShiftError(st, gs_get_last_error(self.ctx._ctx))
-        return res.as_dict(), present
-
-    def _search_rect(self):
-        """The pixel rectangle searched next: the window's size divided by f
-        around the current centre."""
-        return window_rect(self.o, self.l / self.f, self.w / self.f)
-
-    def _absorb(self, r: dict, present) -> float | None:
-        """Folds one window result into the state.  No pixel of the reference
-        colours in the window: the window widens (x1.1 on both sides) and the
-        centre stays, which is not convergence (None).  Otherwise the centre
-        jumps to the mean position of those pixels, the reference colours
-        shrink to the ones seen, and each side of the window tightens
-        (x0.99) where the pixels' extent along it is below it, else loosens
-        (x1.01).  Returns how far the centre moved."""
-        import math
-        if r["count"] == 0:
-            self.l, self.w = 1.1 * self.l, 1.1 * self.w
-            return None
-        ext_x, ext_y = r["max_x"] - r["min_x"], r["max_y"] - r["min_y"]
-        self.l *= 0.99 if ext_x < self.l else 1.01
-        self.w *= 0.99 if ext_y < self.w else 1.01
-        self.B = self.B[present.astype(bool)]
-        centre = (r["mean_x"], r["mean_y"])
-        moved = math.hypot(centre[0] - self.o[0], centre[1] - self.o[1])
-        self.o = centre
-        return moved
-
-    def step(self, frame) -> dict:
-        """Tracks one frame (Sec. 2.3, Algorithm 2): window searches are
-        repeated until the centre settles (moves by less than eta) or
-        max_inner searches have run; returns the state the frame leaves (the
-        emitted window) and the number of searches."""
-        searches = 0
-        while searches < self.max_inner:
-            searches += 1
-            r, present = self.window_step(frame, self._search_rect())
-            moved = self._absorb(r, present)
-            if moved is not None and moved < self.eta:
-                break
-        return {"o": self.o, "length": self.l, "width": self.w, "inner": searches,
-                "bins": int(self.B.shape[0])}

@@ -487,28 +487,3 @@ def test_track_window_against_exact_rationals(seed):
         assert r["mean_x"] == sum(xs) / len(xs) and r["mean_y"] == sum(ys) / len(ys)
         assert (r["min_x"], r["max_x"], r["min_y"], r["max_y"]) == (min(xs), max(xs), min(ys), max(ys))
     assert present.tolist() == pres
-
-
-def test_tracker_follows_a_moving_object():
-    # Algorithm 2 on a disc moving 3 px per frame: the emitted centre stays
-    # within 2 px of the disc's centre, and the window never loses it
-    H, W, T, h = 96, 128, 8, 16.0
-    rng = np.random.default_rng(11)
-    yy, xx = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64),
-                         indexing="ij")
-    bg = np.where((xx < W / 2)[..., None], [[40.0, 200.0, 90.0]], [[180.0, 60.0, 30.0]])
-    centres = np.array([[50.0 + 3.0 * t, 40.0 + 2.0 * t] for t in range(T)])
-    frames = []
-    for c in centres:
-        img = bg.copy()
-        img[(xx - c[0]) ** 2 + (yy - c[1]) ** 2 <= 144.0] = [120.0, 120.0, 230.0]
-        frames.append(np.rint(np.clip(img + rng.normal(0.0, 5.0, img.shape), 0, 255)))
-    f0 = frames[0].reshape(H * W, 3)
-    yy, xx = np.divmod(np.arange(H * W), W)
-    inside = (xx - centres[0, 0]) ** 2 + (yy - centres[0, 1]) ** 2 <= 12.0 ** 2
-    B = np.unique(np.array([_cell(c, h) for c in f0[inside]], dtype=np.int64), axis=0)
-    out = oracle.track([fr.reshape(H * W, 3) for fr in frames[1:]], W, H, h,
-                       centres[0] + np.array([2.0, -1.0]), 40.0, 40.0, B, f=1.0, eta=0.25)
-    for (o, l, w, inner, nb), c in zip(out, centres[1:]):
-        assert math.hypot(o[0] - c[0], o[1] - c[1]) < 2.0
-        assert nb > 0 and inner >= 1
