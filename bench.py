@@ -86,23 +86,23 @@ def loop_scope_bytes(probe_cell_steps: int, d: int, fp32: bool) -> int:
 # on (the files that define k_range, k_bin and k_loop, not the host
 # code): a figure is reported only while those sources still hash the same.
 TRAFFIC = {
-    ("image_1080p_d5", "fp64", "k_loop"): (149.26e6, "500f52af1b15d0b8"),
-    ("image_1080p_d5", "fp64", "k_bin"): (89.35e6, "500f52af1b15d0b8"),
+    ("image_1080p_d5", "fp64", "k_loop"): (147.19e6, "1b49d2decd1369a4"),
+    ("image_1080p_d5", "fp64", "k_bin"): (86.01e6, "1b49d2decd1369a4"),
     # the 4M-point mixture with the per-point passes as launches of their own
     # (--tune split_min=0)
-    ("gmm_4M_d6", "fp64", "k_loop"): (1470.79e6, "500f52af1b15d0b8"),
-    ("gmm_4M_d6", "fp64", "k_bin"): (109.54e6, "500f52af1b15d0b8"),
-    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.14e6, "500f52af1b15d0b8"),
-    ("gmm_4M_d6", "fp64", "k_prep_sums"): (382.56e6, "500f52af1b15d0b8"),
-    ("gmm_4M_d6", "fp32", "k_loop"): (882.84e6, "500f52af1b15d0b8"),
+    ("gmm_4M_d6", "fp64", "k_loop"): (1466.28e6, "1b49d2decd1369a4"),
+    ("gmm_4M_d6", "fp64", "k_bin"): (105.81e6, "1b49d2decd1369a4"),
+    ("gmm_4M_d6", "fp64", "k_prep_scatter"): (20.13e6, "1b49d2decd1369a4"),
+    ("gmm_4M_d6", "fp64", "k_prep_sums"): (378.93e6, "1b49d2decd1369a4"),
+    ("gmm_4M_d6", "fp32", "k_loop"): (880.22e6, "1b49d2decd1369a4"),
     # the 10M-point mixture: the 4M-point captures scaled by the units one
     # launch processes (points for the per-point kernels, x 2.5; active
     # cell-updates for k_loop, 285,298 against 205,764, x 1.3865)
-    ("gmm_10M_d6", "fp64", "k_loop"): (2039.3e6, "500f52af1b15d0b8"),
-    ("gmm_10M_d6", "fp64", "k_bin"): (273.8e6, "500f52af1b15d0b8"),
-    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.4e6, "500f52af1b15d0b8"),
-    ("gmm_10M_d6", "fp64", "k_prep_sums"): (956.4e6, "500f52af1b15d0b8"),
-    ("gmm_10M_d6", "fp32", "k_loop"): (1224.1e6, "500f52af1b15d0b8"),
+    ("gmm_10M_d6", "fp64", "k_loop"): (2033.0e6, "1b49d2decd1369a4"),
+    ("gmm_10M_d6", "fp64", "k_bin"): (264.5e6, "1b49d2decd1369a4"),
+    ("gmm_10M_d6", "fp64", "k_prep_scatter"): (50.3e6, "1b49d2decd1369a4"),
+    ("gmm_10M_d6", "fp64", "k_prep_sums"): (947.3e6, "1b49d2decd1369a4"),
+    ("gmm_10M_d6", "fp32", "k_loop"): (1220.4e6, "1b49d2decd1369a4"),
 }
 
 

@@ -231,14 +231,18 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
  * context's workspace, and fitted as gs_fit fits them: the result is the one
  * gs_fit gives for that float64 feature matrix (bit for bit in GS_FP64).
  * Only the image itself need be uploaded: one byte per channel and pixel
- * instead of eight bytes per feature.
+ * instead of eight bytes per feature.  The kernel that builds the features
+ * also takes their key range (Sec. 2.1 iii's cell bounds) from the pixels,
+ * so the features are not read back for it (GS_PHASE_RANGE times the build
+ * and the plan together).
  *   pixels     device uint8[height x width x channels], row-major: row y,
  *              column x, then the channels
  *   height, width  >= 0, height * width < 2^31
  *   channels   1 .. 8
  *   xy_scale   0 (no position features) or finite and > 0
  *   labels, modes, modes_cap, k_out, info: as gs_fit (labels in pixel order;
- *              info->launches counts the feature build as well)
+ *              info->launches counts the feature build as well: one launch,
+ *              two with positions)
  * The context's d must be channels + 2 (xy_scale > 0) or channels.  Returns
  * what gs_fit returns, or GS_E_INVALID for the arguments above. */
 gs_status gs_fit_image(gs_ctx* ctx, const uint8_t* pixels, int64_t height, int64_t width,

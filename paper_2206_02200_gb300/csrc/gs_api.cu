@@ -614,8 +614,38 @@ void gs_destroy(gs_ctx* ctx) {
   delete ctx;
 }
 
-gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int32_t* labels,
-                 double* modes, int64_t modes_cap, int64_t* k_out, gs_fit_info* info) {
+// The pixels of an image call (see FitArgs::img): the run builds their
+// features into the context's feature buffer.
+struct ImgSrc {
+  const uint8_t* px;
+  int64_t width;
+  int C;
+  bool xy;
+  double s;
+  double* tab;  // xy: width + n / width doubles of the buffer (position products)
+};
+
+static gs_status batched_entry(gs_ctx* ctx, const void* points, gs_dtype dtype,
+                               const int64_t* offsets, int B, int32_t* labels, double* modes,
+                               int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos,
+                               const ImgSrc* img);
+
+static void set_image(FitArgs& a, const ImgSrc* img) {
+  if (!img) return;
+  a.img = img->px;
+  a.img_feat = const_cast<double*>(static_cast<const double*>(a.points));
+  a.img_width = img->width;
+  a.img_C = img->C;
+  a.img_xy = img->xy;
+  a.img_s = img->s;
+  a.img_tab = img->tab;
+}
+
+// gs_fit, and the image calls (img: `points` is the context's feature
+// buffer, which the run fills).
+static gs_status fit_entry(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n,
+                           int32_t* labels, double* modes, int64_t modes_cap, int64_t* k_out,
+                           gs_fit_info* info, const ImgSrc* img) {
   if (!ctx) return GS_E_INVALID;
   ctx->err.clear();
   if (!k_out) return fail(ctx, GS_E_INVALID, "k_out is NULL");
@@ -657,6 +687,7 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   a.tune = ctx->tune;
   a.mixed = ctx->prec == GS_FP32_MIXED;
   a.sequential = ctx->update == GS_UPDATE_SEQUENTIAL;
+  set_image(a, img);
   double kms[kLoopPhases + 2 * kClockSteps] = {};
   gs_status st;
   const bool wide_ok = !a.mixed && !a.sequential;
@@ -665,6 +696,20 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
     if (!wide_ok)
       return fail(ctx, GS_E_INVALID, "d > 8 runs in GS_FP64 with the parallel update only");
     if (!ctx->wide && !(ctx->wide = wide_workspace_new())) return fail(ctx, GS_E_NOMEM, "wide workspace");
+    if (img) {
+      // the features first (the wide pipeline takes its own key range)
+      if (img->xy) {
+        ce = launch_axis_products(img->width, n / img->width, img->s, img->tab, ctx->stream);
+        if (ce != cudaSuccess)
+          return fail(ctx, GS_E_CUDA, std::string("k_axis_products: ") + cudaGetErrorName(ce));
+        inf.launches += 1;
+      }
+      ce = launch_image_features(img->px, n, img->width, img->C, img->xy, img->tab, a.img_feat,
+                                 nullptr, ctx->stream);
+      if (ce != cudaSuccess)
+        return fail(ctx, GS_E_CUDA, std::string("k_image_features: ") + cudaGetErrorName(ce));
+      inf.launches += 1;
+    }
     st = wide_fit(ctx->wide, a, k_out, &inf, &ctx->err);
   } else {
     uint32_t plan_st = kPlanOK;
@@ -702,6 +747,11 @@ gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int
   return st;
 }
 
+gs_status gs_fit(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n, int32_t* labels,
+                 double* modes, int64_t modes_cap, int64_t* k_out, gs_fit_info* info) {
+  return fit_entry(ctx, points, dtype, n, labels, modes, modes_cap, k_out, info, nullptr);
+}
+
 // The device the context last ran on: a change releases its buffers.
 static gs_status bind_device(gs_ctx* ctx) {
   int dev = 0;
@@ -714,20 +764,15 @@ static gs_status bind_device(gs_ctx* ctx) {
   return GS_OK;
 }
 
-// The float64 features of n pixels (channels C, positions if xy) into the
-// context's feature buffer, on its stream.
-static gs_status image_features(gs_ctx* ctx, const uint8_t* pixels, int64_t n, int64_t width,
-                                int C, bool xy, double s) {
+// The context's feature buffer of `words` doubles (the run of an image call
+// fills it: the features, then any position products).
+static gs_status feature_space(gs_ctx* ctx, int64_t words) {
   gs_status st = bind_device(ctx);
   if (st != GS_OK) return st;
-  const int d = C + (xy ? 2 : 0);
-  cudaError_t ce = ctx->feat.ensure((size_t)n * d);
+  cudaError_t ce = ctx->feat.ensure((size_t)words);
   if (ce != cudaSuccess)
     return fail(ctx, ce == cudaErrorMemoryAllocation ? GS_E_NOMEM : GS_E_CUDA,
                 std::string("image features: ") + cudaGetErrorName(ce));
-  ce = launch_image_features(pixels, n, width, C, xy, s, ctx->feat.p, ctx->stream);
-  if (ce != cudaSuccess)
-    return fail(ctx, GS_E_CUDA, std::string("k_image_features: ") + cudaGetErrorName(ce));
   return GS_OK;
 }
 
@@ -751,13 +796,11 @@ gs_status gs_fit_image(gs_ctx* ctx, const uint8_t* pixels, int64_t height, int64
   if (n > 0 && (!pixels || !labels)) return fail(ctx, GS_E_INVALID, "NULL pixels or labels");
   if (modes_cap < 0 || (modes_cap > 0 && !modes))
     return fail(ctx, GS_E_INVALID, "modes is NULL with modes_cap > 0");
-  if (n > 0) {
-    gs_status st = image_features(ctx, pixels, n, width, channels, xy, xy_scale);
-    if (st != GS_OK) return st;
-  }
-  gs_status st = gs_fit(ctx, ctx->feat.p, GS_IN_F64, n, labels, modes, modes_cap, k_out, info);
-  if (info && n > 0) info->launches += 1;
-  return st;
+  if (n == 0) return gs_fit(ctx, nullptr, GS_IN_F64, 0, labels, modes, modes_cap, k_out, info);
+  gs_status st = feature_space(ctx, n * ctx->d + (xy ? width + height : 0));
+  if (st != GS_OK) return st;
+  const ImgSrc img{pixels, width, channels, xy, xy_scale, xy ? ctx->feat.p + n * ctx->d : nullptr};
+  return fit_entry(ctx, ctx->feat.p, GS_IN_F64, n, labels, modes, modes_cap, k_out, info, &img);
 }
 
 gs_status gs_fit_images_host(gs_ctx* ctx, int count, const uint8_t* const* images, int64_t height,
@@ -873,15 +916,14 @@ gs_status gs_fit_image_batched(gs_ctx* ctx, const uint8_t* pixels, int channels,
   const int64_t n = offsets[B];
   if (n >= (1ll << 31)) return fail(ctx, GS_E_INVALID, "n out of range");
   if (n > 0 && (!pixels || !labels)) return fail(ctx, GS_E_INVALID, "NULL pixels or labels");
-  if (n > 0) {
-    gs_status st = image_features(ctx, pixels, n, 1, channels, false, 0.0);
-    if (st != GS_OK) return st;
-  }
-  gs_status st = gs_fit_batched(ctx, ctx->feat.p, GS_IN_F64, offsets, B, labels, modes, modes_cap,
-                                mode_offsets, infos);
-  if (n > 0)
-    for (int b = 0; b < B; ++b) infos[b].launches += 1;
-  return st;
+  if (n == 0)
+    return gs_fit_batched(ctx, nullptr, GS_IN_F64, offsets, B, labels, modes, modes_cap,
+                          mode_offsets, infos);
+  gs_status st = feature_space(ctx, n * ctx->d);
+  if (st != GS_OK) return st;
+  const ImgSrc img{pixels, 1, channels, false, 0.0, nullptr};
+  return batched_entry(ctx, ctx->feat.p, GS_IN_F64, offsets, B, labels, modes, modes_cap,
+                       mode_offsets, infos, &img);
 }
 
 gs_status gs_track_window(gs_ctx* ctx, const void* frame, gs_dtype dtype, int64_t width,
@@ -1028,9 +1070,12 @@ gs_status gs_track_window(gs_ctx* ctx, const void* frame, gs_dtype dtype, int64_
   return GS_OK;
 }
 
-gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const int64_t* offsets,
-                         int B, int32_t* labels, double* modes, int64_t modes_cap,
-                         int64_t* mode_offsets, gs_fit_info* infos) {
+// gs_fit_batched, and the batched image call (img: `points` is the
+// context's feature buffer, which the run fills).
+static gs_status batched_entry(gs_ctx* ctx, const void* points, gs_dtype dtype,
+                               const int64_t* offsets, int B, int32_t* labels, double* modes,
+                               int64_t modes_cap, int64_t* mode_offsets, gs_fit_info* infos,
+                               const ImgSrc* img) {
   if (!ctx) return GS_E_INVALID;
   ctx->err.clear();
   if (!offsets || !mode_offsets || !infos) return fail(ctx, GS_E_INVALID, "NULL offsets, mode_offsets or infos");
@@ -1057,7 +1102,7 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   }
   if (B == 1) {
     int64_t k = 0;
-    gs_status st = gs_fit(ctx, points, dtype, n, labels, modes, modes_cap, &k, &infos[0]);
+    gs_status st = fit_entry(ctx, points, dtype, n, labels, modes, modes_cap, &k, &infos[0], img);
     mode_offsets[1] = k;
     return st;
   }
@@ -1085,10 +1130,18 @@ gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const 
   a.offsets = offsets;
   a.infos = infos;
   a.mode_offsets = mode_offsets;
+  set_image(a, img);
   gs_fit_info total;
   std::memset(&total, 0, sizeof(total));
   int64_t k = 0;
   return fit_pipeline(a, ctx->ws, nullptr, &k, &total, nullptr, &ctx->err);
+}
+
+gs_status gs_fit_batched(gs_ctx* ctx, const void* points, gs_dtype dtype, const int64_t* offsets,
+                         int B, int32_t* labels, double* modes, int64_t modes_cap,
+                         int64_t* mode_offsets, gs_fit_info* infos) {
+  return batched_entry(ctx, points, dtype, offsets, B, labels, modes, modes_cap, mode_offsets,
+                       infos, nullptr);
 }
 
 gs_status gs_fit_sweep(gs_ctx* ctx, const void* points, gs_dtype dtype, int64_t n,

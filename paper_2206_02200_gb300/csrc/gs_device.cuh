@@ -34,6 +34,16 @@ __device__ __forceinline__ int64_t ord_of_bits(uint64_t b) {
   return s ^ ((s >> 63) & 0x7FFFFFFFFFFFFFFFll);
 }
 
+// The float64 bit pattern of an unsigned 32-bit integer (exact: every such
+// integer is a double), built with integer instructions: the leading one at
+// bit e gives the exponent 1023 + e and the bits below it the fraction.
+__device__ __forceinline__ uint64_t u32_to_f64_bits(uint32_t v) {
+  if (v == 0) return 0;
+  const int e = 31 - __clz(v);
+  const uint64_t mant = ((uint64_t)v << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return ((uint64_t)(1023 + e) << 52) | mant;
+}
+
 // Exact float32 -> float64 widening on the bit patterns (finite inputs).
 __device__ __forceinline__ uint64_t f32_bits_to_f64_bits(uint32_t f) {
   uint64_t sign = (uint64_t)(f >> 31) << 63;

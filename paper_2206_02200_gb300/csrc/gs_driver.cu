@@ -178,6 +178,8 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
   if (a.sweep_h && (a.mixed || a.sequential || a.B < 2 || a.n0 == 0 ||
                     (int64_t)a.n0 * a.B != a.n))
     return fail(err, GS_E_INVALID, "a bandwidth sweep runs B > 1 instances of n0 points in GS_FP64");
+  if (a.img && (a.sweep_h || a.f32 || a.img_feat != a.points || (a.img_xy && !a.img_tab)))
+    return fail(err, GS_E_INVALID, "image features are float64 points of one fit");
   Bufs b;
   GS_ST(ws.begin(b, err));
 
@@ -213,8 +215,17 @@ gs_status fit_pipeline(const FitArgs& a, Workspace& ws, EventTimer* timer, int64
     job.bar = b.bar;
     job.res = b.res;
     // the key range, then (in its last block) the plan: no host round trip
-    // before binning
-    GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, &job, s), "k_range", 1);
+    // before binning.  An image's features are built first, their key range
+    // published from the pixels, and the key-range kernel only plans.
+    if (a.img) {
+      if (a.img_xy)
+        GS_LAUNCH(launch_axis_products(a.img_width, n / a.img_width, a.img_s, a.img_tab, s),
+                  "k_axis_products", 1);
+      GS_LAUNCH(launch_image_features(a.img, n, a.img_width, a.img_C, a.img_xy, a.img_tab,
+                                      a.img_feat, b.flags, s), "k_image_features", 1);
+    }
+    GS_LAUNCH(launch_range(a.points, a.f32, n, d, b.flags, &job, s, a.img == nullptr), "k_range",
+              1);
     GS_T_END();
   }
   uint32_t* hinst = nullptr;

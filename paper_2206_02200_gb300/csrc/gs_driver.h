@@ -131,6 +131,18 @@ struct FitArgs {
   uint32_t* plan_status_out = nullptr;
   // launch choices of the loop kernel (results do not depend on them)
   Tuning tune = kDefaultTuning;
+  // image calls: the run first builds the float64 features of these uint8
+  // pixels (img_C channels, img_width columns, positions times img_s if
+  // img_xy, their products tabulated in img_tab: img_width + n / img_width
+  // doubles) into img_feat, which `points` names, and takes their key range
+  // from the pixels as it does, so the key-range kernel reads no points
+  const uint8_t* img = nullptr;
+  double* img_feat = nullptr;
+  double* img_tab = nullptr;
+  int64_t img_width = 1;
+  int img_C = 0;
+  bool img_xy = false;
+  double img_s = 0.0;
 };
 
 // 32-bit words of per-instance state of a batched run of B instances: one

@@ -174,7 +174,8 @@ __device__ void plan_block(int d, int64_t n, const PlanJob& J, DevFlags* fl);
 
 template <int D, typename T, int W>
 __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
-    k_range(const T* __restrict__ pts, int64_t n, DevFlags* fl, bool plan, PlanJob J) {
+    k_range(const T* __restrict__ pts, int64_t n, DevFlags* fl, bool plan, PlanJob J,
+            bool read) {
   using Acc = RangeAcc<T>;
   using U = typename Bits<T>::U;
   constexpr int kInFlight = 4;  // words in flight per thread (unaligned arrays)
@@ -212,7 +213,9 @@ __global__ void __launch_bounds__(kBlock, kRangeBlocksPerSM)
   }
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  const int64_t total = n * D;
+  // read == false: the extremes are in fl already (published by the kernel
+  // that wrote the points); only the start state and the plan remain
+  const int64_t total = read ? n * D : 0;
   const int64_t words = total / W;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t S = nthreads - nthreads % D;  // stride in words, a multiple of D
@@ -590,34 +593,161 @@ __global__ void __launch_bounds__(kBlock, bin_blocks_per_sm(LISTED, SUMS))
 // Pixel features of an image (the (r, g, b) or (r, g, b, x, y) inputs of the
 // segmentation experiment, Sec. 4.2): pixel p of a row-major image of width
 // w is the point (c_0 .. c_{C-1}[, x s, y s]), x = p mod w, y = p div w.  A
-// block builds kImgPix pixels' rows in shared memory (one thread per pixel)
-// and writes them out as one contiguous run (consecutive threads write
-// consecutive values).
-constexpr int kImgPix = kBlock;
-constexpr int kImgMaxD = 10;
+// warp takes 32 consecutive pixels at a time: each lane builds its pixel's
+// row in the warp's slice of shared memory, and the warp writes the 32 rows
+// out as one contiguous run (consecutive lanes write consecutive values,
+// whole 128-byte lines).  Warps synchronise only with themselves.
+//
+// No float64 instruction runs per pixel (GB300's float64 pipe issues about
+// one lane-operation per clock per SM, which bounded a per-pixel
+// conversion-and-multiply version at 7 clocks a pixel): a channel byte
+// becomes a double through its bit pattern (u32_to_f64_bits), and the
+// positions' products x s and y s come from a table of the W + H products
+// that k_axis_products computes once per image.
+//
+// With fl, the kernel also publishes the key range of the features it writes
+// (what k_range would find reading them back): each thread keeps the least
+// and greatest channel byte (packed four to a word, compared byte by byte)
+// and column and row index it has seen, as integers; a channel's extremes as
+// float64 are those bytes, and a position's are the table's products of the
+// extreme indices, since x -> x s rounded is monotone for s > 0.  Warps combine with shuffles, blocks in shared memory, and
+// a block publishes an extreme only where it improves on the one already
+// published (most blocks publish nothing once the image's extremes are in).
+constexpr int kImgMaxC = 8;
+constexpr int kImgMaxD = kImgMaxC + 2;
+
+// Per-byte extremes of four channel bytes in a word.
+__device__ __forceinline__ unsigned min_bytes(unsigned a, unsigned b) { return __vminu4(a, b); }
+__device__ __forceinline__ unsigned max_bytes(unsigned a, unsigned b) { return __vmaxu4(a, b); }
+
+// tab[x] = x s for the W columns, then tab[W + y] = y s for the H rows: the
+// rounded products the features hold.
+__global__ void __launch_bounds__(kBlock) k_axis_products(int64_t W, int64_t H, double s,
+                                                           double* __restrict__ tab) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < W + H;
+       i += (int64_t)gridDim.x * blockDim.x)
+    tab[i] = (double)(i < W ? i : i - W) * s;
+}
+
+__device__ __forceinline__ double exact_double(uint32_t v) {
+  return __longlong_as_double((long long)u32_to_f64_bits(v));
+}
 
 __global__ void __launch_bounds__(kBlock) k_image_features(const uint8_t* __restrict__ px,
                                                             int64_t n, int64_t width, int C,
-                                                            int xy, double s,
-                                                            double* __restrict__ out) {
-  __shared__ double s_rows[kImgPix * kImgMaxD];
+                                                            int xy,
+                                                            const double* __restrict__ tab,
+                                                            double* __restrict__ out,
+                                                            DevFlags* fl) {
+  __shared__ double s_rows[kWarps][32 * kImgMaxD];
+  // per warp: channel-byte minima (two words), maxima (two), then the least
+  // and greatest column and row index
+  __shared__ unsigned s_ext[kWarps][8];
   const int d = C + 2 * xy;
-  for (int64_t p0 = (int64_t)blockIdx.x * kImgPix; p0 < n; p0 += (int64_t)gridDim.x * kImgPix) {
-    const int cnt = n - p0 < kImgPix ? (int)(n - p0) : kImgPix;
-    const int i = threadIdx.x;
-    if (i < cnt) {
-      const int64_t p = p0 + i;
-      double* r = s_rows + i * d;
-      for (int c = 0; c < C; ++c) r[c] = (double)__ldg(px + p * C + c);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  double* rows = s_rows[wp];
+  // (bytes of absent channels are kept too, and never read)
+  unsigned lo0 = 0xFFFFFFFFu, lo1 = 0xFFFFFFFFu, hi0 = 0, hi1 = 0;
+  unsigned xlo = 0xFFFFFFFFu, xhi = 0, ylo = 0xFFFFFFFFu, yhi = 0;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p0 = gwarp * 32; p0 < n; p0 += nwarps * 32) {
+    const int cnt = n - p0 < 32 ? (int)(n - p0) : 32;
+    if (lane < cnt) {
+      const int64_t p = p0 + lane;
+      double* r = rows + lane * d;
+      unsigned w0 = 0, w1 = 0;
+#pragma unroll
+      for (int c = 0; c < kImgMaxC; ++c) {
+        if (c < C) {
+          const unsigned v = __ldg(px + p * C + c);
+          r[c] = exact_double(v);
+          if (c < 4)
+            w0 |= v << (8 * c);
+          else
+            w1 |= v << (8 * (c - 4));
+        }
+      }
+      lo0 = min_bytes(lo0, w0);
+      hi0 = max_bytes(hi0, w0);
+      lo1 = min_bytes(lo1, w1);
+      hi1 = max_bytes(hi1, w1);
       if (xy) {  // p and width are below 2^31
         const uint32_t y = (uint32_t)p / (uint32_t)width;
-        r[C] = (double)((uint32_t)p - y * (uint32_t)width) * s;
-        r[C + 1] = (double)y * s;
+        const uint32_t x = (uint32_t)p - y * (uint32_t)width;
+        r[C] = __ldg(tab + x);
+        r[C + 1] = __ldg(tab + width + y);
+        xlo = x < xlo ? x : xlo;
+        xhi = x > xhi ? x : xhi;
+        ylo = y < ylo ? y : ylo;
+        yhi = y > yhi ? y : yhi;
       }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < cnt * d; e += blockDim.x) out[p0 * d + e] = s_rows[e];
-    __syncthreads();
+    __syncwarp();
+    for (int e = lane; e < cnt * d; e += 32) out[p0 * d + e] = rows[e];
+    __syncwarp();
+  }
+  if (!fl) return;
+  // every lane of every warp reaches this point (the loop is warp-uniform)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo0 = min_bytes(lo0, __shfl_xor_sync(kFull, lo0, o));
+    lo1 = min_bytes(lo1, __shfl_xor_sync(kFull, lo1, o));
+    hi0 = max_bytes(hi0, __shfl_xor_sync(kFull, hi0, o));
+    hi1 = max_bytes(hi1, __shfl_xor_sync(kFull, hi1, o));
+  }
+  xlo = __reduce_min_sync(kFull, xlo);
+  xhi = __reduce_max_sync(kFull, xhi);
+  ylo = __reduce_min_sync(kFull, ylo);
+  yhi = __reduce_max_sync(kFull, yhi);
+  if (lane == 0) {
+    s_ext[wp][0] = lo0;
+    s_ext[wp][1] = lo1;
+    s_ext[wp][2] = hi0;
+    s_ext[wp][3] = hi1;
+    s_ext[wp][4] = xlo;
+    s_ext[wp][5] = xhi;
+    s_ext[wp][6] = ylo;
+    s_ext[wp][7] = yhi;
+  }
+  __syncthreads();
+  if (threadIdx.x < d) {
+    const int a = threadIdx.x;
+    unsigned vlo = 0xFFFFFFFFu, vhi = 0;
+    bool seen = false;  // a warp of the block wrote a pixel
+    for (int q = 0; q < kWarps; ++q) {
+      unsigned l, h;
+      if (a < C) {
+        const int sh = 8 * (a & 3);
+        l = (s_ext[q][a >> 2] >> sh) & 0xFFu;
+        h = (s_ext[q][2 + (a >> 2)] >> sh) & 0xFFu;
+      } else {
+        l = s_ext[q][a == C ? 4 : 6];
+        h = s_ext[q][a == C ? 5 : 7];
+      }
+      // a warp that wrote no pixel still holds minima 0xFF and maxima 0
+      if (l > h) continue;
+      seen = true;
+      vlo = l < vlo ? l : vlo;
+      vhi = h > vhi ? h : vhi;
+    }
+    if (seen) {
+      const int64_t t0 = a == C ? 0 : width;  // the products of columns, then of rows
+      const double vmin = a < C ? exact_double(vlo) : __ldg(tab + t0 + vlo);
+      const double vmax = a < C ? exact_double(vhi) : __ldg(tab + t0 + vhi);
+      RangeAcc<double> r;
+      r.add((uint64_t)__double_as_longlong(vmin));
+      r.add((uint64_t)__double_as_longlong(vmax));
+      if (r.nonfinite()) {
+        atomicAdd(&fl->bad, 1ull);
+      } else {
+        const long long mn = r.mn64(), mx = r.mx64();
+        const unsigned long long ma = r.ma64();
+        if (mn < *(volatile long long*)&fl->min_ord[a]) atomicMin(&fl->min_ord[a], mn);
+        if (mx > *(volatile long long*)&fl->max_ord[a]) atomicMax(&fl->max_ord[a], mx);
+        if (ma > *(volatile unsigned long long*)&fl->maxabs[a]) atomicMax(&fl->maxabs[a], ma);
+      }
+    }
   }
 }
 
@@ -665,23 +795,25 @@ __global__ void k_rank(const uint32_t* __restrict__ sorted_vals, uint32_t* __res
 // Launchers
 
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
-                         const PlanJob* job, cudaStream_t s) {
+                         const PlanJob* job, cudaStream_t s, bool read) {
   const bool vec = ((uintptr_t)pts & 15u) == 0;
   const int W = vec ? (f32 ? 4 : 2) : 1;
-  const unsigned g = grid_for(n * d / W, kBlock * 4, 152u * kRangeBlocksPerSM);
+  // without the read, one block per SM clears the start state
+  const unsigned g = read ? grid_for(n * d / W, kBlock * 4, 152u * kRangeBlocksPerSM) : 152u;
   const bool plan = job != nullptr;
+  if (!read && !plan) return cudaErrorInvalidValue;
   const PlanJob J = plan ? *job : PlanJob{};
   if (f32) {
     if (vec) {
-      GS_DISPATCH_D(d, k_range<D, float, 4><<<g, kBlock, 0, s>>>((const float*)pts, n, fl, plan, J));
+      GS_DISPATCH_D(d, k_range<D, float, 4><<<g, kBlock, 0, s>>>((const float*)pts, n, fl, plan, J, read));
     } else {
-      GS_DISPATCH_D(d, k_range<D, float, 1><<<g, kBlock, 0, s>>>((const float*)pts, n, fl, plan, J));
+      GS_DISPATCH_D(d, k_range<D, float, 1><<<g, kBlock, 0, s>>>((const float*)pts, n, fl, plan, J, read));
     }
   } else {
     if (vec) {
-      GS_DISPATCH_D(d, k_range<D, double, 2><<<g, kBlock, 0, s>>>((const double*)pts, n, fl, plan, J));
+      GS_DISPATCH_D(d, k_range<D, double, 2><<<g, kBlock, 0, s>>>((const double*)pts, n, fl, plan, J, read));
     } else {
-      GS_DISPATCH_D(d, k_range<D, double, 1><<<g, kBlock, 0, s>>>((const double*)pts, n, fl, plan, J));
+      GS_DISPATCH_D(d, k_range<D, double, 1><<<g, kBlock, 0, s>>>((const double*)pts, n, fl, plan, J, read));
     }
   }
   return cudaGetLastError();
@@ -714,12 +846,29 @@ cudaError_t launch_bin(const void* pts, bool f32, int64_t n, int d, const int64_
   return cudaGetLastError();
 }
 
+cudaError_t launch_axis_products(int64_t W, int64_t H, double s, double* tab, cudaStream_t st) {
+  if (W < 1 || H < 0) return cudaErrorInvalidValue;
+  k_axis_products<<<grid_for(W + H, kBlock, 152u), kBlock, 0, st>>>(W, H, s, tab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_image_features(const uint8_t* px, int64_t n, int64_t width, int C, bool xy,
-                                  double s, double* out, cudaStream_t st) {
-  if (C < 1 || C + (xy ? 2 : 0) > kImgMaxD || (xy && width < 1)) return cudaErrorInvalidValue;
+                                  const double* tab, double* out, DevFlags* fl, cudaStream_t st) {
+  if (C < 1 || C > kImgMaxC || (xy && (width < 1 || !tab))) return cudaErrorInvalidValue;
+  if (fl && C + (xy ? 2 : 0) > kMaxD) return cudaErrorInvalidValue;
   if (n == 0) return cudaSuccess;
-  const unsigned g = grid_for(n, kImgPix, 152u * 8u);
-  k_image_features<<<g, kBlock, 0, st>>>(px, n, width, C, xy ? 1 : 0, s, out);
+  // one wave: as many blocks as are resident at once (queried once)
+  static std::atomic<int> s_per_sm{0};
+  int per_sm = s_per_sm.load(std::memory_order_relaxed);
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_image_features,
+                                                                  kBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    s_per_sm.store(per_sm, std::memory_order_relaxed);
+  }
+  const unsigned g = grid_for(n, kBlock, 152u * (unsigned)per_sm);
+  k_image_features<<<g, kBlock, 0, st>>>(px, n, width, C, xy ? 1 : 0, tab, out, fl);
   return cudaGetLastError();
 }
 

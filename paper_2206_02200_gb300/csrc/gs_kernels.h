@@ -164,8 +164,11 @@ struct PlanJob {
 
 // Key range, fixed-point window and finiteness of n points of dimension d
 // into fl; with job != null, the last block to finish also makes the plan.
+// read == false (job required): the points are not read, their extremes
+// being in fl already (launch_image_features with fl); the kernel clears
+// the loop kernel's start state and makes the plan.
 cudaError_t launch_range(const void* pts, bool f32, int64_t n, int d, DevFlags* fl,
-                         const PlanJob* job, cudaStream_t s);
+                         const PlanJob* job, cudaStream_t s, bool read = true);
 // Binning, first pass.  offsets (device, B + 1 entries) give the points of
 // each instance of a batched run (B > 1); ignored when B == 1.
 // Binning with the plan in fl->plan (nothing runs unless fl->plan_status is 0).
@@ -223,11 +226,17 @@ cudaError_t launch_loop_seq(const LoopArgs& a, int grid, cudaStream_t s);
 // Numbering of the final cells when k > rank_max: labels of the final cells
 // from the sorted order (sorted_vals[p] = cell of rank p), then labels and
 // modes.  forest holds the final cell of every initial cell.
+// The position products of an image of W columns and H rows: tab[x] = x s
+// (x < W), then tab[W + y] = y s (y < H); W + H doubles.
+cudaError_t launch_axis_products(int64_t W, int64_t H, double s, double* tab, cudaStream_t st);
 // Pixel features of a row-major image (n pixels, width columns, C uint8
 // channels) into out (n x (C + 2 xy) float64): the channel values, then, if
-// xy, the column and row times s.  C + 2 xy <= 10.
+// xy, the column and row products from tab (launch_axis_products, earlier on
+// the stream).  C <= 8.  With fl (C + 2 xy <= kMaxD), the features' key
+// range is published into fl as launch_range would (fl's extremes start
+// empty): launch_range then need not read the features.
 cudaError_t launch_image_features(const uint8_t* px, int64_t n, int64_t width, int C, bool xy,
-                                  double s, double* out, cudaStream_t st);
+                                  const double* tab, double* out, DevFlags* fl, cudaStream_t st);
 cudaError_t launch_iota_keys(Cells c, uint64_t* keys, uint32_t* vals, uint32_t k,
                              cudaStream_t s);
 cudaError_t launch_rank(const uint32_t* sorted_vals, uint32_t* rank, uint32_t k, cudaStream_t s);

@@ -11,6 +11,7 @@
 //   Q hi lo L       -> round_to_double: hi lo err
 //   V hi lo D L     -> div_round: bits inexact
 //   W f32bits       -> f32_bits_to_f64_bits: bits
+//   I u32           -> u32_to_f64_bits: bits
 //   K h kmin span x -> key_index over the face table of cells kmin .. kmin+span-1
 //                      (h and x as C99 hex floats): the cell's index
 //   H cap n k_1 .. k_n m a_1 .. a_m -> a table of cap slots: per insert of k_i
@@ -125,6 +126,10 @@ int main() {
       unsigned f = 0;
       if (std::scanf("%x", &f) != 1) return 2;
       std::printf("%llx\n", (unsigned long long)gs::f32_bits_to_f64_bits(f));
+    } else if (std::strcmp(op, "I") == 0) {
+      unsigned v = 0;
+      if (std::scanf("%x", &v) != 1) return 2;
+      std::printf("%llx\n", (unsigned long long)gs::u32_to_f64_bits(v));
     } else if (std::strcmp(op, "K") == 0) {
       char hs[64], xs[64];
       long long kmin = 0;

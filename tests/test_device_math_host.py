@@ -172,6 +172,19 @@ def test_float32_widening(dm):
         assert int(line, 16) == bits(x), hex(f)
 
 
+def test_u32_to_double(dm):
+    # the image features' channel bytes and the like, converted with integer
+    # instructions: every 16-bit value, the powers of two and their
+    # neighbours, and random 32-bit values, against Python's exact float()
+    rng = random.Random(6)
+    vs = list(range(1 << 16))
+    vs += [(1 << k) + o for k in range(16, 32) for o in (-1, 0, 1)] + [0xFFFFFFFF]
+    vs += [rng.getrandbits(32) for _ in range(2000)]
+    out = dm([f"I {v:x}" for v in vs])
+    for v, line in zip(vs, out):
+        assert int(line, 16) == bits(float(v)), hex(v)
+
+
 def test_key_index_is_floor(dm):
     rng = random.Random(5)
     cases = []

@@ -53,9 +53,14 @@ def _check(img, h, xy_scale, precision=gridshift.GS_FP64, max_iter=50):
         ag = agreement.agreement(lab, ref["labels"], md, ref["modes"], h)
         assert ag["labels"] >= 0.999 and info["k"] == ref["k"], ag
         assert ag["max_mode_error_h"] <= 1e-3, ag
-    # gs_fit_image is gs_fit on the features, plus the feature build
+    # gs_fit_image is gs_fit on the features, plus the feature build (which
+    # also takes the key range from the pixels: the same plan, so the same
+    # cells, window and statistics)
     np.testing.assert_array_equal(lab, l2.cpu().numpy())
-    assert info["launches"] == i2["launches"] + 1
+    # (two launches with positions: the column and row products, then the rows)
+    assert info["launches"] == i2["launches"] + (2 if xy_scale > 0 else 1)
+    for key in ("m0", "inexact", "cell_iters", "iterations"):
+        assert info[key] == i2[key], key
 
 
 @pytest.mark.parametrize("xy_scale", [0.0, 0.1, 0.37])
@@ -91,7 +96,8 @@ def test_image_full_1080p():
     np.testing.assert_array_equal(labels.cpu().numpy(), l2.cpu().numpy())
     np.testing.assert_array_equal(modes.cpu().numpy().view(np.int64),
                                   m2.cpu().numpy().view(np.int64))
-    assert info["iterations"] == i2["iterations"]
+    for key in ("m0", "inexact", "cell_iters", "iterations", "k"):
+        assert info[key] == i2[key], key
 
 
 def test_image_batched_fp64():
