@@ -598,6 +598,10 @@ __global__ void __launch_bounds__(kBlock, bin_blocks_per_sm(LISTED, SUMS))
 // out as one contiguous run (consecutive lanes write consecutive values,
 // whole 128-byte lines).  Warps synchronise only with themselves.
 //
+// The channel count and the position flag are template parameters: a
+// runtime loop over up to eight channels issued every channel's
+// instructions, predicated off or not.
+//
 // No float64 instruction runs per pixel (GB300's float64 pipe issues about
 // one lane-operation per clock per SM, which bounded a per-pixel
 // conversion-and-multiply version at 7 clocks a pixel): a channel byte
@@ -633,17 +637,17 @@ __device__ __forceinline__ double exact_double(uint32_t v) {
   return __longlong_as_double((long long)u32_to_f64_bits(v));
 }
 
+template <int C, bool XY>
 __global__ void __launch_bounds__(kBlock) k_image_features(const uint8_t* __restrict__ px,
-                                                            int64_t n, int64_t width, int C,
-                                                            int xy,
+                                                            int64_t n, int64_t width,
                                                             const double* __restrict__ tab,
                                                             double* __restrict__ out,
                                                             DevFlags* fl) {
-  __shared__ double s_rows[kWarps][32 * kImgMaxD];
+  constexpr int d = C + (XY ? 2 : 0);
+  __shared__ double s_rows[kWarps][32 * d];
   // per warp: channel-byte minima (two words), maxima (two), then the least
   // and greatest column and row index
   __shared__ unsigned s_ext[kWarps][8];
-  const int d = C + 2 * xy;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   double* rows = s_rows[wp];
   // (bytes of absent channels are kept too, and never read)
@@ -658,21 +662,21 @@ __global__ void __launch_bounds__(kBlock) k_image_features(const uint8_t* __rest
       double* r = rows + lane * d;
       unsigned w0 = 0, w1 = 0;
 #pragma unroll
-      for (int c = 0; c < kImgMaxC; ++c) {
-        if (c < C) {
-          const unsigned v = __ldg(px + p * C + c);
-          r[c] = exact_double(v);
-          if (c < 4)
-            w0 |= v << (8 * c);
-          else
-            w1 |= v << (8 * (c - 4));
-        }
+      for (int c = 0; c < C; ++c) {
+        const unsigned v = __ldg(px + p * C + c);
+        r[c] = exact_double(v);
+        if (c < 4)
+          w0 |= v << (8 * c);
+        else
+          w1 |= v << (8 * (c - 4));
       }
       lo0 = min_bytes(lo0, w0);
       hi0 = max_bytes(hi0, w0);
-      lo1 = min_bytes(lo1, w1);
-      hi1 = max_bytes(hi1, w1);
-      if (xy) {  // p and width are below 2^31
+      if (C > 4) {
+        lo1 = min_bytes(lo1, w1);
+        hi1 = max_bytes(hi1, w1);
+      }
+      if (XY) {  // p and width are below 2^31
         const uint32_t y = (uint32_t)p / (uint32_t)width;
         const uint32_t x = (uint32_t)p - y * (uint32_t)width;
         r[C] = __ldg(tab + x);
@@ -684,7 +688,11 @@ __global__ void __launch_bounds__(kBlock) k_image_features(const uint8_t* __rest
       }
     }
     __syncwarp();
-    for (int e = lane; e < cnt * d; e += 32) out[p0 * d + e] = rows[e];
+#pragma unroll
+    for (int k = 0; k < d; ++k) {
+      const int e = lane + 32 * k;
+      if (e < cnt * d) out[p0 * d + e] = rows[e];
+    }
     __syncwarp();
   }
   if (!fl) return;
@@ -852,24 +860,48 @@ cudaError_t launch_axis_products(int64_t W, int64_t H, double s, double* tab, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_image_features(const uint8_t* px, int64_t n, int64_t width, int C, bool xy,
-                                  const double* tab, double* out, DevFlags* fl, cudaStream_t st) {
-  if (C < 1 || C > kImgMaxC || (xy && (width < 1 || !tab))) return cudaErrorInvalidValue;
-  if (fl && C + (xy ? 2 : 0) > kMaxD) return cudaErrorInvalidValue;
-  if (n == 0) return cudaSuccess;
+template <int C, bool XY>
+static cudaError_t launch_image_features_c(const uint8_t* px, int64_t n, int64_t width,
+                                           const double* tab, double* out, DevFlags* fl,
+                                           cudaStream_t st) {
   // one wave: as many blocks as are resident at once (queried once)
   static std::atomic<int> s_per_sm{0};
   int per_sm = s_per_sm.load(std::memory_order_relaxed);
   if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_image_features,
-                                                                  kBlock, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_image_features<C, XY>, kBlock, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     s_per_sm.store(per_sm, std::memory_order_relaxed);
   }
   const unsigned g = grid_for(n, kBlock, 152u * (unsigned)per_sm);
-  k_image_features<<<g, kBlock, 0, st>>>(px, n, width, C, xy ? 1 : 0, tab, out, fl);
+  k_image_features<C, XY><<<g, kBlock, 0, st>>>(px, n, width, tab, out, fl);
   return cudaGetLastError();
+}
+
+template <int C>
+static cudaError_t launch_image_features_xy(const uint8_t* px, int64_t n, int64_t width, bool xy,
+                                            const double* tab, double* out, DevFlags* fl,
+                                            cudaStream_t st) {
+  return xy ? launch_image_features_c<C, true>(px, n, width, tab, out, fl, st)
+            : launch_image_features_c<C, false>(px, n, width, tab, out, fl, st);
+}
+
+cudaError_t launch_image_features(const uint8_t* px, int64_t n, int64_t width, int C, bool xy,
+                                  const double* tab, double* out, DevFlags* fl, cudaStream_t st) {
+  if (C < 1 || C > kImgMaxC || (xy && (width < 1 || !tab))) return cudaErrorInvalidValue;
+  if (fl && C + (xy ? 2 : 0) > kMaxD) return cudaErrorInvalidValue;
+  if (n == 0) return cudaSuccess;
+  switch (C) {
+    case 1: return launch_image_features_xy<1>(px, n, width, xy, tab, out, fl, st);
+    case 2: return launch_image_features_xy<2>(px, n, width, xy, tab, out, fl, st);
+    case 3: return launch_image_features_xy<3>(px, n, width, xy, tab, out, fl, st);
+    case 4: return launch_image_features_xy<4>(px, n, width, xy, tab, out, fl, st);
+    case 5: return launch_image_features_xy<5>(px, n, width, xy, tab, out, fl, st);
+    case 6: return launch_image_features_xy<6>(px, n, width, xy, tab, out, fl, st);
+    case 7: return launch_image_features_xy<7>(px, n, width, xy, tab, out, fl, st);
+    default: return launch_image_features_xy<8>(px, n, width, xy, tab, out, fl, st);
+  }
 }
 
 cudaError_t launch_iota_keys(Cells c, uint64_t* keys, uint32_t* vals, uint32_t k,
