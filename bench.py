@@ -354,23 +354,28 @@ class OracleWorkers:
 
 
 def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8,
-                 update: str = "parallel") -> dict:
+                 update: str = "parallel", results: list | None = None) -> dict:
     """Times the CPU oracle (as it stands) on the same workload: single-threaded
     (a bounded number of full runs of the sample), and on all the host's cores
     as independent copies (two steps of OracleWorkers).  The all-core figure is
-    the line's value; the single-core one is nested."""
+    the line's value; the single-core one is nested.  With `results`, the
+    first run's oracle result is appended to it when that run covered the
+    whole workload (one point set, one bandwidth)."""
     from oracle import oracle
     oracle.build()
     sample = _oracle_sample(w)
     hs, it = w.get("hs", [w["h"]]), w["max_iter"]
     n = sum(len(X) for X in sample) * len(hs)
+    whole = "parts" not in w and len(hs) == 1 and len(sample[0]) == len(w["points"])
     runs, total = 0, 0.0
     while runs < max_runs and (runs == 0 or total < budget_s):
         t0 = time.perf_counter()
         for X in sample:
             for h in hs:
-                oracle.fit(X, h, it, update=update)
+                r = oracle.fit(X, h, it, update=update)
         total += time.perf_counter() - t0
+        if runs == 0 and whole and results is not None:
+            results.append(r)
         runs += 1
     what = _sample_what(w, sample)
     single = {"value": n * runs / total / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -386,6 +391,29 @@ def cpu_baseline(w: dict, budget_s: float = 12.0, max_runs: int = 8,
             "sample": (f"{len(ts)} steps of {P} independent single-threaded oracle processes, "
                        f"each running {what} ({n} points) once per step, {sum(ts):.1f} s"),
             "single_core": single}
+
+
+def oracle_agreement(lab, md, k: int, iterations: int, ref: dict, h: float) -> dict:
+    """The FP64 path's result (labels, the k modes, iterations) against the
+    oracle's on the same workload: the partition and its numbering, the
+    cluster count, the iteration count and the modes bit for bit, with the
+    largest mode difference in units of h."""
+    import numpy as np
+    lab_ref, md_ref, k_ref = ref["labels"], ref["modes"][:int(ref["k"])], int(ref["k"])
+    same_shape = lab.shape == lab_ref.shape
+    out = {"against": "the oracle (FP64), the same workload, its first cpu_baseline run",
+           "labels": float(np.mean(lab == lab_ref)) if same_shape and lab.size else
+           (1.0 if same_shape else 0.0),
+           "labels_identical": bool(same_shape and np.array_equal(lab, lab_ref)),
+           "k": int(k), "k_ref": k_ref,
+           "iterations": int(iterations), "iterations_ref": int(ref["iterations"])}
+    if k == k_ref and md.shape == md_ref.shape:
+        out["modes_bit_identical"] = bool(np.array_equal(md.view(np.int64), md_ref.view(np.int64)))
+        out["max_mode_error_h"] = float(np.max(np.abs(md - md_ref))) / h if k_ref else 0.0
+    else:
+        out["modes_bit_identical"] = False
+        out["max_mode_error_h"] = None
+    return out
 
 
 def run_reference(args, rank: int, world: int):
@@ -527,6 +555,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clk = clocks.stop()
     g.set_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    # the last timed step's result (outside the timed region), for the
+    # comparison with the oracle
+    last = None
+    if not batched and not fp32:
+        last = (labels.cpu().numpy().copy(), modes[:k].cpu().numpy().copy(), int(k),
+                int(infos[0]["iterations"]))
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     median_ms = max_over_ranks(statistics.median(step_ms), world, dev)
     value = job_rate(n, args.steps, world, total_ms / 1e3)
@@ -774,7 +808,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if sequential is not None:
             line["sequential"] = sequential
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, update=args.update)
+            refs = []
+            line["cpu_baseline"] = cpu_baseline(w, update=args.update, results=refs)
+            if last is not None and refs:
+                try:
+                    line["agreement"] = oracle_agreement(*last, refs[0], w["h"])
+                except Exception as e:  # an informational field: never lose the line
+                    line["agreement"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     g.close()
     return 0

@@ -60,3 +60,30 @@ def test_reference_arm_uses_every_core():
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["cpu_baseline"]["cores"] == line["cpu_baseline"]["nproc"] >= 1
+
+
+def test_oracle_agreement_of_the_fp64_line():
+    # the FP64 line's comparison with the oracle: identical results read as
+    # identical; one label, one mode bit or the cluster count off is reported
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    from oracle import oracle
+    from paper_2206_02200_gb300 import synth
+    X = synth.image_features(synth.voronoi_image(40, 56, 5, 8.0, seed=3), xy_scale=0.1)
+    ref = oracle.fit(X, 12.0, 50)
+    k = int(ref["k"])
+    same = bench.oracle_agreement(ref["labels"].copy(), ref["modes"][:k].copy(), k,
+                                  ref["iterations"], ref, 12.0)
+    assert same["labels_identical"] and same["modes_bit_identical"] and same["labels"] == 1.0
+    assert same["k"] == same["k_ref"] == k and same["max_mode_error_h"] == 0.0
+    lab = ref["labels"].copy()
+    lab[7] = (lab[7] + 1) % k
+    md = ref["modes"][:k].copy()
+    md[0, 0] = np.nextafter(md[0, 0], np.inf)
+    off = bench.oracle_agreement(lab, md, k, ref["iterations"], ref, 12.0)
+    assert not off["labels_identical"] and off["labels"] == 1.0 - 1.0 / len(lab)
+    assert not off["modes_bit_identical"] and 0.0 < off["max_mode_error_h"] < 1e-12
+    fewer = bench.oracle_agreement(lab, md[:k - 1], k - 1, ref["iterations"], ref, 12.0)
+    assert fewer["k"] == k - 1 and fewer["max_mode_error_h"] is None
